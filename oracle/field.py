@@ -1,0 +1,140 @@
+"""Field sum, property maps, mismatch loss and adjoint, FP64 (numpy).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+The field (Sec. 4.1, Eq. DiscreteFT, real reading; see ``modes``):
+
+    Y(x) = mu + sum_{j=0}^{N-1} A_j cos(2 pi (a_j . x + psi_j))
+
+evaluated in FP64 at every cell centre, modes in ascending j, with the phase
+t = a_j . x + psi_j reduced as r = t - rint(t) before the cosine.  Cell
+coordinates given as float32 are widened to FP64 exactly.
+
+Maps (Sec. 3.1 single truncation rule, Sec. 4.1 scaling, Appendix B):
+
+* lognormal:  K = K_ref exp(Y)   (log-permeability is the Gaussian field);
+* indicator:  label = #{m : Y > t_m} for ascending thresholds t_m in Y units,
+  so Y equal to a threshold falls in the lower facies;
+* values:     property = values[label] (Appendix B `values`);
+* porosity:   clamp(phi0 + phi1 (Y - mu)/sigma, phi_min, phi_max).  The paper
+  gives no porosity formula; this affine-clamp of the standardised field is
+  the reading taken.
+
+Adjoint of the field sum with g_i = dL/dY_i and theta_ij = 2 pi (a_j.x_i + psi_j):
+
+    dL/dmu    = sum_i g_i
+    dL/dA_j   = sum_i g_i cos theta_ij
+    dL/dpsi_j = -2 pi A_j sum_i g_i sin theta_ij
+    dL/da_jc  = -2 pi A_j sum_i g_i sin theta_ij x_ic
+    dL/dsigma = sum_j rho_j dL/dA_j                  (A_j = sigma rho_j)
+    dL/dl_c   = -sum_j (a_jc / l_c) dL/da_jc          (a_jc = kappa_jc/(2 pi l_c))
+"""
+import math
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+def _cells64(cells):
+    c = np.asarray(cells)
+    if c.ndim == 1:
+        c = c[:, None]
+    return c.astype(np.float64)
+
+
+def phase_turns(a_j, psi_j, cells):
+    """Reduced phase r = t - rint(t), t = a_j.x + psi_j, for one mode."""
+    t = cells @ np.asarray(a_j, dtype=np.float64) + psi_j
+    return t - np.rint(t)
+
+
+def synth(a, amp, psi, mu, cells):
+    """Y at every cell.  a: (N, d); amp, psi: (N,); cells: (M, d)."""
+    x = _cells64(cells)
+    a = np.asarray(a, dtype=np.float64).reshape(len(amp), -1)
+    acc = np.zeros(x.shape[0], dtype=np.float64)
+    for j in range(len(amp)):
+        acc += amp[j] * np.cos(TWO_PI * phase_turns(a[j], psi[j], x))
+    return mu + acc
+
+
+def lognormal(Y, k_ref=1.0):
+    return k_ref * np.exp(np.asarray(Y, dtype=np.float64))
+
+
+def indicator(Y, thresholds):
+    Y = np.asarray(Y, dtype=np.float64)
+    lab = np.zeros(Y.shape, dtype=np.uint8)
+    for t in thresholds:
+        lab += (Y > t).astype(np.uint8)
+    return lab
+
+
+def facies_values(labels, values):
+    return np.asarray(values, dtype=np.float64)[np.asarray(labels, dtype=np.int64)]
+
+
+def porosity(Y, mu, sigma, phi0, phi1, phi_min, phi_max):
+    p = phi0 + phi1 * (np.asarray(Y, dtype=np.float64) - mu) / sigma
+    return np.clip(p, phi_min, phi_max)
+
+
+def quantile_thresholds(mu, sigma, q):
+    """Thresholds in Y units at Gaussian quantiles q: t = mu + sigma Phi^-1(q)."""
+    from scipy.stats import norm
+    return mu + sigma * norm.ppf(np.asarray(q, dtype=np.float64))
+
+
+def mismatch_loss(K, K_target):
+    """L = mean (K - K_target)^2 and g = dL/dY for K = exp(Y)."""
+    K = np.asarray(K, dtype=np.float64)
+    T = np.asarray(K_target, dtype=np.float64)
+    diff = K - T
+    loss = float(np.mean(diff * diff))
+    g = 2.0 * diff * K / K.size
+    return loss, g
+
+
+def mode_sums(a, psi, cells, g):
+    """Per-mode S_cos[j], S_sin[j], S_sinx[j, c] (sums over cells, FP64)."""
+    x = _cells64(cells)
+    a = np.asarray(a, dtype=np.float64).reshape(len(psi), -1)
+    g = np.asarray(g, dtype=np.float64)
+    n, d = a.shape
+    s_cos = np.empty(n)
+    s_sin = np.empty(n)
+    s_sinx = np.empty((n, d))
+    for j in range(n):
+        th = TWO_PI * phase_turns(a[j], psi[j], x)
+        c = np.cos(th)
+        s = np.sin(th)
+        s_cos[j] = np.sum(g * c)
+        s_sin[j] = np.sum(g * s)
+        s_sinx[j] = (g * s) @ x
+    return s_cos, s_sin, s_sinx
+
+
+def grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g):
+    """Chain rule from per-mode sums to all parameter gradients."""
+    amp = np.asarray(amp, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64).reshape(len(amp), -1)
+    ell = np.asarray(ell, dtype=np.float64)[: a.shape[1]]
+    dA = np.asarray(s_cos, dtype=np.float64)
+    dpsi = -TWO_PI * amp * s_sin
+    da = -TWO_PI * amp[:, None] * s_sinx
+    rho = amp / sigma
+    return {
+        "dA": dA,
+        "dpsi": dpsi,
+        "da": da,
+        "dmu": float(np.sum(np.asarray(g, dtype=np.float64))),
+        "dsigma": float(np.sum(rho * dA)),
+        "dell": -np.sum(a * da, axis=0) / ell,
+    }
+
+
+def backward(a, amp, psi, sigma, ell, cells, g):
+    """All gradients of a loss with dL/dY = g (see module docstring)."""
+    s_cos, s_sin, s_sinx = mode_sums(a, psi, cells, g)
+    return grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g)

@@ -1,0 +1,240 @@
+"""Pins of the oracle's field sum, maps and adjoint (no GPU).
+
+* single-mode closed forms (phase at 0, 1/4, 1/2, 3/4 turn);
+* the amplitude/phase form equals the W cos + W' sin form of Eq. DiscreteFT;
+* brute force in 50-digit arithmetic (mpmath) on a small grid;
+* one-point and two-point statistics over many seeds: mean mu, variance
+  sigma^2, covariance C(r) of Appendix A (exact for every N under the
+  randomisation reading), threshold proportions Phi((t - mu)/sigma) and the
+  facies proportions p_i = G(t_i) - G(t_{i-1}) (Sec. 3.1);
+* resolution independence (Sec. 4.1) and permutation equivariance;
+* the adjoint against central finite differences of the FP64 loss, and its
+  chain-rule identities;
+* the C oracle against the numpy oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import field, modes, native, spectra
+
+
+def _grid2d(n):
+    c = (np.arange(n) + 0.5) / n
+    X, Yg = np.meshgrid(c, c, indexing="xy")
+    return np.stack([X.ravel(), Yg.ravel()], axis=-1).astype(np.float32)
+
+
+def test_single_mode_closed_forms():
+    mu, A = 0.7, 1.9
+    a = np.array([[0.25, 0.0, 0.0]])
+    x = np.array([[0.0, 0.3, 0.9], [1.0, 0.1, 0.2], [2.0, 0.5, 0.5], [3.0, 0.7, 0.1]])
+    y = field.synth(a, np.array([A]), np.array([0.0]), mu, x)
+    assert np.allclose(y, [mu + A, mu, mu - A, mu], rtol=0, atol=1e-15)
+    # psi shifts the phase: a.x + psi = 1/2 at x = 0
+    y2 = field.synth(a, np.array([A]), np.array([0.5]), mu, x[:1])
+    assert y2[0] == pytest.approx(mu - A, abs=1e-15)
+    # linear in A, shift by mu
+    m = modes.gen_modes(spectra.GAUSSIAN, 1.0, [0.1, 0.1, 0.1], 3, 20, seed=3)
+    xr = np.random.default_rng(1).random((50, 3))
+    y1 = field.synth(m["a"], m["amp"], m["psi"], 0.0, xr)
+    y3 = field.synth(m["a"], 3.0 * m["amp"], m["psi"], 2.0, xr)
+    assert np.allclose(y3, 2.0 + 3.0 * y1, rtol=0, atol=1e-13)
+
+
+def test_amplitude_phase_form_equals_discrete_ft():
+    n, sig2, mu = 64, 2.0, -0.3
+    m = modes.gen_modes(spectra.EXPONENTIAL, sig2, [0.2, 0.05], 2, n, seed=9)
+    x = _grid2d(16).astype(np.float64)
+    th = 2 * np.pi * (x @ m["a"].T)
+    direct = mu + math.sqrt(sig2 / n) * np.sum(m["W"] * np.cos(th) + m["Wp"] * np.sin(th), axis=1)
+    y = field.synth(m["a"], m["amp"], m["psi"], mu, x)
+    assert np.allclose(y, direct, rtol=0, atol=1e-12)
+
+
+def test_brute_force_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    n = 32
+    m = modes.gen_modes(spectra.MATERN, 1.5, [0.3, 0.2], 2, n, seed=11, nu=1.5)
+    x = _grid2d(8)
+    y = field.synth(m["a"], m["amp"], m["psi"], 0.25, x)
+    yc = native.synth(m["a"], m["amp"], m["psi"], 0.25, x)
+    worst = 0.0
+    bound = 0.0
+    for i in range(x.shape[0]):
+        acc = mpmath.mpf(0)
+        for j in range(n):
+            t = mpmath.mpf(float(m["psi"][j]))
+            for c in range(2):
+                t += mpmath.mpf(float(m["a"][j, c])) * mpmath.mpf(float(x[i, c]))
+            acc += mpmath.mpf(float(m["amp"][j])) * mpmath.cos(2 * mpmath.pi * t)
+        exact = float(acc + mpmath.mpf(0.25))
+        worst = max(worst, abs(y[i] - exact), abs(yc[i] - exact))
+        # rounding bound: each phase carries ~4 ulp of |t|, each term ~4 ulp of A
+        tmag = np.abs(m["psi"]) + np.abs(m["a"]) @ np.abs(x[i].astype(np.float64)) + 1.0
+        bound = max(bound, float(np.sum(m["amp"] * (2 * np.pi * 8 * 2.0 ** -53 * tmag + 8 * 2.0 ** -53))) + 1e-15)
+    assert worst <= bound
+    assert worst < 1e-13 * math.sqrt(1.5)
+
+
+@pytest.mark.slow
+def test_point_statistics_over_seeds():
+    # exact for every N: mean mu, variance sigma^2, Cov = C(r) (Appendix A)
+    R, n, sig2, mu = 3000, 16, 2.0, 0.5
+    ell = np.array([0.2, 0.05])
+    x0 = np.array([0.31, 0.47])
+    lags = np.array([[0.0, 0.0], [0.1, 0.0], [0.2, 0.0], [0.0, 0.025], [0.0, 0.05], [0.1, 0.05]])
+    pts = x0 + lags
+    for family, nu in ((spectra.GAUSSIAN, 0.0), (spectra.EXPONENTIAL, 0.0), (spectra.MATERN, 1.5)):
+        vals = np.empty((R, len(pts)))
+        for r in range(R):
+            m = modes.gen_modes(family, sig2, ell, 2, n, seed=1000 + r, nu=nu)
+            vals[r] = field.synth(m["a"], m["amp"], m["psi"], mu, pts)
+        se_mean = math.sqrt(sig2 / R)
+        assert abs(vals[:, 0].mean() - mu) < 5 * se_mean
+        dev = vals - mu
+        cov = (dev[:, :1] * dev).mean(axis=0)
+        want = spectra.covariance(family, lags, ell, sig2, nu=spectra.effective_nu(family, nu))
+        se = sig2 * np.sqrt((1.0 + (want / sig2) ** 2) / R)
+        assert np.all(np.abs(cov - want) < 5 * se), (family, cov, want)
+
+
+@pytest.mark.slow
+def test_threshold_and_facies_proportions():
+    R, n, sig2, mu = 4000, 8, 4.0, 1.0
+    q = np.array([1.0 / 3.0, 2.0 / 3.0])
+    t = field.quantile_thresholds(mu, math.sqrt(sig2), q)
+    x = np.array([[0.1, 0.2, 0.3]])
+    ys = np.empty(R)
+    for r in range(R):
+        m = modes.gen_modes(spectra.EXPONENTIAL, sig2, [0.2, 0.2, 0.05], 3, n, seed=50000 + r)
+        ys[r] = field.synth(m["a"], m["amp"], m["psi"], mu, x)[0]
+    # marginal is exactly N(mu, sigma^2) under the randomisation reading
+    assert stats.kstest((ys - mu) / math.sqrt(sig2), "norm").pvalue > 1e-3
+    lab = field.indicator(ys, t)
+    G = stats.norm.cdf((np.concatenate([[-np.inf], t, [np.inf]]) - mu) / math.sqrt(sig2))
+    p = np.diff(G)  # p_i = G(t_i) - G(t_{i-1})
+    assert np.allclose(p, [1 / 3, 1 / 3, 1 / 3], atol=1e-12)
+    counts = np.bincount(lab, minlength=3)
+    se = np.sqrt(p * (1 - p) / R)
+    assert np.all(np.abs(counts / R - p) < 5 * se)
+    # lognormal mean
+    K = field.lognormal(ys)
+    sdK = math.sqrt((math.exp(sig2) - 1) * math.exp(2 * mu + sig2) / R)
+    assert abs(K.mean() - math.exp(mu + sig2 / 2)) < 6 * sdK
+
+
+def test_maps_definitions():
+    Y = np.array([-1.0, 0.0, 0.2, 0.5, 2.0])
+    assert field.indicator(Y, [0.0]).tolist() == [0, 0, 1, 1, 1]  # Y == t -> lower facies
+    assert field.indicator(Y, [0.0, 0.5]).tolist() == [0, 0, 1, 1, 2]
+    assert np.allclose(field.facies_values([0, 2, 1], [10.0, 20.0, 30.0]), [10.0, 30.0, 20.0])
+    assert np.allclose(field.lognormal(Y, 2.0), 2.0 * np.exp(Y))
+    phi = field.porosity(Y, 0.5, 2.0, 0.3, 0.1, 0.1, 0.35)
+    assert np.allclose(phi, np.clip(0.3 + 0.1 * (Y - 0.5) / 2.0, 0.1, 0.35))
+    t = field.quantile_thresholds(0.0, 2.0, [1 / 3, 2 / 3])
+    assert np.allclose(t, [-0.861454, 0.861454], atol=1e-6)
+
+
+def test_resolution_independence_and_permutation():
+    m = modes.gen_modes(spectra.GAUSSIAN, 1.0, [0.1, 0.1], 2, 100, seed=1)
+    g64 = _grid2d(64)
+    g192 = _grid2d(192)
+    y64 = native.synth(m["a"], m["amp"], m["psi"], 0.0, g64)
+    y192 = native.synth(m["a"], m["amp"], m["psi"], 0.0, g192)
+    # centre (i+1/2)/64 equals centre (3i+1+1/2)/192
+    idx = np.arange(64) * 3 + 1
+    sub = y192.reshape(192, 192)[np.ix_(idx, idx)].ravel()
+    assert np.array_equal(sub, y64)
+    perm = np.random.default_rng(5).permutation(len(g64))
+    yp = native.synth(m["a"], m["amp"], m["psi"], 0.0, g64[perm])
+    assert np.array_equal(yp, y64[perm])
+
+
+def test_native_matches_numpy():
+    for family, d in ((spectra.GAUSSIAN, 1), (spectra.EXPONENTIAL, 2), (spectra.MATERN, 3)):
+        m = modes.gen_modes(family, 2.0, [0.2, 0.1, 0.05], d, 300, seed=4)
+        x = np.random.default_rng(2).random((500, d)).astype(np.float32)
+        y1 = field.synth(m["a"], m["amp"], m["psi"], 0.1, x)
+        y2 = native.synth(m["a"], m["amp"], m["psi"], 0.1, x)
+        tmag = np.sum(m["amp"] * (np.abs(m["a"]).sum(axis=1) + 1.0))
+        assert np.max(np.abs(y1 - y2)) < 64 * 2.0 ** -53 * 2 * np.pi * tmag
+        g = np.random.default_rng(3).standard_normal(500)
+        s1 = field.mode_sums(m["a"], m["psi"], x, g)
+        s2 = native.mode_sums(m["a"], m["psi"], x, g)
+        for u, v in zip(s1, s2):
+            assert np.allclose(u, v, rtol=1e-9, atol=1e-9)
+
+
+def _loss_for(params, cells, target):
+    m = modes.gen_modes(params["family"], params["sigma"] ** 2, params["ell"], cells.shape[1],
+                        params["n"], params["seed"])
+    amp = m["amp"].copy()
+    psi = m["psi"].copy()
+    a = m["a"].copy()
+    if "dA" in params:
+        amp[params["dA"][0]] += params["dA"][1]
+    if "dpsi" in params:
+        psi[params["dpsi"][0]] += params["dpsi"][1]
+    if "da" in params:
+        a[params["da"][0], params["da"][1]] += params["da"][2]
+    y = field.synth(a, amp, psi, params["mu"], cells)
+    return field.mismatch_loss(field.lognormal(y), target)[0]
+
+
+def test_adjoint_against_finite_differences():
+    n3 = 8
+    c = (np.arange(n3) + 0.5) / n3
+    X, Yg, Z = np.meshgrid(c, c, c, indexing="ij")
+    cells = np.stack([X.ravel(), Yg.ravel(), Z.ravel()], axis=-1)
+    base = {"family": spectra.GAUSSIAN, "sigma": 1.0, "ell": np.array([0.3, 0.25, 0.2]), "n": 24,
+            "seed": 1, "mu": 0.0}
+    mt = modes.gen_modes(spectra.GAUSSIAN, 1.0, base["ell"], 3, 24, seed=2)
+    target = field.lognormal(field.synth(mt["a"], mt["amp"], mt["psi"], 0.0, cells))
+    m = modes.gen_modes(spectra.GAUSSIAN, 1.0, base["ell"], 3, 24, seed=1)
+    y = field.synth(m["a"], m["amp"], m["psi"], 0.0, cells)
+    K = field.lognormal(y)
+    _, g = field.mismatch_loss(K, target)
+    gr = field.backward(m["a"], m["amp"], m["psi"], 1.0, base["ell"], cells, g)
+    h = 1e-4
+
+    def shifted(step, **kw):
+        p1 = dict(base)
+        for k, v in kw.items():
+            if k in ("mu", "sigma"):
+                p1[k] = base[k] + step
+            elif k == "ell":
+                e1 = base["ell"].copy()
+                e1[v] += step
+                p1["ell"] = e1
+            elif k == "dA" or k == "dpsi":
+                p1[k] = (v, step)
+            elif k == "da":
+                p1[k] = (v[0], v[1], step)
+        return _loss_for(p1, cells, target)
+
+    def fd(**kw):
+        # central differences at h and 2h combined (Richardson): error O(h^4)
+        d1 = (shifted(h, **kw) - shifted(-h, **kw)) / (2 * h)
+        d2 = (shifted(2 * h, **kw) - shifted(-2 * h, **kw)) / (4 * h)
+        return (4.0 * d1 - d2) / 3.0
+
+    def close(x, y):
+        return abs(x - y) <= 1e-6 * max(abs(x), abs(y)) + 1e-12
+
+    assert close(gr["dmu"], fd(mu=True))
+    assert close(gr["dsigma"], fd(sigma=True))
+    for c_ in range(3):
+        assert close(gr["dell"][c_], fd(ell=c_))
+    for j in (0, 5, 17, 23):
+        assert close(gr["dA"][j], fd(dA=j))
+        assert close(gr["dpsi"][j], fd(dpsi=j))
+        for c_ in range(3):
+            assert close(gr["da"][j, c_], fd(da=(j, c_)))
+    # chain-rule identities
+    assert gr["dsigma"] * 1.0 == pytest.approx(np.sum(m["amp"] * gr["dA"]), rel=1e-12)
+    assert np.allclose(base["ell"] * gr["dell"], -np.sum(m["a"] * gr["da"], axis=0), rtol=1e-12)
+    assert gr["dmu"] == pytest.approx(np.sum(g), rel=1e-12)
