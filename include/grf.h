@@ -1,0 +1,347 @@
+/*
+ * grf.h -- C ABI of the GB300 spectral Gaussian-random-field library.
+ *
+ * Method (Icardi et al., "Computational framework for complex flow and
+ * transport in heterogeneous porous media", arXiv 2212.10961):
+ *   Sec. 4.1, Eq. (DiscreteFT): a Gaussian random field evaluated directly at
+ *     arbitrary cell centres as a finite sum of N cosine modes (no FFT), with
+ *     frequencies drawn from the spectral density of the covariance and a
+ *     per-axis rescaling of frequency space for anisotropy;
+ *   Appendix A, Eqs. (gauSpe), (expSpe), (matSpe): Gaussian, exponential and
+ *     Matern covariances and their spectra;
+ *   Sec. 3.1 and Sec. 4.1 / Appendix B: scaling to mean and variance
+ *     (lognormal permeability), single truncation rule (facies thresholds),
+ *     facies values; Appendix B lists the user parameters mirrored by
+ *     grf_params.
+ *
+ * Real form used everywhere (see grf_gen_modes for the reading of the
+ * paper's complex "+ i sum sin"):
+ *     Y(x) = mu + sum_{j<N} A_j cos(2 pi (a_j . x + psi_j)),
+ *     A_j = sigma rho_j,  a_j = kappa_j / (2 pi l)  (per axis).
+ *
+ * Conventions for every entry point:
+ *   - Return value: GRF_OK (0) or a negative GRF_E* code.  No C++ exception
+ *     crosses the ABI.  grf_last_error() gives a message for the calling
+ *     thread's last failure.
+ *   - Ownership: the caller allocates and frees every buffer.  The library
+ *     allocates no device memory; it may allocate small host buffers.
+ *   - "device" pointers are CUDA global-memory addresses of the current
+ *     device; "host" pointers are ordinary process memory.  A `stream`
+ *     argument is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on that stream; host
+ *     buffers handed to an asynchronous copy must stay valid until the stream
+ *     reaches it.
+ *   - Cell centres are structure-of-arrays float32: x[i], y[i], z[i];
+ *     y is ignored (may be NULL) when dim < 2 and z when dim < 3.
+ */
+#ifndef GRF_H
+#define GRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes                                                         */
+/* ------------------------------------------------------------------ */
+#define GRF_OK 0
+#define GRF_EINVAL (-1)     /* invalid argument: NULL pointer, size, range or order */
+#define GRF_EWORKSPACE (-2) /* a caller buffer is smaller than required */
+#define GRF_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define GRF_ETIMEOUT (-4)   /* a bounded device-side wait expired; kernel returned early */
+#define GRF_ENOMEM (-5)     /* a host allocation failed */
+#define GRF_EDEVICE (-6)    /* a device-side check failed (see grf_read_status) */
+
+/* Message describing the calling thread's most recent failure ("" if none).
+ * The pointer stays valid until the next library call on the same thread. */
+const char *grf_last_error(void);
+
+/* Library version string, e.g. "grf-gb300 1.0". */
+const char *grf_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Parameters (Appendix B: correlation, Kmean, Ksigma, Lcorr, nu, nfreq, */
+/* disableY/disableZ)                                                   */
+/* ------------------------------------------------------------------ */
+enum grf_family {
+    GRF_GAUSSIAN = 0,    /* Appendix A, Eq. (gauSpe) */
+    GRF_EXPONENTIAL = 1, /* Appendix A, Eq. (expSpe); equals Matern nu = 1/2 */
+    GRF_MATERN = 2       /* Appendix A, Eq. (matSpe) */
+};
+
+typedef struct grf_params {
+    int32_t family;   /* enum grf_family */
+    int32_t dim;      /* 1, 2 or 3 (Appendix B disableY / disableZ) */
+    double nu;        /* Matern smoothness, > 0 (read only for GRF_MATERN) */
+    double sigma2;    /* variance of Y ("Ksigma"), > 0 */
+    double mean;      /* mean of Y ("Kmean") */
+    double ell[3];    /* correlation length per axis ("Lcorr"), > 0; ell[c], c < dim */
+    int64_t n_modes;  /* N ("nfreq"), 1 .. GRF_MAX_MODES */
+    uint64_t seed;    /* generator key */
+    uint32_t stream;  /* independent generator stream (e.g. 2nd field of a pair) */
+    uint32_t reserved;/* must be 0 */
+} grf_params;
+
+#define GRF_MAX_MODES (1 << 24)
+
+/* ------------------------------------------------------------------ */
+/* S1: drawing the modes (host, FP64)                                   */
+/* ------------------------------------------------------------------ */
+/*
+ * Host FP64 mode set, arrays allocated by the caller with n entries
+ * (n * dim for kappa and a, row-major: element (j, c) at j * dim + c).
+ */
+typedef struct grf_modes {
+    int64_t n;      /* number of modes, must equal params->n_modes */
+    int32_t dim;    /* must equal params->dim */
+    int32_t reserved;
+    double *kappa;  /* standardised wave-vectors (k_c * l_c) */
+    double *rho;    /* amplitude weights sqrt((W^2 + W'^2) / N) */
+    double *psi;    /* phases in turns, in (-1/2, 1/2] */
+    double *a;      /* frequencies in turns per unit length, kappa_c / (2 pi l_c) */
+    double *amp;    /* amplitudes A_j = sigma * rho_j */
+} grf_modes;
+
+/*
+ * grf_gen_modes -- draw the N modes of one realisation.
+ * Sec. 4.1 (Eq. DiscreteFT, rescaling of frequency space) and Appendix A.
+ *
+ * Readings: the field is the real sum W_j cos + W'_j sin with exactly N
+ * terms; a_j are i.i.d. draws from the spectral density normalised to a
+ * probability density, so the amplitude is sigma/sqrt(N) times the Gaussian
+ * weights (exact covariance for every N).  Standardised wave-vectors:
+ * Gaussian kappa_c = sqrt(pi/2) z_c; Matern(nu) (exponential: nu = 1/2)
+ * kappa = z sqrt(2 nu / w), w ~ chi^2 with 2 nu degrees of freedom.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ * key = (seed lo, seed hi) and counter = (j lo, block, stream, j hi);
+ * per mode, normals 0, 1 are W, W'; normals 2 .. 1+dim are z; for integer
+ * 2 nu <= 32, w sums the squares of the next 2 nu normals; otherwise
+ * w = 2 Gamma(nu) by Marsaglia-Tsang (attempt t: first normal of block
+ * 64 + 2t, first uniform of block 65 + 2t; nu < 1 boosted with the first
+ * uniform of block 63).  A block's two 64-bit words u give uniforms
+ * (floor(u / 2^12) + 1/2) 2^-52; Box-Muller turns them into two normals.
+ *
+ * Arguments: p (host, read), out (host, arrays written).  Returns GRF_EINVAL
+ * for bad parameters or mismatched out->n / out->dim, GRF_OK otherwise.
+ * Deterministic: the same (seed, stream, j) always gives the same mode j,
+ * whatever N.
+ */
+int grf_gen_modes(const grf_params *p, grf_modes *out);
+
+/* ------------------------------------------------------------------ */
+/* Device mode table                                                    */
+/* ------------------------------------------------------------------ */
+/*
+ * The device table is an opaque, 256-byte aligned image built on the host by
+ * grf_pack_table and copied to the device by grf_upload_table.  It holds,
+ * per mode, FP32 angular frequencies 2 pi a, the amplitude A, the frequency
+ * and phase as FP32 hi/lo pairs (for the compensated phase split), the
+ * original mode index, and a per-extent table of how many modes need the
+ * compensated path.  Modes are stored in decreasing order of |a|_1; the sum
+ * is order independent.
+ */
+size_t grf_table_bytes(int64_t n_modes);
+
+/* Build the table image of modes m (A = m->amp, a = m->a, psi = m->psi)
+ * into host memory `host_table` of `bytes` >= grf_table_bytes(m->n).
+ * GRF_EWORKSPACE if too small, GRF_EINVAL for NULL arrays or bad sizes. */
+int grf_pack_table(const grf_modes *m, void *host_table, size_t bytes);
+
+/* Enqueue the host->device copy of a packed table (cudaMemcpyAsync).
+ * host_table must stay valid until the copy has run (pinned memory makes
+ * the copy truly asynchronous).  dev_table must be 256-byte aligned. */
+int grf_upload_table(const void *host_table, void *dev_table, size_t bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Cell plan (spatial binning of arbitrary cell centres)                */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper evaluates Eq. (DiscreteFT) at the cell centres of an arbitrary
+ * mesh (Sec. 4.1: Cartesian grids are treated as unstructured).  The plan
+ * is a permutation that groups nearby cells so that each warp works on a
+ * compact set, which keeps the FP32 phase split accurate.  It is built on
+ * the device once per mesh (bounding box, Morton brick keys, stable radix
+ * sort, gather of sorted SoA coordinates) and reused for every realisation
+ * on that mesh.
+ *
+ * Several independent meshes ("segments", e.g. the grids of an ensemble)
+ * can share one plan: seg_offsets (host, n_segments + 1 entries, ascending,
+ * seg_offsets[0] = 0) delimit their cells in x/y/z.
+ */
+size_t grf_plan_bytes(int64_t n_cells, int32_t n_segments);
+
+/* x, y, z: device float32 arrays of seg_offsets[n_segments] cells.
+ * plan: device buffer, 256-byte aligned, plan_bytes >= grf_plan_bytes().
+ * The input arrays are read only while the stream runs the planning
+ * kernels; the plan keeps its own sorted copy of the coordinates.
+ * Coordinates must be finite (GRF_EDEVICE via grf_read_status otherwise). */
+int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t *seg_offsets,
+                   const float *x, const float *y, const float *z, void *plan,
+                   size_t plan_bytes, void *stream);
+
+/* Device status word of a plan (0 = no device-side error).  Synchronises
+ * the stream.  Bits: 1 = non-finite coordinate, 2 = bounded wait expired,
+ * 4 = table/plan mismatch detected on the device. */
+int grf_read_status(const void *plan, int32_t *status_out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* S2-S4: field synthesis with fused property maps                      */
+/* ------------------------------------------------------------------ */
+#define GRF_MAX_THRESHOLDS 15
+
+enum grf_map_bits {
+    GRF_MAP_Y = 1,         /* write the Gaussian field Y */
+    GRF_MAP_LOGNORMAL = 2, /* K = k_ref exp(Y)  (Sec. 4.1, log-permeability field) */
+    GRF_MAP_FACIES = 4,    /* label = #{m : Y > t_m}  (Sec. 3.1 single truncation rule) */
+    GRF_MAP_VALUES = 8,    /* prop = values[label]  (Appendix B `values`) */
+    GRF_MAP_POROSITY = 16  /* prop = clamp(phi0 + phi1 (Y - mu)/sigma, phi_min, phi_max) */
+};
+
+typedef struct grf_map {
+    int32_t bits;          /* OR of grf_map_bits; VALUES and POROSITY exclusive */
+    int32_t n_thresholds;  /* 0 .. GRF_MAX_THRESHOLDS (FACIES / VALUES) */
+    float thresholds[GRF_MAX_THRESHOLDS]; /* ascending, in Y units */
+    float values[GRF_MAX_THRESHOLDS + 1]; /* value per facies (VALUES) */
+    float k_ref;           /* LOGNORMAL prefactor (1 = plain exp) */
+    float phi0, phi1, phi_min, phi_max;   /* POROSITY */
+} grf_map;
+
+/* Device outputs in the caller's original cell order; an output may be
+ * NULL when its bit is not requested. */
+typedef struct grf_outputs {
+    float *Y;         /* GRF_MAP_Y */
+    float *K;         /* GRF_MAP_LOGNORMAL */
+    uint8_t *facies;  /* GRF_MAP_FACIES */
+    float *prop;      /* GRF_MAP_VALUES or GRF_MAP_POROSITY */
+} grf_outputs;
+
+/*
+ * grf_synth_field -- Y_i = mu + sum_j A_j cos(2 pi (a_j . x_i + psi_j)) at
+ * every cell of segment `segment` of `plan`, followed by the requested maps,
+ * all in one kernel.  Sec. 4.1, Eq. (DiscreteFT); maps Sec. 3.1, Sec. 4.1,
+ * Appendix B.
+ *
+ * table: device table (grf_upload_table) of p->n_modes modes, dim p->dim.
+ * p: host; mean and sigma2 are read (porosity standardisation), the rest is
+ * checked against the table.  map, out: host structs of device pointers.
+ * Arithmetic: FP32 with a compensated phase split (per-warp origin with
+ * hi/lo frequencies, exact path for modes whose phase span is large) and
+ * compensated accumulation; the hardware cosine.  Results agree with the
+ * FP64 definition to about 1e-6 sigma (max-abs).
+ */
+int grf_synth_field(const void *table, const grf_params *p, const void *plan, int32_t segment,
+                    const grf_map *map, const grf_outputs *out, void *stream);
+
+/*
+ * grf_map_property -- the maps of grf_synth_field applied to an existing
+ * field Y (device, n values), writing `out` in the same order.  Memory bound.
+ * mean, sigma: the Gaussian field's mean and standard deviation (porosity).
+ */
+int grf_map_property(const grf_map *map, double mean, double sigma, int64_t n, const float *Y,
+                     const grf_outputs *out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* S5: adjoint                                                          */
+/* ------------------------------------------------------------------ */
+/* Device FP64 gradient outputs (original mode order j of grf_gen_modes). */
+typedef struct grf_grads {
+    double *dA;     /* [N]      dL/dA_j   = sum_i g_i cos theta_ij */
+    double *dpsi;   /* [N]      dL/dpsi_j = -2 pi A_j sum_i g_i sin theta_ij */
+    double *da;     /* [N*dim]  dL/da_jc  = -2 pi A_j sum_i g_i sin theta_ij x_ic */
+    double *dmu;    /* [1]      sum_i g_i */
+    double *dsigma; /* [1]      sum_j (A_j / sigma) dL/dA_j */
+    double *dell;   /* [dim]    -sum_j (a_jc / l_c) dL/da_jc */
+} grf_grads;
+
+/* Workspace for grf_synth_backward on n_cells cells and n_modes modes. */
+size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);
+
+/*
+ * grf_synth_backward -- gradients of a loss L with respect to the mode
+ * amplitudes, phases and frequencies, the mean, sigma and the correlation
+ * lengths, given gY = dL/dY (device float32, original cell order, cells of
+ * segment `segment` of `plan`).  Derivative of Eq. (DiscreteFT) with the
+ * reparameterisation A = sigma rho, a = kappa / (2 pi l) of Sec. 4.1.
+ * The sines and cosines are recomputed, never stored.  Per-block FP64
+ * partials go to `workspace` and are reduced in a fixed order, so results
+ * are deterministic.  All outputs in `g` are written (device).
+ */
+int grf_synth_backward(const void *table, const grf_params *p, const void *plan, int32_t segment,
+                       const float *gY, const grf_grads *g, void *workspace, size_t ws_bytes,
+                       void *stream);
+
+/* Workspace for grf_mismatch_grad on n cells. */
+size_t grf_mismatch_workspace_bytes(int64_t n);
+
+/*
+ * grf_mismatch_grad -- field-mismatch loss L = mean_i (K_i - T_i)^2 of a
+ * lognormal field K = exp(Y) against a target T, and gY = dL/dY =
+ * 2 (K - T) K / n (device float32).  loss: device double[1], reduced
+ * deterministically through `workspace`.
+ */
+int grf_mismatch_grad(int64_t n, const float *K, const float *K_target, float *gY, double *loss,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* S6: batched ensembles (many realisations, one persistent launch)     */
+/* ------------------------------------------------------------------ */
+typedef struct grf_batch_item {
+    const void *table;  /* device table of this realisation */
+    int64_t n_modes;
+    int32_t dim;
+    int32_t segment;    /* plan segment holding this realisation's cells */
+    double mean;
+    double sigma;
+    grf_map map;
+    grf_outputs out;    /* device outputs, segment-local original order */
+} grf_batch_item;
+
+/* Workspace for a batch of n_items realisations whose plan covers n_cells. */
+size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells);
+
+/*
+ * grf_batch_prepare -- copy the descriptors of n_items realisations and a
+ * cost-ordered work list into `workspace` (H2D from host_staging, which
+ * must hold grf_batch_workspace_bytes() bytes and stay valid until the copy
+ * has run).  tile_cells selects the cells per work tile (0 = library
+ * choice, otherwise 512, 1024 or 2048).  Call once per batch layout.
+ */
+int grf_batch_prepare(int32_t n_items, const grf_batch_item *items, const void *plan,
+                      int32_t tile_cells, void *workspace, size_t ws_bytes, void *host_staging,
+                      void *stream);
+
+/*
+ * grf_batch_launch -- one persistent launch synthesising every prepared
+ * realisation (Eq. DiscreteFT and maps, as grf_synth_field).  Blocks pull
+ * work tiles from a counter in `workspace`, which this call resets first
+ * (a memset node plus one kernel node: safe to capture in a CUDA graph
+ * and replay).
+ */
+int grf_batch_launch(void *workspace, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Measurement helpers                                                  */
+/* ------------------------------------------------------------------ */
+/* Device properties used by the roofline: SM count and max SM clock (kHz). */
+int grf_device_info(int32_t *sm_count, int32_t *sm_clock_khz);
+
+/* Number of kernels the library launched on this process so far (all
+ * entry points).  Used to report kernel counts in benchmarks. */
+int64_t grf_launch_count(void);
+
+/*
+ * grf_mufu_probe -- throughput probe of the hardware cosine: `iters`
+ * dependent-free cos.approx evaluations per thread over a grid of
+ * `blocks` x 256 threads; writes one float per thread to `sink` (device,
+ * blocks * 256 floats) so nothing is optimised away.
+ */
+int grf_mufu_probe(int32_t blocks, int32_t iters, float *sink, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRF_H */

@@ -1,0 +1,158 @@
+// Device helpers shared by the CUDA kernels: hardware cosine/sine, the
+// compensated phase of one mode at one point, compensated accumulation, and
+// the mbarrier / bulk-copy primitives used to stage mode chunks.
+#pragma once
+
+#include <cstdint>
+
+#include "grf_internal.h"
+
+namespace grf {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+// (v + 1.5*2^23) - 1.5*2^23 rounds v to the nearest integer for |v| < 2^22.
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+
+// Hardware approximate cosine / sine (PTX cos.approx / sin.approx), radians.
+__device__ __forceinline__ float hw_cos(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float hw_sin(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Fractional part about the nearest integer, exact for every finite v:
+// v - rint(v) (for |v| >= 2^23, v is an integer and the result is 0).
+__device__ __forceinline__ float frac_nearest(float v) { return v - rintf(v); }
+
+// Same for |v| <= 2 with FP32 adds only (round-to-nearest-even magic).
+__device__ __forceinline__ float frac_nearest_small(float v) {
+    return v - ((v + kRoundMagic) - kRoundMagic);
+}
+
+// Exact reduced phase of one mode at point x, in turns, in [-1/2, 1/2]:
+//   t = a . x + psi  with a = ah + al, psi = psi_h + psi_l (FP32 pairs).
+// For each axis ah*x is split exactly into p + e (FMA), the integer part of
+// p is removed exactly, and the small remainders are summed with the high
+// part kept in [-1/2, 1/2] after every addition.  c0 = (ah_x, al_x, ah_y,
+// al_y), c1 = (ah_z, al_z, psi_h, psi_l).
+template <int DIM>
+__device__ __forceinline__ float phase_exact_turns(const float* x, float4 c0, float4 c1) {
+    float hi = c1.z;
+    float lo = c1.w;
+    const float ah[3] = {c0.x, c0.z, c1.x};
+    const float al[3] = {c0.y, c0.w, c1.y};
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        float p = ah[c] * x[c];
+        float e = fmaf(ah[c], x[c], -p);
+        hi = frac_nearest_small(hi + frac_nearest(p));
+        lo += fmaf(al[c], x[c], e);
+    }
+    // lo may exceed one turn only for astronomically large a*x; reduce it too.
+    return frac_nearest_small(hi + frac_nearest(lo));
+}
+
+// Accumulate partial sum p into (s, e) with an exact TwoSum error term.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float p) {
+    float t = s + p;
+    float bp = t - s;
+    float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    e += err;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk copy (global -> shared), PTX.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: returns false if the phase did not complete within about
+// two seconds (checked on the global timer every 256 polls).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared, completion reported to `bar` as tx bytes.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Map epilogue of one cell (Sec. 3.1 truncation rule, Sec. 4.1 lognormal).
+__device__ __forceinline__ void map_store(const MapDev& m, int64_t o, float y) {
+    const int bits = m.bits;
+    if (bits & GRF_MAP_Y) m.Y[o] = y;
+    if (bits & GRF_MAP_LOGNORMAL) m.K[o] = m.k_ref * expf(y);
+    if (bits & (GRF_MAP_FACIES | GRF_MAP_VALUES)) {
+        int lab = 0;
+        for (int t = 0; t < m.n_thr; ++t) lab += (y > m.thr[t]) ? 1 : 0;
+        if (bits & GRF_MAP_FACIES) m.F[o] = static_cast<uint8_t>(lab);
+        if (bits & GRF_MAP_VALUES) m.P[o] = m.values[lab];
+    }
+    if (bits & GRF_MAP_POROSITY) {
+        float p = fmaf(m.phi1, (y - m.mu) * m.sigma_inv, m.phi0);
+        m.P[o] = fminf(fmaxf(p, m.phi_min), m.phi_max);
+    }
+}
+
+}  // namespace grf

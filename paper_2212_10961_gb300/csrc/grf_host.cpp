@@ -1,0 +1,688 @@
+// Host side of the C ABI (include/grf.h): argument checking, error reporting,
+// the counter-based generator and mode drawing (S1), packing of the device
+// mode table, the plan registry, and dispatch to the CUDA launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "grf_internal.h"
+
+namespace grf {
+
+// ---------------------------------------------------------------------------
+// Errors and counters
+// ---------------------------------------------------------------------------
+namespace {
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(int err, const char* what) {
+    return fail(GRF_ECUDA, "%s: %s", what, cudaGetErrorString(static_cast<cudaError_t>(err)));
+}
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+}  // namespace
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// ---------------------------------------------------------------------------
+namespace {
+struct Block4 {
+    uint32_t w[4];
+};
+
+Block4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+    const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = M0 * c0;
+        const uint64_t p1 = M1 * c2;
+        const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n1 = static_cast<uint32_t>(p1);
+        const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
+        const uint32_t n3 = static_cast<uint32_t>(p0);
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    return Block4{{c0, c1, c2, c3}};
+}
+
+// Generator stream of one mode: key = seed, counter = (j lo, block, stream, j hi).
+class ModeStream {
+  public:
+    ModeStream(uint64_t seed, uint32_t stream, uint64_t j)
+        : k0_(static_cast<uint32_t>(seed)), k1_(static_cast<uint32_t>(seed >> 32)), st_(stream),
+          jlo_(static_cast<uint32_t>(j)), jhi_(static_cast<uint32_t>(j >> 32)) {}
+
+    // Two uniforms in (0, 1) from block b: (floor(u64 / 2^12) + 1/2) * 2^-52.
+    void uniforms(uint32_t b, double& u0, double& u1) const {
+        const Block4 o = philox10(jlo_, b, st_, jhi_, k0_, k1_);
+        const uint64_t a = (static_cast<uint64_t>(o.w[1]) << 32) | o.w[0];
+        const uint64_t c = (static_cast<uint64_t>(o.w[3]) << 32) | o.w[2];
+        const double s = std::ldexp(1.0, -52);
+        u0 = (static_cast<double>(a >> 12) + 0.5) * s;
+        u1 = (static_cast<double>(c >> 12) + 0.5) * s;
+    }
+    // Normal number k (Box-Muller of block k / 2; even k cosine, odd k sine).
+    double normal(uint32_t k) const {
+        double u0, u1;
+        uniforms(k / 2, u0, u1);
+        const double r = std::sqrt(-2.0 * std::log(u0));
+        const double ang = 2.0 * M_PI * u1;
+        return (k % 2 == 0) ? r * std::cos(ang) : r * std::sin(ang);
+    }
+
+  private:
+    uint32_t k0_, k1_, st_, jlo_, jhi_;
+};
+
+constexpr int kGammaAttempts = 256;
+
+// Gamma(alpha, 1), alpha >= 1, Marsaglia & Tsang (2000), with the block
+// layout of grf_gen_modes.  Returns false if no attempt was accepted.
+bool gamma_mt(const ModeStream& g, double alpha, double& out) {
+    const double d = alpha - 1.0 / 3.0;
+    const double c = 1.0 / std::sqrt(9.0 * d);
+    for (int t = 0; t < kGammaAttempts; ++t) {
+        const double x = g.normal(2u * (64u + 2u * t));
+        double u, unused;
+        g.uniforms(65u + 2u * t, u, unused);
+        const double v = (1.0 + c * x) * (1.0 + c * x) * (1.0 + c * x);
+        if (v <= 0.0) continue;
+        if (std::log(u) < 0.5 * x * x + d - d * v + d * std::log(v)) {
+            out = d * v;
+            return true;
+        }
+    }
+    return false;
+}
+
+int check_params(const grf_params* p) {
+    if (!p) return fail(GRF_EINVAL, "params is NULL");
+    if (p->family < GRF_GAUSSIAN || p->family > GRF_MATERN)
+        return fail(GRF_EINVAL, "unknown covariance family %d", p->family);
+    if (p->dim < 1 || p->dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3 (got %d)", p->dim);
+    if (!(p->sigma2 > 0.0) || !std::isfinite(p->sigma2))
+        return fail(GRF_EINVAL, "sigma2 must be finite and > 0");
+    if (!std::isfinite(p->mean)) return fail(GRF_EINVAL, "mean must be finite");
+    for (int c = 0; c < p->dim; ++c)
+        if (!(p->ell[c] > 0.0) || !std::isfinite(p->ell[c]))
+            return fail(GRF_EINVAL, "ell[%d] must be finite and > 0", c);
+    if (p->family == GRF_MATERN && (!(p->nu > 0.0) || !std::isfinite(p->nu)))
+        return fail(GRF_EINVAL, "Matern nu must be finite and > 0");
+    if (p->n_modes < 1 || p->n_modes > GRF_MAX_MODES)
+        return fail(GRF_EINVAL, "n_modes must be in [1, %d]", GRF_MAX_MODES);
+    if (p->reserved != 0) return fail(GRF_EINVAL, "reserved field must be 0");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan registry: host copy of each plan's segment table, keyed by the plan's
+// device address (set by grf_plan_cells).
+// ---------------------------------------------------------------------------
+struct PlanMeta {
+    int32_t dim;
+    std::vector<int64_t> offsets;
+    PlanLayout layout;
+};
+std::mutex g_reg_mu;
+std::unordered_map<const void*, PlanMeta> g_plans;
+
+bool lookup_plan(const void* plan, PlanMeta& out) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    auto it = g_plans.find(plan);
+    if (it == g_plans.end()) return false;
+    out = it->second;
+    return true;
+}
+
+struct BatchMeta {
+    BatchHeader hdr;
+    int32_t plan_dim;
+};
+std::unordered_map<const void*, BatchMeta> g_batches;
+
+MapDev make_map(const grf_map* m, const grf_outputs* out, double mean, double sigma) {
+    MapDev d{};
+    d.bits = m ? m->bits : 0;
+    d.n_thr = m ? m->n_thresholds : 0;
+    for (int t = 0; t < GRF_MAX_THRESHOLDS; ++t) d.thr[t] = m ? m->thresholds[t] : 0.f;
+    for (int t = 0; t <= GRF_MAX_THRESHOLDS; ++t) d.values[t] = m ? m->values[t] : 0.f;
+    d.k_ref = m ? m->k_ref : 1.f;
+    d.phi0 = m ? m->phi0 : 0.f;
+    d.phi1 = m ? m->phi1 : 0.f;
+    d.phi_min = m ? m->phi_min : 0.f;
+    d.phi_max = m ? m->phi_max : 0.f;
+    d.mu = static_cast<float>(mean);
+    d.sigma_inv = static_cast<float>(1.0 / sigma);
+    d.Y = out ? out->Y : nullptr;
+    d.K = out ? out->K : nullptr;
+    d.F = out ? out->facies : nullptr;
+    d.P = out ? out->prop : nullptr;
+    return d;
+}
+
+int check_map(const grf_map* m, const grf_outputs* out) {
+    if (!m) return fail(GRF_EINVAL, "map is NULL");
+    if (!out) return fail(GRF_EINVAL, "outputs is NULL");
+    const int known = GRF_MAP_Y | GRF_MAP_LOGNORMAL | GRF_MAP_FACIES | GRF_MAP_VALUES | GRF_MAP_POROSITY;
+    if (m->bits & ~known) return fail(GRF_EINVAL, "unknown map bits 0x%x", m->bits);
+    if ((m->bits & GRF_MAP_VALUES) && (m->bits & GRF_MAP_POROSITY))
+        return fail(GRF_EINVAL, "VALUES and POROSITY share the prop output");
+    if (m->n_thresholds < 0 || m->n_thresholds > GRF_MAX_THRESHOLDS)
+        return fail(GRF_EINVAL, "n_thresholds must be in [0, %d]", GRF_MAX_THRESHOLDS);
+    for (int t = 0; t < m->n_thresholds; ++t) {
+        if (!std::isfinite(m->thresholds[t])) return fail(GRF_EINVAL, "threshold %d is not finite", t);
+        if (t > 0 && !(m->thresholds[t] > m->thresholds[t - 1]))
+            return fail(GRF_EINVAL, "thresholds must be strictly ascending");
+    }
+    if ((m->bits & GRF_MAP_Y) && !out->Y) return fail(GRF_EINVAL, "Y output is NULL");
+    if ((m->bits & GRF_MAP_LOGNORMAL) && !out->K) return fail(GRF_EINVAL, "K output is NULL");
+    if ((m->bits & GRF_MAP_FACIES) && !out->facies) return fail(GRF_EINVAL, "facies output is NULL");
+    if ((m->bits & (GRF_MAP_VALUES | GRF_MAP_POROSITY)) && !out->prop)
+        return fail(GRF_EINVAL, "prop output is NULL");
+    if ((m->bits & GRF_MAP_POROSITY) && !(m->phi_min <= m->phi_max))
+        return fail(GRF_EINVAL, "phi_min must not exceed phi_max");
+    return GRF_OK;
+}
+
+}  // namespace
+}  // namespace grf
+
+using namespace grf;
+
+extern "C" {
+
+const char* grf_last_error(void) { return g_last_error.c_str(); }
+
+const char* grf_version(void) { return "grf-gb300 1.0"; }
+
+int64_t grf_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// S1: modes
+// ---------------------------------------------------------------------------
+int grf_gen_modes(const grf_params* p, grf_modes* out) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!out) return fail(GRF_EINVAL, "modes output is NULL");
+    if (out->n != p->n_modes || out->dim != p->dim)
+        return fail(GRF_EINVAL, "modes arrays sized for n=%lld dim=%d, params say n=%lld dim=%d",
+                    (long long)out->n, out->dim, (long long)p->n_modes, p->dim);
+    if (!out->kappa || !out->rho || !out->psi || !out->a || !out->amp)
+        return fail(GRF_EINVAL, "a modes array is NULL");
+    const int64_t N = p->n_modes;
+    const int d = p->dim;
+    const double sigma = std::sqrt(p->sigma2);
+    const double nu = p->family == GRF_EXPONENTIAL ? 0.5 : p->nu;
+    const double dof = 2.0 * nu;
+    const bool sum_sq = (p->family != GRF_GAUSSIAN) && dof == std::round(dof) && dof >= 1.0 && dof <= 32.0;
+    for (int64_t j = 0; j < N; ++j) {
+        const ModeStream g(p->seed, p->stream, static_cast<uint64_t>(j));
+        const double W = g.normal(0);
+        const double Wp = g.normal(1);
+        double z[3];
+        for (int c = 0; c < d; ++c) z[c] = g.normal(2u + c);
+        double scale;
+        if (p->family == GRF_GAUSSIAN) {
+            scale = std::sqrt(0.5 * M_PI);
+        } else {
+            double w = 0.0;
+            if (sum_sq) {
+                const int m = static_cast<int>(dof);
+                for (int i = 0; i < m; ++i) {
+                    const double v = g.normal(static_cast<uint32_t>(2 + d + i));
+                    w += v * v;
+                }
+            } else {
+                double G;
+                const double alpha = nu >= 1.0 ? nu : nu + 1.0;
+                if (!gamma_mt(g, alpha, G))
+                    return fail(GRF_EINVAL, "gamma sampler did not accept for mode %lld", (long long)j);
+                if (nu < 1.0) {
+                    double ub, unused;
+                    g.uniforms(63u, ub, unused);
+                    G *= std::pow(ub, 1.0 / nu);
+                }
+                w = 2.0 * G;
+            }
+            scale = std::sqrt(dof / w);
+        }
+        const double rho = std::sqrt((W * W + Wp * Wp) / static_cast<double>(N));
+        out->rho[j] = rho;
+        out->amp[j] = sigma * rho;
+        out->psi[j] = -std::atan2(Wp, W) / (2.0 * M_PI);
+        for (int c = 0; c < d; ++c) {
+            const double kap = z[c] * scale;
+            out->kappa[j * d + c] = kap;
+            out->a[j * d + c] = kap / (2.0 * M_PI * p->ell[c]);
+        }
+    }
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device table
+// ---------------------------------------------------------------------------
+size_t grf_table_bytes(int64_t n_modes) {
+    if (n_modes < 1 || n_modes > GRF_MAX_MODES) return 0;
+    return static_cast<size_t>(table_layout(n_modes).total);
+}
+
+int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
+    if (!m || !host_table) return fail(GRF_EINVAL, "modes or table is NULL");
+    if (m->n < 1 || m->n > GRF_MAX_MODES) return fail(GRF_EINVAL, "n_modes out of range");
+    if (m->dim < 1 || m->dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
+    if (!m->a || !m->amp || !m->psi) return fail(GRF_EINVAL, "a, amp or psi array is NULL");
+    const TableLayout L = table_layout(m->n);
+    if (bytes < static_cast<size_t>(L.total))
+        return fail(GRF_EWORKSPACE, "table buffer %zu bytes < %lld needed", bytes, (long long)L.total);
+    const int64_t N = m->n;
+    const int d = m->dim;
+    for (int64_t j = 0; j < N; ++j) {
+        if (!std::isfinite(m->amp[j]) || !std::isfinite(m->psi[j]))
+            return fail(GRF_EINVAL, "mode %lld has a non-finite amplitude or phase", (long long)j);
+        for (int c = 0; c < d; ++c)
+            if (!std::isfinite(m->a[j * d + c]))
+                return fail(GRF_EINVAL, "mode %lld has a non-finite frequency", (long long)j);
+    }
+    unsigned char* base = static_cast<unsigned char*>(host_table);
+    std::memset(base, 0, static_cast<size_t>(L.total));
+    std::vector<double> h(N);
+    for (int64_t j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int c = 0; c < d; ++c) s += std::fabs(m->a[j * d + c]);
+        h[j] = s;
+    }
+    std::vector<int64_t> ord(N);
+    std::iota(ord.begin(), ord.end(), int64_t(0));
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t u, int64_t v) { return h[u] > h[v]; });
+
+    TableHeader hd{};
+    hd.magic = kTableMagic;
+    hd.n_modes = static_cast<int32_t>(N);
+    hd.n_pad = static_cast<int32_t>(L.n_pad);
+    hd.dim = d;
+    hd.tau = kTauTurns;
+    hd.n_buckets = kBuckets;
+    hd.bucket_bias = kBucketBias;
+    hd.off_hot = L.off_hot;
+    hd.off_cold = L.off_cold;
+    hd.off_order = L.off_order;
+    hd.off_kpref = L.off_kpref;
+    hd.total_bytes = L.total;
+    std::memcpy(base, &hd, sizeof(hd));
+
+    float* hot = reinterpret_cast<float*>(base + L.off_hot);
+    float* cold = reinterpret_cast<float*>(base + L.off_cold);
+    int32_t* order = reinterpret_cast<int32_t*>(base + L.off_order);
+    int32_t* kpref = reinterpret_cast<int32_t*>(base + L.off_kpref);
+    for (int64_t s = 0; s < L.n_pad; ++s) {
+        order[s] = -1;
+        if (s >= N) continue;
+        const int64_t j = ord[s];
+        order[s] = static_cast<int32_t>(j);
+        double a[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < d; ++c) a[c] = m->a[j * d + c];
+        for (int c = 0; c < 3; ++c) hot[s * 4 + c] = static_cast<float>(2.0 * M_PI * a[c]);
+        hot[s * 4 + 3] = static_cast<float>(m->amp[j]);
+        float ah[3], al[3];
+        for (int c = 0; c < 3; ++c) {
+            ah[c] = static_cast<float>(a[c]);
+            al[c] = static_cast<float>(a[c] - static_cast<double>(ah[c]));
+        }
+        const float ph = static_cast<float>(m->psi[j]);
+        const float pl = static_cast<float>(m->psi[j] - static_cast<double>(ph));
+        float* c0 = cold + s * 8;
+        c0[0] = ah[0];
+        c0[1] = al[0];
+        c0[2] = ah[1];
+        c0[3] = al[1];
+        c0[4] = ah[2];
+        c0[5] = al[2];
+        c0[6] = ph;
+        c0[7] = pl;
+    }
+    // kpref[b] = #{s : h_s * E_b > tau}, E_b = 2^((b - bias) / 4)
+    for (int b = 0; b < kBuckets; ++b) {
+        const double Eb = std::pow(2.0, (b - kBucketBias) / 4.0);
+        int64_t k = 0;
+        while (k < N && h[ord[k]] * Eb > static_cast<double>(kTauTurns)) ++k;
+        kpref[b] = static_cast<int32_t>(k);
+    }
+    return GRF_OK;
+}
+
+int grf_upload_table(const void* host_table, void* dev_table, size_t bytes, void* stream) {
+    if (!host_table || !dev_table) return fail(GRF_EINVAL, "table pointer is NULL");
+    if (!aligned256(dev_table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
+    TableHeader hd;
+    std::memcpy(&hd, host_table, sizeof(hd));
+    if (hd.magic != kTableMagic) return fail(GRF_EINVAL, "host table was not built by grf_pack_table");
+    if (bytes < static_cast<size_t>(hd.total_bytes))
+        return fail(GRF_EWORKSPACE, "device table %zu bytes < %lld needed", bytes, (long long)hd.total_bytes);
+    cudaError_t e = cudaMemcpyAsync(dev_table, host_table, static_cast<size_t>(hd.total_bytes),
+                                    cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "table upload");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+size_t grf_plan_bytes(int64_t n_cells, int32_t n_segments) {
+    if (n_cells < 0 || n_cells > INT32_MAX || n_segments < 1) return 0;
+    return static_cast<size_t>(plan_layout(n_cells, n_segments).total);
+}
+
+int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t* seg_offsets, const float* x,
+                   const float* y, const float* z, void* plan, size_t plan_bytes, void* stream) {
+    if (dim < 1 || dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
+    if (n_segments < 1) return fail(GRF_EINVAL, "n_segments must be >= 1");
+    if (!seg_offsets) return fail(GRF_EINVAL, "seg_offsets is NULL");
+    if (seg_offsets[0] != 0) return fail(GRF_EINVAL, "seg_offsets[0] must be 0");
+    for (int s = 0; s < n_segments; ++s)
+        if (seg_offsets[s + 1] < seg_offsets[s]) return fail(GRF_EINVAL, "seg_offsets must be ascending");
+    const int64_t n = seg_offsets[n_segments];
+    if (n > INT32_MAX) return fail(GRF_EINVAL, "at most 2^31-1 cells per plan");
+    if (!plan) return fail(GRF_EINVAL, "plan is NULL");
+    if (!aligned256(plan)) return fail(GRF_EINVAL, "plan must be 256-byte aligned");
+    if (n > 0 && (!x || (dim > 1 && !y) || (dim > 2 && !z)))
+        return fail(GRF_EINVAL, "a coordinate array is NULL");
+    const PlanLayout L = plan_layout(n, n_segments);
+    if (plan_bytes < static_cast<size_t>(L.total))
+        return fail(GRF_EWORKSPACE, "plan buffer %zu bytes < %lld needed", plan_bytes, (long long)L.total);
+    const int err = launch_plan(dim, n_segments, seg_offsets, x, y, z, plan, L, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
+    PlanMeta meta;
+    meta.dim = dim;
+    meta.offsets.assign(seg_offsets, seg_offsets + n_segments + 1);
+    meta.layout = L;
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_plans[plan] = std::move(meta);
+    return GRF_OK;
+}
+
+int grf_read_status(const void* plan, int32_t* status_out, void* stream) {
+    if (!plan || !status_out) return fail(GRF_EINVAL, "NULL argument");
+    PlanMeta meta;
+    if (!lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    const PlanHeader* hdr = static_cast<const PlanHeader*>(plan);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(status_out, &hdr->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Synthesis
+// ---------------------------------------------------------------------------
+namespace {
+int fwd_desc(const void* table, int64_t n_modes, int32_t dim, const void* plan,
+             const PlanMeta& meta, int32_t segment, const MapDev& map, FwdDesc& d) {
+    if (segment < 0 || segment >= static_cast<int32_t>(meta.offsets.size()) - 1)
+        return fail(GRF_EINVAL, "segment %d out of range", segment);
+    if (dim > meta.dim) return fail(GRF_EINVAL, "field dim %d exceeds plan dim %d", dim, meta.dim);
+    if (!aligned256(table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
+    const TableLayout TL = table_layout(n_modes);
+    const unsigned char* tb = static_cast<const unsigned char*>(table);
+    const unsigned char* pb = static_cast<const unsigned char*>(plan);
+    const int64_t begin = meta.offsets[segment];
+    d.hot = reinterpret_cast<const float4*>(tb + TL.off_hot);
+    d.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
+    d.kpref = reinterpret_cast<const int32_t*>(tb + TL.off_kpref);
+    d.n_pad = static_cast<int32_t>(TL.n_pad);
+    d.dim = meta.dim;
+    d.xs = reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin;
+    d.ys = reinterpret_cast<const float*>(pb + meta.layout.off_ys) + begin;
+    d.zs = reinterpret_cast<const float*>(pb + meta.layout.off_zs) + begin;
+    d.perm = reinterpret_cast<const int32_t*>(pb + meta.layout.off_perm) + begin;
+    d.perm_base = begin;
+    d.n_cells = meta.offsets[segment + 1] - begin;
+    d.map = map;
+    return GRF_OK;
+}
+}  // namespace
+
+int grf_synth_field(const void* table, const grf_params* p, const void* plan, int32_t segment,
+                    const grf_map* map, const grf_outputs* out, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!table) return fail(GRF_EINVAL, "table is NULL");
+    rc = check_map(map, out);
+    if (rc) return rc;
+    if (map->bits == 0) return fail(GRF_EINVAL, "no output requested");
+    PlanMeta meta;
+    if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    FwdDesc d{};
+    rc = fwd_desc(table, p->n_modes, p->dim, plan, meta, segment,
+                  make_map(map, out, p->mean, std::sqrt(p->sigma2)), d);
+    if (rc) return rc;
+    int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
+    const int err = launch_synth_fwd(d, 0, status, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
+    return GRF_OK;
+}
+
+int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, const float* Y,
+                     const grf_outputs* out, void* stream) {
+    int rc = check_map(map, out);
+    if (rc) return rc;
+    if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
+    if (n > 0 && !Y) return fail(GRF_EINVAL, "Y is NULL");
+    if (!(sigma > 0.0)) return fail(GRF_EINVAL, "sigma must be > 0");
+    const int err = launch_map(make_map(map, out, mean, sigma), n, Y, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "map kernel");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
+    if (n_modes < 1 || n_modes > GRF_MAX_MODES || dim < 1 || dim > 3 || n_cells < 0) return 0;
+    return bwd_workspace_bytes(n_cells, n_modes, dim);
+}
+
+int grf_synth_backward(const void* table, const grf_params* p, const void* plan, int32_t segment,
+                       const float* gY, const grf_grads* g, void* workspace, size_t ws_bytes,
+                       void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!table || !g || !g->dA || !g->dpsi || !g->da || !g->dmu || !g->dsigma || !g->dell)
+        return fail(GRF_EINVAL, "table or a gradient output is NULL");
+    PlanMeta meta;
+    if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    if (p->dim != meta.dim) return fail(GRF_EINVAL, "params dim %d != plan dim %d", p->dim, meta.dim);
+    if (segment < 0 || segment >= static_cast<int32_t>(meta.offsets.size()) - 1)
+        return fail(GRF_EINVAL, "segment %d out of range", segment);
+    const int64_t begin = meta.offsets[segment];
+    const int64_t n = meta.offsets[segment + 1] - begin;
+    if (n > 0 && !gY) return fail(GRF_EINVAL, "gY is NULL");
+    if (!workspace) return fail(GRF_EINVAL, "workspace is NULL");
+    if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
+    if (!aligned256(table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
+    const size_t need = bwd_workspace_bytes(n, p->n_modes, p->dim);
+    if (ws_bytes < need) return fail(GRF_EWORKSPACE, "backward workspace %zu < %zu bytes", ws_bytes, need);
+    const unsigned char* pb = static_cast<const unsigned char*>(plan);
+    int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
+    const int err = launch_synth_bwd(
+        table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell,
+        reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin,
+        reinterpret_cast<const float*>(pb + meta.layout.off_ys) + begin,
+        reinterpret_cast<const float*>(pb + meta.layout.off_zs) + begin,
+        reinterpret_cast<const int32_t*>(pb + meta.layout.off_perm) + begin, begin, n, gY, *g,
+        workspace, status, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "backward kernels");
+    return GRF_OK;
+}
+
+size_t grf_mismatch_workspace_bytes(int64_t n) {
+    if (n < 0) return 0;
+    return mismatch_workspace_bytes(n);
+}
+
+int grf_mismatch_grad(int64_t n, const float* K, const float* K_target, float* gY, double* loss,
+                      void* workspace, size_t ws_bytes, void* stream) {
+    if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
+    if (n > 0 && (!K || !K_target || !gY)) return fail(GRF_EINVAL, "K, K_target or gY is NULL");
+    if (!loss || !workspace) return fail(GRF_EINVAL, "loss or workspace is NULL");
+    const size_t need = mismatch_workspace_bytes(n);
+    if (ws_bytes < need) return fail(GRF_EWORKSPACE, "mismatch workspace %zu < %zu bytes", ws_bytes, need);
+    const int err = launch_mismatch(n, K, K_target, gY, loss, workspace, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "mismatch kernels");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched ensembles
+// ---------------------------------------------------------------------------
+size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells) {
+    if (n_items < 1 || n_cells < 0) return 0;
+    const int64_t min_tile = 512;
+    const int64_t max_work = n_cells / min_tile + n_items;
+    return static_cast<size_t>(256 + align256(int64_t(n_items) * int64_t(sizeof(FwdDesc))) +
+                               align256(max_work * int64_t(sizeof(WorkItem))) + 256);
+}
+
+int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* plan,
+                      int32_t tile_cells, void* workspace, size_t ws_bytes, void* host_staging,
+                      void* stream) {
+    if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
+    if (!workspace || !host_staging) return fail(GRF_EINVAL, "workspace or staging is NULL");
+    if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
+    PlanMeta meta;
+    if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    int cfg;
+    switch (tile_cells) {
+        case 0:
+        case 1024: cfg = 0; break;
+        case 2048: cfg = 1; break;
+        case 512: cfg = 2; break;
+        default: return fail(GRF_EINVAL, "tile_cells must be 0, 512, 1024 or 2048");
+    }
+    const int64_t tc = fwd_tile_cells(cfg);
+    const size_t need = grf_batch_workspace_bytes(n_items, meta.offsets.back());
+    if (ws_bytes < need) return fail(GRF_EWORKSPACE, "batch workspace %zu < %zu bytes", ws_bytes, need);
+    BatchHeader h{};
+    h.magic = kBatchMagic;
+    h.n_items = n_items;
+    h.tile_cells = static_cast<int32_t>(tc);
+    h.cfg = cfg;
+    h.dim_max = meta.dim;
+    h.off_desc = 256;
+    h.off_work = h.off_desc + align256(int64_t(n_items) * int64_t(sizeof(FwdDesc)));
+    unsigned char* hs = static_cast<unsigned char*>(host_staging);
+    FwdDesc* descs = reinterpret_cast<FwdDesc*>(hs + h.off_desc);
+    std::vector<int64_t> order(n_items);
+    for (int32_t r = 0; r < n_items; ++r) {
+        const grf_batch_item& it = items[r];
+        if (!it.table) return fail(GRF_EINVAL, "item %d: table is NULL", r);
+        if (it.n_modes < 1 || it.n_modes > GRF_MAX_MODES) return fail(GRF_EINVAL, "item %d: n_modes", r);
+        if (it.dim < 1 || it.dim > 3) return fail(GRF_EINVAL, "item %d: dim", r);
+        if (!(it.sigma > 0.0) || !std::isfinite(it.mean)) return fail(GRF_EINVAL, "item %d: sigma/mean", r);
+        int rc = check_map(&it.map, &it.out);
+        if (rc) return fail(rc, "item %d: %s", r, g_last_error.c_str());
+        if (it.map.bits == 0) return fail(GRF_EINVAL, "item %d: no output requested", r);
+        FwdDesc d{};
+        rc = fwd_desc(it.table, it.n_modes, it.dim, plan, meta, it.segment,
+                      make_map(&it.map, &it.out, it.mean, it.sigma), d);
+        if (rc) return fail(rc, "item %d: %s", r, g_last_error.c_str());
+        std::memcpy(&descs[r], &d, sizeof(FwdDesc));
+        order[r] = r;
+    }
+    // longest-processing-time first: realisations with more modes first
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t u, int64_t v) { return descs[u].n_pad > descs[v].n_pad; });
+    WorkItem* work = reinterpret_cast<WorkItem*>(hs + h.off_work);
+    int64_t nw = 0;
+    const int64_t cap = (static_cast<int64_t>(need) - h.off_work) / int64_t(sizeof(WorkItem));
+    for (int64_t q = 0; q < n_items; ++q) {
+        const int64_t r = order[q];
+        const int64_t tiles = (descs[r].n_cells + tc - 1) / tc;
+        for (int64_t t = 0; t < tiles; ++t) {
+            if (nw >= cap) return fail(GRF_EWORKSPACE, "work list exceeds workspace");
+            work[nw].r = static_cast<int32_t>(r);
+            work[nw].t = static_cast<int32_t>(t);
+            ++nw;
+        }
+    }
+    h.n_work = static_cast<int32_t>(nw);
+    h.off_counter = h.off_work + align256(nw * int64_t(sizeof(WorkItem)));
+    h.total_bytes = h.off_counter + 256;
+    std::memcpy(hs, &h, sizeof(h));
+    cudaError_t e = cudaMemcpyAsync(workspace, host_staging, static_cast<size_t>(h.off_counter),
+                                    cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+    BatchMeta bm{h, meta.dim};
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_batches[workspace] = bm;
+    return GRF_OK;
+}
+
+int grf_batch_launch(void* workspace, void* stream) {
+    BatchMeta bm;
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        auto it = g_batches.find(workspace);
+        if (it == g_batches.end()) return fail(GRF_EINVAL, "workspace was not prepared by grf_batch_prepare");
+        bm = it->second;
+    }
+    unsigned char* base = static_cast<unsigned char*>(workspace);
+    int32_t* counter = reinterpret_cast<int32_t*>(base + bm.hdr.off_counter);
+    int32_t* status = counter + 1;
+    const int err = launch_synth_batched(workspace, bm.hdr, status, counter, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "batched kernel");
+    return GRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Measurement helpers
+// ---------------------------------------------------------------------------
+int grf_device_info(int32_t* sm_count, int32_t* sm_clock_khz) {
+    if (!sm_count || !sm_clock_khz) return fail(GRF_EINVAL, "NULL argument");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(sm_clock_khz, cudaDevAttrClockRate, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    return GRF_OK;
+}
+
+int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) {
+    if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
+    const int err = launch_mufu_probe(blocks, iters, sink, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "probe kernel");
+    return GRF_OK;
+}
+
+}  // extern "C"

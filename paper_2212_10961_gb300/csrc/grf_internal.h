@@ -1,0 +1,200 @@
+// Internal layout shared by the host code and the CUDA kernels of the
+// spectral Gaussian-random-field library.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "grf.h"
+
+namespace grf {
+
+// ---------------------------------------------------------------------------
+// Device mode table (built on the host by grf_pack_table).
+//
+// Modes are stored in decreasing order of h_j = sum_c |a_jc| (turns per unit
+// length) and padded with zero-amplitude modes to a multiple of kChunk, so the
+// chunked loops need no tail.  Sections (byte offsets from the table start,
+// all 256-byte aligned):
+//   hot  : float4[n_pad]   (2 pi a_x, 2 pi a_y, 2 pi a_z, A)  -- radians/unit
+//   cold : float4[2*n_pad] (ah_x, al_x, ah_y, al_y), (ah_z, al_z, psi_h, psi_l)
+//          a = ah + al and psi = psi_h + psi_l as FP32 pairs (turns)
+//   order: int32[n_pad]    original mode index j (-1 for padding)
+//   kpref: int32[kBuckets] number of leading modes that take the exact phase
+//          path for a warp whose half-extent E <= bucket_extent(b)
+// ---------------------------------------------------------------------------
+constexpr int kChunk = 128;          // modes per shared-memory chunk
+constexpr int kBuckets = 160;        // extent buckets
+constexpr int kBucketBias = 100;     // E_b = 2^((b - kBucketBias) / 4)
+constexpr float kTauTurns = 0.5f;    // light path iff h_j * E <= tau (turns)
+constexpr uint32_t kTableMagic = 0x54465247u;  // "GRFT"
+
+struct TableHeader {
+    uint32_t magic;
+    int32_t n_modes;
+    int32_t n_pad;
+    int32_t dim;
+    float tau;
+    int32_t n_buckets;
+    int32_t bucket_bias;
+    int32_t reserved0;
+    int64_t off_hot;
+    int64_t off_cold;
+    int64_t off_order;
+    int64_t off_kpref;
+    int64_t total_bytes;
+    int64_t reserved[7];
+};
+static_assert(sizeof(TableHeader) <= 256, "table header must fit in 256 bytes");
+
+inline int64_t align256(int64_t v) { return (v + 255) & ~int64_t(255); }
+inline int64_t pad_modes(int64_t n) { return (n + kChunk - 1) / kChunk * kChunk; }
+
+struct TableLayout {
+    int64_t n_pad, off_hot, off_cold, off_order, off_kpref, total;
+};
+
+inline TableLayout table_layout(int64_t n_modes) {
+    TableLayout L;
+    L.n_pad = pad_modes(n_modes);
+    L.off_hot = 256;
+    L.off_cold = L.off_hot + align256(L.n_pad * 16);
+    L.off_order = L.off_cold + align256(L.n_pad * 32);
+    L.off_kpref = L.off_order + align256(L.n_pad * 4);
+    L.total = L.off_kpref + align256(kBuckets * 4);
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Cell plan (device buffer built by grf_plan_cells).
+//   header  : PlanHeader (256 B)
+//   segs    : SegInfo[n_segments]
+//   xs,ys,zs: float[n_cells] sorted coordinates
+//   perm    : int32[n_cells] original (plan-global) index of sorted cell i
+//   keys_in, keys_out : uint64[n_cells]   (planning scratch)
+//   vals_in           : int32[n_cells]    (planning scratch)
+//   sort_tmp          : radix-sort temporary storage
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPlanMagic = 0x4E4C5047u;  // "GPLN"
+constexpr int kMortonBits = 10;                // brick coordinate bits per axis
+constexpr int kBrickTarget = 256;              // target cells per brick
+
+struct PlanHeader {
+    uint32_t magic;
+    int32_t status;       // device-side error bits
+    int32_t dim;
+    int32_t n_segments;
+    int64_t n_cells;
+    int64_t off_segs, off_xs, off_ys, off_zs, off_perm, off_keys_in, off_keys_out, off_vals_in,
+        off_sort_tmp, sort_tmp_bytes, total_bytes;
+    int64_t reserved[14];
+};
+static_assert(sizeof(PlanHeader) <= 256, "plan header must fit in 256 bytes");
+
+struct SegInfo {
+    int64_t begin;        // first cell (global index)
+    int64_t count;
+    float lo[3];          // bounding box (float bits ordered as ints during the reduction)
+    float hi[3];
+    float inv_brick[3];   // bricks per unit length per axis
+    int32_t nb[3];        // bricks per axis
+    int32_t pad;
+};
+
+struct PlanLayout {
+    int64_t off_segs, off_xs, off_ys, off_zs, off_perm, off_keys_in, off_keys_out, off_vals_in,
+        off_sort_tmp, sort_tmp_bytes, total;
+};
+
+size_t radix_sort_temp_bytes(int64_t n_cells);  // defined in plan.cu
+
+inline PlanLayout plan_layout(int64_t n_cells, int32_t n_segments) {
+    PlanLayout L;
+    L.off_segs = 256;
+    L.off_xs = L.off_segs + align256(int64_t(n_segments) * int64_t(sizeof(SegInfo)));
+    L.off_ys = L.off_xs + align256(n_cells * 4);
+    L.off_zs = L.off_ys + align256(n_cells * 4);
+    L.off_perm = L.off_zs + align256(n_cells * 4);
+    L.off_keys_in = L.off_perm + align256(n_cells * 4);
+    L.off_keys_out = L.off_keys_in + align256(n_cells * 8);
+    L.off_vals_in = L.off_keys_out + align256(n_cells * 8);
+    L.off_sort_tmp = L.off_vals_in + align256(n_cells * 4);
+    L.sort_tmp_bytes = int64_t(radix_sort_temp_bytes(n_cells));
+    L.total = L.off_sort_tmp + align256(L.sort_tmp_bytes);
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Map parameters as the kernels see them.
+// ---------------------------------------------------------------------------
+struct MapDev {
+    int32_t bits;
+    int32_t n_thr;
+    float thr[GRF_MAX_THRESHOLDS];
+    float values[GRF_MAX_THRESHOLDS + 1];
+    float k_ref, phi0, phi1, phi_min, phi_max;
+    float mu, sigma_inv;
+    float* Y;
+    float* K;
+    uint8_t* F;
+    float* P;
+};
+
+// One realisation as the forward kernel sees it.
+struct FwdDesc {
+    const float4* hot;
+    const float4* cold;
+    const int32_t* kpref;
+    int32_t n_pad;
+    int32_t dim;
+    const float* xs;      // sorted coordinates of this realisation's segment
+    const float* ys;
+    const float* zs;
+    const int32_t* perm;  // original (plan-global) index of each sorted cell
+    int64_t perm_base;    // first plan-global index of the segment
+    int64_t n_cells;
+    MapDev map;
+};
+
+// Work tile of the batched launch: realisation r, tile index t inside it.
+struct WorkItem {
+    int32_t r;
+    int32_t t;
+};
+
+// Batched workspace layout.
+struct BatchHeader {
+    uint32_t magic;
+    int32_t n_items;
+    int32_t n_work;
+    int32_t tile_cells;
+    int32_t cfg;          // kernel configuration index
+    int32_t dim_max;
+    int64_t off_desc, off_work, off_counter, total_bytes;
+    int64_t reserved[24];
+};
+constexpr uint32_t kBatchMagic = 0x48435442u;  // "BTCH"
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files), all asynchronous on `stream`.
+// Return cudaError_t as int.
+// ---------------------------------------------------------------------------
+int launch_synth_fwd(const FwdDesc& d, int cells_per_cta, int32_t* status, void* stream);
+int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
+                         int32_t* counter, void* stream);
+int fwd_tile_cells(int cfg);
+int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream);
+int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
+                const float* y, const float* z, void* plan, const PlanLayout& L, void* stream);
+int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
+                     const double* ell, const float* xs, const float* ys, const float* zs,
+                     const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
+                     const grf_grads& g, void* workspace, int32_t* status, void* stream);
+size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);
+int launch_mismatch(int64_t n, const float* K, const float* T, float* gY, double* loss, void* ws,
+                    void* stream);
+size_t mismatch_workspace_bytes(int64_t n);
+int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream);
+void count_launches(int64_t n);
+
+}  // namespace grf

@@ -1,0 +1,417 @@
+// Adjoint of the spectral field sum (derivative of Eq. DiscreteFT, Sec. 4.1,
+// with the reparameterisation A = sigma rho, a = kappa / (2 pi l)).
+//
+// Given g_i = dL/dY_i, per mode j (theta_ij = 2 pi (a_j . x_i + psi_j)):
+//     S_cos[j] = sum_i g_i cos theta_ij,  S_sin[j] = sum_i g_i sin theta_ij,
+//     S_x[j,c] = sum_i g_i sin theta_ij x_ic
+// and then dA = S_cos, dpsi = -2 pi A S_sin, da = -2 pi A S_x,
+// dsigma = sum_j (A_j / sigma) dA_j, dl_c = -sum_j (a_jc / l_c) da_jc,
+// dmu = sum_i g_i.
+//
+// Kernel 1 (mode-stationary): a block owns kBwdThreads * MPT consecutive
+// modes (MPT per thread, registers) and a contiguous range of spatially
+// sorted cell tiles of kBwdTile cells.  Each tile is staged in shared memory
+// with its bounding-box origin x0; phases are split exactly as in the
+// forward kernel (per (tile, mode) compensated origin phase, FP32 offsets;
+// exact per-cell path for the modes whose span over the tile is large).
+// sin and cos are recomputed with the hardware MUFU (never stored).  Tile
+// sums are FP32, folded into TwoSum-compensated accumulators, and written as
+// FP64 partials per (split, mode).
+// Kernel 2 sums the partials over splits in a fixed order (deterministic)
+// and applies the chain rule per mode; kernel 3 reduces the scalar
+// gradients (sigma, l, mu) in a fixed order.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace grf {
+
+namespace {
+
+constexpr int kBwdThreads = 128;
+constexpr int kBwdTile = 256;
+constexpr int kBwdMaxSplits = 256;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct BwdArgs {
+    const float4* hot;
+    const float4* cold;
+    const int32_t* order;
+    const int32_t* kpref;
+    int32_t n_modes;
+    int32_t n_pad;
+    int32_t dim;
+    int32_t splits;
+    double sigma;
+    double ell[3];
+    const float* xs;
+    const float* ys;
+    const float* zs;
+    const int32_t* perm;
+    int64_t perm_base;
+    int64_t n_cells;
+    const float* gY;
+    double* part;     // [splits][n_pad][5]
+    double* gpart;    // [splits]
+    double* contrib;  // [n_pad][4]: (A/sigma) dA, -(a_c/l_c) da_c
+    grf_grads g;
+};
+
+__device__ __forceinline__ int bucket_of_bwd(float E) {
+    if (!(E > 0.0f)) return 0;
+    int b = static_cast<int>(ceilf(4.0f * __log2f(E))) + kBucketBias + 1;
+    return b < 0 ? 0 : b;
+}
+
+struct DF {  // double-float accumulator
+    float hi, lo;
+    __device__ __forceinline__ void add(float v) { two_sum_acc(hi, lo, v); }
+    __device__ __forceinline__ double value() const {
+        return static_cast<double>(hi) + static_cast<double>(lo);
+    }
+};
+
+template <int DIM, int MPT>
+__global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, int32_t* status) {
+    __shared__ float4 cd[kBwdTile];  // (dx, dy, dz, g)
+    __shared__ float4 cx[kBwdTile];  // (x, y, z, -)
+    __shared__ float red_mn[kBwdThreads / 32][3];
+    __shared__ float red_mx[kBwdThreads / 32][3];
+    __shared__ float s_x0[3];
+    __shared__ int s_k;
+    __shared__ double s_g[kBwdThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int m_base = blockIdx.x * (kBwdThreads * MPT) + tid * MPT;
+
+    // mode parameters (padding modes and slots past n_pad have A = 0 / skipped)
+    float4 hot[MPT], c0[MPT], c1[MPT];
+    bool live[MPT];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+        const int m = m_base + k;
+        live[k] = m < args.n_pad;
+        const int mm = live[k] ? m : 0;
+        hot[k] = args.hot[mm];
+        c0[k] = args.cold[2 * mm];
+        c1[k] = args.cold[2 * mm + 1];
+    }
+    DF accC[MPT], accS[MPT], accX[MPT][3];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+        accC[k] = DF{0.f, 0.f};
+        accS[k] = DF{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) accX[k][c] = DF{0.f, 0.f};
+    }
+    double gsum = 0.0;
+
+    const int64_t n = args.n_cells;
+    const int64_t n_tiles = (n + kBwdTile - 1) / kBwdTile;
+    const int64_t per_split = (n_tiles + args.splits - 1) / args.splits;
+    const int64_t t_begin = blockIdx.y * per_split;
+    const int64_t t_end = t_begin + per_split < n_tiles ? t_begin + per_split : n_tiles;
+
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        const int64_t tb = t * kBwdTile;
+        // ---- stage the tile ----------------------------------------------------
+        float xv[2][3];
+        float gv[2];
+        float mn[3], mx[3];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t i = tb + q * kBwdThreads + tid;
+            const bool in = i < n;
+            const int64_t ii = in ? i : tb;
+            xv[q][0] = args.xs[ii];
+            xv[q][1] = DIM > 1 ? args.ys[ii] : 0.f;
+            xv[q][2] = DIM > 2 ? args.zs[ii] : 0.f;
+            gv[q] = in ? args.gY[static_cast<int64_t>(args.perm[i]) - args.perm_base] : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = fminf(xv[0][c], xv[1][c]);
+            mx[c] = fmaxf(xv[0][c], xv[1][c]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+                mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+            }
+            if (lane == 0) {
+                red_mn[warp][c] = mn[c];
+                red_mx[warp][c] = mx[c];
+            }
+        }
+        if (blockIdx.x == 0) gsum += static_cast<double>(gv[0]) + static_cast<double>(gv[1]);
+        __syncthreads();
+        if (tid == 0) {
+            float E = 0.f;
+            for (int c = 0; c < DIM; ++c) {
+                float a = red_mn[0][c], b = red_mx[0][c];
+                for (int w = 1; w < kBwdThreads / 32; ++w) {
+                    a = fminf(a, red_mn[w][c]);
+                    b = fmaxf(b, red_mx[w][c]);
+                }
+                const float o = 0.5f * a + 0.5f * b;
+                s_x0[c] = o;
+                E = fmaxf(E, fmaxf(b - o, o - a));
+            }
+            for (int c = DIM; c < 3; ++c) s_x0[c] = 0.f;
+            const int bk = bucket_of_bwd(E);
+            s_k = bk >= kBuckets ? args.n_pad : args.kpref[bk];
+        }
+        __syncthreads();
+        const float x0[3] = {s_x0[0], s_x0[1], s_x0[2]};
+        const int k_heavy = s_k;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int idx = q * kBwdThreads + tid;
+            cd[idx] = make_float4(xv[q][0] - x0[0], xv[q][1] - x0[1], xv[q][2] - x0[2], gv[q]);
+            cx[idx] = make_float4(xv[q][0], xv[q][1], xv[q][2], 0.f);
+        }
+        __syncthreads();
+
+        // ---- per-mode sums over the tile ------------------------------------------
+        const bool any_heavy = m_base < k_heavy;
+        float sc[MPT], ss[MPT], sx[MPT][3];
+        float t0[MPT];
+#pragma unroll
+        for (int k = 0; k < MPT; ++k) {
+            sc[k] = 0.f;
+            ss[k] = 0.f;
+            sx[k][0] = sx[k][1] = sx[k][2] = 0.f;
+            t0[k] = kTwoPiF * phase_exact_turns<DIM>(x0, c0[k], c1[k]);
+        }
+        if (!any_heavy) {
+#pragma unroll 2
+            for (int i = 0; i < kBwdTile; ++i) {
+                const float4 c = cd[i];
+#pragma unroll
+                for (int k = 0; k < MPT; ++k) {
+                    float th = fmaf(hot[k].x, c.x, t0[k]);
+                    if (DIM > 1) th = fmaf(hot[k].y, c.y, th);
+                    if (DIM > 2) th = fmaf(hot[k].z, c.z, th);
+                    const float cs = hw_cos(th);
+                    const float sn = hw_sin(th);
+                    const float gs = c.w * sn;
+                    sc[k] = fmaf(c.w, cs, sc[k]);
+                    ss[k] += gs;
+                    sx[k][0] = fmaf(gs, c.x, sx[k][0]);
+                    if (DIM > 1) sx[k][1] = fmaf(gs, c.y, sx[k][1]);
+                    if (DIM > 2) sx[k][2] = fmaf(gs, c.z, sx[k][2]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MPT; ++k) {
+                const bool heavy = (m_base + k) < k_heavy;
+                for (int i = 0; i < kBwdTile; ++i) {
+                    const float4 c = cd[i];
+                    float th;
+                    if (heavy) {
+                        const float4 xx = cx[i];
+                        const float xa[3] = {xx.x, xx.y, xx.z};
+                        th = kTwoPiF * phase_exact_turns<DIM>(xa, c0[k], c1[k]);
+                    } else {
+                        th = fmaf(hot[k].x, c.x, t0[k]);
+                        if (DIM > 1) th = fmaf(hot[k].y, c.y, th);
+                        if (DIM > 2) th = fmaf(hot[k].z, c.z, th);
+                    }
+                    const float cs = hw_cos(th);
+                    const float sn = hw_sin(th);
+                    const float gs = c.w * sn;
+                    sc[k] = fmaf(c.w, cs, sc[k]);
+                    ss[k] += gs;
+                    sx[k][0] = fmaf(gs, c.x, sx[k][0]);
+                    if (DIM > 1) sx[k][1] = fmaf(gs, c.y, sx[k][1]);
+                    if (DIM > 2) sx[k][2] = fmaf(gs, c.z, sx[k][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < MPT; ++k) {
+            accC[k].add(sc[k]);
+            accS[k].add(ss[k]);
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                accX[k][c].add(sx[k][c]);
+                accX[k][c].add(x0[c] * ss[k]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- write FP64 partials ---------------------------------------------------------
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+        if (!live[k]) continue;
+        const int m = m_base + k;
+        double* o = args.part + (static_cast<int64_t>(blockIdx.y) * args.n_pad + m) * 5;
+        o[0] = accC[k].value();
+        o[1] = accS[k].value();
+        o[2] = accX[k][0].value();
+        o[3] = DIM > 1 ? accX[k][1].value() : 0.0;
+        o[4] = DIM > 2 ? accX[k][2].value() : 0.0;
+    }
+    if (blockIdx.x == 0) {
+        for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
+        if (lane == 0) s_g[warp] = gsum;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < kBwdThreads / 32; ++w) tot += s_g[w];
+            args.gpart[blockIdx.y] = tot;
+        }
+    }
+    (void)status;
+}
+
+// Kernel 2: per mode, fixed-order sum over splits, chain rule, scatter to the
+// original mode index.
+__global__ void bwd_reduce_kernel(BwdArgs args) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= args.n_pad) return;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int s = 0; s < args.splits; ++s) {
+        const double* p = args.part + (static_cast<int64_t>(s) * args.n_pad + m) * 5;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] += p[q];
+    }
+    const int j = args.order[m];
+    double* ct = args.contrib + static_cast<int64_t>(m) * 4;
+    if (j < 0) {
+        ct[0] = ct[1] = ct[2] = ct[3] = 0.0;
+        return;
+    }
+    const float4 h = args.hot[m];
+    const float4 q0 = args.cold[2 * m];
+    const float4 q1 = args.cold[2 * m + 1];
+    const double A = static_cast<double>(h.w);
+    const double a[3] = {static_cast<double>(q0.x) + static_cast<double>(q0.y),
+                         static_cast<double>(q0.z) + static_cast<double>(q0.w),
+                         static_cast<double>(q1.x) + static_cast<double>(q1.y)};
+    args.g.dA[j] = v[0];
+    args.g.dpsi[j] = -kTwoPi * A * v[1];
+    ct[0] = (A / args.sigma) * v[0];
+    for (int c = 0; c < 3; ++c) {
+        if (c < args.dim) {
+            const double da = -kTwoPi * A * v[2 + c];
+            args.g.da[static_cast<int64_t>(j) * args.dim + c] = da;
+            ct[1 + c] = -(a[c] / args.ell[c]) * da;
+        } else {
+            ct[1 + c] = 0.0;
+        }
+    }
+}
+
+// Kernel 3: scalar gradients, one block, fixed-order reductions.
+__global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
+    __shared__ double red[256];
+    for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int m = threadIdx.x; m < args.n_pad; m += 256)
+            acc += args.contrib[static_cast<int64_t>(m) * 4 + q];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int off = 128; off > 0; off >>= 1) {
+            if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (q == 0)
+                args.g.dsigma[0] = red[0];
+            else if (q - 1 < args.dim)
+                args.g.dell[q - 1] = red[0];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < args.splits; ++k) s += args.gpart[k];
+        args.g.dmu[0] = s;
+    }
+}
+
+constexpr int kMPT = 2;
+
+int choose_splits(int64_t n_cells, int mode_blocks) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (n_cells + kBwdTile - 1) / kBwdTile;
+    int64_t want = (static_cast<int64_t>(sms) * 8 + mode_blocks - 1) / mode_blocks;
+    if (want > tiles) want = tiles;
+    if (want > kBwdMaxSplits) want = kBwdMaxSplits;
+    if (want < 1) want = 1;
+    return static_cast<int>(want);
+}
+
+}  // namespace
+
+size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
+    (void)n_cells;
+    (void)dim;
+    const int64_t n_pad = pad_modes(n_modes);
+    const int64_t part = int64_t(kBwdMaxSplits) * n_pad * 5 * 8;
+    const int64_t gpart = int64_t(kBwdMaxSplits) * 8;
+    const int64_t contrib = n_pad * 4 * 8;
+    return static_cast<size_t>(align256(part) + align256(gpart) + align256(contrib));
+}
+
+int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
+                     const double* ell, const float* xs, const float* ys, const float* zs,
+                     const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
+                     const grf_grads& g, void* workspace, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const TableLayout TL = table_layout(n_modes);
+    const unsigned char* tb = static_cast<const unsigned char*>(table);
+    BwdArgs a{};
+    a.hot = reinterpret_cast<const float4*>(tb + TL.off_hot);
+    a.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
+    a.order = reinterpret_cast<const int32_t*>(tb + TL.off_order);
+    a.kpref = reinterpret_cast<const int32_t*>(tb + TL.off_kpref);
+    a.n_modes = static_cast<int32_t>(n_modes);
+    a.n_pad = static_cast<int32_t>(TL.n_pad);
+    a.dim = dim;
+    a.sigma = sigma;
+    for (int c = 0; c < 3; ++c) a.ell[c] = c < dim ? ell[c] : 1.0;
+    a.xs = xs;
+    a.ys = ys;
+    a.zs = zs;
+    a.perm = perm;
+    a.perm_base = perm_base;
+    a.n_cells = n_cells;
+    a.gY = gY;
+    a.g = g;
+    const int mode_blocks = static_cast<int>((TL.n_pad + kBwdThreads * kMPT - 1) / (kBwdThreads * kMPT));
+    a.splits = n_cells > 0 ? choose_splits(n_cells, mode_blocks) : 1;
+    const int64_t n_pad = TL.n_pad;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    a.part = reinterpret_cast<double*>(ws);
+    a.gpart = reinterpret_cast<double*>(ws + align256(int64_t(kBwdMaxSplits) * n_pad * 5 * 8));
+    a.contrib = reinterpret_cast<double*>(ws + align256(int64_t(kBwdMaxSplits) * n_pad * 5 * 8) +
+                                          align256(int64_t(kBwdMaxSplits) * 8));
+    if (n_cells == 0) {
+        // no cells: all gradients are zero
+        cudaMemsetAsync(a.part, 0, sizeof(double) * n_pad * 5, st);
+        cudaMemsetAsync(a.gpart, 0, sizeof(double), st);
+        a.splits = 1;
+    } else {
+        dim3 grid(mode_blocks, a.splits);
+        switch (dim) {
+            case 1: bwd_partial_kernel<1, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
+            case 2: bwd_partial_kernel<2, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
+            case 3: bwd_partial_kernel<3, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
+            default: return cudaErrorInvalidValue;
+        }
+        count_launches(1);
+    }
+    bwd_reduce_kernel<<<static_cast<unsigned>((n_pad + 255) / 256), 256, 0, st>>>(a);
+    bwd_scalar_kernel<<<1, 256, 0, st>>>(a);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace grf

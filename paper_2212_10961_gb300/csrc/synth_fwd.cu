@@ -1,0 +1,356 @@
+// Forward synthesis kernel: Y_i = mu + sum_j A_j cos(2 pi (a_j . x_i + psi_j))
+// at arbitrary cell centres (Icardi et al., arXiv 2212.10961, Sec. 4.1,
+// Eq. DiscreteFT), with the property maps of Sec. 3.1 / Sec. 4.1 fused into
+// the epilogue.
+//
+// Work decomposition.  Cells arrive spatially sorted (cell plan).  A warp owns
+// 32*C consecutive sorted cells (C per lane, in registers) and takes the
+// midpoint of their bounding box as its origin x0, with half-extent E.  The
+// phase of mode j at cell i is split as
+//     theta_ij = 2 pi (a_j . x0 + psi_j  mod 1)  +  (2 pi a_j) . (x_i - x0),
+// the first term computed once per (warp, mode) in compensated FP32
+// (phase_exact_turns), the second per cell-mode with three FFMAs.  Modes whose
+// phase span over the warp, |a_j|_1 * E, exceeds tau turns (a prefix of the
+// table, which is sorted by |a_j|_1) take the exact per-cell path instead.
+// The hot loop is one MUFU cosine, one FMUL (radian scaling inside
+// cos.approx), DIM FFMAs for the phase and one FFMA to accumulate.
+//
+// Mode chunks (kChunk modes, 48 B each) are staged in shared memory by 1-D
+// bulk copies into two buffers completed on mbarriers; every wait is bounded
+// and reports GRF_ETIMEOUT through the status word instead of hanging.
+// Per-chunk FP32 partials are folded into a TwoSum-compensated accumulator.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace grf {
+
+namespace {
+
+constexpr int kChunkBytes = kChunk * 48;  // hot (16 B) + cold (32 B) per mode
+
+template <int C, int W>
+struct FwdSmem {
+    float4 buf[2][kChunk * 3];  // [hot kChunk][cold 2*kChunk]
+    float t0[W][kChunk];        // per-warp origin phase (radians)
+    uint64_t full[2];
+    int32_t abort_flag;
+    int32_t work;               // batched: current work index
+    FwdDesc desc;               // batched: current descriptor
+};
+
+__device__ __forceinline__ int bucket_of(float E) {
+    if (!(E > 0.0f)) return 0;
+    // conservative bucket: smallest b with 2^((b - bias)/4) >= E (one extra
+    // step covers the approximate log2)
+    int b = static_cast<int>(ceilf(4.0f * __log2f(E))) + kBucketBias + 1;
+    return b < 0 ? 0 : b;
+}
+
+// Issue the bulk copies of chunk `ch` of descriptor d into buffer `bi`.
+__device__ __forceinline__ void issue_chunk(const FwdDesc& d, int ch, float4* dst, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, kChunkBytes);
+    bulk_g2s(dst, d.hot + static_cast<int64_t>(ch) * kChunk, kChunk * 16, bar);
+    bulk_g2s(dst + kChunk, d.cold + static_cast<int64_t>(ch) * kChunk * 2, kChunk * 32, bar);
+}
+
+// One tile: W warps x 32 lanes x C cells starting at sorted cell `tile_base`.
+// `uses` counts completed waits per buffer (parity tracking across tiles).
+template <int DIM, int C, int W>
+__device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, FwdSmem<C, W>& sm,
+                                           uint32_t (&uses)[2], int32_t* status) {
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = d.n_cells;
+    const int64_t wbase = tile_base + static_cast<int64_t>(warp) * 32 * C;
+    const bool warp_active = wbase < n;
+    const int n_chunks = d.n_pad / kChunk;
+
+    // Prefetch the first two chunks (previous tile's buffers are free: the
+    // tile ended with a block barrier).
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        issue_chunk(d, 0, sm.buf[0], &sm.full[0]);
+        if (n_chunks > 1) issue_chunk(d, 1, sm.buf[1], &sm.full[1]);
+    }
+
+    // ---- load cells, bounding box, origin -------------------------------
+    float x[C][DIM];
+    bool valid[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        int64_t i = wbase + c * 32 + lane;
+        valid[c] = i < n;
+        int64_t ii = valid[c] ? i : (warp_active ? wbase : 0);
+        x[c][0] = d.xs[ii];
+        if (DIM > 1) x[c][1] = d.ys[ii];
+        if (DIM > 2) x[c][2] = d.zs[ii];
+    }
+    float x0[DIM];
+    float E = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        float mn = x[0][k], mx = x[0][k];
+#pragma unroll
+        for (int c = 1; c < C; ++c) {
+            mn = fminf(mn, x[c][k]);
+            mx = fmaxf(mx, x[c][k]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        x0[k] = 0.5f * mn + 0.5f * mx;
+        E = fmaxf(E, fmaxf(mx - x0[k], x0[k] - mn));
+    }
+    int k_heavy = 0;
+    if (warp_active) {
+        int b = bucket_of(E);
+        k_heavy = b >= kBuckets ? d.n_pad : d.kpref[b];
+    }
+
+    float s[C], e[C], p[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        s[c] = 0.0f;
+        e[c] = 0.0f;
+        p[c] = 0.0f;
+    }
+
+    // ---- exact path for the leading (fast-oscillating) modes -------------
+    for (int j = 0; j < k_heavy; ++j) {
+        const float4 c0 = __ldg(d.cold + 2 * j);
+        const float4 c1 = __ldg(d.cold + 2 * j + 1);
+        const float A = __ldg(&d.hot[j].w);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float r = phase_exact_turns<DIM>(x[c], c0, c1);
+            p[c] = fmaf(A, hw_cos(kTwoPiF * r), p[c]);
+        }
+        if ((j & 31) == 31) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                two_sum_acc(s[c], e[c], p[c]);
+                p[c] = 0.0f;
+            }
+        }
+    }
+
+    // ---- offsets from the origin -------------------------------------------
+    float dx[C][DIM];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - x0[k];
+
+    // ---- split path over staged chunks -----------------------------------------
+    int ch = 0;
+    for (; ch < n_chunks; ++ch) {
+        const int bi = ch & 1;
+        const uint32_t parity = uses[bi] & 1u;
+        bool ok = mbar_wait_bounded(&sm.full[bi], parity);
+        if (!ok) {
+            sm.abort_flag = 1;
+            atomicOr(status, 2);
+        }
+        uses[bi] += 1;
+        const float4* hotS = sm.buf[bi];
+        const float4* coldS = sm.buf[bi] + kChunk;
+        float* t0S = sm.t0[warp];
+        const int jbase = ch * kChunk;
+        if (ok && warp_active && jbase + kChunk > k_heavy) {
+            const int m0 = k_heavy > jbase ? k_heavy - jbase : 0;
+            for (int m = lane; m < kChunk; m += 32) {
+                float r = phase_exact_turns<DIM>(x0, coldS[2 * m], coldS[2 * m + 1]);
+                t0S[m] = kTwoPiF * r;
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int m = m0; m < kChunk; ++m) {
+                const float4 h = hotS[m];
+                const float t0 = t0S[m];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float th = fmaf(h.x, dx[c][0], t0);
+                    if (DIM > 1) th = fmaf(h.y, dx[c][1], th);
+                    if (DIM > 2) th = fmaf(h.z, dx[c][2], th);
+                    p[c] = fmaf(h.w, hw_cos(th), p[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                two_sum_acc(s[c], e[c], p[c]);
+                p[c] = 0.0f;
+            }
+        }
+        __syncthreads();
+        if (sm.abort_flag) break;
+        if (threadIdx.x == 0 && ch + 2 < n_chunks) {
+            fence_proxy_async_smem();
+            issue_chunk(d, ch + 2, sm.buf[bi], &sm.full[bi]);
+        }
+    }
+    if (sm.abort_flag) {
+        // Give the copies still in flight (chunks ch and ch + 1) a bounded
+        // chance to land before the block's shared memory is released.
+        if (threadIdx.x == 0) {
+            mbar_wait_bounded(&sm.full[ch & 1], (uses[ch & 1] - 1u) & 1u);
+            if (ch + 1 < n_chunks) mbar_wait_bounded(&sm.full[(ch + 1) & 1], uses[(ch + 1) & 1] & 1u);
+        }
+        return;
+    }
+
+    // ---- epilogue: field value and fused maps ------------------------------------
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        two_sum_acc(s[c], e[c], p[c]);
+        if (warp_active && valid[c]) {
+            const int64_t i = wbase + c * 32 + lane;
+            const float y = (s[c] + e[c]) + d.map.mu;
+            map_store(d.map, static_cast<int64_t>(d.perm[i]) - d.perm_base, y);
+        }
+    }
+}
+
+template <int DIM, int C, int W>
+__device__ __forceinline__ void init_smem(FwdSmem<C, W>& sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.full[0], 1);
+        mbar_init(&sm.full[1], 1);
+        sm.abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+template <int DIM, int C, int W>
+__global__ void __launch_bounds__(W * 32) synth_fwd_kernel(FwdDesc d, int32_t* status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<FwdSmem<C, W>*>(smem_raw);
+    init_smem<DIM, C, W>(sm);
+    uint32_t uses[2] = {0u, 0u};
+    const int64_t tile_base = static_cast<int64_t>(blockIdx.x) * (W * 32 * C);
+    synth_tile<DIM, C, W>(d, tile_base, sm, uses, status);
+}
+
+// Persistent batched kernel: blocks pull (realisation, tile) work items from
+// a counter until the list is exhausted.  DIM is the plan's dimension; a
+// realisation of lower dimension has zero frequencies on the extra axes.
+template <int DIM, int C, int W>
+__global__ void __launch_bounds__(W * 32) synth_batched_kernel(const FwdDesc* __restrict__ descs,
+                                                                const WorkItem* __restrict__ work,
+                                                                int32_t n_work, int32_t* counter,
+                                                                int32_t* status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<FwdSmem<C, W>*>(smem_raw);
+    init_smem<DIM, C, W>(sm);
+    uint32_t uses[2] = {0u, 0u};
+    for (;;) {
+        if (threadIdx.x == 0) sm.work = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = sm.work;
+        if (w >= n_work) break;
+        const WorkItem it = work[w];
+        // copy the descriptor into shared memory (word by word)
+        {
+            const int nwords = static_cast<int>(sizeof(FwdDesc) / 4);
+            const int32_t* src = reinterpret_cast<const int32_t*>(descs + it.r);
+            int32_t* dst = reinterpret_cast<int32_t*>(&sm.desc);
+            for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();
+        const int64_t tile_base = static_cast<int64_t>(it.t) * (W * 32 * C);
+        synth_tile<DIM, C, W>(sm.desc, tile_base, sm, uses, status);
+        if (sm.abort_flag) break;
+        __syncthreads();
+    }
+}
+
+template <int DIM, int C, int W>
+int launch_fwd_cfg(const FwdDesc& d, int32_t* status, cudaStream_t st) {
+    const size_t smem = sizeof(FwdSmem<C, W>);
+    auto kern = synth_fwd_kernel<DIM, C, W>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    const int64_t per_cta = int64_t(W) * 32 * C;
+    const int64_t grid = (d.n_cells + per_cta - 1) / per_cta;
+    if (grid == 0) return cudaSuccess;
+    kern<<<static_cast<unsigned>(grid), W * 32, smem, st>>>(d, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Configuration used by the single-realisation path: C = 8 cells per lane,
+// W = 4 warps (1024 cells per block).
+int fwd_tile_cells(int cfg) {
+    switch (cfg) {
+        case 0: return 4 * 32 * 8;
+        case 1: return 8 * 32 * 8;
+        case 2: return 4 * 32 * 4;
+        default: return 0;
+    }
+}
+
+int launch_synth_fwd(const FwdDesc& d, int cells_per_cta, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    (void)cells_per_cta;
+    switch (d.dim) {
+        case 1: return launch_fwd_cfg<1, 8, 4>(d, status, st);
+        case 2: return launch_fwd_cfg<2, 8, 4>(d, status, st);
+        case 3: return launch_fwd_cfg<3, 8, 4>(d, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+namespace {
+template <int DIM, int C, int W>
+int launch_batched_cfg(const FwdDesc* descs, const WorkItem* work, int32_t n_work,
+                       int32_t* counter, int32_t* status, cudaStream_t st) {
+    const size_t smem = sizeof(FwdSmem<C, W>);
+    auto kern = synth_batched_kernel<DIM, C, W>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    kern<<<sms * per_sm, W * 32, smem, st>>>(descs, work, n_work, counter, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int DIM>
+int launch_batched_dim(int cfg, const FwdDesc* descs, const WorkItem* work, int32_t n_work,
+                       int32_t* counter, int32_t* status, cudaStream_t st) {
+    switch (cfg) {
+        case 0: return launch_batched_cfg<DIM, 8, 4>(descs, work, n_work, counter, status, st);
+        case 1: return launch_batched_cfg<DIM, 8, 8>(descs, work, n_work, counter, status, st);
+        case 2: return launch_batched_cfg<DIM, 4, 4>(descs, work, n_work, counter, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
+                         int32_t* counter, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned char* base = static_cast<const unsigned char*>(workspace);
+    const FwdDesc* descs = reinterpret_cast<const FwdDesc*>(base + h.off_desc);
+    const WorkItem* work = reinterpret_cast<const WorkItem*>(base + h.off_work);
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
+    if (err != cudaSuccess) return err;
+    switch (h.dim_max) {
+        case 1: return launch_batched_dim<1>(h.cfg, descs, work, h.n_work, counter, status, st);
+        case 2: return launch_batched_dim<2>(h.cfg, descs, work, h.n_work, counter, status, st);
+        case 3: return launch_batched_dim<3>(h.cfg, descs, work, h.n_work, counter, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace grf

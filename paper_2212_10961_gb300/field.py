@@ -1,0 +1,490 @@
+"""Python API over the C ABI: mode drawing, device tables, cell plans,
+synthesis with fused maps, the adjoint, autograd wrappers and batches.
+
+PyTorch provides device memory, pinned host buffers and streams; all
+arithmetic of the method runs in libgrf.so (host C++ for the O(N) mode
+drawing and table packing, CUDA kernels for everything per cell).
+
+Method: Icardi et al., arXiv 2212.10961 -- Sec. 4.1 Eq. (DiscreteFT) (direct
+spectral sum at arbitrary cell centres), Appendix A (covariances and
+spectra), Sec. 3.1 / Appendix B (thresholds, facies values, lognormal
+scaling).
+"""
+import ctypes
+import math
+from dataclasses import dataclass, field as dc_field
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+FAMILIES = {"gaussian": _abi.GRF_GAUSSIAN, "exponential": _abi.GRF_EXPONENTIAL,
+            "matern": _abi.GRF_MATERN}
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _require_cuda(t, dtype, name):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+@dataclass
+class FieldParams:
+    """Parameters of one Gaussian random field (Appendix B dictionary keys:
+    correlation, Kmean, Ksigma, Lcorr, nu, nfreq, disableY/disableZ)."""
+    family: str = "gaussian"
+    sigma2: float = 1.0
+    mean: float = 0.0
+    ell: Sequence[float] = (1.0, 1.0, 1.0)
+    dim: int = 3
+    n_modes: int = 1000
+    seed: int = 1
+    nu: float = 1.5
+    stream: int = 0
+
+    @property
+    def sigma(self):
+        return math.sqrt(self.sigma2)
+
+    def to_c(self):
+        p = _abi.grf_params()
+        fam = self.family if isinstance(self.family, int) else FAMILIES[self.family.lower()]
+        p.family = fam
+        p.dim = int(self.dim)
+        p.nu = float(self.nu)
+        p.sigma2 = float(self.sigma2)
+        p.mean = float(self.mean)
+        ell = list(self.ell) + [1.0] * (3 - len(self.ell))
+        for c in range(3):
+            p.ell[c] = float(ell[c])
+        p.n_modes = int(self.n_modes)
+        p.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
+        p.stream = int(self.stream)
+        p.reserved = 0
+        return p
+
+
+def _modes_struct(n, dim, arrays):
+    m = _abi.grf_modes()
+    m.n = n
+    m.dim = dim
+    for k in ("kappa", "rho", "psi", "a", "amp"):
+        setattr(m, k, arrays[k].ctypes.data_as(_abi.c_dp))
+    return m
+
+
+def gen_modes(params: FieldParams):
+    """Draw the N modes (host FP64): dict with kappa (N, d), rho, psi, a (N, d), amp."""
+    n, d = int(params.n_modes), int(params.dim)
+    arrays = {"kappa": np.empty((n, d)), "rho": np.empty(n), "psi": np.empty(n),
+              "a": np.empty((n, d)), "amp": np.empty(n)}
+    m = _modes_struct(n, d, arrays)
+    check(lib().grf_gen_modes(ctypes.byref(params.to_c()), ctypes.byref(m)))
+    return arrays
+
+
+class ModeTable:
+    """Device mode table: packed on the host, copied to the device."""
+
+    def __init__(self, amp, psi, a, device=None, stream=None):
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(len(amp), -1))
+        self.n_modes, self.dim = a.shape
+        self.nbytes = int(lib().grf_table_bytes(self.n_modes))
+        if self.nbytes == 0:
+            raise ValueError("n_modes out of range")
+        arrays = {"kappa": a, "rho": amp, "psi": psi, "a": a, "amp": amp}
+        m = _modes_struct(self.n_modes, self.dim, arrays)
+        self.host = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
+        check(lib().grf_pack_table(ctypes.byref(m), _ptr(self.host), self.nbytes))
+        device = device or torch.device("cuda", torch.cuda.current_device())
+        self.dev = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self._uploaded = torch.cuda.Event()
+        self.upload(stream)
+
+    def upload(self, stream=None):
+        check(lib().grf_upload_table(_ptr(self.host), _ptr(self.dev), self.nbytes, _stream_handle(stream)))
+        self._uploaded.record(stream if stream is not None else torch.cuda.current_stream())
+
+    def update(self, amp, psi, a, stream=None):
+        """Repack new modes (same N and dim) into this table and upload them.
+        Waits for the previous upload from the pinned staging buffer first."""
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(len(amp), -1))
+        if a.shape != (self.n_modes, self.dim):
+            raise ValueError("update needs the same number of modes and dimension")
+        self._uploaded.synchronize()
+        arrays = {"kappa": a, "rho": amp, "psi": psi, "a": a, "amp": amp}
+        m = _modes_struct(self.n_modes, self.dim, arrays)
+        check(lib().grf_pack_table(ctypes.byref(m), _ptr(self.host), self.nbytes))
+        self.upload(stream)
+
+    @classmethod
+    def from_modes(cls, modes, **kw):
+        return cls(modes["amp"], modes["psi"], modes["a"], **kw)
+
+    @property
+    def ptr(self):
+        return _ptr(self.dev)
+
+
+class CellPlan:
+    """Spatially sorted copy of one or more sets of cell centres (segments).
+
+    x, y, z: CUDA float32 tensors (SoA); segments: cell counts per segment
+    (default: one segment).  The plan is built on the device once and reused
+    for every realisation on those cells.
+    """
+
+    def __init__(self, x, y=None, z=None, dim=None, segments=None, stream=None):
+        x = _require_cuda(x, torch.float32, "x")
+        y = _require_cuda(y, torch.float32, "y")
+        z = _require_cuda(z, torch.float32, "z")
+        self.dim = dim or (1 + (y is not None) + (z is not None))
+        self.n_cells = x.numel()
+        sizes = [self.n_cells] if segments is None else [int(s) for s in segments]
+        if sum(sizes) != self.n_cells:
+            raise ValueError("segment sizes do not add up to the number of cells")
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.n_segments = len(sizes)
+        self.nbytes = int(lib().grf_plan_bytes(self.n_cells, self.n_segments))
+        self.buf = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=x.device)
+        self._inputs = (x, y, z)  # kept alive until the planning kernels have run
+        check(lib().grf_plan_cells(self.dim, self.n_segments,
+                                   self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   _ptr(x), _ptr(y), _ptr(z), _ptr(self.buf), self.nbytes,
+                                   _stream_handle(stream)))
+
+    def segment_size(self, s):
+        return int(self.offsets[s + 1] - self.offsets[s])
+
+    def status(self, stream=None):
+        v = ctypes.c_int32(0)
+        check(lib().grf_read_status(_ptr(self.buf), ctypes.byref(v), _stream_handle(stream)))
+        return v.value
+
+    @property
+    def ptr(self):
+        return _ptr(self.buf)
+
+
+@dataclass
+class MapSpec:
+    """Which outputs to write (Sec. 3.1, Sec. 4.1, Appendix B)."""
+    y: bool = True
+    lognormal: bool = False
+    k_ref: float = 1.0
+    thresholds: Sequence[float] = ()
+    facies: bool = False
+    values: Optional[Sequence[float]] = None
+    porosity: Optional[Sequence[float]] = None  # (phi0, phi1, phi_min, phi_max)
+
+    def to_c(self):
+        m = _abi.grf_map()
+        bits = 0
+        if self.y:
+            bits |= _abi.GRF_MAP_Y
+        if self.lognormal:
+            bits |= _abi.GRF_MAP_LOGNORMAL
+        if self.facies:
+            bits |= _abi.GRF_MAP_FACIES
+        if self.values is not None:
+            bits |= _abi.GRF_MAP_VALUES
+        if self.porosity is not None:
+            bits |= _abi.GRF_MAP_POROSITY
+        m.bits = bits
+        thr = list(self.thresholds)
+        m.n_thresholds = len(thr)
+        if len(thr) > _abi.GRF_MAX_THRESHOLDS:
+            raise ValueError("at most %d thresholds" % _abi.GRF_MAX_THRESHOLDS)
+        for i, t in enumerate(thr):
+            m.thresholds[i] = float(t)
+        if self.values is not None:
+            if len(self.values) != len(thr) + 1:
+                raise ValueError("values needs one entry per facies (len(thresholds) + 1)")
+            for i, v in enumerate(self.values):
+                m.values[i] = float(v)
+        m.k_ref = float(self.k_ref)
+        if self.porosity is not None:
+            m.phi0, m.phi1, m.phi_min, m.phi_max = [float(v) for v in self.porosity]
+        return m
+
+    def allocate(self, n, device):
+        out = {}
+        if self.y:
+            out["Y"] = torch.empty(n, dtype=torch.float32, device=device)
+        if self.lognormal:
+            out["K"] = torch.empty(n, dtype=torch.float32, device=device)
+        if self.facies:
+            out["facies"] = torch.empty(n, dtype=torch.uint8, device=device)
+        if self.values is not None or self.porosity is not None:
+            out["prop"] = torch.empty(n, dtype=torch.float32, device=device)
+        return out
+
+
+def _outputs_struct(out):
+    o = _abi.grf_outputs()
+    o.Y = out["Y"].data_ptr() if "Y" in out else None
+    o.K = out["K"].data_ptr() if "K" in out else None
+    o.facies = out["facies"].data_ptr() if "facies" in out else None
+    o.prop = out["prop"].data_ptr() if "prop" in out else None
+    return o
+
+
+def synth(table: ModeTable, params: FieldParams, plan: CellPlan, segment=0, maps=None, out=None,
+          stream=None):
+    """Field and fused maps at every cell of `segment` (original cell order)."""
+    maps = maps or MapSpec()
+    n = plan.segment_size(segment)
+    if out is None:
+        out = maps.allocate(n, plan.buf.device)
+    check(lib().grf_synth_field(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
+                                ctypes.byref(maps.to_c()), ctypes.byref(_outputs_struct(out)),
+                                _stream_handle(stream)))
+    return out
+
+
+def map_property(Y, maps: MapSpec, mean, sigma, out=None, stream=None):
+    """Standalone property map of an existing field Y (CUDA float32)."""
+    Y = _require_cuda(Y, torch.float32, "Y")
+    if out is None:
+        m2 = MapSpec(**{**maps.__dict__, "y": False})
+        out = m2.allocate(Y.numel(), Y.device)
+    m = maps.to_c()
+    m.bits &= ~_abi.GRF_MAP_Y
+    check(lib().grf_map_property(ctypes.byref(m), float(mean), float(sigma), Y.numel(), _ptr(Y),
+                                 ctypes.byref(_outputs_struct(out)), _stream_handle(stream)))
+    return out
+
+
+class Workspace:
+    """Grow-only device scratch buffer (256-byte aligned torch allocation)."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes, device):
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_ws_bwd = Workspace()
+_ws_loss = Workspace()
+
+
+def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=0, stream=None,
+             workspace=None):
+    """Gradients (device FP64) of a loss with dL/dY = gY (CUDA float32,
+    original cell order): dA, dpsi, da (N, d) in the original mode order,
+    dmu, dsigma, dell (d)."""
+    gY = _require_cuda(gY, torch.float32, "gY")
+    dev = gY.device
+    n, d = table.n_modes, table.dim
+    g = {"dA": torch.empty(n, dtype=torch.float64, device=dev),
+         "dpsi": torch.empty(n, dtype=torch.float64, device=dev),
+         "da": torch.empty((n, d), dtype=torch.float64, device=dev),
+         "dmu": torch.empty(1, dtype=torch.float64, device=dev),
+         "dsigma": torch.empty(1, dtype=torch.float64, device=dev),
+         "dell": torch.empty(d, dtype=torch.float64, device=dev)}
+    gs = _abi.grf_grads()
+    for k in g:
+        setattr(gs, k, g[k].data_ptr())
+    nbytes = int(lib().grf_backward_workspace_bytes(plan.segment_size(segment), n, d))
+    ws = (workspace or _ws_bwd).get(nbytes, dev)
+    check(lib().grf_synth_backward(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
+                                   _ptr(gY), ctypes.byref(gs), _ptr(ws), ws.numel(),
+                                   _stream_handle(stream)))
+    return g
+
+
+def mismatch_grad(K, K_target, stream=None, workspace=None):
+    """L = mean (K - T)^2 and gY = dL/dY for K = exp(Y): returns (loss (1,) FP64, gY)."""
+    K = _require_cuda(K, torch.float32, "K")
+    T = _require_cuda(K_target, torch.float32, "K_target")
+    n = K.numel()
+    gY = torch.empty_like(K)
+    loss = torch.empty(1, dtype=torch.float64, device=K.device)
+    ws = (workspace or _ws_loss).get(lib().grf_mismatch_workspace_bytes(n), K.device)
+    check(lib().grf_mismatch_grad(n, _ptr(K), _ptr(T), _ptr(gY), _ptr(loss), _ptr(ws), ws.numel(),
+                                  _stream_handle(stream)))
+    return loss, gY
+
+
+# ---------------------------------------------------------------------------
+# Autograd
+# ---------------------------------------------------------------------------
+class _SpectralFieldFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mu, sigma, ell, rho, psi, kappa, plan, segment, family):
+        d = kappa.shape[1]
+        s = float(sigma.detach().cpu())
+        ellv = ell.detach().cpu().double().numpy()
+        amp = s * rho.detach().cpu().double().numpy()
+        a = kappa.detach().cpu().double().numpy() / (2.0 * math.pi * ellv[None, :d])
+        table = ModeTable(amp, psi.detach().cpu().double().numpy(), a)
+        params = FieldParams(family=family, sigma2=s * s, mean=float(mu.detach().cpu()),
+                             ell=tuple(ellv[:d]), dim=d, n_modes=len(amp))
+        y = synth(table, params, plan, segment, MapSpec(y=True))["Y"]
+        ctx.table, ctx.params, ctx.plan, ctx.segment = table, params, plan, segment
+        ctx.save_for_backward(sigma, ell, rho, kappa)
+        return y
+
+    @staticmethod
+    def backward(ctx, gY):
+        sigma, ell, rho, kappa = ctx.saved_tensors
+        g = backward(ctx.table, ctx.params, ctx.plan, gY.contiguous().float(), ctx.segment)
+        d = kappa.shape[1]
+        dev_p = sigma.device
+        s = float(sigma.detach().cpu())
+        ellv = ell.detach().to(torch.float64)
+        dmu = g["dmu"].reshape(()).to(dev_p)
+        dsigma = g["dsigma"].reshape(()).to(dev_p)
+        dell = torch.zeros_like(ell, dtype=torch.float64)
+        dell[:d] = g["dell"].to(ell.device)
+        drho = (s * g["dA"]).to(rho.device)
+        dpsi = g["dpsi"].to(rho.device)
+        dkappa = (g["da"] / (2.0 * math.pi * ellv[:d].to(g["da"].device))).to(kappa.device)
+        return (dmu.to(torch.float64), dsigma.to(torch.float64), dell.to(ell.dtype),
+                drho.to(rho.dtype), dpsi.to(rho.dtype), dkappa.to(kappa.dtype), None, None, None)
+
+
+def spectral_field(mu, sigma, ell, rho, psi, kappa, plan: CellPlan, segment=0, family="gaussian"):
+    """Differentiable Y(x) = mu + sum_j sigma rho_j cos(2 pi (kappa_j/(2 pi l) . x + psi_j)).
+
+    Gradients flow to mu, sigma, ell (correlation lengths) and the per-mode
+    rho, psi, kappa through the CUDA adjoint kernel."""
+    return _SpectralFieldFn.apply(mu, sigma, ell, rho, psi, kappa, plan, segment, family)
+
+
+class _ModeSumFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mu, amp, psi, a, plan, segment):
+        d = a.shape[1]
+        table = ModeTable(amp.detach().cpu().double().numpy(), psi.detach().cpu().double().numpy(),
+                          a.detach().cpu().double().numpy())
+        params = FieldParams(sigma2=1.0, mean=float(mu.detach().cpu()), ell=(1.0,) * d, dim=d,
+                             n_modes=amp.numel())
+        y = synth(table, params, plan, segment, MapSpec(y=True))["Y"]
+        ctx.table, ctx.params, ctx.plan, ctx.segment = table, params, plan, segment
+        ctx.meta = [(t.device, t.dtype) for t in (mu, amp, psi, a)]
+        return y
+
+    @staticmethod
+    def backward(ctx, gY):
+        g = backward(ctx.table, ctx.params, ctx.plan, gY.contiguous().float(), ctx.segment)
+        grads = (g["dmu"].reshape(()), g["dA"], g["dpsi"], g["da"])
+        out = tuple(v.to(device=dv, dtype=dt) for v, (dv, dt) in zip(grads, ctx.meta))
+        return out + (None, None)
+
+
+def mode_sum(mu, amp, psi, a, plan: CellPlan, segment=0):
+    """Differentiable Y = mu + sum_j A_j cos(2 pi (a_j . x + psi_j)) with
+    gradients to mu and the per-mode amplitudes, phases and frequencies."""
+    return _ModeSumFn.apply(mu, amp, psi, a, plan, segment)
+
+
+# ---------------------------------------------------------------------------
+# Convenience: one realisation on a set of cells
+# ---------------------------------------------------------------------------
+class GaussianField:
+    """One realisation: draws its modes, builds its table, synthesises on cells."""
+
+    def __init__(self, params: FieldParams):
+        self.params = params
+        self.modes = gen_modes(params)
+        self.table = ModeTable.from_modes(self.modes)
+
+    def synth(self, plan: CellPlan, maps=None, segment=0, out=None, stream=None):
+        return synth(self.table, self.params, plan, segment, maps, out, stream)
+
+
+# ---------------------------------------------------------------------------
+# Batched ensembles
+# ---------------------------------------------------------------------------
+class Batch:
+    """Many realisations on the segments of one plan, one persistent launch.
+
+    items: list of (table, params, segment, MapSpec, out dict)."""
+
+    def __init__(self, plan: CellPlan, items, tile_cells=0, stream=None):
+        self.plan = plan
+        self.items = items
+        n = len(items)
+        arr = (_abi.grf_batch_item * n)()
+        for i, (table, params, segment, maps, out) in enumerate(items):
+            it = arr[i]
+            it.table = table.dev.data_ptr()
+            it.n_modes = table.n_modes
+            it.dim = table.dim
+            it.segment = int(segment)
+            it.mean = float(params.mean)
+            it.sigma = float(params.sigma)
+            it.map = maps.to_c()
+            it.out = _outputs_struct(out)
+        self._arr = arr
+        self.nbytes = int(lib().grf_batch_workspace_bytes(n, plan.n_cells))
+        dev = plan.buf.device
+        self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        self.host = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
+        check(lib().grf_batch_prepare(n, arr, plan.ptr, int(tile_cells), _ptr(self.ws), self.nbytes,
+                                      _ptr(self.host), _stream_handle(stream)))
+        self.graph = None
+
+    def launch(self, stream=None):
+        check(lib().grf_batch_launch(_ptr(self.ws), _stream_handle(stream)))
+
+    def capture(self):
+        """Capture one launch into a CUDA graph (replay with .replay())."""
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.launch(stream=s)
+        torch.cuda.synchronize()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+
+def device_info():
+    sms = ctypes.c_int32(0)
+    khz = ctypes.c_int32(0)
+    check(lib().grf_device_info(ctypes.byref(sms), ctypes.byref(khz)))
+    return sms.value, khz.value
+
+
+def launch_count():
+    return int(lib().grf_launch_count())
+
+
+def mufu_probe(blocks, iters, stream=None):
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    check(lib().grf_mufu_probe(int(blocks), int(iters), _ptr(sink), _stream_handle(stream)))
+    return sink

@@ -1,0 +1,179 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol declared in include/grf.h, draws the same modes as the oracle, packs
+the device table as documented and rejects bad arguments."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import modes as omodes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_10961_gb300 import _abi
+    _abi.lib()
+    return _abi
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "grf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(grf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(abi):
+    names = header_functions()
+    assert len(names) >= 20
+    L = abi.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(abi.exported_symbols()) == names
+
+
+def test_version_and_launch_count(abi):
+    assert abi.lib().grf_version().decode().startswith("grf-gb300")
+    assert abi.lib().grf_launch_count() >= 0
+
+
+@pytest.mark.parametrize("family,nu,dim", [(0, 0.0, 1), (0, 0.0, 3), (1, 0.0, 2), (1, 0.0, 3),
+                                           (2, 1.5, 3), (2, 1.3, 2), (2, 0.7, 3), (2, 2.25, 1)])
+def test_gen_modes_matches_oracle(abi, family, nu, dim):
+    from paper_2212_10961_gb300 import field as F
+    ell = (0.2, 0.1, 0.05)
+    p = F.FieldParams(family=family, sigma2=2.5, ell=ell[:dim], dim=dim, n_modes=777, seed=123456789012,
+                      nu=nu, stream=3)
+    got = F.gen_modes(p)
+    want = omodes.gen_modes(family, 2.5, ell, dim, 777, 123456789012, nu=nu, stream=3)
+    for k in ("kappa", "rho", "psi", "a", "amp"):
+        np.testing.assert_allclose(got[k], want[k], rtol=4e-15, atol=1e-300, err_msg=k)
+
+
+def _params(abi, **kw):
+    p = abi.grf_params()
+    p.family, p.dim, p.nu, p.sigma2, p.mean = 0, 2, 1.5, 1.0, 0.0
+    p.ell[0] = p.ell[1] = p.ell[2] = 0.1
+    p.n_modes, p.seed, p.stream, p.reserved = 10, 1, 0, 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _modes_for(abi, n, dim):
+    arr = {k: np.zeros(n * (dim if k in ("kappa", "a") else 1)) for k in ("kappa", "rho", "psi", "a", "amp")}
+    m = abi.grf_modes()
+    m.n, m.dim = n, dim
+    for k in arr:
+        setattr(m, k, arr[k].ctypes.data_as(abi.c_dp))
+    return m, arr
+
+
+@pytest.mark.parametrize("bad", [dict(family=5), dict(dim=0), dict(dim=4), dict(sigma2=0.0),
+                                 dict(sigma2=float("nan")), dict(n_modes=0), dict(reserved=1),
+                                 dict(family=2, nu=-1.0)])
+def test_gen_modes_rejects_bad_params(abi, bad):
+    p = _params(abi, **bad)
+    m, _ = _modes_for(abi, 10, 2)
+    rc = abi.lib().grf_gen_modes(ctypes.byref(p), ctypes.byref(m))
+    assert rc == abi.GRF_EINVAL
+    assert len(abi.lib().grf_last_error()) > 0
+
+
+def test_gen_modes_rejects_mismatched_output(abi):
+    p = _params(abi)
+    m, _ = _modes_for(abi, 9, 2)
+    assert abi.lib().grf_gen_modes(ctypes.byref(p), ctypes.byref(m)) == abi.GRF_EINVAL
+    p2 = _params(abi, ell=(ctypes.c_double * 3)(0.1, -1.0, 0.1))
+    m2, _ = _modes_for(abi, 10, 2)
+    assert abi.lib().grf_gen_modes(ctypes.byref(p2), ctypes.byref(m2)) == abi.GRF_EINVAL
+
+
+def _parse_table(buf, n, dim):
+    b = np.frombuffer(buf, dtype=np.uint8)
+    hdr = np.frombuffer(b[:256].tobytes(), dtype=np.int32)
+    magic, n_modes, n_pad, d = hdr[0], hdr[1], hdr[2], hdr[3]
+    off = np.frombuffer(b[32:72].tobytes(), dtype=np.int64)
+    off_hot, off_cold, off_order, off_kpref, total = off
+    hot = np.frombuffer(b[off_hot:off_hot + n_pad * 16].tobytes(), dtype=np.float32).reshape(n_pad, 4)
+    cold = np.frombuffer(b[off_cold:off_cold + n_pad * 32].tobytes(), dtype=np.float32).reshape(n_pad, 8)
+    order = np.frombuffer(b[off_order:off_order + n_pad * 4].tobytes(), dtype=np.int32)
+    kpref = np.frombuffer(b[off_kpref:off_kpref + 160 * 4].tobytes(), dtype=np.int32)
+    return dict(magic=magic, n=n_modes, n_pad=n_pad, dim=d, hot=hot, cold=cold, order=order, kpref=kpref,
+                total=total)
+
+
+@pytest.mark.parametrize("n,dim", [(1, 1), (130, 2), (1000, 3)])
+def test_pack_table_layout(abi, n, dim):
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(family="exponential", sigma2=4.0, ell=(0.2, 0.2, 0.05)[:dim], dim=dim, n_modes=n, seed=5)
+    md = F.gen_modes(p)
+    nbytes = abi.lib().grf_table_bytes(n)
+    buf = (ctypes.c_uint8 * nbytes)()
+    m = F._modes_struct(n, dim, md)
+    assert abi.lib().grf_pack_table(ctypes.byref(m), buf, nbytes) == 0
+    t = _parse_table(bytes(buf), n, dim)
+    assert t["magic"] == 0x54465247 and t["n"] == n and t["dim"] == dim
+    assert t["n_pad"] % 128 == 0 and t["n_pad"] >= n and t["total"] == nbytes
+    order = t["order"]
+    assert sorted(order[:n].tolist()) == list(range(n)) and np.all(order[n:] == -1)
+    a = md["a"][order[:n]]
+    h = np.sum(np.abs(a), axis=1)
+    assert np.all(np.diff(h) <= 0)  # sorted by |a|_1, descending
+    np.testing.assert_array_equal(t["hot"][:n, :dim], (2 * math.pi * a).astype(np.float32))
+    np.testing.assert_array_equal(t["hot"][:n, 3], md["amp"][order[:n]].astype(np.float32))
+    assert np.all(t["hot"][n:] == 0) and np.all(t["cold"][n:] == 0)
+    c = t["cold"][:n].astype(np.float64)
+    rec = np.stack([c[:, 0] + c[:, 1], c[:, 2] + c[:, 3], c[:, 4] + c[:, 5]], axis=1)[:, :dim]
+    np.testing.assert_allclose(rec, a, rtol=2.0 ** -46, atol=0)
+    np.testing.assert_allclose(c[:, 6] + c[:, 7], md["psi"][order[:n]], rtol=0, atol=1e-15)
+    for b in range(160):
+        Eb = 2.0 ** ((b - 100) / 4.0)
+        assert t["kpref"][b] == int(np.sum(h * Eb > 0.5))
+
+
+def test_pack_and_sizes_reject(abi):
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(n_modes=10, dim=2, ell=(0.1, 0.1))
+    md = F.gen_modes(p)
+    m = F._modes_struct(10, 2, md)
+    small = (ctypes.c_uint8 * 64)()
+    assert abi.lib().grf_pack_table(ctypes.byref(m), small, 64) == abi.GRF_EWORKSPACE
+    md["a"][3, 1] = float("inf")
+    nb = abi.lib().grf_table_bytes(10)
+    buf = (ctypes.c_uint8 * nb)()
+    assert abi.lib().grf_pack_table(ctypes.byref(m), buf, nb) == abi.GRF_EINVAL
+    assert abi.lib().grf_table_bytes(0) == 0
+    assert abi.lib().grf_plan_bytes(100, 0) == 0
+    assert abi.lib().grf_plan_bytes(1000, 1) > 1000 * 16
+    assert abi.lib().grf_backward_workspace_bytes(1000, 0, 3) == 0
+    assert abi.lib().grf_batch_workspace_bytes(0, 10) == 0
+
+
+def test_null_and_unknown_handles_rejected(abi):
+    L = abi.lib()
+    p = _params(abi)
+    mp = abi.grf_map()
+    mp.bits = abi.GRF_MAP_Y
+    out = abi.grf_outputs()
+    out.Y = 4096
+    fake_plan = ctypes.c_void_p(1 << 20)
+    # unknown plan: rejected on the host before any device work
+    assert L.grf_synth_field(ctypes.c_void_p(1 << 16), ctypes.byref(p), fake_plan, 0, ctypes.byref(mp),
+                             ctypes.byref(out), None) == abi.GRF_EINVAL
+    mp.bits = abi.GRF_MAP_FACIES
+    mp.n_thresholds = 2
+    mp.thresholds[0], mp.thresholds[1] = 0.5, 0.1  # not ascending
+    out.facies = 4096
+    assert L.grf_map_property(ctypes.byref(mp), 0.0, 1.0, 10, ctypes.c_void_p(4096), ctypes.byref(out),
+                              None) == abi.GRF_EINVAL
+    assert L.grf_batch_launch(ctypes.c_void_p(1 << 12), None) == abi.GRF_EINVAL
+    offs = (ctypes.c_int64 * 2)(5, 10)
+    assert L.grf_plan_cells(3, 1, offs, None, None, None, ctypes.c_void_p(1 << 12), 1 << 20,
+                            None) == abi.GRF_EINVAL

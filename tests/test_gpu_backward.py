@@ -1,0 +1,163 @@
+"""GPU parity of the adjoint (S5) against the FP64 oracle gradient, the
+chain-rule identities at full size, the loss kernel, and the autograd
+wrappers."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import GRAD_TOL, gpu_env, oracle_field, oracle_modes, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = gpu_env()
+    from paper_2212_10961_gb300 import field as F
+    from paper_2212_10961_gb300 import workloads as W
+    return torch, F, W
+
+
+def _oracle_grads(om, cells, g, sigma, ell):
+    from oracle import field as of
+    from oracle import native
+    c = np.stack(cells, axis=-1)
+    s_cos, s_sin, s_sinx = native.mode_sums(om["a"], om["psi"], c, g.astype(np.float64))
+    return of.grads_from_sums(s_cos, s_sin, s_sinx, om["amp"], om["a"], sigma, ell, g.astype(np.float64))
+
+
+def _check(got, ref, name):
+    got = np.asarray(got, dtype=np.float64).reshape(np.shape(ref))
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got - ref))
+    assert err <= GRAD_TOL * scale, "%s: max err %.3e vs scale %.3e" % (name, err, scale)
+    return err / scale
+
+
+@pytest.mark.parametrize("dim,family", [(3, "gaussian"), (2, "exponential"), (1, "matern")])
+def test_backward_matches_oracle(env, dim, family):
+    torch, F, W = env
+    shape = {3: (24, 20, 18), 2: (90, 70), 1: (4000,)}[dim]
+    cells = W.grid_centres(shape)
+    ell = (0.1, 0.15, 0.2)[:dim]
+    p = F.FieldParams(family=family, sigma2=1.7, mean=0.1, ell=ell, dim=dim, n_modes=600, seed=7)
+    gf = F.GaussianField(p)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    g = np.random.default_rng(dim).standard_normal(len(cells[0])).astype(np.float32)
+    gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    om = oracle_modes(family, 1.7, ell, dim, 600, 7)
+    ref = _oracle_grads(om, cells, g, math.sqrt(1.7), ell)
+    for k in ("dA", "dpsi", "da"):
+        _check(gr[k].cpu().numpy(), ref[k], k)
+    assert gr["dmu"].item() == pytest.approx(ref["dmu"], rel=1e-9, abs=1e-9)
+    assert gr["dsigma"].item() == pytest.approx(ref["dsigma"], rel=GRAD_TOL, abs=GRAD_TOL * np.max(np.abs(ref["dA"])))
+    np.testing.assert_allclose(gr["dell"].cpu().numpy(), ref["dell"], rtol=GRAD_TOL,
+                               atol=GRAD_TOL * np.max(np.abs(ref["dell"])))
+
+
+def test_diff128_loss_and_gradients(env):
+    torch, F, W = env
+    w = W.WORKLOADS["diff128"]
+    # reduced grid for a full oracle comparison, same modes and loss
+    cells = W.grid_centres((40, 40, 40))
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=1)
+    pt = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=2)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    K = F.GaussianField(p).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    loss, gY = F.mismatch_grad(K, T)
+    gf = F.GaussianField(p)
+    gr = F.backward(gf.table, p, plan, gY)
+    torch.cuda.synchronize()
+    from oracle import field as of
+    om = oracle_modes("gaussian", 1.0, w["ell"], 3, w["n_modes"], 1)
+    omt = oracle_modes("gaussian", 1.0, w["ell"], 3, w["n_modes"], 2)
+    y_or = oracle_field(om, 0.0, cells)
+    t_or = np.exp(oracle_field(omt, 0.0, cells))
+    l_or, g_or = of.mismatch_loss(np.exp(y_or), t_or)
+    assert loss.item() == pytest.approx(l_or, rel=1e-4)
+    g_gpu = gY.cpu().numpy()
+    assert np.max(np.abs(g_gpu - g_or)) <= 1e-4 * np.max(np.abs(g_or))
+    # oracle gradient from the oracle's own dL/dY (independent of the GPU path)
+    ref = _oracle_grads(om, cells, g_or, 1.0, w["ell"])
+    errs = {k: _check(gr[k].cpu().numpy(), ref[k], k) for k in ("dA", "dpsi", "da")}
+    assert abs(gr["dmu"].item() - ref["dmu"]) <= 1e-4 * abs(ref["dmu"]) + 1e-12
+    assert abs(gr["dsigma"].item() - ref["dsigma"]) <= GRAD_TOL * np.max(np.abs(ref["dA"])) * 10
+    np.testing.assert_allclose(gr["dell"].cpu().numpy(), ref["dell"], rtol=1e-3)
+    print("diff 40^3 gradient errors (relative to max):", errs)
+
+
+def test_diff128_full_size_identities(env):
+    torch, F, W = env
+    w = W.WORKLOADS["diff128"]
+    cells = W.workload_cells("diff128")
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=1)
+    pt = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=2)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    gf = F.GaussianField(p)
+    K = gf.synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    loss, gY = F.mismatch_grad(K, T)
+    gr = F.backward(gf.table, p, plan, gY)
+    torch.cuda.synchronize()
+    amp = gf.modes["amp"]
+    a = gf.modes["a"]
+    dA = gr["dA"].cpu().numpy()
+    da = gr["da"].cpu().numpy()
+    # sigma dL/dsigma = sum_j A_j dL/dA_j ; l_c dL/dl_c = -sum_j a_jc dL/da_jc ; dL/dmu = sum g
+    assert gr["dsigma"].item() == pytest.approx(np.sum(amp * dA), rel=1e-5)
+    np.testing.assert_allclose(np.asarray(w["ell"]) * gr["dell"].cpu().numpy(), -np.sum(a * da, axis=0),
+                               rtol=1e-5)
+    assert gr["dmu"].item() == pytest.approx(float(np.sum(gY.cpu().numpy().astype(np.float64))), rel=1e-6)
+    # per-mode sums on a few modes against the oracle over all 2M cells
+    from oracle import native
+    om = oracle_modes("gaussian", 1.0, w["ell"], 3, w["n_modes"], 1)
+    sel = np.array([0, 1, 2, 100, 1000, 2047])
+    c = np.stack(cells, axis=-1)
+    s_cos, s_sin, s_sinx = native.mode_sums(om["a"][sel], om["psi"][sel], c, gY.cpu().numpy().astype(np.float64))
+    scale = np.max(np.abs(dA))
+    assert np.max(np.abs(dA[sel] - s_cos)) <= GRAD_TOL * scale
+    dpsi_ref = -2 * np.pi * om["amp"][sel] * s_sin
+    assert np.max(np.abs(gr["dpsi"].cpu().numpy()[sel] - dpsi_ref)) <= GRAD_TOL * np.max(np.abs(gr["dpsi"].cpu().numpy()))
+    # deterministic
+    gr2 = F.backward(gf.table, p, plan, gY)
+    torch.cuda.synchronize()
+    assert np.array_equal(gr2["dA"].cpu().numpy(), dA)
+
+
+def test_autograd_wrappers(env):
+    torch, F, W = env
+    cells = W.grid_centres((30, 30, 12))
+    plan = F.CellPlan(*to_dev(torch, cells))
+    p = F.FieldParams(family="gaussian", sigma2=1.3, ell=(0.2, 0.15, 0.1), dim=3, n_modes=256, seed=5)
+    m = F.gen_modes(p)
+    dt = torch.float64
+    mu = torch.tensor(0.2, dtype=dt, requires_grad=True)
+    sigma = torch.tensor(math.sqrt(1.3), dtype=dt, requires_grad=True)
+    ell = torch.tensor([0.2, 0.15, 0.1], dtype=dt, requires_grad=True)
+    rho = torch.tensor(m["rho"], requires_grad=True)
+    psi = torch.tensor(m["psi"], requires_grad=True)
+    kappa = torch.tensor(m["kappa"], requires_grad=True)
+    y = F.spectral_field(mu, sigma, ell, rho, psi, kappa, plan)
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(y.numel()).astype(np.float32)).cuda()
+    (y * g).sum().backward()
+    om = oracle_modes("gaussian", 1.3, (0.2, 0.15, 0.1), 3, 256, 5)
+    ref = _oracle_grads(om, cells, g.cpu().numpy(), math.sqrt(1.3), (0.2, 0.15, 0.1))
+    assert mu.grad.item() == pytest.approx(ref["dmu"], rel=1e-6)
+    assert sigma.grad.item() == pytest.approx(ref["dsigma"], rel=1e-3, abs=1e-3 * np.max(np.abs(ref["dA"])))
+    np.testing.assert_allclose(ell.grad.numpy(), ref["dell"], rtol=1e-3, atol=1e-4 * np.max(np.abs(ref["dell"])))
+    _check(rho.grad.numpy() / math.sqrt(1.3), ref["dA"], "drho")
+    _check(psi.grad.numpy(), ref["dpsi"], "dpsi")
+    _check(kappa.grad.numpy() * 2 * np.pi * np.array([0.2, 0.15, 0.1]), ref["da"], "dkappa")
+    # direct mode-sum form
+    amp = torch.tensor(m["amp"], requires_grad=True)
+    a = torch.tensor(m["a"], requires_grad=True)
+    psi2 = torch.tensor(m["psi"], requires_grad=True)
+    mu2 = torch.tensor(0.2, dtype=dt, requires_grad=True)
+    y2 = F.mode_sum(mu2, amp, psi2, a, plan)
+    assert torch.allclose(y2, y, atol=1e-6)
+    (y2 * g).sum().backward()
+    _check(amp.grad.cpu().numpy(), ref["dA"], "dA")
+    _check(a.grad.cpu().numpy(), ref["da"], "da")

@@ -1,0 +1,116 @@
+"""GPU checks of the batched ensemble path (S6): one persistent launch over
+realisations of uneven size, dimension, mode count and covariance, against
+the single-realisation path and the FP64 oracle; CUDA-graph replay."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import check_forward, gpu_env, oracle_field, oracle_modes, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = gpu_env()
+    from paper_2212_10961_gb300 import field as F
+    from paper_2212_10961_gb300 import workloads as W
+    return torch, F, W
+
+
+def _ensemble(env, recipe, tile_cells=0):
+    torch, F, W = env
+    segs = []
+    xs, ys, zs = [], [], []
+    for r in recipe:
+        c = W.grid_centres(r["shape"])
+        if len(c) == 2:
+            c = c + [np.zeros_like(c[0])]
+        xs.append(c[0])
+        ys.append(c[1])
+        zs.append(c[2])
+        segs.append(len(c[0]))
+    cells = [np.concatenate(v) for v in (xs, ys, zs)]
+    plan = F.CellPlan(*to_dev(torch, cells), dim=3, segments=segs)
+    items = []
+    fields = []
+    for s, r in enumerate(recipe):
+        p = F.FieldParams(family=r["family"], sigma2=r["sigma2"], mean=r["mean"], ell=r["ell"], dim=r["dim"],
+                          n_modes=r["n_modes"], seed=r["seed"])
+        gf = F.GaussianField(p)
+        maps = F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True)
+        out = maps.allocate(segs[s], plan.buf.device)
+        items.append((gf.table, p, s, maps, out))
+        fields.append(gf)
+    batch = F.Batch(plan, items, tile_cells=tile_cells)
+    return plan, batch, items, fields
+
+
+SMALL = [dict(shape=(40, 33), dim=2, n_modes=300, family="gaussian"),
+         dict(shape=(16, 12, 9), dim=3, n_modes=1024, family="exponential"),
+         dict(shape=(7, 5), dim=2, n_modes=129, family="exponential"),
+         dict(shape=(100, 64), dim=2, n_modes=640, family="gaussian"),
+         dict(shape=(3, 3, 3), dim=3, n_modes=1, family="gaussian")]
+
+
+def _recipe():
+    out = []
+    for i, r in enumerate(SMALL):
+        out.append(dict(r, ell=(0.1,) * r["dim"], sigma2=1.0 + 0.5 * i, mean=0.1 * i, seed=77 + i))
+    return out
+
+
+@pytest.mark.parametrize("tile_cells", [0, 512, 2048])
+def test_batched_matches_single_and_oracle(env, tile_cells):
+    torch, F, W = env
+    recipe = _recipe()
+    plan, batch, items, fields = _ensemble(env, recipe, tile_cells)
+    batch.launch()
+    torch.cuda.synchronize()
+    for s, (table, p, seg, maps, out) in enumerate(items):
+        single = F.synth(table, p, plan, seg, maps)
+        torch.cuda.synchronize()
+        yb = out["Y"].cpu().numpy()
+        ys = single["Y"].cpu().numpy()
+        assert np.max(np.abs(yb - ys)) <= 1e-6 * p.sigma
+        r = recipe[s]
+        om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
+        cells = W.grid_centres(r["shape"])
+        check_forward(yb, oracle_field(om, r["mean"], cells), p.sigma, "batch item %d" % s)
+        assert np.array_equal(out["facies"].cpu().numpy(), single["facies"].cpu().numpy()) or \
+            np.mean(out["facies"].cpu().numpy() != single["facies"].cpu().numpy()) < 1e-3
+
+
+def test_graph_replay(env):
+    torch, F, W = env
+    recipe = _recipe()
+    plan, batch, items, fields = _ensemble(env, recipe)
+    batch.launch()
+    torch.cuda.synchronize()
+    ref = [it[4]["Y"].clone() for it in items]
+    for it in items:
+        it[4]["Y"].zero_()
+    batch.capture()
+    batch.replay()
+    batch.replay()
+    torch.cuda.synchronize()
+    for r, it in zip(ref, items):
+        assert torch.equal(r, it[4]["Y"])
+
+
+def test_ensemble256_sampled(env):
+    torch, F, W = env
+    recipe = W.ensemble_recipe()[:48]
+    plan, batch, items, fields = _ensemble(env, recipe)
+    batch.capture()
+    batch.replay()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for s in rng.choice(len(recipe), 6, replace=False):
+        r = recipe[s]
+        cells = W.grid_centres(r["shape"])
+        idx = rng.choice(len(cells[0]), min(3000, len(cells[0])), replace=False)
+        om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
+        yb = items[s][4]["Y"].cpu().numpy()[idx]
+        check_forward(yb, oracle_field(om, r["mean"], cells, idx), math.sqrt(r["sigma2"]), "ensemble %d" % s)

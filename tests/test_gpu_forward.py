@@ -1,0 +1,218 @@
+"""GPU parity of the forward synthesis and maps against the FP64 oracle.
+
+Every case runs the CUDA path through the C ABI and the oracle on the same
+seeded inputs.  Small cases compare every cell (several warp tiles and a
+ragged tail); full-size workloads compare a seeded sample of cells.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import (check_facies, check_forward, check_lognormal, gpu_env, oracle_field, oracle_modes,
+                     to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = gpu_env()
+    from paper_2212_10961_gb300 import field as F
+    from paper_2212_10961_gb300 import workloads as W
+    return torch, F, W
+
+
+def run(env, cells, family, sigma2, ell, n_modes, seed, mean=0.0, nu=1.5, maps=None, plan=None):
+    torch, F, W = env
+    dim = len(cells)
+    p = F.FieldParams(family=family, sigma2=sigma2, mean=mean, ell=ell, dim=dim, n_modes=n_modes, seed=seed, nu=nu)
+    gf = F.GaussianField(p)
+    if plan is None:
+        plan = F.CellPlan(*to_dev(torch, cells))
+    out = gf.synth(plan, maps or F.MapSpec(y=True))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return {k: v.cpu().numpy() for k, v in out.items()}, p, plan
+
+
+def test_grid2d_64_all_cells(env):
+    torch, F, W = env
+    w = W.WORKLOADS["grid2d_64"]
+    cells = W.workload_cells("grid2d_64")
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True)
+    out, p, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], maps=maps)
+    om = oracle_modes(w["family"], w["sigma2"], w["ell"], 2, w["n_modes"], w["seed"])
+    y_or = oracle_field(om, 0.0, cells)
+    check_forward(out["Y"], y_or, 1.0, "grid2d_64")
+    check_lognormal(out["K"], y_or, 1.0)
+    check_facies(out["facies"], y_or, [0.0], 1.0)
+    # binary facies at t = 0 is the sign of Y - mu away from the band
+    far = np.abs(y_or) > 1e-4
+    assert np.array_equal(out["facies"][far], (y_or[far] > 0).astype(np.uint8))
+
+
+@pytest.mark.parametrize("family,nu", [("gaussian", 1.5), ("exponential", 0.5), ("matern", 1.5),
+                                       ("matern", 0.7)])
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_families_and_dims_ragged(env, family, nu, dim):
+    rng = np.random.default_rng(10 * dim + len(family))
+    n_cells = 3000 + 77  # several tiles and a ragged tail
+    cells = [rng.random(n_cells).astype(np.float32) * e for e in (2.0, 1.0, 0.5)[:dim]]
+    ell = (0.2, 0.1, 0.05)[:dim]
+    out, p, _ = run(env, cells, family, 2.0, ell, 300, seed=11, mean=0.3, nu=nu)
+    om = oracle_modes(family, 2.0, ell, dim, 300, 11, nu=nu)
+    check_forward(out["Y"], oracle_field(om, 0.3, cells), math.sqrt(2.0), "%s d%d" % (family, dim))
+
+
+@pytest.mark.parametrize("n_cells,n_modes", [(1, 1), (31, 129), (257, 128), (1025, 1000)])
+def test_edge_sizes(env, n_cells, n_modes):
+    rng = np.random.default_rng(n_cells)
+    cells = [rng.random(n_cells).astype(np.float32) for _ in range(3)]
+    out, p, _ = run(env, cells, "gaussian", 1.0, (0.1, 0.1, 0.1), n_modes, seed=3)
+    om = oracle_modes("gaussian", 1.0, (0.1, 0.1, 0.1), 3, n_modes, 3)
+    check_forward(out["Y"], oracle_field(om, 0.0, cells), 1.0, "edge %d/%d" % (n_cells, n_modes))
+
+
+def test_grid3d_256_reduced_all_cells(env):
+    torch, F, W = env
+    w = W.WORKLOADS["grid3d_256"]
+    cells = W.grid_centres((64, 64, 64))
+    sig = math.sqrt(w["sigma2"])
+    thr = W.quantile_thresholds(0.0, sig, w["quantiles"])
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=thr, facies=True)
+    out, p, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], maps=maps)
+    om = oracle_modes(w["family"], w["sigma2"], w["ell"], 3, w["n_modes"], w["seed"])
+    idx = np.random.default_rng(0).choice(len(cells[0]), 60000, replace=False)
+    y_or = oracle_field(om, 0.0, cells, idx)
+    err = check_forward(out["Y"][idx], y_or, sig, "grid3d 64^3")
+    check_lognormal(out["K"][idx], y_or, sig)
+    check_facies(out["facies"][idx], y_or, thr, sig)
+    print("grid3d 64^3 max err %.3e sigma" % err)
+
+
+def test_grid3d_256_full_size_sampled(env):
+    torch, F, W = env
+    w = W.WORKLOADS["grid3d_256"]
+    cells = W.workload_cells("grid3d_256")
+    sig = math.sqrt(w["sigma2"])
+    thr = W.quantile_thresholds(0.0, sig, w["quantiles"])
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=thr, facies=True)
+    out, p, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], maps=maps)
+    om = oracle_modes(w["family"], w["sigma2"], w["ell"], 3, w["n_modes"], w["seed"])
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([rng.choice(len(cells[0]), 30000, replace=False),
+                          np.arange(256), len(cells[0]) - 1 - np.arange(256)])
+    y_or = oracle_field(om, 0.0, cells, idx)
+    err = check_forward(out["Y"][idx], y_or, sig, "grid3d 256^3")
+    check_lognormal(out["K"][idx], y_or, sig)
+    nb = check_facies(out["facies"][idx], y_or, thr, sig)
+    print("grid3d 256^3 sampled max err %.3e sigma, %d cells in the threshold band" % (err, nb))
+
+
+def test_jitter3d_reduced_and_full_sampled(env):
+    torch, F, W = env
+    w = W.WORKLOADS["jitter3d_2m"]
+    sig = math.sqrt(w["sigma2"])
+    om = oracle_modes(w["family"], w["sigma2"], w["ell"], 3, w["n_modes"], w["seed"], nu=w["nu"])
+    small = W.workload_cells("jitter3d_2m", scale=4)
+    out, _, _ = run(env, small, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], nu=w["nu"])
+    check_forward(out["Y"], oracle_field(om, 0.0, small), sig, "jitter reduced")
+    cells = W.workload_cells("jitter3d_2m")
+    assert len(cells[0]) == 2000376
+    out, _, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], nu=w["nu"])
+    idx = np.random.default_rng(2).choice(len(cells[0]), 20000, replace=False)
+    err = check_forward(out["Y"][idx], oracle_field(om, 0.0, cells, idx), sig, "jitter full")
+    print("jitter3d full sampled max err %.3e sigma" % err)
+
+
+def test_shuffled_cells_and_determinism(env):
+    torch, F, W = env
+    cells = W.grid_centres((48, 40, 20))
+    sh, perm = W.shuffled(cells, 9)
+    out1, p, plan = run(env, sh, "exponential", 4.0, (0.2, 0.2, 0.05), 1024, seed=4)
+    om = oracle_modes("exponential", 4.0, (0.2, 0.2, 0.05), 3, 1024, 4)
+    check_forward(out1["Y"], oracle_field(om, 0.0, sh), 2.0, "shuffled")
+    out2, _, _ = run(env, sh, "exponential", 4.0, (0.2, 0.2, 0.05), 1024, seed=4, plan=plan)
+    assert np.array_equal(out1["Y"], out2["Y"])  # deterministic
+    out3, _, _ = run(env, sh, "exponential", 4.0, (0.2, 0.2, 0.05), 1024, seed=4)
+    assert np.array_equal(out1["Y"], out3["Y"])  # plan is deterministic too
+
+
+def test_large_coordinates_exact_path(env):
+    # cells far from the origin: phases of hundreds of thousands of turns
+    rng = np.random.default_rng(5)
+    cells = [(1000.0 + rng.random(5000)).astype(np.float32) for _ in range(3)]
+    out, p, _ = run(env, cells, "exponential", 1.0, (0.05, 0.05, 0.05), 512, seed=8)
+    om = oracle_modes("exponential", 1.0, (0.05, 0.05, 0.05), 3, 512, 8)
+    check_forward(out["Y"], oracle_field(om, 0.0, cells), 1.0, "far cells")
+
+
+def test_maps_standalone_and_fused(env):
+    torch, F, W = env
+    rng = np.random.default_rng(6)
+    cells = [rng.random(5000).astype(np.float32) for _ in range(2)]
+    thr = (-0.5, 0.25, 1.0)
+    vals = (10.0, 20.0, 30.0, 40.0)
+    maps = F.MapSpec(y=True, lognormal=True, k_ref=2.5, thresholds=thr, facies=True, values=vals)
+    out, p, plan = run(env, cells, "matern", 1.5, (0.1, 0.1), 500, seed=2, mean=0.2, maps=maps)
+    Yd = torch.from_numpy(out["Y"]).cuda()
+    st = F.map_property(Yd, F.MapSpec(y=False, lognormal=True, k_ref=2.5, thresholds=thr, facies=True,
+                                      values=vals), 0.2, math.sqrt(1.5))
+    torch.cuda.synchronize()
+    assert np.array_equal(st["K"].cpu().numpy(), out["K"])
+    assert np.array_equal(st["facies"].cpu().numpy(), out["facies"])
+    assert np.array_equal(st["prop"].cpu().numpy(), out["prop"])
+    lab = out["facies"]
+    assert np.array_equal(out["prop"], np.asarray(vals, dtype=np.float32)[lab])
+    # porosity map
+    por = F.map_property(Yd, F.MapSpec(y=False, porosity=(0.25, 0.05, 0.1, 0.35)), 0.2, math.sqrt(1.5))
+    torch.cuda.synchronize()
+    from oracle import field as of
+    want = of.porosity(out["Y"].astype(np.float64), 0.2, math.sqrt(1.5), 0.25, 0.05, 0.1, 0.35)
+    np.testing.assert_allclose(por["prop"].cpu().numpy(), want, rtol=0, atol=1e-6)
+    om = oracle_modes("matern", 1.5, (0.1, 0.1), 2, 500, 2)
+    y_or = oracle_field(om, 0.2, cells)
+    check_lognormal(out["K"], y_or, math.sqrt(1.5), k_ref=2.5)
+    check_facies(out["facies"], y_or, thr, math.sqrt(1.5))
+
+
+def test_segments_share_one_plan(env):
+    torch, F, W = env
+    a = W.grid_centres((40, 30))
+    b = W.grid_centres((17, 23))
+    cells = [np.concatenate([a[k], b[k] * 3.0]) for k in range(2)]
+    plan = F.CellPlan(*to_dev(torch, cells), segments=[1200, 391])
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=700, seed=21)
+    gf = F.GaussianField(p)
+    om = oracle_modes("gaussian", 1.0, (0.1, 0.1), 2, 700, 21)
+    for s, c in ((0, a), (1, [b[0] * 3.0, b[1] * 3.0])):
+        out = gf.synth(plan, F.MapSpec(y=True), segment=s)
+        torch.cuda.synchronize()
+        check_forward(out["Y"].cpu().numpy(), oracle_field(om, 0.0, c), 1.0, "segment %d" % s)
+
+
+def test_rejects_bad_calls(env):
+    torch, F, W = env
+    from paper_2212_10961_gb300 import _abi
+    cells = W.grid_centres((16, 16))
+    plan = F.CellPlan(*to_dev(torch, cells))
+    p = F.FieldParams(dim=2, ell=(0.1, 0.1), n_modes=64)
+    gf = F.GaussianField(p)
+    with pytest.raises(_abi.GRFError) as e:
+        F.synth(gf.table, p, plan, segment=1)
+    assert e.value.code == _abi.GRF_EINVAL
+    with pytest.raises(_abi.GRFError):
+        F.synth(gf.table, p, plan, maps=F.MapSpec(y=False))
+    g = torch.zeros(256, dtype=torch.float32, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    import ctypes
+    gs = _abi.grf_grads()
+    bufs = [torch.empty(64 * 2, dtype=torch.float64, device="cuda") for _ in range(6)]
+    for k, bb in zip(("dA", "dpsi", "da", "dmu", "dsigma", "dell"), bufs):
+        setattr(gs, k, bb.data_ptr())
+    rc = _abi.lib().grf_synth_backward(gf.table.ptr, ctypes.byref(p.to_c()), plan.ptr, 0,
+                                       ctypes.c_void_p(g.data_ptr()), ctypes.byref(gs),
+                                       ctypes.c_void_p(ws.data_ptr()), 1024, None)
+    assert rc == _abi.GRF_EWORKSPACE
+    assert plan.status() == 0
