@@ -202,10 +202,11 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     torch.cuda.synchronize()
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kev[warmup:]]))
     assert plan.status() == 0
+    per_step = launches / float(steps + warmup)
     res = {"workload": name, "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
            "kernel_ms": max_over_ranks(torch, world, kern_ms), "plan_ms": plan_ms,
-           "cell_modes_per_step": float(M) * N, "launches_in_timed_region": launches - 2 * warmup,
-           "launches_per_step": launches / float(steps + warmup)}
+           "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
+           "launches_per_step": per_step}
     if with_e2e:
         res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(2, steps // 3))
     return res
@@ -350,6 +351,16 @@ def roofline(kern_ms, cell_modes, clocks, sms):
     return out
 
 
+HEAD_METRIC = "Gcell.mode/s forward (fused Y, lognormal K, 3 facies) at <=1e-5 sigma vs FP64"
+
+
+def head_config(scale, cells, modes):
+    return {"workload": "grid3d_256" if scale == 1 else "grid3d_256/%d" % scale,
+            "cells": cells, "modes": modes, "covariance": "exponential", "ell": [0.2, 0.2, 0.05],
+            "sigma2": 4.0, "outputs": "Y,K,facies(3)",
+            "l2": "inputs (sorted coordinates 201 MB + permutation 67 MB) exceed the 129 MB L2"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -369,11 +380,11 @@ def run_reference(args):
     val = float(np.median([s["value"] for s in steps]))
     w = W.WORKLOADS[name]
     cm = float(len(W.workload_cells(name, args.scale)[0])) * w["n_modes"]
-    line = {"impl": "reference", "metric": "Gcell.mode/s (forward, FP64 oracle on host cores)", "value": val,
+    line = {"impl": "reference", "metric": HEAD_METRIC, "value": val,
             "unit": "Gcell.mode/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cm / (val * 1e9) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "cells": int(cm / w["n_modes"]), "modes": w["n_modes"]},
+            "config": head_config(args.scale, int(cm / w["n_modes"]), w["n_modes"]),
             "cpu_baseline": {"value": val, "unit": "Gcell.mode/s", "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": val, "unit": "Gcell.mode/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -432,15 +443,12 @@ def main():
     value = head["cell_modes_per_step"] * world / (head["ms_per_step"] * 1e-3) / 1e9
     e2e = head.get("e2e")
     line = {
-        "metric": "Gcell.mode/s forward (fused Y, lognormal K, 3 facies) at <=1e-5 sigma vs FP64",
+        "metric": HEAD_METRIC,
         "value": value, "unit": "Gcell.mode/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "grid3d_256" if args.scale == 1 else "grid3d_256/%d" % args.scale,
-                   "cells": head["cells"], "modes": head["modes"], "covariance": "exponential",
-                   "ell": [0.2, 0.2, 0.05], "sigma2": 4.0, "outputs": "Y,K,facies(3)",
-                   "l2": "inputs (sorted coordinates 201 MB + permutation 67 MB) exceed the 129 MB L2",
-                   "plan_ms_once_per_mesh": head["plan_ms"]},
+        "config": dict(head_config(args.scale, head["cells"], head["modes"]),
+                       plan_ms_once_per_mesh=head["plan_ms"]),
         "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms),
         "kernel_ms": head["kernel_ms"],
         "gpu_launches": head["launches_in_timed_region"],

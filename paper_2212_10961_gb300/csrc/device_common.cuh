@@ -25,21 +25,21 @@ __device__ __forceinline__ float hw_sin(float x) {
     return y;
 }
 
-// Fractional part about the nearest integer, exact for every finite v:
-// v - rint(v) (for |v| >= 2^23, v is an integer and the result is 0).
-__device__ __forceinline__ float frac_nearest(float v) { return v - rintf(v); }
-
-// Same for |v| <= 2 with FP32 adds only (round-to-nearest-even magic).
-__device__ __forceinline__ float frac_nearest_small(float v) {
+// Remove an integer from v exactly with FP32 adds only (no conversion unit):
+// r = v - ((v + 1.5*2^23) - 1.5*2^23).  For |v| < 2^22 the subtracted value is
+// rint(v) and |r| <= 1/2; for 2^22 <= |v| < 2^46 it is an integer within one
+// of v (|r| <= 1, r == v mod 1).  Exact in every case.
+__device__ __forceinline__ float frac_turn(float v) {
     return v - ((v + kRoundMagic) - kRoundMagic);
 }
 
-// Exact reduced phase of one mode at point x, in turns, in [-1/2, 1/2]:
+// Exact reduced phase of one mode at point x, in turns, |result| <= 1/2:
 //   t = a . x + psi  with a = ah + al, psi = psi_h + psi_l (FP32 pairs).
 // For each axis ah*x is split exactly into p + e (FMA), the integer part of
-// p is removed exactly, and the small remainders are summed with the high
-// part kept in [-1/2, 1/2] after every addition.  c0 = (ah_x, al_x, ah_y,
-// al_y), c1 = (ah_z, al_z, psi_h, psi_l).
+// p is removed exactly, and the remainders are summed with the high part kept
+// in [-1/2, 1/2] after every addition (error <= 2^-24 turn per addition).
+// c0 = (ah_x, al_x, ah_y, al_y), c1 = (ah_z, al_z, psi_h, psi_l).  Valid for
+// |ah * x| < 2^46.
 template <int DIM>
 __device__ __forceinline__ float phase_exact_turns(const float* x, float4 c0, float4 c1) {
     float hi = c1.z;
@@ -48,13 +48,12 @@ __device__ __forceinline__ float phase_exact_turns(const float* x, float4 c0, fl
     const float al[3] = {c0.y, c0.w, c1.y};
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-        float p = ah[c] * x[c];
-        float e = fmaf(ah[c], x[c], -p);
-        hi = frac_nearest_small(hi + frac_nearest(p));
+        const float p = ah[c] * x[c];
+        const float e = fmaf(ah[c], x[c], -p);
+        hi = frac_turn(hi + frac_turn(p));
         lo += fmaf(al[c], x[c], e);
     }
-    // lo may exceed one turn only for astronomically large a*x; reduce it too.
-    return frac_nearest_small(hi + frac_nearest(lo));
+    return frac_turn(hi + frac_turn(lo));
 }
 
 // Accumulate partial sum p into (s, e) with an exact TwoSum error term.

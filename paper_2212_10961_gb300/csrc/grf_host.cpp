@@ -311,8 +311,9 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
         if (!std::isfinite(m->amp[j]) || !std::isfinite(m->psi[j]))
             return fail(GRF_EINVAL, "mode %lld has a non-finite amplitude or phase", (long long)j);
         for (int c = 0; c < d; ++c)
-            if (!std::isfinite(m->a[j * d + c]))
-                return fail(GRF_EINVAL, "mode %lld has a non-finite frequency", (long long)j);
+            if (!std::isfinite(m->a[j * d + c]) || std::fabs(m->a[j * d + c]) > kMaxFrequency)
+                return fail(GRF_EINVAL, "mode %lld has a frequency that is not finite or exceeds 2^30 turns per unit",
+                            (long long)j);
     }
     unsigned char* base = static_cast<unsigned char*>(host_table);
     std::memset(base, 0, static_cast<size_t>(L.total));
@@ -331,7 +332,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
     hd.n_modes = static_cast<int32_t>(N);
     hd.n_pad = static_cast<int32_t>(L.n_pad);
     hd.dim = d;
-    hd.tau = kTauTurns;
+    hd.tau = 1.0f;
     hd.n_buckets = kBuckets;
     hd.bucket_bias = kBucketBias;
     hd.off_hot = L.off_hot;
@@ -371,11 +372,11 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
         c0[6] = ph;
         c0[7] = pl;
     }
-    // kpref[b] = #{s : h_s * E_b > tau}, E_b = 2^((b - bias) / 4)
+    // kpref[b] = #{s : h_s * E_b > 1}, E_b = 2^((b - bias) / 4)
     for (int b = 0; b < kBuckets; ++b) {
         const double Eb = std::pow(2.0, (b - kBucketBias) / 4.0);
         int64_t k = 0;
-        while (k < N && h[ord[k]] * Eb > static_cast<double>(kTauTurns)) ++k;
+        while (k < N && h[ord[k]] * Eb > 1.0) ++k;
         kpref[b] = static_cast<int32_t>(k);
     }
     return GRF_OK;
@@ -462,6 +463,8 @@ int fwd_desc(const void* table, int64_t n_modes, int32_t dim, const void* plan,
     d.kpref = reinterpret_cast<const int32_t*>(tb + TL.off_kpref);
     d.n_pad = static_cast<int32_t>(TL.n_pad);
     d.dim = meta.dim;
+    d.inv_tau1 = 1.0f / kTauLight;
+    d.inv_tau2 = 1.0f / kTauMedium;
     d.xs = reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin;
     d.ys = reinterpret_cast<const float*>(pb + meta.layout.off_ys) + begin;
     d.zs = reinterpret_cast<const float*>(pb + meta.layout.off_zs) + begin;

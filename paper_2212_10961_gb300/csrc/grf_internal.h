@@ -20,14 +20,19 @@ namespace grf {
 //   cold : float4[2*n_pad] (ah_x, al_x, ah_y, al_y), (ah_z, al_z, psi_h, psi_l)
 //          a = ah + al and psi = psi_h + psi_l as FP32 pairs (turns)
 //   order: int32[n_pad]    original mode index j (-1 for padding)
-//   kpref: int32[kBuckets] number of leading modes that take the exact phase
-//          path for a warp whose half-extent E <= bucket_extent(b)
+//   kpref: int32[kBuckets] kpref[b] = #{j : h_j * 2^((b - bias)/4) > 1}, the
+//          length of the prefix of modes whose phase span over a box of
+//          half-extent E exceeds tau turns is read at bucket(E / tau)
 // ---------------------------------------------------------------------------
 constexpr int kChunk = 128;          // modes per shared-memory chunk
 constexpr int kBuckets = 160;        // extent buckets
 constexpr int kBucketBias = 100;     // E_b = 2^((b - kBucketBias) / 4)
-constexpr float kTauTurns = 0.5f;    // light path iff h_j * E <= tau (turns)
+constexpr float kTauLight = 1.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
+constexpr float kTauMedium = 2.0f;   // lane-origin path iff h_j * E_lane <= tau2 (turns)
 constexpr uint32_t kTableMagic = 0x54465247u;  // "GRFT"
+// Largest |a_c| (turns per unit length) accepted: with |x| < 2^16 the exact
+// phase split needs |a x| < 2^46.
+constexpr double kMaxFrequency = 1073741824.0;  // 2^30
 
 struct TableHeader {
     uint32_t magic;
@@ -76,8 +81,7 @@ inline TableLayout table_layout(int64_t n_modes) {
 //   sort_tmp          : radix-sort temporary storage
 // ---------------------------------------------------------------------------
 constexpr uint32_t kPlanMagic = 0x4E4C5047u;  // "GPLN"
-constexpr int kMortonBits = 10;                // brick coordinate bits per axis
-constexpr int kBrickTarget = 256;              // target cells per brick
+constexpr int kMortonBits = 10;                // quantised coordinate bits per axis
 
 struct PlanHeader {
     uint32_t magic;
@@ -96,8 +100,8 @@ struct SegInfo {
     int64_t count;
     float lo[3];          // bounding box (float bits ordered as ints during the reduction)
     float hi[3];
-    float inv_brick[3];   // bricks per unit length per axis
-    int32_t nb[3];        // bricks per axis
+    float inv_brick[3];   // quantisation levels per unit length (same on every axis)
+    int32_t nb[3];        // quantisation levels per axis (<= 2^kMortonBits)
     int32_t pad;
 };
 
@@ -147,6 +151,8 @@ struct FwdDesc {
     const int32_t* kpref;
     int32_t n_pad;
     int32_t dim;
+    float inv_tau1;       // 1 / (span limit of the light class, turns)
+    float inv_tau2;       // 1 / (span limit of the medium class, turns)
     const float* xs;      // sorted coordinates of this realisation's segment
     const float* ys;
     const float* zs;

@@ -5,8 +5,8 @@
 // split each phase at a per-warp origin, which is accurate and cheap only when
 // a warp's cells are close together.  The plan provides that locality:
 //   1. bounding box of every segment (ordered-int atomics, warp-aggregated);
-//   2. brick grid per segment with ~kBrickTarget cells per brick;
-//   3. 64-bit keys (segment << 30 | Morton code of the brick);
+//   2. an isotropic quantisation grid of 2^10 levels along the longest axis;
+//   3. 64-bit keys (segment << 30 | Morton code of the quantised position);
 //   4. stable LSD radix sort of (key, original index), 8-bit digits;
 //   5. gather of the sorted SoA coordinates.
 // Everything runs on the stream without host synchronisation and is
@@ -94,15 +94,16 @@ __global__ void bbox_kernel(const float* __restrict__ x, const float* __restrict
     }
 }
 
-// Brick grid per segment: about kBrickTarget cells per brick, bricks as close
-// to cubes as the extents allow, at most 2^kMortonBits per axis.
+// Quantisation grid per segment: cubic cells of side L_max / 2^kMortonBits
+// (L_max = largest bounding-box extent), so that the Morton (Z-order) code
+// of the quantised position orders cells along a space-filling curve and
+// every aligned run of 2^k sorted cells is a compact, roughly cubic block.
 __global__ void brick_kernel(SegInfo* segs, int n_segments, int dim) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_segments) return;
     SegInfo& g = segs[s];
     float L[3] = {0.f, 0.f, 0.f};
-    int active = 0;
-    double vol = 1.0;
+    float Lmax = 0.f;
     for (int k = 0; k < 3; ++k) {
         float lo = ordered_to_float(reinterpret_cast<int32_t*>(g.lo)[k]);
         float hi = ordered_to_float(reinterpret_cast<int32_t*>(g.hi)[k]);
@@ -113,22 +114,20 @@ __global__ void brick_kernel(SegInfo* segs, int n_segments, int dim) {
         g.lo[k] = lo;
         g.hi[k] = hi;
         L[k] = hi - lo;
-        if (L[k] > 0.f) {
-            ++active;
-            vol *= static_cast<double>(L[k]);
-        }
+        Lmax = fmaxf(Lmax, L[k]);
     }
-    double bricks = static_cast<double>(g.count) / kBrickTarget;
-    if (bricks < 1.0) bricks = 1.0;
-    double side = active > 0 ? pow(vol / bricks, 1.0 / active) : 1.0;
+    const double levels = double(1 << kMortonBits);
     for (int k = 0; k < 3; ++k) {
         int nb = 1;
-        if (L[k] > 0.f && side > 0.0) {
-            double q = ceil(static_cast<double>(L[k]) / side);
-            nb = q < 1.0 ? 1 : (q > double(1 << kMortonBits) ? (1 << kMortonBits) : int(q));
+        float inv = 0.f;
+        if (L[k] > 0.f && Lmax > 0.f) {
+            const double per_unit = levels / static_cast<double>(Lmax);
+            double q = ceil(static_cast<double>(L[k]) * per_unit);
+            nb = q < 1.0 ? 1 : (q > levels ? int(levels) : int(q));
+            inv = static_cast<float>(per_unit);
         }
         g.nb[k] = nb;
-        g.inv_brick[k] = L[k] > 0.f ? static_cast<float>(nb / static_cast<double>(L[k])) : 0.f;
+        g.inv_brick[k] = inv;
     }
 }
 

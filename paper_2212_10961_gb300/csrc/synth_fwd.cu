@@ -39,14 +39,6 @@ struct FwdSmem {
     FwdDesc desc;               // batched: current descriptor
 };
 
-__device__ __forceinline__ int bucket_of(float E) {
-    if (!(E > 0.0f)) return 0;
-    // conservative bucket: smallest b with 2^((b - bias)/4) >= E (one extra
-    // step covers the approximate log2)
-    int b = static_cast<int>(ceilf(4.0f * __log2f(E))) + kBucketBias + 1;
-    return b < 0 ? 0 : b;
-}
-
 // Issue the bulk copies of chunk `ch` of descriptor d into buffer `bi`.
 __device__ __forceinline__ void issue_chunk(const FwdDesc& d, int ch, float4* dst, uint64_t* bar) {
     mbar_arrive_expect_tx(bar, kChunkBytes);
@@ -54,7 +46,38 @@ __device__ __forceinline__ void issue_chunk(const FwdDesc& d, int ch, float4* ds
     bulk_g2s(dst + kChunk, d.cold + static_cast<int64_t>(ch) * kChunk * 2, kChunk * 32, bar);
 }
 
+// Conservative extent bucket: smallest b with 2^((b - bias)/4) >= E (one
+// extra step covers the approximate log2).  kpref[b] counts the modes with
+// |a_j|_1 * 2^((b - bias)/4) > 1, so querying with E / tau gives the modes
+// whose phase span over a box of half-extent E exceeds tau turns.
+__device__ __forceinline__ int prefix_for(const int32_t* kpref, int n_pad, float E_over_tau) {
+    if (!(E_over_tau > 0.0f)) return 0;
+    const int b = static_cast<int>(ceilf(4.0f * __log2f(E_over_tau))) + kBucketBias + 1;
+    if (b >= kBuckets) return n_pad;
+    return b < 0 ? 0 : __ldg(kpref + b);
+}
+
+// Warp-wide min / max.
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
 // One tile: W warps x 32 lanes x C cells starting at sorted cell `tile_base`.
+// Lane l of a warp owns the C consecutive sorted cells wbase + C l + c, a
+// compact block of the Z-order (2x2x2 for C = 8).  Three classes of modes,
+// all prefixes of the table (sorted by |a|_1, descending):
+//   super  : span over the lane's block > tau2 turns -> exact phase per cell;
+//   medium : span over the warp's block > tau1 turns -> exact phase at the
+//            lane origin xt once per (lane, mode), FP32 offsets per cell;
+//   light  : the rest -> exact phase at the warp origin x0 once per
+//            (warp, mode), FP32 offsets per cell (the hot loop).
 // `uses` counts completed waits per buffer (parity tracking across tiles).
 template <int DIM, int C, int W>
 __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, FwdSmem<C, W>& sm,
@@ -74,20 +97,41 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         if (n_chunks > 1) issue_chunk(d, 1, sm.buf[1], &sm.full[1]);
     }
 
-    // ---- load cells, bounding box, origin -------------------------------
+    // ---- load cells (lane-contiguous), bounding boxes, origins ------------
+    const int64_t lbase = wbase + static_cast<int64_t>(lane) * C;
     float x[C][DIM];
     bool valid[C];
+    {
+        const float* src[3] = {d.xs, d.ys, d.zs};
+        const int64_t safe = warp_active ? wbase : 0;  // a valid cell of this warp
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        int64_t i = wbase + c * 32 + lane;
-        valid[c] = i < n;
-        int64_t ii = valid[c] ? i : (warp_active ? wbase : 0);
-        x[c][0] = d.xs[ii];
-        if (DIM > 1) x[c][1] = d.ys[ii];
-        if (DIM > 2) x[c][2] = d.zs[ii];
+        for (int c = 0; c < C; ++c) valid[c] = lbase + c < n;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            // vector loads only when all C cells exist and the address is
+            // 16-byte aligned (a segment may start at any cell index)
+            const bool vec = (C % 4) == 0 && lbase + C <= n &&
+                             (reinterpret_cast<uintptr_t>(src[k] + lbase) & 15u) == 0;
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < C / 4; ++q) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(src[k] + lbase) + q);
+                    x[4 * q + 0][k] = v.x;
+                    x[4 * q + 1][k] = v.y;
+                    x[4 * q + 2][k] = v.z;
+                    x[4 * q + 3][k] = v.w;
+                }
+            } else {
+                // ragged tail: invalid cells repeat the lane's first valid cell
+                // (or the warp's first cell) so that bounding boxes are unaffected
+                const int64_t first = lbase < n ? lbase : safe;
+#pragma unroll
+                for (int c = 0; c < C; ++c) x[c][k] = __ldg(src[k] + (valid[c] ? lbase + c : first));
+            }
+        }
     }
-    float x0[DIM];
-    float E = 0.0f;
+    float x0[DIM], xt[DIM];
+    float Ew = 0.0f, Et = 0.0f;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         float mn = x[0][k], mx = x[0][k];
@@ -96,18 +140,18 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
             mn = fminf(mn, x[c][k]);
             mx = fmaxf(mx, x[c][k]);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        }
+        xt[k] = 0.5f * mn + 0.5f * mx;
+        Et = fmaxf(Et, fmaxf(mx - xt[k], xt[k] - mn));
+        mn = warp_min(mn);
+        mx = warp_max(mx);
         x0[k] = 0.5f * mn + 0.5f * mx;
-        E = fmaxf(E, fmaxf(mx - x0[k], x0[k] - mn));
+        Ew = fmaxf(Ew, fmaxf(mx - x0[k], x0[k] - mn));
     }
-    int k_heavy = 0;
+    Et = warp_max(Et);
+    int k_med = 0, k_sup = 0;
     if (warp_active) {
-        int b = bucket_of(E);
-        k_heavy = b >= kBuckets ? d.n_pad : d.kpref[b];
+        k_med = prefix_for(d.kpref, d.n_pad, Ew * d.inv_tau1);
+        k_sup = min(k_med, prefix_for(d.kpref, d.n_pad, Et * d.inv_tau2));
     }
 
     float s[C], e[C], p[C];
@@ -118,17 +162,17 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         p[c] = 0.0f;
     }
 
-    // ---- exact path for the leading (fast-oscillating) modes -------------
-    for (int j = 0; j < k_heavy; ++j) {
+    // ---- super class: exact phase at every cell ---------------------------------
+    for (int j = 0; j < k_sup; ++j) {
         const float4 c0 = __ldg(d.cold + 2 * j);
         const float4 c1 = __ldg(d.cold + 2 * j + 1);
         const float A = __ldg(&d.hot[j].w);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            float r = phase_exact_turns<DIM>(x[c], c0, c1);
+            const float r = phase_exact_turns<DIM>(x[c], c0, c1);
             p[c] = fmaf(A, hw_cos(kTwoPiF * r), p[c]);
         }
-        if ((j & 31) == 31) {
+        if ((j & 63) == 63) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 two_sum_acc(s[c], e[c], p[c]);
@@ -137,14 +181,44 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         }
     }
 
-    // ---- offsets from the origin -------------------------------------------
-    float dx[C][DIM];
+    // ---- medium class: exact phase at the lane origin -------------------------
+    float dx[C][DIM];  // offsets from the lane origin, then from the warp origin
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - x0[k];
+        for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - xt[k];
+    for (int j = k_sup; j < k_med; ++j) {
+        const float4 c0 = __ldg(d.cold + 2 * j);
+        const float4 c1 = __ldg(d.cold + 2 * j + 1);
+        const float4 h = __ldg(d.hot + j);
+        const float t0 = kTwoPiF * phase_exact_turns<DIM>(xt, c0, c1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float th = fmaf(h.x, dx[c][0], t0);
+            if (DIM > 1) th = fmaf(h.y, dx[c][1], th);
+            if (DIM > 2) th = fmaf(h.z, dx[c][2], th);
+            p[c] = fmaf(h.w, hw_cos(th), p[c]);
+        }
+        if (((j - k_sup) & 63) == 63) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                two_sum_acc(s[c], e[c], p[c]);
+                p[c] = 0.0f;
+            }
+        }
+    }
+    // re-base the offsets on the warp origin: dx = (x - xt) + (xt - x0)
+    {
+        float D[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) D[k] = xt[k] - x0[k];
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) dx[c][k] += D[k];
+    }
 
-    // ---- split path over staged chunks -----------------------------------------
+    // ---- light class over staged chunks ------------------------------------------
     int ch = 0;
     for (; ch < n_chunks; ++ch) {
         const int bi = ch & 1;
@@ -159,12 +233,10 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         const float4* coldS = sm.buf[bi] + kChunk;
         float* t0S = sm.t0[warp];
         const int jbase = ch * kChunk;
-        if (ok && warp_active && jbase + kChunk > k_heavy) {
-            const int m0 = k_heavy > jbase ? k_heavy - jbase : 0;
-            for (int m = lane; m < kChunk; m += 32) {
-                float r = phase_exact_turns<DIM>(x0, coldS[2 * m], coldS[2 * m + 1]);
-                t0S[m] = kTwoPiF * r;
-            }
+        if (ok && warp_active && jbase + kChunk > k_med) {
+            const int m0 = k_med > jbase ? k_med - jbase : 0;
+            for (int m = m0 + lane; m < kChunk; m += 32)
+                t0S[m] = kTwoPiF * phase_exact_turns<DIM>(x0, coldS[2 * m], coldS[2 * m + 1]);
             __syncwarp();
 #pragma unroll 4
             for (int m = m0; m < kChunk; ++m) {
@@ -206,9 +278,9 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
     for (int c = 0; c < C; ++c) {
         two_sum_acc(s[c], e[c], p[c]);
         if (warp_active && valid[c]) {
-            const int64_t i = wbase + c * 32 + lane;
+            const int64_t i = lbase + c;
             const float y = (s[c] + e[c]) + d.map.mu;
-            map_store(d.map, static_cast<int64_t>(d.perm[i]) - d.perm_base, y);
+            map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
         }
     }
 }

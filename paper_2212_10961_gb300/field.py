@@ -176,6 +176,9 @@ class CellPlan:
                                    _stream_handle(stream)))
 
     def segment_size(self, s):
+        """Cells in segment s (0 for an out-of-range index; the C ABI rejects it)."""
+        if not 0 <= s < self.n_segments:
+            return 0
         return int(self.offsets[s + 1] - self.offsets[s])
 
     def status(self, stream=None):

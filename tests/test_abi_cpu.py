@@ -135,7 +135,7 @@ def test_pack_table_layout(abi, n, dim):
     np.testing.assert_allclose(c[:, 6] + c[:, 7], md["psi"][order[:n]], rtol=0, atol=1e-15)
     for b in range(160):
         Eb = 2.0 ** ((b - 100) / 4.0)
-        assert t["kpref"][b] == int(np.sum(h * Eb > 0.5))
+        assert t["kpref"][b] == int(np.sum(h * Eb > 1.0))
 
 
 def test_pack_and_sizes_reject(abi):

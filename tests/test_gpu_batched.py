@@ -73,7 +73,11 @@ def test_batched_matches_single_and_oracle(env, tile_cells):
         torch.cuda.synchronize()
         yb = out["Y"].cpu().numpy()
         ys = single["Y"].cpu().numpy()
-        assert np.max(np.abs(yb - ys)) <= 1e-6 * p.sigma
+        if tile_cells in (0, 1024, 2048):
+            # same 256-cell warp tiles as the single-realisation kernel
+            assert np.array_equal(yb, ys)
+        else:
+            assert np.max(np.abs(yb - ys)) <= 2 * 1e-5 * p.sigma
         r = recipe[s]
         om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
         cells = W.grid_centres(r["shape"])
