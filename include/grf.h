@@ -285,6 +285,31 @@ size_t grf_mismatch_workspace_bytes(int64_t n);
 int grf_mismatch_grad(int64_t n, const float *K, const float *K_target, float *gY, double *loss,
                       void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * grf_mismatch_grad_noalloc -- the same loss and gradient as
+ * grf_mismatch_grad, for callers that cannot allocate device memory at the
+ * call site (for example code running inside a host callback, a plugin that
+ * must not touch the caller's allocator, or a process whose memory budget is
+ * fixed once at start-up).  No counterpart in the paper: it only changes
+ * where the per-block partial sums live.
+ *
+ * The partial sums go to a fixed array inside the library,
+ * GRF_NOALLOC_MAX_BLOCKS doubles (512 KiB) in device memory, which every GPU
+ * that loads the library keeps until the process exits.  n may therefore be
+ * at most GRF_NOALLOC_MAX_CELLS (134,217,728); larger n returns GRF_EINVAL
+ * before any device work.  The first call on a device looks up the array's
+ * device address on that device (cudaGetSymbolAddress); make that first call
+ * outside any CUDA-graph stream capture.  All calls share the one array, so
+ * calls that can overlap on the GPU (different streams, no ordering between
+ * them) race and may return wrong losses: order them on one stream.  Nothing
+ * in the array needs to start at zero; every call writes all the entries it
+ * reads.  Arguments and results are those of grf_mismatch_grad.
+ */
+#define GRF_NOALLOC_MAX_BLOCKS 65536
+#define GRF_NOALLOC_MAX_CELLS (134217728LL)
+int grf_mismatch_grad_noalloc(int64_t n, const float *K, const float *K_target, float *gY,
+                              double *loss, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* S6: batched ensembles (many realisations, one persistent launch)     */
 /* ------------------------------------------------------------------ */

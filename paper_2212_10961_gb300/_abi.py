@@ -97,6 +97,8 @@ _SIGS = {
     "grf_mismatch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "grf_mismatch_grad": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "grf_mismatch_grad_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "grf_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64]),
     "grf_batch_prepare": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(grf_batch_item), ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,

@@ -3,6 +3,8 @@
 // loss and its gradient, and a throughput probe of the hardware cosine.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "device_common.cuh"
 
 namespace grf {
@@ -114,6 +116,40 @@ int launch_mismatch(int64_t n, const float* K, const float* T, float* gY, double
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Zero-allocation variant of the mismatch loss: the per-block partial sums
+// live in a fixed device array owned by the library (see
+// grf_mismatch_grad_noalloc in grf.h for the contract).
+// ---------------------------------------------------------------------------
+static_assert(int64_t(GRF_NOALLOC_MAX_BLOCKS) * kLossThreads * kLossItems == GRF_NOALLOC_MAX_CELLS,
+              "cell limit must match the scratch size");
+static __device__ __align__(256) double g_noalloc_partials[GRF_NOALLOC_MAX_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol's own address: on the host it
+// names a stand-in, not the device memory).
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mufu_probe_kernel<<<blocks, 256, 0, st>>>(iters, sink);
@@ -122,3 +158,21 @@ int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) 
 }
 
 }  // namespace grf
+
+extern "C" int grf_mismatch_grad_noalloc(int64_t n, const float* K, const float* K_target, float* gY,
+                                         double* loss, void* stream) {
+    if (n < 0) return grf::set_error(GRF_EINVAL, "n must be >= 0");
+    if (n > GRF_NOALLOC_MAX_CELLS)
+        return grf::set_error(GRF_EINVAL,
+                              "n exceeds GRF_NOALLOC_MAX_CELLS (134217728) of the fixed scratch array; "
+                              "use grf_mismatch_grad with a caller workspace");
+    if (n > 0 && (!K || !K_target || !gY)) return grf::set_error(GRF_EINVAL, "K, K_target or gY is NULL");
+    if (!loss) return grf::set_error(GRF_EINVAL, "loss is NULL");
+    double* scratch = nullptr;
+    int err = grf::noalloc_scratch(&scratch);
+    if (err != cudaSuccess)
+        return grf::set_error(GRF_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+    err = grf::launch_mismatch(n, K, K_target, gY, loss, scratch, stream);
+    if (err != cudaSuccess) return grf::set_error(GRF_ECUDA, cudaGetErrorString(static_cast<cudaError_t>(err)));
+    return GRF_OK;
+}
