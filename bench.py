@@ -202,11 +202,16 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     torch.cuda.synchronize()
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kev[warmup:]]))
     assert plan.status() == 0
+    # field of the workload's own seed, kept for the accuracy check of the CPU-baseline leg
+    p0 = params_for(F, w, dim, w["seed"])
+    m0 = F.gen_modes(p0)
+    ring[0].update(m0["amp"], m0["psi"], m0["a"])
+    y_seed = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True))["Y"].cpu().numpy()
     per_step = launches / float(steps + warmup)
     res = {"workload": name, "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
            "kernel_ms": max_over_ranks(torch, world, kern_ms), "plan_ms": plan_ms,
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
-           "launches_per_step": per_step}
+           "launches_per_step": per_step, "y_seed": y_seed}
     if with_e2e:
         res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(2, steps // 3))
     return res
@@ -315,8 +320,10 @@ def bench_batched(torch, F, W, rank, world, steps, warmup, scale):
             "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1}
 
 
-def cpu_baseline(W, name, scale, target_s=10.0):
-    """FP64 C oracle (OpenMP, all host cores) on a seeded sample of the workload."""
+def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
+    """FP64 C oracle (OpenMP, all host cores) on a seeded sample of the workload.
+    With y_gpu (the GPU field of the workload's own seed) the sample also gives
+    the max-abs error of the GPU field against the oracle on those cells."""
     from oracle import modes as om
     from oracle import native
     w = W.WORKLOADS[name]
@@ -329,14 +336,19 @@ def cpu_baseline(W, name, scale, target_s=10.0):
     while True:
         idx = rng.choice(len(c), min(n, len(c)), replace=False)
         t0 = time.perf_counter()
-        native.synth(m["a"], m["amp"], m["psi"], w["mean"], c[idx])
+        y_or = native.synth(m["a"], m["amp"], m["psi"], w["mean"], c[idx])
         dt = time.perf_counter() - t0
         if dt > target_s / 4 or n >= len(c):
             break
         n = int(min(len(c), n * max(2.0, min(16.0, target_s / 4 / max(dt, 1e-3)))))
     rate = len(idx) * float(w["n_modes"]) / dt
-    return {"value": rate / 1e9, "unit": "Gcell.mode/s", "cores": native.threads(), "kind": "oracle",
-            "sample": "%d random cells of %s x %d modes, FP64 C + OpenMP, %.1f s" % (len(idx), name, w["n_modes"], dt)}
+    res = {"value": rate / 1e9, "unit": "Gcell.mode/s", "cores": native.threads(), "kind": "oracle",
+           "sample": "%d random cells of %s x %d modes, FP64 C + OpenMP, %.1f s" % (len(idx), name, w["n_modes"], dt)}
+    if y_gpu is not None:
+        err = float(np.max(np.abs(y_gpu[idx].astype(np.float64) - y_or)))
+        res["gpu_max_abs_err_sigma"] = err / math.sqrt(w["sigma2"])
+        res["gpu_err_cells"] = int(len(idx))
+    return res
 
 
 def roofline(kern_ms, cell_modes, clocks, sms):
@@ -426,6 +438,9 @@ def main():
     ck = clocks.stop()
     if rank != 0:
         return
+    y_seed_head = head.pop("y_seed", None) if head is not None else None
+    for v in extra.values():
+        v.pop("y_seed", None)
     for k, v in extra.items():
         v["gcell_modes_per_s"] = v["cell_modes_per_step"] * world / (v["ms_per_step"] * 1e-3) / 1e9
         if "kernel_ms" in v:
@@ -462,7 +477,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         from oracle import native
         native.build()
-        line["cpu_baseline"] = cpu_baseline(W, "grid3d_256", args.scale)
+        line["cpu_baseline"] = cpu_baseline(W, "grid3d_256", args.scale, y_gpu=y_seed_head)
     print(json.dumps(line))
 
 

@@ -347,6 +347,18 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item *items, const void *
  */
 int grf_batch_launch(void *workspace, void *stream);
 
+/*
+ * grf_selftest_wait -- exercise the bounded-wait failure path on the device.
+ * Launches one block that waits on a shared-memory mbarrier nothing ever
+ * completes, with the same bounded wait the synthesis kernels use but a
+ * limit of `limit_us` microseconds (1 .. 2,000,000).  The block records the
+ * expiry in a device status word and returns; the call synchronises the
+ * stream and returns GRF_ETIMEOUT when the wait expired as designed (GRF_OK
+ * would mean the wait completed, which cannot happen).  The context stays
+ * usable afterwards.  `status_dev` is a caller device int32 (set to 2).
+ */
+int grf_selftest_wait(int32_t limit_us, int32_t *status_dev, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Measurement helpers                                                  */
 /* ------------------------------------------------------------------ */

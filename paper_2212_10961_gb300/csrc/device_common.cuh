@@ -107,17 +107,22 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Bounded wait: returns false if the phase did not complete within about
-// two seconds (checked on the global timer every 256 polls).
+// Bounded wait: returns false if the phase did not complete within
+// `limit_ns` (two seconds by default, checked on the global timer every 256
+// polls) or within 2^24 polls, whichever comes first, so the wait ends even
+// if the timer does not advance.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+constexpr uint32_t kWaitMaxRounds = 1u << 16;  // x 256 polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    for (;;) {
+    for (uint32_t round = 0; round < kWaitMaxRounds; ++round) {
         for (int i = 0; i < 256; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+    return false;
 }
 
 // 1-D bulk copy global -> shared, completion reported to `bar` as tx bytes.

@@ -683,6 +683,20 @@ int grf_device_info(int32_t* sm_count, int32_t* sm_clock_khz) {
     return GRF_OK;
 }
 
+int grf_selftest_wait(int32_t limit_us, int32_t* status_dev, void* stream) {
+    if (limit_us < 1 || limit_us > 2000000) return fail(GRF_EINVAL, "limit_us must be in [1, 2000000]");
+    if (!status_dev) return fail(GRF_EINVAL, "status_dev is NULL");
+    int err = launch_selftest_wait(static_cast<uint64_t>(limit_us) * 1000ull, status_dev, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "self-test kernel");
+    int32_t st = -1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(&st, status_dev, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test status read");
+    if (st == 2) return fail(GRF_ETIMEOUT, "bounded device wait expired after %d us (expected)", limit_us);
+    return GRF_OK;
+}
+
 int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) {
     if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
     const int err = launch_mufu_probe(blocks, iters, sink, stream);

@@ -201,6 +201,7 @@ int launch_mismatch(int64_t n, const float* K, const float* T, float* gY, double
                     void* stream);
 size_t mismatch_workspace_bytes(int64_t n);
 int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream);
+int launch_selftest_wait(uint64_t limit_ns, int32_t* status, void* stream);
 void count_launches(int64_t n);
 // Record `message` as the calling thread's last error and return `code`.
 int set_error(int code, const char* message);

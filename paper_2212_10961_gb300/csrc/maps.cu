@@ -80,7 +80,27 @@ __global__ void __launch_bounds__(256) mufu_probe_kernel(int32_t iters, float* s
     sink[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
 }
 
+// One block waits on an mbarrier that no thread arrives at and no copy
+// completes, through the same bounded wait as the synthesis kernels.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (threadIdx.x == 0) *status = ok ? 0 : 2;
+}
+
 }  // namespace
+
+int launch_selftest_wait(uint64_t limit_ns, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream) {
     if (n == 0) return cudaSuccess;

@@ -26,6 +26,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
 constexpr int kRadix = 256;
+static_assert(kRadix == kSortThreads, "the scatter kernel scans digit totals with one thread per digit");
 
 __device__ __forceinline__ int32_t float_to_ordered(float f) {
     int32_t b = __float_as_int(f);
@@ -57,40 +58,82 @@ __global__ void seg_init_kernel(SegInfo* segs, int n_segments) {
     }
 }
 
-__global__ void bbox_kernel(const float* __restrict__ x, const float* __restrict__ y,
-                            const float* __restrict__ z, int dim, int64_t n, SegInfo* segs,
-                            int n_segments, int32_t* status) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const bool in = i < n;
-    const int seg = in ? find_segment(segs, n_segments, i) : -1;
-    float v[3] = {0.f, 0.f, 0.f};
-    if (in) {
-        v[0] = x[i];
-        if (dim > 1) v[1] = y[i];
-        if (dim > 2) v[2] = z[i];
-        for (int k = 0; k < dim; ++k)
-            if (!isfinite(v[k])) atomicOr(status, 1);
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, in);
-    if (!in) return;
-    const int seg0 = __shfl_sync(mask, seg, __ffs(mask) - 1);
-    const bool uniform = __all_sync(mask, seg == seg0) && mask == 0xffffffffu;
+// Bounding boxes: a block covers kBoxItems consecutive cells.  When they all
+// belong to one segment (the usual case) the block reduces them first and
+// issues one atomic per axis and bound; blocks that straddle a segment
+// boundary fall back to per-thread atomics on change of segment.
+constexpr int kBoxThreads = 256;
+constexpr int kBoxItems = kBoxThreads * 16;
+
+__device__ __forceinline__ void box_flush(SegInfo* segs, int seg, int dim, const int32_t* lo,
+                                          const int32_t* hi) {
     for (int k = 0; k < dim; ++k) {
-        int32_t lo = float_to_ordered(v[k]);
-        int32_t hi = lo;
-        if (uniform) {
-            for (int off = 16; off > 0; off >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        atomicMin(reinterpret_cast<int32_t*>(segs[seg].lo) + k, lo[k]);
+        atomicMax(reinterpret_cast<int32_t*>(segs[seg].hi) + k, hi[k]);
+    }
+}
+
+__global__ void __launch_bounds__(kBoxThreads)
+    bbox_kernel(const float* __restrict__ x, const float* __restrict__ y, const float* __restrict__ z,
+                int dim, int64_t n, SegInfo* segs, int n_segments, int32_t* status) {
+    __shared__ int32_t red_lo[kBoxThreads / 32][3];
+    __shared__ int32_t red_hi[kBoxThreads / 32][3];
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kBoxItems;
+    const int64_t c1 = c0 + kBoxItems < n ? c0 + kBoxItems : n;
+    const int s_first = find_segment(segs, n_segments, c0);
+    const int s_last = find_segment(segs, n_segments, c1 - 1);
+    const bool single = s_first == s_last;
+    const float* src[3] = {x, y, z};
+    int32_t lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = float_to_ordered(INFINITY);
+        hi[k] = float_to_ordered(-INFINITY);
+    }
+    int seg = s_first;
+    int64_t seg_end = s_first + 1 < n_segments ? segs[s_first + 1].begin : n;
+    bool bad = false;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kBoxThreads) {
+        if (!single && i >= seg_end) {
+            box_flush(segs, seg, dim, lo, hi);
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = float_to_ordered(INFINITY);
+                hi[k] = float_to_ordered(-INFINITY);
             }
-            if ((threadIdx.x & 31) == 0) {
-                atomicMin(reinterpret_cast<int32_t*>(segs[seg].lo) + k, lo);
-                atomicMax(reinterpret_cast<int32_t*>(segs[seg].hi) + k, hi);
-            }
-        } else {
-            atomicMin(reinterpret_cast<int32_t*>(segs[seg].lo) + k, lo);
-            atomicMax(reinterpret_cast<int32_t*>(segs[seg].hi) + k, hi);
+            seg = find_segment(segs, n_segments, i);
+            seg_end = seg + 1 < n_segments ? segs[seg + 1].begin : n;
         }
+        for (int k = 0; k < dim; ++k) {
+            const float v = src[k][i];
+            bad |= !isfinite(v);
+            const int32_t o = float_to_ordered(v);
+            lo[k] = min(lo[k], o);
+            hi[k] = max(hi[k], o);
+        }
+    }
+    if (bad) atomicOr(status, 1);
+    if (!single) {
+        box_flush(segs, seg, dim, lo, hi);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    for (int k = 0; k < dim; ++k) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red_lo[warp][k] = lo[k];
+            red_hi[warp][k] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBoxThreads / 32; ++w)
+            for (int k = 0; k < dim; ++k) {
+                lo[k] = min(lo[k], red_lo[w][k]);
+                hi[k] = max(hi[k], red_hi[w][k]);
+            }
+        box_flush(segs, s_first, dim, lo, hi);
     }
 }
 
@@ -193,28 +236,33 @@ __global__ void __launch_bounds__(kSortThreads)
         counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
 }
 
-// Exclusive scan of `len` counts in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ data, int64_t len) {
-    __shared__ uint32_t part[1024];
-    const int64_t per = (len + 1023) / 1024;
-    const int64_t b = threadIdx.x * per;
-    const int64_t e = b + per < len ? b + per : len;
+// Exclusive scan of each digit's row of per-block counts, one block per
+// digit (rows are counts[d * nblk .. (d + 1) * nblk)), plus the row total.
+constexpr int kScanThreads = 256;
+__global__ void __launch_bounds__(kScanThreads)
+    scan_rows_kernel(uint32_t* __restrict__ counts, int nblk, uint32_t* __restrict__ totals) {
+    __shared__ uint32_t part[kScanThreads];
+    uint32_t* row = counts + static_cast<int64_t>(blockIdx.x) * nblk;
+    const int per = (nblk + kScanThreads - 1) / kScanThreads;
+    const int b = threadIdx.x * per;
+    const int e = b + per < nblk ? b + per : nblk;
     uint32_t sum = 0u;
-    for (int64_t k = b; k < e; ++k) sum += data[k];
+    for (int k = b; k < e; ++k) sum += row[k];
     part[threadIdx.x] = sum;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
         __syncthreads();
         part[threadIdx.x] += v;
         __syncthreads();
     }
     uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
-    for (int64_t k = b; k < e; ++k) {
-        uint32_t v = data[k];
-        data[k] = run;
+    for (int k = b; k < e; ++k) {
+        const uint32_t v = row[k];
+        row[k] = run;
         run += v;
     }
+    if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = part[kScanThreads - 1];
 }
 
 // Stable scatter: item order inside a tile is (round, warp, lane), which is
@@ -222,7 +270,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ data,
 __global__ void __launch_bounds__(kSortThreads)
     radix_scatter_kernel(const uint64_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
                          uint64_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
-                         int64_t n, int shift, const uint32_t* __restrict__ offsets, int nblk) {
+                         int64_t n, int shift, const uint32_t* __restrict__ offsets,
+                         const uint32_t* __restrict__ totals, int nblk) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t base[kRadix];           // global start of each digit for this tile
     __shared__ uint32_t running[kRadix];        // items of each digit placed so far
@@ -230,8 +279,20 @@ __global__ void __launch_bounds__(kSortThreads)
     __shared__ uint32_t warp_off[kWarps][kRadix];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-        base[d] = offsets[static_cast<int64_t>(d) * nblk + blockIdx.x];
+    // digit offsets: exclusive scan of the digit totals (kRadix == blockDim.x)
+    {
+        const int d = threadIdx.x;
+        running[d] = totals[d];
+        __syncthreads();
+        for (int off = 1; off < kRadix; off <<= 1) {
+            const uint32_t v = d >= off ? running[d - off] : 0u;
+            __syncthreads();
+            running[d] += v;
+            __syncthreads();
+        }
+        const uint32_t excl = running[d] - totals[d];
+        __syncthreads();
+        base[d] = excl + offsets[static_cast<int64_t>(d) * nblk + blockIdx.x];
         running[d] = 0u;
     }
     for (int k = threadIdx.x; k < kWarps * kRadix; k += blockDim.x) (&warp_cnt[0][0])[k] = 0u;
@@ -286,7 +347,7 @@ int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 }  // namespace
 
 size_t radix_sort_temp_bytes(int64_t n_cells) {
-    return static_cast<size_t>(sort_blocks(n_cells)) * kRadix * sizeof(uint32_t);
+    return static_cast<size_t>(sort_blocks(n_cells) + 1) * kRadix * sizeof(uint32_t);
 }
 
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
@@ -304,6 +365,7 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     uint64_t* keys_b = reinterpret_cast<uint64_t*>(base + L.off_keys_out);
     int32_t* vals_b = reinterpret_cast<int32_t*>(base + L.off_vals_in);
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_sort_tmp);
+    uint32_t* totals = counts + sort_blocks(n) * kRadix;  // kRadix digit totals
 
     // header and segment table from the host (small synchronous-staging copies)
     PlanHeader h{};
@@ -342,7 +404,8 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     if (n == 0) return cudaGetLastError();
     const int tpb = 256;
     const unsigned grid = static_cast<unsigned>((n + tpb - 1) / tpb);
-    bbox_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, &hdr->status);
+    bbox_kernel<<<static_cast<unsigned>((n + kBoxItems - 1) / kBoxItems), kBoxThreads, 0, st>>>(
+        x, y, z, dim, n, segs, n_segments, &hdr->status);
     brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim);
     key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, perm);
     count_launches(3);
@@ -365,9 +428,9 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
         const int shift = 8 * p;
         radix_hist_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(kin, n, shift, counts,
                                                                                   static_cast<int>(nblk));
-        scan_kernel<<<1, 1024, 0, st>>>(counts, nblk * kRadix);
+        scan_rows_kernel<<<kRadix, kScanThreads, 0, st>>>(counts, static_cast<int>(nblk), totals);
         radix_scatter_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(
-            kin, vin, kout, vout, n, shift, counts, static_cast<int>(nblk));
+            kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
         count_launches(3);
         uint64_t* tk = kin;
         kin = kout;
