@@ -227,13 +227,24 @@ typedef struct grf_outputs {
  * table: device table (grf_upload_table) of p->n_modes modes, dim p->dim.
  * p: host; mean and sigma2 are read (porosity standardisation), the rest is
  * checked against the table.  map, out: host structs of device pointers.
+ * workspace: optional device scratch (NULL or ws_bytes too small: no mode
+ * split); see grf_synth_workspace_bytes.  Calls that share a workspace must
+ * be ordered on one stream.
  * Arithmetic: FP32 with a compensated phase split (per-warp origin with
  * hi/lo frequencies, exact path for modes whose phase span is large) and
  * compensated accumulation; the hardware cosine.  Results agree with the
- * FP64 definition to about 1e-6 sigma (max-abs).
+ * FP64 definition to a few 1e-6 sigma (max-abs).
  */
 int grf_synth_field(const void *table, const grf_params *p, const void *plan, int32_t segment,
-                    const grf_map *map, const grf_outputs *out, void *stream);
+                    const grf_map *map, const grf_outputs *out, void *workspace, size_t ws_bytes,
+                    void *stream);
+
+/* Workspace that lets grf_synth_field split the modes of a segment of
+ * n_cells cells over up to 8 groups of blocks (8 float2 per cell).  The split
+ * is used only when the segment has too few cell tiles to fill the GPU; the
+ * per-group partial sums are combined in a fixed order, so results do not
+ * depend on it beyond FP32 rounding and are reproducible. */
+size_t grf_synth_workspace_bytes(int64_t n_cells);
 
 /*
  * grf_map_property -- the maps of grf_synth_field applied to an existing

@@ -86,7 +86,9 @@ _SIGS = {
     "grf_read_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "grf_synth_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grf_params), ctypes.c_void_p,
                                        ctypes.c_int32, ctypes.POINTER(grf_map),
-                                       ctypes.POINTER(grf_outputs), ctypes.c_void_p]),
+                                       ctypes.POINTER(grf_outputs), ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_void_p]),
+    "grf_synth_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "grf_map_property": (ctypes.c_int, [ctypes.POINTER(grf_map), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(grf_outputs),
                                         ctypes.c_void_p]),

@@ -478,8 +478,14 @@ int fwd_desc(const void* table, int64_t n_modes, int32_t dim, const void* plan,
 }
 }  // namespace
 
+size_t grf_synth_workspace_bytes(int64_t n_cells) {
+    if (n_cells < 0) return 0;
+    return synth_workspace_bytes(n_cells);
+}
+
 int grf_synth_field(const void* table, const grf_params* p, const void* plan, int32_t segment,
-                    const grf_map* map, const grf_outputs* out, void* stream) {
+                    const grf_map* map, const grf_outputs* out, void* workspace, size_t ws_bytes,
+                    void* stream) {
     int rc = check_params(p);
     if (rc) return rc;
     if (!table) return fail(GRF_EINVAL, "table is NULL");
@@ -493,7 +499,8 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
                   make_map(map, out, p->mean, std::sqrt(p->sigma2)), d);
     if (rc) return rc;
     int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
-    const int err = launch_synth_fwd(d, 0, status, stream);
+    if (workspace && !aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
+    const int err = launch_synth_fwd(d, workspace, workspace ? ws_bytes : 0, status, stream);
     if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
     return GRF_OK;
 }

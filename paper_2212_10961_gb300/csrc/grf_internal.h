@@ -185,7 +185,8 @@ constexpr uint32_t kBatchMagic = 0x48435442u;  // "BTCH"
 // Kernel launchers (defined in the .cu files), all asynchronous on `stream`.
 // Return cudaError_t as int.
 // ---------------------------------------------------------------------------
-int launch_synth_fwd(const FwdDesc& d, int cells_per_cta, int32_t* status, void* stream);
+int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream);
+size_t synth_workspace_bytes(int64_t n_cells);
 int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
                          int32_t* counter, void* stream);
 int fwd_tile_cells(int cfg);

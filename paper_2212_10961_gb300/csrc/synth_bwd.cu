@@ -31,6 +31,7 @@ namespace {
 constexpr int kBwdThreads = 128;
 constexpr int kBwdTile = 256;
 constexpr int kBwdMaxSplits = 256;
+constexpr int kMPT = 2;  // modes per thread
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 struct BwdArgs {
@@ -334,18 +335,33 @@ __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
     }
 }
 
-constexpr int kMPT = 2;
-
+// Cell splits: the grid (mode_blocks x splits) should be a whole number of
+// waves of resident blocks, so that no SM idles in a partial last wave.
+template <int DIM>
 int choose_splits(int64_t n_cells, int mode_blocks) {
-    int dev = 0, sms = 148;
+    int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_partial_kernel<DIM, kMPT>, kBwdThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t resident = static_cast<int64_t>(sms) * per_sm;
     const int64_t tiles = (n_cells + kBwdTile - 1) / kBwdTile;
-    int64_t want = (static_cast<int64_t>(sms) * 8 + mode_blocks - 1) / mode_blocks;
-    if (want > tiles) want = tiles;
-    if (want > kBwdMaxSplits) want = kBwdMaxSplits;
-    if (want < 1) want = 1;
-    return static_cast<int>(want);
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int64_t s = 1; s <= kBwdMaxSplits && s <= tiles; ++s) {
+        const int64_t blocks = s * mode_blocks;
+        const int64_t waves = (blocks + resident - 1) / resident;
+        const double fill = static_cast<double>(blocks) / static_cast<double>(waves * resident);
+        // per-block work is ceil(tiles / s) tiles; penalise the imbalance too
+        const double per = static_cast<double>((tiles + s - 1) / s);
+        const double bal = static_cast<double>(tiles) / (per * s);
+        const double eff = fill * bal - 0.002 * static_cast<double>(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    return static_cast<int>(best);
 }
 
 }  // namespace
@@ -386,7 +402,14 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.gY = gY;
     a.g = g;
     const int mode_blocks = static_cast<int>((TL.n_pad + kBwdThreads * kMPT - 1) / (kBwdThreads * kMPT));
-    a.splits = n_cells > 0 ? choose_splits(n_cells, mode_blocks) : 1;
+    a.splits = 1;
+    if (n_cells > 0) {
+        switch (dim) {
+            case 1: a.splits = choose_splits<1>(n_cells, mode_blocks); break;
+            case 2: a.splits = choose_splits<2>(n_cells, mode_blocks); break;
+            default: a.splits = choose_splits<3>(n_cells, mode_blocks); break;
+        }
+    }
     const int64_t n_pad = TL.n_pad;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     a.part = reinterpret_cast<double*>(ws);

@@ -28,6 +28,7 @@ namespace grf {
 namespace {
 
 constexpr int kChunkBytes = kChunk * 48;  // hot (16 B) + cold (32 B) per mode
+constexpr int kMaxSplit = 8;              // most mode splits of one launch
 
 template <int C, int W>
 struct FwdSmem {
@@ -80,21 +81,25 @@ __device__ __forceinline__ float warp_max(float v) {
 //            (warp, mode), FP32 offsets per cell (the hot loop).
 // `uses` counts completed waits per buffer (parity tracking across tiles).
 template <int DIM, int C, int W>
-__device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, FwdSmem<C, W>& sm,
-                                           uint32_t (&uses)[2], int32_t* status) {
+__device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, int cb, int ce,
+                                           float2* partial, FwdSmem<C, W>& sm, uint32_t (&uses)[2],
+                                           int32_t* status) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t n = d.n_cells;
     const int64_t wbase = tile_base + static_cast<int64_t>(warp) * 32 * C;
     const bool warp_active = wbase < n;
-    const int n_chunks = d.n_pad / kChunk;
+    // this block's modes: chunks [cb, ce) of the table (the whole table unless
+    // the modes are split over blocks, see synth_split_finalize)
+    const int jlo = cb * kChunk;
+    const int jhi = ce * kChunk;
 
     // Prefetch the first two chunks (previous tile's buffers are free: the
     // tile ended with a block barrier).
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        issue_chunk(d, 0, sm.buf[0], &sm.full[0]);
-        if (n_chunks > 1) issue_chunk(d, 1, sm.buf[1], &sm.full[1]);
+        issue_chunk(d, cb, sm.buf[0], &sm.full[0]);
+        if (cb + 1 < ce) issue_chunk(d, cb + 1, sm.buf[1], &sm.full[1]);
     }
 
     // ---- load cells (lane-contiguous), bounding boxes, origins ------------
@@ -163,7 +168,8 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
     }
 
     // ---- super class: exact phase at every cell ---------------------------------
-    for (int j = 0; j < k_sup; ++j) {
+    const int sup_end = min(k_sup, jhi);
+    for (int j = jlo; j < sup_end; ++j) {
         const float4 c0 = __ldg(d.cold + 2 * j);
         const float4 c1 = __ldg(d.cold + 2 * j + 1);
         const float A = __ldg(&d.hot[j].w);
@@ -187,7 +193,8 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
     for (int c = 0; c < C; ++c)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - xt[k];
-    for (int j = k_sup; j < k_med; ++j) {
+    const int med_end = min(k_med, jhi);
+    for (int j = max(k_sup, jlo); j < med_end; ++j) {
         const float4 c0 = __ldg(d.cold + 2 * j);
         const float4 c1 = __ldg(d.cold + 2 * j + 1);
         const float4 h = __ldg(d.hot + j);
@@ -219,9 +226,9 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
     }
 
     // ---- light class over staged chunks ------------------------------------------
-    int ch = 0;
-    for (; ch < n_chunks; ++ch) {
-        const int bi = ch & 1;
+    int ch = cb;
+    for (; ch < ce; ++ch) {
+        const int bi = (ch - cb) & 1;
         const uint32_t parity = uses[bi] & 1u;
         bool ok = mbar_wait_bounded(&sm.full[bi], parity);
         if (!ok) {
@@ -258,7 +265,7 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         }
         __syncthreads();
         if (sm.abort_flag) break;
-        if (threadIdx.x == 0 && ch + 2 < n_chunks) {
+        if (threadIdx.x == 0 && ch + 2 < ce) {
             fence_proxy_async_smem();
             issue_chunk(d, ch + 2, sm.buf[bi], &sm.full[bi]);
         }
@@ -267,8 +274,9 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         // Give the copies still in flight (chunks ch and ch + 1) a bounded
         // chance to land before the block's shared memory is released.
         if (threadIdx.x == 0) {
-            mbar_wait_bounded(&sm.full[ch & 1], (uses[ch & 1] - 1u) & 1u);
-            if (ch + 1 < n_chunks) mbar_wait_bounded(&sm.full[(ch + 1) & 1], uses[(ch + 1) & 1] & 1u);
+            const int b0 = (ch - cb) & 1;
+            mbar_wait_bounded(&sm.full[b0], (uses[b0] - 1u) & 1u);
+            if (ch + 1 < ce) mbar_wait_bounded(&sm.full[b0 ^ 1], uses[b0 ^ 1] & 1u);
         }
         return;
     }
@@ -279,8 +287,12 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         two_sum_acc(s[c], e[c], p[c]);
         if (warp_active && valid[c]) {
             const int64_t i = lbase + c;
-            const float y = (s[c] + e[c]) + d.map.mu;
-            map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
+            if (partial != nullptr) {
+                partial[i] = make_float2(s[c], e[c]);
+            } else {
+                const float y = (s[c] + e[c]) + d.map.mu;
+                map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
+            }
         }
     }
 }
@@ -296,14 +308,38 @@ __device__ __forceinline__ void init_smem(FwdSmem<C, W>& sm) {
     __syncthreads();
 }
 
+// blockIdx.x: cell tile; blockIdx.y: mode split (gridDim.y splits of the
+// chunk range; with more than one split every block writes its TwoSum
+// partial (s, e) per sorted cell to partial[split * n_cells + i]).
 template <int DIM, int C, int W>
-__global__ void __launch_bounds__(W * 32) synth_fwd_kernel(FwdDesc d, int32_t* status) {
+__global__ void __launch_bounds__(W * 32) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FwdSmem<C, W>*>(smem_raw);
     init_smem<DIM, C, W>(sm);
     uint32_t uses[2] = {0u, 0u};
     const int64_t tile_base = static_cast<int64_t>(blockIdx.x) * (W * 32 * C);
-    synth_tile<DIM, C, W>(d, tile_base, sm, uses, status);
+    const int n_chunks = d.n_pad / kChunk;
+    const int split = blockIdx.y, n_split = gridDim.y;
+    const int cb = static_cast<int>(static_cast<int64_t>(n_chunks) * split / n_split);
+    const int ce = static_cast<int>(static_cast<int64_t>(n_chunks) * (split + 1) / n_split);
+    float2* part = n_split > 1 ? partial + static_cast<int64_t>(split) * d.n_cells : nullptr;
+    synth_tile<DIM, C, W>(d, tile_base, cb, ce, part, sm, uses, status);
+}
+
+// Combine the per-split partials of every sorted cell in split order (a
+// fixed order, so results are deterministic) and apply the maps.
+__global__ void __launch_bounds__(256) synth_split_finalize(FwdDesc d, const float2* __restrict__ partial,
+                                                            int n_split) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= d.n_cells) return;
+    float s = 0.0f, e = 0.0f;
+    for (int k = 0; k < n_split; ++k) {
+        const float2 v = partial[static_cast<int64_t>(k) * d.n_cells + i];
+        two_sum_acc(s, e, v.x);
+        e += v.y;
+    }
+    const float y = (s + e) + d.map.mu;
+    map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
 }
 
 // Persistent batched kernel: blocks pull (realisation, tile) work items from
@@ -333,14 +369,27 @@ __global__ void __launch_bounds__(W * 32) synth_batched_kernel(const FwdDesc* __
         }
         __syncthreads();
         const int64_t tile_base = static_cast<int64_t>(it.t) * (W * 32 * C);
-        synth_tile<DIM, C, W>(sm.desc, tile_base, sm, uses, status);
+        synth_tile<DIM, C, W>(sm.desc, tile_base, 0, sm.desc.n_pad / kChunk, nullptr, sm, uses, status);
         if (sm.abort_flag) break;
         __syncthreads();
     }
 }
 
+// Mode splits for a launch of `tiles` blocks: enough to fill about eight
+// waves of resident blocks, at most kMaxSplit, at least two chunks per split,
+// and only as many as the workspace holds.
+int choose_split(int64_t tiles, int n_chunks, int resident, int64_t n_cells, size_t ws_bytes) {
+    if (tiles <= 0) return 1;
+    int64_t want = (8 * static_cast<int64_t>(resident) + tiles - 1) / tiles;
+    if (want > kMaxSplit) want = kMaxSplit;
+    if (want > n_chunks / 2) want = n_chunks / 2;
+    const int64_t fits = n_cells > 0 ? static_cast<int64_t>(ws_bytes / (sizeof(float2) * n_cells)) : 0;
+    if (want > fits) want = fits;
+    return want < 2 ? 1 : static_cast<int>(want);
+}
+
 template <int DIM, int C, int W>
-int launch_fwd_cfg(const FwdDesc& d, int32_t* status, cudaStream_t st) {
+int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, cudaStream_t st) {
     const size_t smem = sizeof(FwdSmem<C, W>);
     auto kern = synth_fwd_kernel<DIM, C, W>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -349,8 +398,21 @@ int launch_fwd_cfg(const FwdDesc& d, int32_t* status, cudaStream_t st) {
     const int64_t per_cta = int64_t(W) * 32 * C;
     const int64_t grid = (d.n_cells + per_cta - 1) / per_cta;
     if (grid == 0) return cudaSuccess;
-    kern<<<static_cast<unsigned>(grid), W * 32, smem, st>>>(d, status);
+    int n_split = 1;
+    if (workspace != nullptr) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+        n_split = choose_split(grid, d.n_pad / kChunk, sms * (per_sm > 0 ? per_sm : 1), d.n_cells, ws_bytes);
+    }
+    float2* partial = static_cast<float2*>(workspace);
+    kern<<<dim3(static_cast<unsigned>(grid), n_split), W * 32, smem, st>>>(d, partial, status);
     count_launches(1);
+    if (n_split > 1) {
+        synth_split_finalize<<<static_cast<unsigned>((d.n_cells + 255) / 256), 256, 0, st>>>(d, partial, n_split);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -367,13 +429,16 @@ int fwd_tile_cells(int cfg) {
     }
 }
 
-int launch_synth_fwd(const FwdDesc& d, int cells_per_cta, int32_t* status, void* stream) {
+size_t synth_workspace_bytes(int64_t n_cells) {
+    return static_cast<size_t>(align256(int64_t(kMaxSplit) * n_cells * int64_t(sizeof(float2))));
+}
+
+int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    (void)cells_per_cta;
     switch (d.dim) {
-        case 1: return launch_fwd_cfg<1, 8, 4>(d, status, st);
-        case 2: return launch_fwd_cfg<2, 8, 4>(d, status, st);
-        case 3: return launch_fwd_cfg<3, 8, 4>(d, status, st);
+        case 1: return launch_fwd_cfg<1, 8, 4>(d, workspace, ws_bytes, status, st);
+        case 2: return launch_fwd_cfg<2, 8, 4>(d, workspace, ws_bytes, status, st);
+        case 3: return launch_fwd_cfg<3, 8, 4>(d, workspace, ws_bytes, status, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -255,15 +255,23 @@ def _outputs_struct(out):
 
 
 def synth(table: ModeTable, params: FieldParams, plan: CellPlan, segment=0, maps=None, out=None,
-          stream=None):
-    """Field and fused maps at every cell of `segment` (original cell order)."""
+          stream=None, workspace=None):
+    """Field and fused maps at every cell of `segment` (original cell order).
+
+    workspace: a Workspace for the mode split of small segments (default: a
+    module-level one; pass workspace=False for none)."""
     maps = maps or MapSpec()
     n = plan.segment_size(segment)
     if out is None:
         out = maps.allocate(n, plan.buf.device)
+    if workspace is False:
+        ws, nbytes = None, 0
+    else:
+        nbytes = int(lib().grf_synth_workspace_bytes(n))
+        ws = (workspace or _ws_fwd).get(nbytes, plan.buf.device)
     check(lib().grf_synth_field(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
                                 ctypes.byref(maps.to_c()), ctypes.byref(_outputs_struct(out)),
-                                _stream_handle(stream)))
+                                _ptr(ws), nbytes, _stream_handle(stream)))
     return out
 
 
@@ -295,6 +303,7 @@ class Workspace:
 
 _ws_bwd = Workspace()
 _ws_loss = Workspace()
+_ws_fwd = Workspace()
 
 
 def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=0, stream=None,

@@ -166,7 +166,7 @@ def test_null_and_unknown_handles_rejected(abi):
     fake_plan = ctypes.c_void_p(1 << 20)
     # unknown plan: rejected on the host before any device work
     assert L.grf_synth_field(ctypes.c_void_p(1 << 16), ctypes.byref(p), fake_plan, 0, ctypes.byref(mp),
-                             ctypes.byref(out), None) == abi.GRF_EINVAL
+                             ctypes.byref(out), None, 0, None) == abi.GRF_EINVAL
     mp.bits = abi.GRF_MAP_FACIES
     mp.n_thresholds = 2
     mp.thresholds[0], mp.thresholds[1] = 0.5, 0.1  # not ascending

@@ -69,7 +69,7 @@ def test_batched_matches_single_and_oracle(env, tile_cells):
     batch.launch()
     torch.cuda.synchronize()
     for s, (table, p, seg, maps, out) in enumerate(items):
-        single = F.synth(table, p, plan, seg, maps)
+        single = F.synth(table, p, plan, seg, maps, workspace=False)
         torch.cuda.synchronize()
         yb = out["Y"].cpu().numpy()
         ys = single["Y"].cpu().numpy()

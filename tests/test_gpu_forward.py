@@ -216,3 +216,27 @@ def test_rejects_bad_calls(env):
                                        ctypes.c_void_p(ws.data_ptr()), 1024, None)
     assert rc == _abi.GRF_EWORKSPACE
     assert plan.status() == 0
+
+
+def test_mode_split_matches_unsplit_and_oracle(env):
+    # a small segment (few cell tiles) is split over mode groups through the
+    # workspace; partials are combined in a fixed order
+    torch, F, W = env
+    cells = W.grid_centres((40, 36, 30))
+    plan = F.CellPlan(*to_dev(torch, cells))
+    p = F.FieldParams(family="exponential", sigma2=4.0, ell=(0.2, 0.2, 0.05), dim=3, n_modes=3000, seed=12)
+    gf = F.GaussianField(p)
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=(-0.5, 0.5), facies=True)
+    split = F.synth(gf.table, p, plan, 0, maps)
+    split2 = F.synth(gf.table, p, plan, 0, maps)
+    whole = F.synth(gf.table, p, plan, 0, maps, workspace=False)
+    torch.cuda.synchronize()
+    ys, yw = split["Y"].cpu().numpy(), whole["Y"].cpu().numpy()
+    assert np.array_equal(ys, split2["Y"].cpu().numpy())
+    assert np.max(np.abs(ys - yw)) <= 2e-6 * 2.0
+    om = oracle_modes("exponential", 4.0, (0.2, 0.2, 0.05), 3, 3000, 12)
+    y_or = oracle_field(om, 0.0, cells)
+    check_forward(ys, y_or, 2.0, "split")
+    check_lognormal(split["K"].cpu().numpy(), y_or, 2.0)
+    check_facies(split["facies"].cpu().numpy(), y_or, (-0.5, 0.5), 2.0)
+    assert plan.status() == 0
