@@ -18,7 +18,9 @@ Maps (Sec. 3.1 single truncation rule, Sec. 4.1 scaling, Appendix B):
 * values:     property = values[label] (Appendix B `values`);
 * porosity:   clamp(phi0 + phi1 (Y - mu)/sigma, phi_min, phi_max).  The paper
   gives no porosity formula; this affine-clamp of the standardised field is
-  the reading taken.
+  the reading taken;
+* bitruncated: two independent fields (same parameters drawn on generator
+  streams 0 and 1) and a two-dimensional truncation rule (Sec. 3.1).
 
 Adjoint of the field sum with g_i = dL/dY_i and theta_ij = 2 pi (a_j.x_i + psi_j):
 
@@ -69,6 +71,27 @@ def indicator(Y, thresholds):
     for t in thresholds:
         lab += (Y > t).astype(np.uint8)
     return lab
+
+
+def bitruncated(Y1, Y2, t, s, rule):
+    """Pluri-Gaussian (bitruncated) facies, Sec. 3.1 and Appendix B
+    `bitruncated`: i = #{m : Y1 > t_m}, j = #{m : Y2 > s_m} index one of the
+    (len(t) + 1) x (len(s) + 1) Cartesian regions of the truncation rule, and
+    rule[i][j] is the facies that region is merged into."""
+    i = indicator(Y1, t).astype(np.int64)
+    j = indicator(Y2, s).astype(np.int64)
+    return np.asarray(rule, dtype=np.uint8)[i, j]
+
+
+def region_proportions(mu1, sigma1, t, mu2, sigma2, s):
+    """p_ij = [G1(t_i) - G1(t_{i-1})] [G2(s_j) - G2(s_{j-1})] (Sec. 3.1) with
+    G the Gaussian CDF of each field, t_{-1} = s_{-1} = -inf, t_I = s_J = +inf."""
+    from scipy.stats import norm
+    tt = np.concatenate([[-np.inf], np.asarray(t, dtype=np.float64), [np.inf]])
+    ss = np.concatenate([[-np.inf], np.asarray(s, dtype=np.float64), [np.inf]])
+    p1 = np.diff(norm.cdf((tt - mu1) / sigma1))
+    p2 = np.diff(norm.cdf((ss - mu2) / sigma2))
+    return np.outer(p1, p2)
 
 
 def facies_values(labels, values):

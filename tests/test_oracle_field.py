@@ -238,3 +238,41 @@ def test_adjoint_against_finite_differences():
     assert gr["dsigma"] * 1.0 == pytest.approx(np.sum(m["amp"] * gr["dA"]), rel=1e-12)
     assert np.allclose(base["ell"] * gr["dell"], -np.sum(m["a"] * gr["da"], axis=0), rtol=1e-12)
     assert gr["dmu"] == pytest.approx(np.sum(g), rel=1e-12)
+
+
+def test_bitruncated_rule_definition():
+    from oracle import field as of
+    Y1 = np.array([-2.0, -0.1, 0.3, 0.3, 2.0, 0.0])
+    Y2 = np.array([0.0, 1.0, -1.0, 0.6, 0.6, 0.5])
+    t = [0.0, 1.0]          # 3 classes along Y1
+    s = [0.5]               # 2 classes along Y2
+    rule = [[0, 1], [2, 1], [3, 3]]
+    got = of.bitruncated(Y1, Y2, t, s, rule)
+    # (i, j): (0,0) (0,1) (1,0) (1,1) (2,1) (0,0)  -- Y == threshold goes to the lower class
+    assert got.tolist() == [0, 1, 2, 1, 3, 0]
+
+
+@pytest.mark.slow
+def test_bitruncated_proportions_over_seeds():
+    # two independent fields (streams 0 and 1 of one seed); region proportions
+    # p_ij = [G1(t_i) - G1(t_{i-1})][G2(s_j) - G2(s_{j-1})] (Sec. 3.1)
+    from oracle import field as of
+    R, n = 3000, 16
+    t = [-0.5, 0.7]
+    s = [0.2]
+    x = np.array([[0.31, 0.62]])
+    y1 = np.empty(R)
+    y2 = np.empty(R)
+    for r in range(R):
+        m1 = modes.gen_modes(spectra.GAUSSIAN, 1.0, [0.1, 0.1], 2, n, seed=90000 + r, stream=0)
+        m2 = modes.gen_modes(spectra.EXPONENTIAL, 2.0, [0.2, 0.1], 2, n, seed=90000 + r, stream=1)
+        y1[r] = field.synth(m1["a"], m1["amp"], m1["psi"], 0.0, x)[0]
+        y2[r] = field.synth(m2["a"], m2["amp"], m2["psi"], 0.5, x)[0]
+    assert abs(np.corrcoef(y1, y2)[0, 1]) < 5 / math.sqrt(R)  # independent streams
+    rule = np.arange(6).reshape(3, 2)  # every region its own facies
+    lab = of.bitruncated(y1, y2, t, s, rule)
+    p = of.region_proportions(0.0, 1.0, t, 0.5, math.sqrt(2.0), s)
+    assert p.sum() == pytest.approx(1.0, abs=1e-12)
+    counts = np.bincount(lab, minlength=6).reshape(3, 2) / R
+    se = np.sqrt(p * (1 - p) / R)
+    assert np.all(np.abs(counts - p) < 5 * se)
