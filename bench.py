@@ -36,6 +36,15 @@ sys.path.insert(0, ROOT)
 MUFU_PER_CLK_PER_SM = 16  # cos.approx results per clock per SM (SFU)
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,7 +223,56 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
            "launches_per_step": per_step, "y_seed": y_seed}
     if with_e2e:
         res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(2, steps // 3))
+        res["s1_host"] = bench_gen_modes(F, w, dim, base_seed)
+        res["map_standalone"] = bench_map(torch, F, maps, out["Y"], w, steps)
     return res
+
+
+def bench_gen_modes(F, w, dim, seed, reps=10):
+    """S1 on the host: mode drawing (grf_gen_modes) and table packing, per realisation."""
+    import ctypes
+    from paper_2212_10961_gb300 import _abi
+    p = params_for(F, w, dim, seed)
+    t0 = time.perf_counter()
+    for k in range(reps):
+        m = F.gen_modes(params_for(F, w, dim, seed + k))
+    t1 = time.perf_counter()
+    nb = _abi.lib().grf_table_bytes(p.n_modes)
+    buf = (ctypes.c_uint8 * nb)()
+    ms = F._modes_struct(p.n_modes, dim, m)
+    for k in range(reps):
+        _abi.check(_abi.lib().grf_pack_table(ctypes.byref(ms), buf, nb))
+    t2 = time.perf_counter()
+    return {"gen_modes_ms": (t1 - t0) / reps * 1e3, "pack_table_ms": (t2 - t1) / reps * 1e3,
+            "modes": p.n_modes, "note": "host C++, overlapped with the previous kernel in the step"}
+
+
+def bench_map(torch, F, maps, Y, w, steps):
+    """Standalone HBM-bound map of an existing field (grf_map_property)."""
+    sig = math.sqrt(w["sigma2"])
+    m2 = F.MapSpec(y=False, lognormal=maps.lognormal, thresholds=maps.thresholds, facies=maps.facies)
+    out = m2.allocate(Y.numel(), Y.device)
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        F.map_property(Y, m2, w["mean"], sig, out)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=Y.device)  # larger than L2
+    times = []
+    for _ in range(max(5, steps)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        F.map_property(Y, m2, w["mean"], sig, out)
+        b.record(st)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in times]))
+    nbytes = Y.numel() * (4 + (4 if m2.lognormal else 0) + (1 if m2.facies else 0))
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    peak, kind = hbm_peak()
+    return {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
+            "frac": gbs / peak, "bound": "hbm",
+            "note": "L2 flushed (256 MB write) before every launch; median of launches"}
 
 
 def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps):
@@ -311,13 +369,14 @@ def bench_batched(torch, F, W, rank, world, steps, warmup, scale):
         out = maps.allocate(segs[s], torch.device("cuda"))
         items.append((gf.table, p, s, maps, out))
         cm += float(segs[s]) * r["n_modes"]
-    batch = F.Batch(plan, items)
+    batch = F.Batch(plan, items, tile_cells="auto")
     batch.launch()
     batch.capture()
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: batch.replay())
     return {"workload": "ensemble256", "realisations": len(recipe), "cells": int(sum(segs)),
-            "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1}
+            "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1,
+            "tile_cells": batch.tile_cells, "autotune_ms": batch.tuned_ms}
 
 
 def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
@@ -469,6 +528,9 @@ def main():
         "gpu_launches": head["launches_in_timed_region"],
         "clocks": ck,
     }
+    for k in ("s1_host", "map_standalone"):
+        if k in head:
+            line[k] = head[k]
     if e2e:
         line["e2e"] = {"value": head["cell_modes_per_step"] * world / (e2e["ms_per_step"] * 1e-3) / 1e9,
                        "unit": "Gcell.mode/s", "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],

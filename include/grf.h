@@ -254,6 +254,28 @@ size_t grf_synth_workspace_bytes(int64_t n_cells);
 int grf_map_property(const grf_map *map, double mean, double sigma, int64_t n, const float *Y,
                      const grf_outputs *out, void *stream);
 
+/*
+ * Bitruncated (pluri-Gaussian) facies, Sec. 3.1 and Appendix B `bitruncated`
+ * / `thresholds2`: two independent Gaussian fields Y1, Y2 (e.g. the same
+ * parameters drawn on generator streams 0 and 1) are binned by ascending
+ * thresholds t (on Y1) and s (on Y2); region (i, j) with
+ * i = #{m : Y1 > t_m}, j = #{m : Y2 > s_m} is merged into facies rule[i][j].
+ */
+typedef struct grf_bimap {
+    int32_t n_t;                                            /* 0 .. GRF_MAX_THRESHOLDS */
+    int32_t n_s;                                            /* 0 .. GRF_MAX_THRESHOLDS */
+    float t[GRF_MAX_THRESHOLDS];                            /* ascending, Y1 units */
+    float s[GRF_MAX_THRESHOLDS];                            /* ascending, Y2 units */
+    uint8_t rule[GRF_MAX_THRESHOLDS + 1][GRF_MAX_THRESHOLDS + 1]; /* facies of region (i, j) */
+    float values[256];                                      /* prop = values[facies] */
+} grf_bimap;
+
+/* Facies (device uint8, required) and optionally prop (device float32,
+ * NULL to skip) of n cells from the two fields Y1, Y2 (device float32, same
+ * cell order).  Memory bound. */
+int grf_map_bitruncated(const grf_bimap *map, int64_t n, const float *Y1, const float *Y2,
+                        uint8_t *facies, float *prop, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* S5: adjoint                                                          */
 /* ------------------------------------------------------------------ */
@@ -342,16 +364,32 @@ size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells);
  * grf_batch_prepare -- copy the descriptors of n_items realisations and a
  * cost-ordered work list into `workspace` (H2D from host_staging, which
  * must hold grf_batch_workspace_bytes() bytes and stay valid until the copy
- * has run).  tile_cells selects the cells per work tile (0 = library
- * choice, otherwise 512, 1024 or 2048).  Call once per batch layout.
+ * has run).  tile_cells selects the cells per work item, one warp's tile
+ * (0 = library choice, otherwise 128 or 256: 4 or 8 cells per lane).  Call
+ * once per batch layout.
  */
 int grf_batch_prepare(int32_t n_items, const grf_batch_item *items, const void *plan,
                       int32_t tile_cells, void *workspace, size_t ws_bytes, void *host_staging,
                       void *stream);
 
 /*
+ * grf_batch_autotune -- choose the work-tile shape for a batch by timing it.
+ * Every candidate (256 and 128 cells per warp tile: 8 or 4 cells per lane)
+ * is prepared and launched twice on `stream` (the second
+ * launch timed with CUDA events), the fastest is written to *tile_cells and
+ * its time in milliseconds to *best_ms, and `workspace` is left prepared for
+ * it.  Results are cached in the process by batch signature (item count,
+ * total cells, total cell-modes, plan dimension), so repeated calls for the
+ * same layout only re-prepare.  Synchronises the stream; the outputs of the
+ * items are overwritten.  Same buffers as grf_batch_prepare.
+ */
+int grf_batch_autotune(int32_t n_items, const grf_batch_item *items, const void *plan,
+                       void *workspace, size_t ws_bytes, void *host_staging, void *stream,
+                       int32_t *tile_cells, float *best_ms);
+
+/*
  * grf_batch_launch -- one persistent launch synthesising every prepared
- * realisation (Eq. DiscreteFT and maps, as grf_synth_field).  Blocks pull
+ * realisation (Eq. DiscreteFT and maps, as grf_synth_field).  Warps pull
  * work tiles from a counter in `workspace`, which this call resets first
  * (a memset node plus one kernel node: safe to capture in a CUDA graph
  * and replay).

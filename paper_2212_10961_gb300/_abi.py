@@ -65,6 +65,13 @@ class grf_grads(ctypes.Structure):
                 ("dmu", ctypes.c_void_p), ("dsigma", ctypes.c_void_p), ("dell", ctypes.c_void_p)]
 
 
+class grf_bimap(ctypes.Structure):
+    _fields_ = [("n_t", ctypes.c_int32), ("n_s", ctypes.c_int32),
+                ("t", ctypes.c_float * GRF_MAX_THRESHOLDS), ("s", ctypes.c_float * GRF_MAX_THRESHOLDS),
+                ("rule", (ctypes.c_uint8 * (GRF_MAX_THRESHOLDS + 1)) * (GRF_MAX_THRESHOLDS + 1)),
+                ("values", ctypes.c_float * 256)]
+
+
 class grf_batch_item(ctypes.Structure):
     _fields_ = [("table", ctypes.c_void_p), ("n_modes", ctypes.c_int64), ("dim", ctypes.c_int32),
                 ("segment", ctypes.c_int32), ("mean", ctypes.c_double), ("sigma", ctypes.c_double),
@@ -92,6 +99,8 @@ _SIGS = {
     "grf_map_property": (ctypes.c_int, [ctypes.POINTER(grf_map), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(grf_outputs),
                                         ctypes.c_void_p]),
+    "grf_map_bitruncated": (ctypes.c_int, [ctypes.POINTER(grf_bimap), ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]),
     "grf_synth_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grf_params), ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(grf_grads),
@@ -105,6 +114,9 @@ _SIGS = {
     "grf_batch_prepare": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(grf_batch_item), ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "grf_batch_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(grf_batch_item), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "grf_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "grf_device_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "grf_launch_count": (ctypes.c_int64, []),

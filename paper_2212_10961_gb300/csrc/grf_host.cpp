@@ -171,6 +171,7 @@ struct BatchMeta {
     int32_t plan_dim;
 };
 std::unordered_map<const void*, BatchMeta> g_batches;
+std::unordered_map<std::string, std::pair<int32_t, float>> g_tuned;  // batch autotuner cache
 
 MapDev make_map(const grf_map* m, const grf_outputs* out, double mean, double sigma) {
     MapDev d{};
@@ -517,6 +518,24 @@ int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, c
     return GRF_OK;
 }
 
+int grf_map_bitruncated(const grf_bimap* map, int64_t n, const float* Y1, const float* Y2, uint8_t* facies,
+                        float* prop, void* stream) {
+    if (!map) return fail(GRF_EINVAL, "map is NULL");
+    if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
+    if (n > 0 && (!Y1 || !Y2 || !facies)) return fail(GRF_EINVAL, "Y1, Y2 or facies is NULL");
+    if (map->n_t < 0 || map->n_t > GRF_MAX_THRESHOLDS || map->n_s < 0 || map->n_s > GRF_MAX_THRESHOLDS)
+        return fail(GRF_EINVAL, "threshold counts must be in [0, %d]", GRF_MAX_THRESHOLDS);
+    for (int q = 0; q < map->n_t; ++q)
+        if (!std::isfinite(map->t[q]) || (q > 0 && !(map->t[q] > map->t[q - 1])))
+            return fail(GRF_EINVAL, "t must be finite and strictly ascending");
+    for (int q = 0; q < map->n_s; ++q)
+        if (!std::isfinite(map->s[q]) || (q > 0 && !(map->s[q] > map->s[q - 1])))
+            return fail(GRF_EINVAL, "s must be finite and strictly ascending");
+    const int err = launch_bimap(*map, n, Y1, Y2, facies, prop, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "bitruncated map kernel");
+    return GRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------
@@ -580,7 +599,7 @@ int grf_mismatch_grad(int64_t n, const float* K, const float* K_target, float* g
 // ---------------------------------------------------------------------------
 size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells) {
     if (n_items < 1 || n_cells < 0) return 0;
-    const int64_t min_tile = 512;
+    const int64_t min_tile = 128;
     const int64_t max_work = n_cells / min_tile + n_items;
     return static_cast<size_t>(256 + align256(int64_t(n_items) * int64_t(sizeof(FwdDesc))) +
                                align256(max_work * int64_t(sizeof(WorkItem))) + 256);
@@ -597,10 +616,9 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
     int cfg;
     switch (tile_cells) {
         case 0:
-        case 1024: cfg = 0; break;
-        case 2048: cfg = 1; break;
-        case 512: cfg = 2; break;
-        default: return fail(GRF_EINVAL, "tile_cells must be 0, 512, 1024 or 2048");
+        case 256: cfg = 0; break;
+        case 128: cfg = 1; break;
+        default: return fail(GRF_EINVAL, "tile_cells must be 0, 128 or 256");
     }
     const int64_t tc = fwd_tile_cells(cfg);
     const size_t need = grf_batch_workspace_bytes(n_items, meta.offsets.back());
@@ -659,6 +677,79 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
     std::lock_guard<std::mutex> lk(g_reg_mu);
     g_batches[workspace] = bm;
     return GRF_OK;
+}
+
+int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void* plan, void* workspace,
+                       size_t ws_bytes, void* host_staging, void* stream, int32_t* tile_cells,
+                       float* best_ms) {
+    if (!tile_cells || !best_ms) return fail(GRF_EINVAL, "tile_cells or best_ms is NULL");
+    if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
+    PlanMeta meta;
+    if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    // signature of the batch layout
+    double cell_modes = 0.0;
+    int64_t cells = 0;
+    for (int32_t r = 0; r < n_items; ++r) {
+        const int32_t sg = items[r].segment;
+        if (sg < 0 || sg >= static_cast<int32_t>(meta.offsets.size()) - 1)
+            return fail(GRF_EINVAL, "item %d: segment out of range", r);
+        const int64_t c = meta.offsets[sg + 1] - meta.offsets[sg];
+        cells += c;
+        cell_modes += static_cast<double>(c) * static_cast<double>(items[r].n_modes);
+    }
+    char key[160];
+    std::snprintf(key, sizeof(key), "%d/%lld/%.6e/%d", n_items, (long long)cells, cell_modes, meta.dim);
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *tile_cells = it->second.first;
+            *best_ms = it->second.second;
+            cached = true;
+        }
+    }
+    // (the registry lock is released before grf_batch_prepare takes it again)
+    if (cached)
+        return grf_batch_prepare(n_items, items, plan, *tile_cells, workspace, ws_bytes, host_staging, stream);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(GRF_ECUDA, "event creation failed");
+    const int32_t candidates[2] = {256, 128};
+    int32_t best = 0;
+    float best_t = 0.f;
+    int rc = GRF_OK;
+    for (int32_t tc : candidates) {
+        rc = grf_batch_prepare(n_items, items, plan, tc, workspace, ws_bytes, host_staging, stream);
+        if (rc) break;
+        rc = grf_batch_launch(workspace, stream);  // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        rc = grf_batch_launch(workspace, stream);
+        if (rc) break;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(GRF_ECUDA, "autotune timing failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0 || ms < best_t) {
+            best = tc;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        g_tuned[key] = std::make_pair(best, best_t);
+    }
+    *tile_cells = best;
+    *best_ms = best_t;
+    return grf_batch_prepare(n_items, items, plan, best, workspace, ws_bytes, host_staging, stream);
 }
 
 int grf_batch_launch(void* workspace, void* stream) {

@@ -191,6 +191,8 @@ int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* s
                          int32_t* counter, void* stream);
 int fwd_tile_cells(int cfg);
 int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream);
+int launch_bimap(const grf_bimap& m, int64_t n, const float* Y1, const float* Y2, uint8_t* F, float* P,
+                 void* stream);
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
                 const float* y, const float* z, void* plan, const PlanLayout& L, void* stream);
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,

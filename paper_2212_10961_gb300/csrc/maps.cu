@@ -22,6 +22,24 @@ __global__ void __launch_bounds__(kMapThreads) map_kernel(MapDev m, int64_t n,
         map_store(m, i, Y[i]);
 }
 
+// Bitruncated truncation rule (Sec. 3.1): region (i, j) of the two fields,
+// then the rule's facies and optionally its value.
+__global__ void __launch_bounds__(kMapThreads) bimap_kernel(grf_bimap m, int64_t n, const float* __restrict__ Y1,
+                                                            const float* __restrict__ Y2,
+                                                            uint8_t* __restrict__ F, float* __restrict__ P) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const float y1 = Y1[k];
+        const float y2 = Y2[k];
+        int i = 0, j = 0;
+        for (int q = 0; q < m.n_t; ++q) i += (y1 > m.t[q]) ? 1 : 0;
+        for (int q = 0; q < m.n_s; ++q) j += (y2 > m.s[q]) ? 1 : 0;
+        const uint8_t f = m.rule[i][j];
+        F[k] = f;
+        if (P != nullptr) P[k] = m.values[f];
+    }
+}
+
 // L = mean (K - T)^2, g = 2 (K - T) K / n.  Per-block FP64 partial sums go to
 // `part`; the last kernel adds them in block order (deterministic).
 __global__ void __launch_bounds__(kLossThreads)
@@ -112,6 +130,21 @@ int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream) {
     const int64_t cap = static_cast<int64_t>(sms) * 8;
     if (blocks > cap) blocks = cap;
     map_kernel<<<static_cast<unsigned>(blocks), kMapThreads, 0, st>>>(m, n, Y);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int launch_bimap(const grf_bimap& m, int64_t n, const float* Y1, const float* Y2, uint8_t* F, float* P,
+                 void* stream) {
+    if (n == 0) return cudaSuccess;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + kMapThreads - 1) / kMapThreads;
+    const int64_t cap = static_cast<int64_t>(sms) * 8;
+    if (blocks > cap) blocks = cap;
+    bimap_kernel<<<static_cast<unsigned>(blocks), kMapThreads, 0, st>>>(m, n, Y1, Y2, F, P);
     count_launches(1);
     return cudaGetLastError();
 }

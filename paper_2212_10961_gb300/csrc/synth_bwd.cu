@@ -72,107 +72,101 @@ struct DF {  // double-float accumulator
     }
 };
 
+// Per-warp shared memory: the warp's current cell tile and the compensated
+// running sums of its modes (hi, lo pairs; kept here to free registers).
+template <int MPT>
+struct BwdWarpSmem {
+    float4 cd[kBwdTile];           // (x - x0, y - y0, z - z0, g)
+    float2 acc[32 * MPT][5];       // per mode: cos, sin, sin*x, sin*y, sin*z
+};
+
+// Every warp works on its own: it owns 32 * MPT consecutive modes (MPT per
+// lane, registers) and walks the block's range of cell tiles, staging each
+// tile in its own shared memory (no block-wide barrier).  The next tile's
+// coordinates and gradients are loaded into registers while the current
+// tile is being summed.
 template <int DIM, int MPT>
-__global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, int32_t* status) {
-    __shared__ float4 cd[kBwdTile];  // (dx, dy, dz, g)
-    __shared__ float4 cx[kBwdTile];  // (x, y, z, -)
-    __shared__ float red_mn[kBwdThreads / 32][3];
-    __shared__ float red_mx[kBwdThreads / 32][3];
-    __shared__ float s_x0[3];
-    __shared__ int s_k;
-    __shared__ double s_g[kBwdThreads / 32];
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs args, int32_t* status) {
+    __shared__ BwdWarpSmem<MPT> wsm[kBwdThreads / 32];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    BwdWarpSmem<MPT>& sm = wsm[warp];
+    const int m_base = (blockIdx.x * (kBwdThreads / 32) + warp) * (32 * MPT) + lane * MPT;
+    if ((blockIdx.x * (kBwdThreads / 32) + warp) * (32 * MPT) >= args.n_pad) return;  // whole warp idle
 
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int lane = tid & 31;
-    const int m_base = blockIdx.x * (kBwdThreads * MPT) + tid * MPT;
-
-    // mode parameters (padding modes and slots past n_pad have A = 0 / skipped)
-    float4 hot[MPT], c0[MPT], c1[MPT];
+    // mode parameters (slots past n_pad are skipped; padding modes have A = 0);
+    // the hi/lo pairs (cold records) are re-read from L1 once per tile
+    float4 hot[MPT];
+    int mm[MPT];
     bool live[MPT];
 #pragma unroll
     for (int k = 0; k < MPT; ++k) {
         const int m = m_base + k;
         live[k] = m < args.n_pad;
-        const int mm = live[k] ? m : 0;
-        hot[k] = args.hot[mm];
-        c0[k] = args.cold[2 * mm];
-        c1[k] = args.cold[2 * mm + 1];
-    }
-    DF accC[MPT], accS[MPT], accX[MPT][3];
+        mm[k] = live[k] ? m : 0;
+        hot[k] = __ldg(args.hot + mm[k]);
 #pragma unroll
-    for (int k = 0; k < MPT; ++k) {
-        accC[k] = DF{0.f, 0.f};
-        accS[k] = DF{0.f, 0.f};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) accX[k][c] = DF{0.f, 0.f};
+        for (int q = 0; q < 5; ++q) sm.acc[lane * MPT + k][q] = make_float2(0.f, 0.f);
     }
     double gsum = 0.0;
+    const bool count_g = blockIdx.x == 0 && warp == 0;  // one warp per split sums g
 
     const int64_t n = args.n_cells;
     const int64_t n_tiles = (n + kBwdTile - 1) / kBwdTile;
     const int64_t per_split = (n_tiles + args.splits - 1) / args.splits;
     const int64_t t_begin = blockIdx.y * per_split;
     const int64_t t_end = t_begin + per_split < n_tiles ? t_begin + per_split : n_tiles;
+    constexpr int kPer = kBwdTile / 32;  // cells per lane per tile
 
-    for (int64_t t = t_begin; t < t_end; ++t) {
+    // registers holding the next tile (cells lane + 32 q)
+    float xv[kPer][3];
+    float gv[kPer];
+    auto load_tile = [&](int64_t t) {
         const int64_t tb = t * kBwdTile;
-        // ---- stage the tile ----------------------------------------------------
-        float xv[2][3];
-        float gv[2];
-        float mn[3], mx[3];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int64_t i = tb + q * kBwdThreads + tid;
+        for (int q = 0; q < kPer; ++q) {
+            const int64_t i = tb + q * 32 + lane;
             const bool in = i < n;
             const int64_t ii = in ? i : tb;
-            xv[q][0] = args.xs[ii];
-            xv[q][1] = DIM > 1 ? args.ys[ii] : 0.f;
-            xv[q][2] = DIM > 2 ? args.zs[ii] : 0.f;
-            gv[q] = in ? args.gY[static_cast<int64_t>(args.perm[i]) - args.perm_base] : 0.f;
+            xv[q][0] = __ldg(args.xs + ii);
+            xv[q][1] = DIM > 1 ? __ldg(args.ys + ii) : 0.f;
+            xv[q][2] = DIM > 2 ? __ldg(args.zs + ii) : 0.f;
+            gv[q] = in ? __ldg(args.gY + (static_cast<int64_t>(__ldg(args.perm + i)) - args.perm_base)) : 0.f;
         }
+    };
+    if (t_begin < t_end) load_tile(t_begin);
+
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        // ---- bounding box and origin of the tile (warp-wide) -----------------
+        float x0[3] = {0.f, 0.f, 0.f};
+        float E = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            mn[c] = fminf(xv[0][c], xv[1][c]);
-            mx[c] = fmaxf(xv[0][c], xv[1][c]);
+        for (int c = 0; c < DIM; ++c) {
+            float mn = xv[0][c], mx = xv[0][c];
+#pragma unroll
+            for (int q = 1; q < kPer; ++q) {
+                mn = fminf(mn, xv[q][c]);
+                mx = fmaxf(mx, xv[q][c]);
+            }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
-                mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
             }
-            if (lane == 0) {
-                red_mn[warp][c] = mn[c];
-                red_mx[warp][c] = mx[c];
-            }
+            x0[c] = 0.5f * mn + 0.5f * mx;
+            E = fmaxf(E, fmaxf(mx - x0[c], x0[c] - mn));
         }
-        if (blockIdx.x == 0) gsum += static_cast<double>(gv[0]) + static_cast<double>(gv[1]);
-        __syncthreads();
-        if (tid == 0) {
-            float E = 0.f;
-            for (int c = 0; c < DIM; ++c) {
-                float a = red_mn[0][c], b = red_mx[0][c];
-                for (int w = 1; w < kBwdThreads / 32; ++w) {
-                    a = fminf(a, red_mn[w][c]);
-                    b = fmaxf(b, red_mx[w][c]);
-                }
-                const float o = 0.5f * a + 0.5f * b;
-                s_x0[c] = o;
-                E = fmaxf(E, fmaxf(b - o, o - a));
-            }
-            for (int c = DIM; c < 3; ++c) s_x0[c] = 0.f;
-            const int bk = bucket_of_bwd(E);
-            s_k = bk >= kBuckets ? args.n_pad : args.kpref[bk];
-        }
-        __syncthreads();
-        const float x0[3] = {s_x0[0], s_x0[1], s_x0[2]};
-        const int k_heavy = s_k;
+        const int bk = bucket_of_bwd(E);
+        const int k_heavy = bk >= kBuckets ? args.n_pad : __ldg(args.kpref + bk);
+        __syncwarp();  // the previous tile's shared data is no longer read
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = q * kBwdThreads + tid;
-            cd[idx] = make_float4(xv[q][0] - x0[0], xv[q][1] - x0[1], xv[q][2] - x0[2], gv[q]);
-            cx[idx] = make_float4(xv[q][0], xv[q][1], xv[q][2], 0.f);
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = q * 32 + lane;
+            sm.cd[idx] = make_float4(xv[q][0] - x0[0], xv[q][1] - x0[1], xv[q][2] - x0[2], gv[q]);
+            if (count_g) gsum += static_cast<double>(gv[q]);
         }
-        __syncthreads();
+        __syncwarp();
+        if (t + 1 < t_end) load_tile(t + 1);  // overlaps with the sums below
 
         // ---- per-mode sums over the tile ------------------------------------------
         const bool any_heavy = m_base < k_heavy;
@@ -183,12 +177,13 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, 
             sc[k] = 0.f;
             ss[k] = 0.f;
             sx[k][0] = sx[k][1] = sx[k][2] = 0.f;
-            t0[k] = kTwoPiF * phase_exact_turns<DIM>(x0, c0[k], c1[k]);
+            t0[k] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(args.cold + 2 * mm[k]),
+                                                      __ldg(args.cold + 2 * mm[k] + 1));
         }
-        if (!any_heavy) {
-#pragma unroll 2
+        if (!__any_sync(0xffffffffu, any_heavy)) {
+#pragma unroll 4
             for (int i = 0; i < kBwdTile; ++i) {
-                const float4 c = cd[i];
+                const float4 c = sm.cd[i];
 #pragma unroll
                 for (int k = 0; k < MPT; ++k) {
                     float th = fmaf(hot[k].x, c.x, t0[k]);
@@ -205,16 +200,21 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, 
                 }
             }
         } else {
+            const int64_t tb = t * kBwdTile;
 #pragma unroll
             for (int k = 0; k < MPT; ++k) {
                 const bool heavy = (m_base + k) < k_heavy;
+                const float4 c0 = __ldg(args.cold + 2 * mm[k]);
+                const float4 c1 = __ldg(args.cold + 2 * mm[k] + 1);
                 for (int i = 0; i < kBwdTile; ++i) {
-                    const float4 c = cd[i];
+                    const float4 c = sm.cd[i];
                     float th;
                     if (heavy) {
-                        const float4 xx = cx[i];
-                        const float xa[3] = {xx.x, xx.y, xx.z};
-                        th = kTwoPiF * phase_exact_turns<DIM>(xa, c0[k], c1[k]);
+                        // exact coordinates re-read (the staged offsets are rounded)
+                        const int64_t ii = tb + i < n ? tb + i : tb;
+                        const float xa[3] = {__ldg(args.xs + ii), DIM > 1 ? __ldg(args.ys + ii) : 0.f,
+                                             DIM > 2 ? __ldg(args.zs + ii) : 0.f};
+                        th = kTwoPiF * phase_exact_turns<DIM>(xa, c0, c1);
                     } else {
                         th = fmaf(hot[k].x, c.x, t0[k]);
                         if (DIM > 1) th = fmaf(hot[k].y, c.y, th);
@@ -233,15 +233,16 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, 
         }
 #pragma unroll
         for (int k = 0; k < MPT; ++k) {
-            accC[k].add(sc[k]);
-            accS[k].add(ss[k]);
+            float2* a = sm.acc[lane * MPT + k];
+            const float v[5] = {sc[k], ss[k], sx[k][0], sx[k][1], sx[k][2]};
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-                accX[k][c].add(sx[k][c]);
-                accX[k][c].add(x0[c] * ss[k]);
+            for (int q = 0; q < 2 + DIM; ++q) {
+                float2 r = a[q];
+                two_sum_acc(r.x, r.y, v[q]);
+                if (q >= 2) two_sum_acc(r.x, r.y, x0[q - 2] * ss[k]);
+                a[q] = r;
             }
         }
-        __syncthreads();
     }
 
     // ---- write FP64 partials ---------------------------------------------------------
@@ -250,21 +251,14 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_partial_kernel(BwdArgs args, 
         if (!live[k]) continue;
         const int m = m_base + k;
         double* o = args.part + (static_cast<int64_t>(blockIdx.y) * args.n_pad + m) * 5;
-        o[0] = accC[k].value();
-        o[1] = accS[k].value();
-        o[2] = accX[k][0].value();
-        o[3] = DIM > 1 ? accX[k][1].value() : 0.0;
-        o[4] = DIM > 2 ? accX[k][2].value() : 0.0;
+        const float2* a = sm.acc[lane * MPT + k];
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            o[q] = q < 2 + DIM ? static_cast<double>(a[q].x) + static_cast<double>(a[q].y) : 0.0;
     }
-    if (blockIdx.x == 0) {
+    if (count_g) {
         for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
-        if (lane == 0) s_g[warp] = gsum;
-        __syncthreads();
-        if (tid == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < kBwdThreads / 32; ++w) tot += s_g[w];
-            args.gpart[blockIdx.y] = tot;
-        }
+        if (lane == 0) args.gpart[blockIdx.y] = gsum;
     }
     (void)status;
 }

@@ -3,22 +3,25 @@
 // Eq. DiscreteFT), with the property maps of Sec. 3.1 / Sec. 4.1 fused into
 // the epilogue.
 //
-// Work decomposition.  Cells arrive spatially sorted (cell plan).  A warp owns
-// 32*C consecutive sorted cells (C per lane, in registers) and takes the
-// midpoint of their bounding box as its origin x0, with half-extent E.  The
-// phase of mode j at cell i is split as
-//     theta_ij = 2 pi (a_j . x0 + psi_j  mod 1)  +  (2 pi a_j) . (x_i - x0),
-// the first term computed once per (warp, mode) in compensated FP32
-// (phase_exact_turns), the second per cell-mode with three FFMAs.  Modes whose
-// phase span over the warp, |a_j|_1 * E, exceeds tau turns (a prefix of the
-// table, which is sorted by |a_j|_1) take the exact per-cell path instead.
-// The hot loop is one MUFU cosine, one FMUL (radian scaling inside
-// cos.approx), DIM FFMAs for the phase and one FFMA to accumulate.
+// Work decomposition.  Cells arrive spatially sorted (cell plan, Z-order).
+// Every warp works on its own: it owns 32*C consecutive sorted cells (C per
+// lane, in registers), takes the midpoint of their bounding box as origin x0
+// (half-extent E), and streams the mode table through its own two shared-
+// memory buffers filled by 1-D bulk copies completed on its own mbarriers.
+// There is no block-wide barrier, so warps never wait for one another.
 //
-// Mode chunks (kChunk modes, 48 B each) are staged in shared memory by 1-D
-// bulk copies into two buffers completed on mbarriers; every wait is bounded
-// and reports GRF_ETIMEOUT through the status word instead of hanging.
-// Per-chunk FP32 partials are folded into a TwoSum-compensated accumulator.
+// Phase split.  For mode j at cell i
+//     theta_ij = 2 pi frac(a_j . x0 + psi_j)  +  (2 pi a_j) . (x_i - x0),
+// the first term once per (warp, mode) in compensated FP32
+// (phase_exact_turns), the second per cell-mode with DIM FFMAs.  Three classes
+// of modes, all prefixes of the table (sorted by |a|_1, descending):
+//   super  : span over the lane's block > tau2 turns -> exact phase per cell;
+//   medium : span over the warp's block > tau1 turns -> exact phase at the
+//            lane origin xt once per (lane, mode), FP32 offsets per cell;
+//   light  : the rest, the hot loop: DIM FFMA, 1 FMUL (radian scaling inside
+//            cos.approx), 1 MUFU cosine, 1 FFMA accumulate per cell-mode.
+// Per-chunk FP32 partials are folded into TwoSum-compensated accumulators.
+// Every mbarrier wait is bounded and reports through the status word.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -27,24 +30,39 @@ namespace grf {
 
 namespace {
 
-constexpr int kChunkBytes = kChunk * 48;  // hot (16 B) + cold (32 B) per mode
-constexpr int kMaxSplit = 8;              // most mode splits of one launch
+constexpr int kWChunk = 128;                 // modes per warp chunk
+constexpr int kWChunkBytes = kWChunk * 16;   // hot records only (16 B per mode)
+constexpr int kStages = 3;                   // chunk buffers per warp (prefetch distance 2)
+constexpr int kMaxSplit = 8;                 // most mode splits of one launch
+static_assert(kChunk % kWChunk == 0, "table padding must be a multiple of the warp chunk");
 
-template <int C, int W>
-struct FwdSmem {
-    float4 buf[2][kChunk * 3];  // [hot kChunk][cold 2*kChunk]
-    float t0[W][kChunk];        // per-warp origin phase (radians)
-    uint64_t full[2];
-    int32_t abort_flag;
-    int32_t work;               // batched: current work index
-    FwdDesc desc;               // batched: current descriptor
+// Shared memory of one warp: a ring of hot-record chunks filled by bulk
+// copies, and the warp-origin phases of the current chunk.  The hi/lo
+// records needed for those phases are read through L1 by the lanes.
+struct WarpSmem {
+    float4 buf[kStages][kWChunk];  // (2 pi a_x, 2 pi a_y, 2 pi a_z, A)
+    float t0[kWChunk];             // warp-origin phase of the chunk's modes (radians)
+    uint64_t full[kStages];
 };
 
-// Issue the bulk copies of chunk `ch` of descriptor d into buffer `bi`.
-__device__ __forceinline__ void issue_chunk(const FwdDesc& d, int ch, float4* dst, uint64_t* bar) {
-    mbar_arrive_expect_tx(bar, kChunkBytes);
-    bulk_g2s(dst, d.hot + static_cast<int64_t>(ch) * kChunk, kChunk * 16, bar);
-    bulk_g2s(dst + kChunk, d.cold + static_cast<int64_t>(ch) * kChunk * 2, kChunk * 32, bar);
+template <int W>
+struct FwdSmem {
+    WarpSmem w[W];
+    FwdDesc desc[W];  // batched: each warp's current realisation
+};
+
+__device__ __forceinline__ void warp_init_barriers(WarpSmem& ws) {
+    if ((threadIdx.x & 31) == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&ws.full[b], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+}
+
+// Lane 0: bulk copy of the hot records of warp chunk `ch` into buffer b.
+__device__ __forceinline__ void issue_wchunk(const FwdDesc& d, int ch, WarpSmem& ws, int b) {
+    mbar_arrive_expect_tx(&ws.full[b], kWChunkBytes);
+    bulk_g2s(ws.buf[b], d.hot + static_cast<int64_t>(ch) * kWChunk, kWChunkBytes, &ws.full[b]);
 }
 
 // Conservative extent bucket: smallest b with 2^((b - bias)/4) >= E (one
@@ -58,7 +76,6 @@ __device__ __forceinline__ int prefix_for(const int32_t* kpref, int n_pad, float
     return b < 0 ? 0 : __ldg(kpref + b);
 }
 
-// Warp-wide min / max.
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -70,36 +87,25 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// One tile: W warps x 32 lanes x C cells starting at sorted cell `tile_base`.
-// Lane l of a warp owns the C consecutive sorted cells wbase + C l + c, a
-// compact block of the Z-order (2x2x2 for C = 8).  Three classes of modes,
-// all prefixes of the table (sorted by |a|_1, descending):
-//   super  : span over the lane's block > tau2 turns -> exact phase per cell;
-//   medium : span over the warp's block > tau1 turns -> exact phase at the
-//            lane origin xt once per (lane, mode), FP32 offsets per cell;
-//   light  : the rest -> exact phase at the warp origin x0 once per
-//            (warp, mode), FP32 offsets per cell (the hot loop).
-// `uses` counts completed waits per buffer (parity tracking across tiles).
-template <int DIM, int C, int W>
-__device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, int cb, int ce,
-                                           float2* partial, FwdSmem<C, W>& sm, uint32_t (&uses)[2],
-                                           int32_t* status) {
-    const int warp = threadIdx.x >> 5;
+// One warp tile: the 32*C sorted cells starting at wbase, modes of warp
+// chunks [cb, ce).  `uses` counts completed waits per buffer (parity across
+// tiles).  Returns false if a bounded wait expired (status bit 2 set).
+// With `partial` the TwoSum pair (s, e) of every cell is written to
+// partial[i] instead of the maps (mode split over blocks).
+template <int DIM, int C>
+__device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase, int cb, int ce,
+                                                float2* partial, WarpSmem& ws, uint32_t (&uses)[kStages],
+                                                int32_t* status) {
     const int lane = threadIdx.x & 31;
     const int64_t n = d.n_cells;
-    const int64_t wbase = tile_base + static_cast<int64_t>(warp) * 32 * C;
-    const bool warp_active = wbase < n;
-    // this block's modes: chunks [cb, ce) of the table (the whole table unless
-    // the modes are split over blocks, see synth_split_finalize)
-    const int jlo = cb * kChunk;
-    const int jhi = ce * kChunk;
+    const int jlo = cb * kWChunk;
+    const int jhi = ce * kWChunk;
 
-    // Prefetch the first two chunks (previous tile's buffers are free: the
-    // tile ended with a block barrier).
-    if (threadIdx.x == 0) {
+    // Prefetch the first chunks (this warp's buffers are free: its previous
+    // tile waited for every copy it issued).
+    if (lane == 0) {
         fence_proxy_async_smem();
-        issue_chunk(d, cb, sm.buf[0], &sm.full[0]);
-        if (cb + 1 < ce) issue_chunk(d, cb + 1, sm.buf[1], &sm.full[1]);
+        for (int q = 0; q < kStages - 1 && cb + q < ce; ++q) issue_wchunk(d, cb + q, ws, q);
     }
 
     // ---- load cells (lane-contiguous), bounding boxes, origins ------------
@@ -108,7 +114,6 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
     bool valid[C];
     {
         const float* src[3] = {d.xs, d.ys, d.zs};
-        const int64_t safe = warp_active ? wbase : 0;  // a valid cell of this warp
 #pragma unroll
         for (int c = 0; c < C; ++c) valid[c] = lbase + c < n;
 #pragma unroll
@@ -129,7 +134,7 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
             } else {
                 // ragged tail: invalid cells repeat the lane's first valid cell
                 // (or the warp's first cell) so that bounding boxes are unaffected
-                const int64_t first = lbase < n ? lbase : safe;
+                const int64_t first = lbase < n ? lbase : wbase;
 #pragma unroll
                 for (int c = 0; c < C; ++c) x[c][k] = __ldg(src[k] + (valid[c] ? lbase + c : first));
             }
@@ -153,11 +158,8 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
         Ew = fmaxf(Ew, fmaxf(mx - x0[k], x0[k] - mn));
     }
     Et = warp_max(Et);
-    int k_med = 0, k_sup = 0;
-    if (warp_active) {
-        k_med = prefix_for(d.kpref, d.n_pad, Ew * d.inv_tau1);
-        k_sup = min(k_med, prefix_for(d.kpref, d.n_pad, Et * d.inv_tau2));
-    }
+    const int k_med = prefix_for(d.kpref, d.n_pad, Ew * d.inv_tau1);
+    const int k_sup = min(k_med, prefix_for(d.kpref, d.n_pad, Et * d.inv_tau2));
 
     float s[C], e[C], p[C];
 #pragma unroll
@@ -225,30 +227,33 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
             for (int k = 0; k < DIM; ++k) dx[c][k] += D[k];
     }
 
-    // ---- light class over staged chunks ------------------------------------------
+    // ---- light class over this warp's staged chunks ------------------------------
+    bool ok = true;
     int ch = cb;
     for (; ch < ce; ++ch) {
-        const int bi = (ch - cb) & 1;
-        const uint32_t parity = uses[bi] & 1u;
-        bool ok = mbar_wait_bounded(&sm.full[bi], parity);
-        if (!ok) {
-            sm.abort_flag = 1;
-            atomicOr(status, 2);
+        const int b = (ch - cb) % kStages;
+        // keep kStages - 1 chunks in flight: refill the buffer freed last
+        if (lane == 0 && ch + kStages - 1 < ce) {
+            fence_proxy_async_smem();
+            issue_wchunk(d, ch + kStages - 1, ws, (ch - cb + kStages - 1) % kStages);
         }
-        uses[bi] += 1;
-        const float4* hotS = sm.buf[bi];
-        const float4* coldS = sm.buf[bi] + kChunk;
-        float* t0S = sm.t0[warp];
-        const int jbase = ch * kChunk;
-        if (ok && warp_active && jbase + kChunk > k_med) {
+        const uint32_t parity = uses[b] & 1u;
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ws.full[b], parity));
+        uses[b] += 1;
+        if (!ok) break;
+        const float4* hotS = ws.buf[b];
+        const int jbase = ch * kWChunk;
+        if (jbase + kWChunk > k_med) {
             const int m0 = k_med > jbase ? k_med - jbase : 0;
-            for (int m = m0 + lane; m < kChunk; m += 32)
-                t0S[m] = kTwoPiF * phase_exact_turns<DIM>(x0, coldS[2 * m], coldS[2 * m + 1]);
+            for (int m = m0 + lane; m < kWChunk; m += 32) {
+                const int j = jbase + m;
+                ws.t0[m] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
+            }
             __syncwarp();
 #pragma unroll 4
-            for (int m = m0; m < kChunk; ++m) {
+            for (int m = m0; m < kWChunk; ++m) {
                 const float4 h = hotS[m];
-                const float t0 = t0S[m];
+                const float t0 = ws.t0[m];
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     float th = fmaf(h.x, dx[c][0], t0);
@@ -263,29 +268,27 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
                 p[c] = 0.0f;
             }
         }
-        __syncthreads();
-        if (sm.abort_flag) break;
-        if (threadIdx.x == 0 && ch + 2 < ce) {
-            fence_proxy_async_smem();
-            issue_chunk(d, ch + 2, sm.buf[bi], &sm.full[bi]);
-        }
+        __syncwarp();  // every lane is done with buffer b and t0
     }
-    if (sm.abort_flag) {
-        // Give the copies still in flight (chunks ch and ch + 1) a bounded
-        // chance to land before the block's shared memory is released.
-        if (threadIdx.x == 0) {
-            const int b0 = (ch - cb) & 1;
-            mbar_wait_bounded(&sm.full[b0], (uses[b0] - 1u) & 1u);
-            if (ch + 1 < ce) mbar_wait_bounded(&sm.full[b0 ^ 1], uses[b0 ^ 1] & 1u);
+    if (!ok) {
+        // Give the copies still in flight (chunks ch .. ch + kStages - 1) a
+        // bounded chance to land before this warp's shared memory is reused.
+        if (lane == 0) {
+            atomicOr(status, 2);
+            for (int q = 0; q < kStages && ch + q < ce; ++q) {
+                const int bq = (ch - cb + q) % kStages;
+                mbar_wait_bounded(&ws.full[bq], (q == 0 ? uses[bq] - 1u : uses[bq]) & 1u);
+            }
         }
-        return;
+        __syncwarp();
+        return false;
     }
 
     // ---- epilogue: field value and fused maps ------------------------------------
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         two_sum_acc(s[c], e[c], p[c]);
-        if (warp_active && valid[c]) {
+        if (valid[c]) {
             const int64_t i = lbase + c;
             if (partial != nullptr) {
                 partial[i] = make_float2(s[c], e[c]);
@@ -295,35 +298,28 @@ __device__ __forceinline__ void synth_tile(const FwdDesc& d, int64_t tile_base, 
             }
         }
     }
+    return true;
 }
 
-template <int DIM, int C, int W>
-__device__ __forceinline__ void init_smem(FwdSmem<C, W>& sm) {
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.full[0], 1);
-        mbar_init(&sm.full[1], 1);
-        sm.abort_flag = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-}
-
-// blockIdx.x: cell tile; blockIdx.y: mode split (gridDim.y splits of the
-// chunk range; with more than one split every block writes its TwoSum
+// blockIdx.x: W warp tiles; blockIdx.y: mode split (gridDim.y splits of the
+// warp-chunk range; with more than one split every warp writes its TwoSum
 // partial (s, e) per sorted cell to partial[split * n_cells + i]).
 template <int DIM, int C, int W>
-__global__ void __launch_bounds__(W * 32) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
+__global__ void __launch_bounds__(W * 32, 6) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<FwdSmem<C, W>*>(smem_raw);
-    init_smem<DIM, C, W>(sm);
-    uint32_t uses[2] = {0u, 0u};
-    const int64_t tile_base = static_cast<int64_t>(blockIdx.x) * (W * 32 * C);
-    const int n_chunks = d.n_pad / kChunk;
+    auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    WarpSmem& ws = sm.w[warp];
+    warp_init_barriers(ws);
+    const int64_t wbase = (static_cast<int64_t>(blockIdx.x) * W + warp) * (32 * C);
+    if (wbase >= d.n_cells) return;
+    uint32_t uses[kStages] = {};
+    const int n_chunks = d.n_pad / kWChunk;
     const int split = blockIdx.y, n_split = gridDim.y;
     const int cb = static_cast<int>(static_cast<int64_t>(n_chunks) * split / n_split);
     const int ce = static_cast<int>(static_cast<int64_t>(n_chunks) * (split + 1) / n_split);
     float2* part = n_split > 1 ? partial + static_cast<int64_t>(split) * d.n_cells : nullptr;
-    synth_tile<DIM, C, W>(d, tile_base, cb, ce, part, sm, uses, status);
+    synth_warp_tile<DIM, C>(d, wbase, cb, ce, part, ws, uses, status);
 }
 
 // Combine the per-split partials of every sorted cell in split order (a
@@ -342,42 +338,45 @@ __global__ void __launch_bounds__(256) synth_split_finalize(FwdDesc d, const flo
     map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
 }
 
-// Persistent batched kernel: blocks pull (realisation, tile) work items from
-// a counter until the list is exhausted.  DIM is the plan's dimension; a
-// realisation of lower dimension has zero frequencies on the extra axes.
+// Persistent batched kernel: every warp pulls (realisation, warp tile) work
+// items from a counter until the list is exhausted.  DIM is the plan's
+// dimension; a realisation of lower dimension has zero frequencies on the
+// extra axes.
 template <int DIM, int C, int W>
-__global__ void __launch_bounds__(W * 32) synth_batched_kernel(const FwdDesc* __restrict__ descs,
+__global__ void __launch_bounds__(W * 32, 5) synth_batched_kernel(const FwdDesc* __restrict__ descs,
                                                                 const WorkItem* __restrict__ work,
                                                                 int32_t n_work, int32_t* counter,
                                                                 int32_t* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<FwdSmem<C, W>*>(smem_raw);
-    init_smem<DIM, C, W>(sm);
-    uint32_t uses[2] = {0u, 0u};
+    auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    WarpSmem& ws = sm.w[warp];
+    FwdDesc& d = sm.desc[warp];
+    warp_init_barriers(ws);
+    uint32_t uses[kStages] = {};
     for (;;) {
-        if (threadIdx.x == 0) sm.work = atomicAdd(counter, 1);
-        __syncthreads();
-        const int w = sm.work;
+        int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= n_work) break;
         const WorkItem it = work[w];
-        // copy the descriptor into shared memory (word by word)
         {
-            const int nwords = static_cast<int>(sizeof(FwdDesc) / 4);
+            constexpr int kWords = static_cast<int>(sizeof(FwdDesc) / 4);
             const int32_t* src = reinterpret_cast<const int32_t*>(descs + it.r);
-            int32_t* dst = reinterpret_cast<int32_t*>(&sm.desc);
-            for (int k = threadIdx.x; k < nwords; k += blockDim.x) dst[k] = src[k];
+            int32_t* dst = reinterpret_cast<int32_t*>(&d);
+            for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
         }
-        __syncthreads();
-        const int64_t tile_base = static_cast<int64_t>(it.t) * (W * 32 * C);
-        synth_tile<DIM, C, W>(sm.desc, tile_base, 0, sm.desc.n_pad / kChunk, nullptr, sm, uses, status);
-        if (sm.abort_flag) break;
-        __syncthreads();
+        __syncwarp();
+        const int64_t wbase = static_cast<int64_t>(it.t) * (32 * C);
+        if (!synth_warp_tile<DIM, C>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status)) break;
+        __syncwarp();  // every lane is done with the descriptor
     }
 }
 
 // Mode splits for a launch of `tiles` blocks: enough to fill about eight
-// waves of resident blocks, at most kMaxSplit, at least two chunks per split,
-// and only as many as the workspace holds.
+// waves of resident blocks, at most kMaxSplit, at least two warp chunks per
+// split, and only as many as the workspace holds.
 int choose_split(int64_t tiles, int n_chunks, int resident, int64_t n_cells, size_t ws_bytes) {
     if (tiles <= 0) return 1;
     int64_t want = (8 * static_cast<int64_t>(resident) + tiles - 1) / tiles;
@@ -390,7 +389,7 @@ int choose_split(int64_t tiles, int n_chunks, int resident, int64_t n_cells, siz
 
 template <int DIM, int C, int W>
 int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, cudaStream_t st) {
-    const size_t smem = sizeof(FwdSmem<C, W>);
+    const size_t smem = sizeof(FwdSmem<W>);
     auto kern = synth_fwd_kernel<DIM, C, W>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
@@ -404,7 +403,7 @@ int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
-        n_split = choose_split(grid, d.n_pad / kChunk, sms * (per_sm > 0 ? per_sm : 1), d.n_cells, ws_bytes);
+        n_split = choose_split(grid, d.n_pad / kWChunk, sms * (per_sm > 0 ? per_sm : 1), d.n_cells, ws_bytes);
     }
     float2* partial = static_cast<float2*>(workspace);
     kern<<<dim3(static_cast<unsigned>(grid), n_split), W * 32, smem, st>>>(d, partial, status);
@@ -416,38 +415,10 @@ int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* 
     return cudaGetLastError();
 }
 
-}  // namespace
-
-// Configuration used by the single-realisation path: C = 8 cells per lane,
-// W = 4 warps (1024 cells per block).
-int fwd_tile_cells(int cfg) {
-    switch (cfg) {
-        case 0: return 4 * 32 * 8;
-        case 1: return 8 * 32 * 8;
-        case 2: return 4 * 32 * 4;
-        default: return 0;
-    }
-}
-
-size_t synth_workspace_bytes(int64_t n_cells) {
-    return static_cast<size_t>(align256(int64_t(kMaxSplit) * n_cells * int64_t(sizeof(float2))));
-}
-
-int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    switch (d.dim) {
-        case 1: return launch_fwd_cfg<1, 8, 4>(d, workspace, ws_bytes, status, st);
-        case 2: return launch_fwd_cfg<2, 8, 4>(d, workspace, ws_bytes, status, st);
-        case 3: return launch_fwd_cfg<3, 8, 4>(d, workspace, ws_bytes, status, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-namespace {
 template <int DIM, int C, int W>
-int launch_batched_cfg(const FwdDesc* descs, const WorkItem* work, int32_t n_work,
-                       int32_t* counter, int32_t* status, cudaStream_t st) {
-    const size_t smem = sizeof(FwdSmem<C, W>);
+int launch_batched_cfg(const FwdDesc* descs, const WorkItem* work, int32_t n_work, int32_t* counter,
+                       int32_t* status, cudaStream_t st) {
+    const size_t smem = sizeof(FwdSmem<W>);
     auto kern = synth_batched_kernel<DIM, C, W>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
@@ -467,12 +438,35 @@ int launch_batched_dim(int cfg, const FwdDesc* descs, const WorkItem* work, int3
                        int32_t* counter, int32_t* status, cudaStream_t st) {
     switch (cfg) {
         case 0: return launch_batched_cfg<DIM, 8, 4>(descs, work, n_work, counter, status, st);
-        case 1: return launch_batched_cfg<DIM, 8, 8>(descs, work, n_work, counter, status, st);
-        case 2: return launch_batched_cfg<DIM, 4, 4>(descs, work, n_work, counter, status, st);
+        case 1: return launch_batched_cfg<DIM, 4, 4>(descs, work, n_work, counter, status, st);
         default: return cudaErrorInvalidValue;
     }
 }
+
 }  // namespace
+
+// Cells per work item (one warp tile) of the batched configurations.
+int fwd_tile_cells(int cfg) {
+    switch (cfg) {
+        case 0: return 32 * 8;
+        case 1: return 32 * 4;
+        default: return 0;
+    }
+}
+
+size_t synth_workspace_bytes(int64_t n_cells) {
+    return static_cast<size_t>(align256(int64_t(kMaxSplit) * n_cells * int64_t(sizeof(float2))));
+}
+
+int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (d.dim) {
+        case 1: return launch_fwd_cfg<1, 8, 4>(d, workspace, ws_bytes, status, st);
+        case 2: return launch_fwd_cfg<2, 8, 4>(d, workspace, ws_bytes, status, st);
+        case 3: return launch_fwd_cfg<3, 8, 4>(d, workspace, ws_bytes, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
                          int32_t* counter, void* stream) {

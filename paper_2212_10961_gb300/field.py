@@ -288,6 +288,57 @@ def map_property(Y, maps: MapSpec, mean, sigma, out=None, stream=None):
     return out
 
 
+def map_bitruncated(Y1, Y2, t, s, rule, values=None, stream=None):
+    """Bitruncated (pluri-Gaussian) facies of two fields (Sec. 3.1):
+    facies = rule[#{Y1 > t}][#{Y2 > s}], and prop = values[facies] if given.
+    Returns (facies uint8, prop float32 or None) on the fields' device."""
+    Y1 = _require_cuda(Y1, torch.float32, "Y1")
+    Y2 = _require_cuda(Y2, torch.float32, "Y2")
+    if Y1.numel() != Y2.numel():
+        raise ValueError("Y1 and Y2 differ in size")
+    m = _abi.grf_bimap()
+    t, s = list(t), list(s)
+    if len(t) > _abi.GRF_MAX_THRESHOLDS or len(s) > _abi.GRF_MAX_THRESHOLDS:
+        raise ValueError("at most %d thresholds per field" % _abi.GRF_MAX_THRESHOLDS)
+    m.n_t, m.n_s = len(t), len(s)
+    for i, v in enumerate(t):
+        m.t[i] = float(v)
+    for i, v in enumerate(s):
+        m.s[i] = float(v)
+    rule = np.asarray(rule, dtype=np.int64)
+    if rule.shape != (len(t) + 1, len(s) + 1) or rule.min() < 0 or rule.max() > 255:
+        raise ValueError("rule must be (len(t)+1) x (len(s)+1) facies indices in 0..255")
+    for i in range(rule.shape[0]):
+        for j in range(rule.shape[1]):
+            m.rule[i][j] = int(rule[i, j])
+    if values is not None:
+        for i, v in enumerate(values):
+            m.values[i] = float(v)
+    fac = torch.empty(Y1.numel(), dtype=torch.uint8, device=Y1.device)
+    prop = torch.empty(Y1.numel(), dtype=torch.float32, device=Y1.device) if values is not None else None
+    check(lib().grf_map_bitruncated(ctypes.byref(m), Y1.numel(), _ptr(Y1), _ptr(Y2), _ptr(fac), _ptr(prop),
+                                    _stream_handle(stream)))
+    return fac, prop
+
+
+class PluriGaussianField:
+    """Two independent fields with the same seed on generator streams 0 and 1
+    (Appendix B `bitruncated`), each with its own covariance parameters."""
+
+    def __init__(self, params1: FieldParams, params2: FieldParams):
+        if params1.seed != params2.seed:
+            raise ValueError("both fields use one seed; their independence comes from the stream tag")
+        p1 = FieldParams(**{**params1.__dict__, "stream": 0})
+        p2 = FieldParams(**{**params2.__dict__, "stream": 1})
+        self.f1, self.f2 = GaussianField(p1), GaussianField(p2)
+
+    def synth(self, plan: CellPlan, t, s, rule, values=None, segment=0, stream=None):
+        y1 = self.f1.synth(plan, MapSpec(y=True), segment, stream=stream)["Y"]
+        y2 = self.f2.synth(plan, MapSpec(y=True), segment, stream=stream)["Y"]
+        fac, prop = map_bitruncated(y1, y2, t, s, rule, values, stream)
+        return {"Y1": y1, "Y2": y2, "facies": fac, "prop": prop}
+
+
 class Workspace:
     """Grow-only device scratch buffer (256-byte aligned torch allocation)."""
 
@@ -438,7 +489,9 @@ class GaussianField:
 class Batch:
     """Many realisations on the segments of one plan, one persistent launch.
 
-    items: list of (table, params, segment, MapSpec, out dict)."""
+    items: list of (table, params, segment, MapSpec, out dict).  tile_cells:
+    cells per warp work item (128 or 256), 0 for the library default, or
+    "auto" to time the candidates on this batch (grf_batch_autotune)."""
 
     def __init__(self, plan: CellPlan, items, tile_cells=0, stream=None):
         self.plan = plan
@@ -460,8 +513,17 @@ class Batch:
         dev = plan.buf.device
         self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
         self.host = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
-        check(lib().grf_batch_prepare(n, arr, plan.ptr, int(tile_cells), _ptr(self.ws), self.nbytes,
-                                      _ptr(self.host), _stream_handle(stream)))
+        self.tuned_ms = None
+        if tile_cells == "auto":
+            tc = ctypes.c_int32(0)
+            ms = ctypes.c_float(0.0)
+            check(lib().grf_batch_autotune(n, arr, plan.ptr, _ptr(self.ws), self.nbytes, _ptr(self.host),
+                                           _stream_handle(stream), ctypes.byref(tc), ctypes.byref(ms)))
+            self.tile_cells, self.tuned_ms = tc.value, ms.value
+        else:
+            check(lib().grf_batch_prepare(n, arr, plan.ptr, int(tile_cells), _ptr(self.ws), self.nbytes,
+                                          _ptr(self.host), _stream_handle(stream)))
+            self.tile_cells = int(tile_cells)
         self.graph = None
 
     def launch(self, stream=None):
