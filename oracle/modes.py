@@ -92,8 +92,14 @@ def chi2_draw(seed, stream, j, d, nu):
     return 2.0 * g * ub ** (1.0 / nu)
 
 
-def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0):
+def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=None):
     """Draw the N modes of one realisation.
+
+    period: optional per-axis domain lengths L_c (0 = not periodic).  Along a
+    periodic axis the frequency is moved to the nearest multiple of 1/L_c,
+    a_c = floor(a_c L_c + 1/2) / L_c, so the field repeats with period L_c
+    (Appendix B `periodic`; the paper gives no construction, this is the
+    reading taken).
 
     Returns a dict of FP64 arrays: kappa (N, d), W, Wp, rho, amp, psi (N,),
     a (N, d) in turns per unit length, plus the scalars sigma, ell (d,).
@@ -117,6 +123,12 @@ def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0):
         kappa = z * np.sqrt(2.0 * nu_e / w)[:, None]
     rho = np.sqrt((W * W + Wp * Wp) / n_modes)
     sigma = math.sqrt(sigma2)
+    a = kappa / (2.0 * math.pi * ell[None, :])
+    if period is not None:
+        for c in range(dim):
+            L = float(period[c]) if c < len(period) else 0.0
+            if L > 0.0:
+                a[:, c] = np.floor(a[:, c] * L + 0.5) / L
     return {
         "kappa": kappa,
         "W": W,
@@ -124,7 +136,7 @@ def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0):
         "rho": rho,
         "amp": sigma * rho,
         "psi": -np.arctan2(Wp, W) / (2.0 * math.pi),
-        "a": kappa / (2.0 * math.pi * ell[None, :]),
+        "a": a,
         "sigma": sigma,
         "ell": ell,
     }

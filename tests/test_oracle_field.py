@@ -276,3 +276,22 @@ def test_bitruncated_proportions_over_seeds():
     counts = np.bincount(lab, minlength=6).reshape(3, 2) / R
     se = np.sqrt(p * (1 - p) / R)
     assert np.all(np.abs(counts - p) < 5 * se)
+
+
+def test_periodic_option_repeats_exactly():
+    # Appendix B `periodic`: frequencies on multiples of 1/L_c make the field
+    # repeat with period L_c along that axis (and only that axis)
+    L = np.array([2.0, 1.0, 0.0])
+    m = modes.gen_modes(spectra.EXPONENTIAL, 1.5, [0.2, 0.1, 0.1], 3, 300, seed=8, period=L)
+    assert np.all(np.abs(m["a"][:, 0] * 2.0 - np.round(m["a"][:, 0] * 2.0)) == 0)
+    assert np.all(np.abs(m["a"][:, 1] - np.round(m["a"][:, 1])) == 0)
+    mp = modes.gen_modes(spectra.EXPONENTIAL, 1.5, [0.2, 0.1, 0.1], 3, 300, seed=8)
+    assert np.array_equal(m["a"][:, 2], mp["a"][:, 2])  # non-periodic axis untouched
+    x = np.random.default_rng(3).random((200, 3))
+    y0 = field.synth(m["a"], m["amp"], m["psi"], 0.0, x)
+    tmag = np.sum(m["amp"] * (np.abs(m["a"]).sum(1) * 3.0 + 1))
+    for shift in ([2.0, 0, 0], [0, 1.0, 0], [4.0, -3.0, 0]):
+        ys = field.synth(m["a"], m["amp"], m["psi"], 0.0, x + np.array(shift))
+        assert np.max(np.abs(ys - y0)) < 64 * 2.0 ** -52 * 2 * np.pi * tmag
+    ynp = field.synth(m["a"], m["amp"], m["psi"], 0.0, x + np.array([0, 0, 0.37]))
+    assert np.max(np.abs(ynp - y0)) > 1e-3  # not periodic along z
