@@ -30,6 +30,10 @@ Adjoint of the field sum with g_i = dL/dY_i and theta_ij = 2 pi (a_j.x_i + psi_j
     dL/da_jc  = -2 pi A_j sum_i g_i sin theta_ij x_ic
     dL/dsigma = sum_j rho_j dL/dA_j                  (A_j = sigma rho_j)
     dL/dl_c   = -sum_j (a_jc / l_c) dL/da_jc          (a_jc = kappa_jc/(2 pi l_c))
+
+With a rotation R of the anisotropy axes (a = R^T u, u = kappa/(2 pi l)) the
+last line reads with u and R dL/da in place of a and dL/da; see
+grads_from_sums.
 """
 import math
 
@@ -138,26 +142,35 @@ def mode_sums(a, psi, cells, g):
     return s_cos, s_sin, s_sinx
 
 
-def grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g):
-    """Chain rule from per-mode sums to all parameter gradients."""
+def grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g, rot=None):
+    """Chain rule from per-mode sums to all parameter gradients.
+
+    With a rotation R (a = R^T u, u = kappa / (2 pi l)): dL/du = R dL/da,
+    dL/dl_c = -sum_j (u_jc / l_c) (dL/du_j)_c, and for R as a free matrix
+    dL/dR_cd = sum_j u_jc dL/da_jd (returned as "drot")."""
     amp = np.asarray(amp, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64).reshape(len(amp), -1)
-    ell = np.asarray(ell, dtype=np.float64)[: a.shape[1]]
+    d = a.shape[1]
+    ell = np.asarray(ell, dtype=np.float64)[:d]
     dA = np.asarray(s_cos, dtype=np.float64)
     dpsi = -TWO_PI * amp * s_sin
     da = -TWO_PI * amp[:, None] * s_sinx
     rho = amp / sigma
+    R = np.eye(d) if rot is None else np.asarray(rot, dtype=np.float64)[:d, :d]
+    u = a @ R.T          # u_j = R a_j
+    du = da @ R.T        # dL/du_j = R dL/da_j
     return {
         "dA": dA,
         "dpsi": dpsi,
         "da": da,
         "dmu": float(np.sum(np.asarray(g, dtype=np.float64))),
         "dsigma": float(np.sum(rho * dA)),
-        "dell": -np.sum(a * da, axis=0) / ell,
+        "dell": -np.sum(u * du, axis=0) / ell,
+        "drot": u.T @ da,
     }
 
 
-def backward(a, amp, psi, sigma, ell, cells, g):
+def backward(a, amp, psi, sigma, ell, cells, g, rot=None):
     """All gradients of a loss with dL/dY = g (see module docstring)."""
     s_cos, s_sin, s_sinx = mode_sums(a, psi, cells, g)
-    return grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g)
+    return grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g, rot)

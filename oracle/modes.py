@@ -92,8 +92,13 @@ def chi2_draw(seed, stream, j, d, nu):
     return 2.0 * g * ub ** (1.0 / nu)
 
 
-def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=None):
+def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=None, rot=None):
     """Draw the N modes of one realisation.
+
+    rot: optional d x d rotation R whose rows are the principal axes of the
+    anisotropy (Sec. 4.1: the per-axis rescaling of frequency space extended
+    by a rotation).  The covariance is C(r) = sigma^2 rho(|diag(1/l) R r|), so
+    with u = kappa / (2 pi l) the frequencies are a = R^T u (a = u without R).
 
     period: optional per-axis domain lengths L_c (0 = not periodic).  Along a
     periodic axis the frequency is moved to the nearest multiple of 1/L_c,
@@ -124,6 +129,9 @@ def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=
     rho = np.sqrt((W * W + Wp * Wp) / n_modes)
     sigma = math.sqrt(sigma2)
     a = kappa / (2.0 * math.pi * ell[None, :])
+    if rot is not None:
+        R = np.asarray(rot, dtype=np.float64)[:dim, :dim]
+        a = a @ R  # row j: (R^T u_j)^T = u_j^T R
     if period is not None:
         for c in range(dim):
             L = float(period[c]) if c < len(period) else 0.0

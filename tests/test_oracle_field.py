@@ -295,3 +295,38 @@ def test_periodic_option_repeats_exactly():
         assert np.max(np.abs(ys - y0)) < 64 * 2.0 ** -52 * 2 * np.pi * tmag
     ynp = field.synth(m["a"], m["amp"], m["psi"], 0.0, x + np.array([0, 0, 0.37]))
     assert np.max(np.abs(ynp - y0)) > 1e-3  # not periodic along z
+
+
+def test_rotated_adjoint_against_finite_differences():
+    from oracle import field as of
+    n3 = 7
+    c = (np.arange(n3) + 0.5) / n3
+    X, Yg, Z = np.meshgrid(c, c, c, indexing="ij")
+    cells = np.stack([X.ravel(), Yg.ravel(), Z.ravel()], axis=-1)
+    ell = np.array([0.3, 0.2, 0.25])
+    th = 0.6
+    R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    base = modes.gen_modes(spectra.GAUSSIAN, 1.0, ell, 3, 20, seed=3)
+    u = base["a"]                     # kappa / (2 pi l)
+    target = of.lognormal(of.synth(u @ R, base["amp"], base["psi"], 0.0, cells) * 0.8)
+
+    def loss(ell_, R_):
+        a = (base["kappa"] / (2 * np.pi * ell_[None, :])) @ R_
+        return of.mismatch_loss(of.lognormal(of.synth(a, base["amp"], base["psi"], 0.0, cells)), target)
+
+    L0, g = loss(ell, R)
+    gr = of.backward(u @ R, base["amp"], base["psi"], 1.0, ell, cells, g, rot=R)
+    h = 1e-5
+
+    def fd(fun):
+        return (fun(h) - fun(-h)) / (2 * h)
+
+    for c_ in range(3):
+        e = np.eye(3)[c_]
+        num = fd(lambda s: loss(ell + s * e, R)[0])
+        assert gr["dell"][c_] == pytest.approx(num, rel=1e-5, abs=1e-9)
+    for (i, j) in ((0, 0), (0, 1), (1, 0), (2, 2), (1, 2)):
+        E = np.zeros((3, 3))
+        E[i, j] = 1.0
+        num = fd(lambda s: loss(ell, R + s * E)[0])
+        assert gr["drot"][i, j] == pytest.approx(num, rel=1e-5, abs=1e-9)

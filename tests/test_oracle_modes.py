@@ -120,3 +120,32 @@ def test_rejects_bad_arguments():
         modes.gen_modes(0, 1.0, ELL3, 4, 10, seed=1)
     with pytest.raises(ValueError):
         modes.gen_modes(0, 1.0, ELL3, 3, 0, seed=1)
+
+
+def _rotation(alpha, beta, gamma):
+    ca, sa, cb, sb, cg, sg = (math.cos(alpha), math.sin(alpha), math.cos(beta), math.sin(beta),
+                              math.cos(gamma), math.sin(gamma))
+    Rz = np.array([[ca, -sa, 0], [sa, ca, 0], [0, 0, 1.0]])
+    Ry = np.array([[cb, 0, sb], [0, 1.0, 0], [-sb, 0, cb]])
+    Rx = np.array([[1.0, 0, 0], [0, cg, -sg], [0, sg, cg]])
+    return Rz @ Ry @ Rx
+
+
+@pytest.mark.parametrize("family,nu", [(spectra.GAUSSIAN, 0.0), (spectra.MATERN, 1.5)])
+def test_rotated_anisotropy_characteristic_function(family, nu):
+    # covariance with principal axes given by the rows of R:
+    # C(r) = sigma^2 rho(|diag(1/l) R r|)  (Sec. 4.1, rotation of the rescaled frequency space)
+    n = 200000
+    R = _rotation(0.7, -0.4, 1.1)
+    m = modes.gen_modes(family, 1.0, ELL3, 3, n, seed=1234, nu=nu, rot=R)
+    rng = np.random.default_rng(8)
+    lags = rng.standard_normal((12, 3)) * 0.1
+    emp = np.cos(2.0 * np.pi * (m["a"] @ lags.T)).mean(axis=0)
+    r_std = np.linalg.norm((lags @ R.T) / ELL3, axis=1)
+    want = spectra.correlation(family, r_std, nu=spectra.effective_nu(family, nu))
+    # the transposed convention would give a different covariance
+    wrong = spectra.correlation(family, np.linalg.norm((lags @ R) / ELL3, axis=1),
+                                nu=spectra.effective_nu(family, nu))
+    tol = 5 * 1.5 / math.sqrt(2.0 * n)
+    assert np.max(np.abs(emp - want)) < tol
+    assert np.max(np.abs(wrong - want)) > 4 * tol
