@@ -181,7 +181,7 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     N = w["n_modes"]
     sig = math.sqrt(w["sigma2"])
     thr = W.quantile_thresholds(w["mean"], sig, w["quantiles"])
-    maps = F.MapSpec(y=True, lognormal=True, thresholds=thr, facies=len(thr) > 0)
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=thr, facies=len(thr) > 0, values=w.get("values"))
     dev_cells = [torch.from_numpy(c).cuda() for c in cells]
     t0 = time.perf_counter()
     plan = F.CellPlan(*dev_cells)
@@ -492,6 +492,8 @@ def main():
         extra["jitter3d_2m"] = bench_forward(torch, F, W, "jitter3d_2m", rank, world, args.steps, args.warmup,
                                              args.scale, with_e2e=False)
     if args.only == "all":
+        extra["hrl2d"] = bench_forward(torch, F, W, "hrl2d", rank, world, args.steps, args.warmup, 1,
+                                       with_e2e=False)
         extra["grid2d_64"] = bench_forward(torch, F, W, "grid2d_64", rank, world, args.steps, args.warmup, 1,
                                            with_e2e=False)
     ck = clocks.stop()

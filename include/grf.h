@@ -83,6 +83,14 @@ typedef struct grf_params {
     uint64_t seed;    /* generator key */
     uint32_t stream;  /* independent generator stream (e.g. 2nd field of a pair) */
     uint32_t reserved;/* must be 0 */
+    double period[3]; /* Appendix B `periodic`: L_c > 0 makes the field repeat with
+                         period L_c along axis c (frequencies moved to the nearest
+                         multiple of 1/L_c); 0 = not periodic */
+    double rot[9];    /* rotation of the anisotropy axes (Sec. 4.1: rescaling of
+                         frequency space "extended by including rotations"): row-major
+                         R whose rows are the principal axes, C(r) = sigma^2
+                         rho(|diag(1/l) R r|); the leading dim x dim block is used and
+                         must be orthonormal.  All zeros = no rotation. */
 } grf_params;
 
 #define GRF_MAX_MODES (1 << 24)
@@ -123,6 +131,11 @@ typedef struct grf_modes {
  * 64 + 2t, first uniform of block 65 + 2t; nu < 1 boosted with the first
  * uniform of block 63).  A block's two 64-bit words u give uniforms
  * (floor(u / 2^12) + 1/2) 2^-52; Box-Muller turns them into two normals.
+ *
+ * Rotation (p->rot non-zero): a_j = R^T u_j with u_jc = kappa_jc / (2 pi l_c).
+ * Periodic axes (p->period[c] > 0, applied after the rotation):
+ * a_jc = floor(a_jc L_c + 1/2) / L_c, so that Y(x + L_c e_c) = Y(x); kappa
+ * keeps the drawn value.
  *
  * Arguments: p (host, read), out (host, arrays written).  Returns GRF_EINVAL
  * for bad parameters or mismatched out->n / out->dim, GRF_OK otherwise.
@@ -286,7 +299,10 @@ typedef struct grf_grads {
     double *da;     /* [N*dim]  dL/da_jc  = -2 pi A_j sum_i g_i sin theta_ij x_ic */
     double *dmu;    /* [1]      sum_i g_i */
     double *dsigma; /* [1]      sum_j (A_j / sigma) dL/dA_j */
-    double *dell;   /* [dim]    -sum_j (a_jc / l_c) dL/da_jc */
+    double *dell;   /* [dim]    -sum_j (u_jc / l_c) (R dL/da_j)_c, u_j = R a_j (R = I
+                       without rotation) */
+    double *drot;   /* [dim*dim] or NULL: dL/dR_cd = sum_j u_jc dL/da_jd, R as a free
+                       row-major matrix (only meaningful with a rotation) */
 } grf_grads;
 
 /* Workspace for grf_synth_backward on n_cells cells and n_modes modes. */

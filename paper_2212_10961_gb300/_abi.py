@@ -39,7 +39,7 @@ class grf_params(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("dim", ctypes.c_int32), ("nu", ctypes.c_double),
                 ("sigma2", ctypes.c_double), ("mean", ctypes.c_double), ("ell", ctypes.c_double * 3),
                 ("n_modes", ctypes.c_int64), ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("reserved", ctypes.c_uint32), ("period", ctypes.c_double * 3), ("rot", ctypes.c_double * 9)]
 
 
 class grf_modes(ctypes.Structure):
@@ -62,7 +62,8 @@ class grf_outputs(ctypes.Structure):
 
 class grf_grads(ctypes.Structure):
     _fields_ = [("dA", ctypes.c_void_p), ("dpsi", ctypes.c_void_p), ("da", ctypes.c_void_p),
-                ("dmu", ctypes.c_void_p), ("dsigma", ctypes.c_void_p), ("dell", ctypes.c_void_p)]
+                ("dmu", ctypes.c_void_p), ("dsigma", ctypes.c_void_p), ("dell", ctypes.c_void_p),
+                ("drot", ctypes.c_void_p)]
 
 
 class grf_bimap(ctypes.Structure):

@@ -25,6 +25,21 @@ __device__ __forceinline__ float hw_sin(float x) {
     return y;
 }
 
+// cos(2 pi f) for |f| <= 1/2 (turns) on the FMA pipe: polynomial of degree 6
+// in s = f^2, Horner in FP32, max abs error 4.0e-7.  Coefficients: FP64
+// least-squares fit on Chebyshev nodes of [0, 1/4] rounded to FP32
+// (gen_cos_poly.py in this directory prints them and the error).
+__device__ __forceinline__ float cos_turns_poly(float f) {
+    const float s = f * f;
+    float r = 6.528658390e+00f;
+    r = fmaf(r, s, -2.596759987e+01f);
+    r = fmaf(r, s, 6.016762924e+01f);
+    r = fmaf(r, s, -8.545014191e+01f);
+    r = fmaf(r, s, 6.493911743e+01f);
+    r = fmaf(r, s, -1.973920441e+01f);
+    return fmaf(r, s, 1.000000000e+00f);
+}
+
 // Remove an integer from v exactly with FP32 adds only (no conversion unit):
 // r = v - ((v + 1.5*2^23) - 1.5*2^23).  For |v| < 2^22 the subtracted value is
 // rint(v) and |r| <= 1/2; for 2^22 <= |v| < 2^46 it is an integer within one
@@ -134,6 +149,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         "[%3];" ::"r"(smem_u32(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Hint: bring the 128-byte line holding `p` into L1 (no register, no wait).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // Orders this thread's generic-proxy shared-memory accesses before later

@@ -127,6 +127,12 @@ bool gamma_mt(const ModeStream& g, double alpha, double& out) {
     return false;
 }
 
+bool has_rotation(const grf_params* p) {
+    for (int k = 0; k < 9; ++k)
+        if (p->rot[k] != 0.0) return true;
+    return false;
+}
+
 int check_params(const grf_params* p) {
     if (!p) return fail(GRF_EINVAL, "params is NULL");
     if (p->family < GRF_GAUSSIAN || p->family > GRF_MATERN)
@@ -143,6 +149,19 @@ int check_params(const grf_params* p) {
     if (p->n_modes < 1 || p->n_modes > GRF_MAX_MODES)
         return fail(GRF_EINVAL, "n_modes must be in [1, %d]", GRF_MAX_MODES);
     if (p->reserved != 0) return fail(GRF_EINVAL, "reserved field must be 0");
+    for (int c = 0; c < 3; ++c)
+        if (!(p->period[c] >= 0.0) || !std::isfinite(p->period[c]))
+            return fail(GRF_EINVAL, "period[%d] must be finite and >= 0", c);
+    if (has_rotation(p)) {
+        const int d = p->dim;
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) {
+                double dot = 0.0;
+                for (int c = 0; c < d; ++c) dot += p->rot[i * 3 + c] * p->rot[k * 3 + c];
+                if (!std::isfinite(dot) || std::fabs(dot - (i == k ? 1.0 : 0.0)) > 1e-9)
+                    return fail(GRF_EINVAL, "rot: the leading %dx%d block must be orthonormal", d, d);
+            }
+    }
     return GRF_OK;
 }
 
@@ -248,6 +267,7 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) {
     const double nu = p->family == GRF_EXPONENTIAL ? 0.5 : p->nu;
     const double dof = 2.0 * nu;
     const bool sum_sq = (p->family != GRF_GAUSSIAN) && dof == std::round(dof) && dof >= 1.0 && dof <= 32.0;
+    const bool rotated = has_rotation(p);
     for (int64_t j = 0; j < N; ++j) {
         const ModeStream g(p->seed, p->stream, static_cast<uint64_t>(j));
         const double W = g.normal(0);
@@ -283,10 +303,21 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) {
         out->rho[j] = rho;
         out->amp[j] = sigma * rho;
         out->psi[j] = -std::atan2(Wp, W) / (2.0 * M_PI);
+        double u[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < d; ++c) {
             const double kap = z[c] * scale;
             out->kappa[j * d + c] = kap;
-            out->a[j * d + c] = kap / (2.0 * M_PI * p->ell[c]);
+            u[c] = kap / (2.0 * M_PI * p->ell[c]);
+        }
+        for (int c = 0; c < d; ++c) {
+            double a = u[c];
+            if (rotated) {  // a = R^T u
+                a = 0.0;
+                for (int k = 0; k < d; ++k) a += p->rot[k * 3 + c] * u[k];
+            }
+            const double L = p->period[c];
+            if (L > 0.0) a = std::floor(a * L + 0.5) / L;  // periodic axis: multiple of 1/L
+            out->a[j * d + c] = a;
         }
     }
     return GRF_OK;
@@ -566,8 +597,11 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
     if (ws_bytes < need) return fail(GRF_EWORKSPACE, "backward workspace %zu < %zu bytes", ws_bytes, need);
     const unsigned char* pb = static_cast<const unsigned char*>(plan);
     int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
+    double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (has_rotation(p))
+        for (int k = 0; k < 9; ++k) rot[k] = p->rot[k];
     const int err = launch_synth_bwd(
-        table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell,
+        table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell, rot,
         reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin,
         reinterpret_cast<const float*>(pb + meta.layout.off_ys) + begin,
         reinterpret_cast<const float*>(pb + meta.layout.off_zs) + begin,

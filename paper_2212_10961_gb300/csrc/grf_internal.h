@@ -27,8 +27,8 @@ namespace grf {
 constexpr int kChunk = 128;          // modes per shared-memory chunk
 constexpr int kBuckets = 160;        // extent buckets
 constexpr int kBucketBias = 100;     // E_b = 2^((b - kBucketBias) / 4)
-constexpr float kTauLight = 1.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
-constexpr float kTauMedium = 2.0f;   // lane-origin path iff h_j * E_lane <= tau2 (turns)
+constexpr float kTauLight = 2.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
+constexpr float kTauMedium = 4.0f;   // lane-origin path iff h_j * E_lane <= tau2 (turns)
 constexpr uint32_t kTableMagic = 0x54465247u;  // "GRFT"
 // Largest |a_c| (turns per unit length) accepted: with |x| < 2^16 the exact
 // phase split needs |a x| < 2^46.
@@ -196,7 +196,8 @@ int launch_bimap(const grf_bimap& m, int64_t n, const float* Y1, const float* Y2
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
                 const float* y, const float* z, void* plan, const PlanLayout& L, void* stream);
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
-                     const double* ell, const float* xs, const float* ys, const float* zs,
+                     const double* ell, const double* rot, const float* xs, const float* ys,
+                     const float* zs,
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream);
 size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);

@@ -15,11 +15,44 @@ constexpr int kMapThreads = 256;
 constexpr int kLossThreads = 256;
 constexpr int kLossItems = 8;  // elements per thread per block pass
 
+// Four consecutive cells per thread: one 16-byte load of Y and, when the
+// outputs are 16-byte (4-byte for facies) aligned, vector stores.
 __global__ void __launch_bounds__(kMapThreads) map_kernel(MapDev m, int64_t n,
-                                                          const float* __restrict__ Y) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-        map_store(m, i, Y[i]);
+                                                          const float* __restrict__ Y, int vec) {
+    const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= n) return;
+    if (vec && i0 + 4 <= n) {
+        const float4 y = __ldg(reinterpret_cast<const float4*>(Y + i0));
+        const float v[4] = {y.x, y.y, y.z, y.w};
+        const int bits = m.bits;
+        if (bits & GRF_MAP_LOGNORMAL)
+            *reinterpret_cast<float4*>(m.K + i0) =
+                make_float4(m.k_ref * expf(v[0]), m.k_ref * expf(v[1]), m.k_ref * expf(v[2]),
+                            m.k_ref * expf(v[3]));
+        if (bits & (GRF_MAP_FACIES | GRF_MAP_VALUES | GRF_MAP_POROSITY)) {
+            int lab[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                lab[q] = 0;
+                for (int t = 0; t < m.n_thr; ++t) lab[q] += (v[q] > m.thr[t]) ? 1 : 0;
+            }
+            if (bits & GRF_MAP_FACIES)
+                *reinterpret_cast<uchar4*>(m.F + i0) = make_uchar4(lab[0], lab[1], lab[2], lab[3]);
+            if (bits & GRF_MAP_VALUES)
+                *reinterpret_cast<float4*>(m.P + i0) =
+                    make_float4(m.values[lab[0]], m.values[lab[1]], m.values[lab[2]], m.values[lab[3]]);
+            if (bits & GRF_MAP_POROSITY) {
+                float ph[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    ph[q] = fminf(fmaxf(fmaf(m.phi1, (v[q] - m.mu) * m.sigma_inv, m.phi0), m.phi_min), m.phi_max);
+                *reinterpret_cast<float4*>(m.P + i0) = make_float4(ph[0], ph[1], ph[2], ph[3]);
+            }
+        }
+        if (bits & GRF_MAP_Y) *reinterpret_cast<float4*>(m.Y + i0) = y;
+        return;
+    }
+    for (int64_t i = i0; i < n && i < i0 + 4; ++i) map_store(m, i, Y[i]);
 }
 
 // Bitruncated truncation rule (Sec. 3.1): region (i, j) of the two fields,
@@ -123,13 +156,12 @@ int launch_selftest_wait(uint64_t limit_ns, int32_t* status, void* stream) {
 int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream) {
     if (n == 0) return cudaSuccess;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (n + kMapThreads - 1) / kMapThreads;
-    const int64_t cap = static_cast<int64_t>(sms) * 8;
-    if (blocks > cap) blocks = cap;
-    map_kernel<<<static_cast<unsigned>(blocks), kMapThreads, 0, st>>>(m, n, Y);
+    auto a16 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    auto a4 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 3u) == 0; };
+    const int vec = a16(Y) && a16(m.Y) && a16(m.K) && a16(m.P) && a4(m.F) ? 1 : 0;
+    const int64_t threads = (n + 3) / 4;
+    const int64_t blocks = (threads + kMapThreads - 1) / kMapThreads;
+    map_kernel<<<static_cast<unsigned>(blocks), kMapThreads, 0, st>>>(m, n, Y, vec);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ constexpr int kBwdThreads = 128;
 constexpr int kBwdTile = 256;
 constexpr int kBwdMaxSplits = 256;
 constexpr int kMPT = 2;  // modes per thread
+constexpr int kContrib = 13;  // per-mode terms of the scalar gradients
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 struct BwdArgs {
@@ -45,6 +46,7 @@ struct BwdArgs {
     int32_t splits;
     double sigma;
     double ell[3];
+    double rot[9];    // row-major rotation of the anisotropy axes (identity: none)
     const float* xs;
     const float* ys;
     const float* zs;
@@ -54,7 +56,7 @@ struct BwdArgs {
     const float* gY;
     double* part;     // [splits][n_pad][5]
     double* gpart;    // [splits]
-    double* contrib;  // [n_pad][4]: (A/sigma) dA, -(a_c/l_c) da_c
+    double* contrib;  // [n_pad][kContrib]: (A/sigma) dA, dl terms (3), dR terms (9)
     grf_grads g;
 };
 
@@ -275,9 +277,9 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
         for (int q = 0; q < 5; ++q) v[q] += p[q];
     }
     const int j = args.order[m];
-    double* ct = args.contrib + static_cast<int64_t>(m) * 4;
+    double* ct = args.contrib + static_cast<int64_t>(m) * kContrib;
     if (j < 0) {
-        ct[0] = ct[1] = ct[2] = ct[3] = 0.0;
+        for (int q = 0; q < kContrib; ++q) ct[q] = 0.0;
         return;
     }
     const float4 h = args.hot[m];
@@ -290,24 +292,31 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
     args.g.dA[j] = v[0];
     args.g.dpsi[j] = -kTwoPi * A * v[1];
     ct[0] = (A / args.sigma) * v[0];
+    const int d = args.dim;
+    double da[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < d; ++c) {
+        da[c] = -kTwoPi * A * v[2 + c];
+        args.g.da[static_cast<int64_t>(j) * d + c] = da[c];
+    }
+    // u = R a (the unrotated frequencies), dL/du = R dL/da
     for (int c = 0; c < 3; ++c) {
-        if (c < args.dim) {
-            const double da = -kTwoPi * A * v[2 + c];
-            args.g.da[static_cast<int64_t>(j) * args.dim + c] = da;
-            ct[1 + c] = -(a[c] / args.ell[c]) * da;
-        } else {
-            ct[1 + c] = 0.0;
+        double u = 0.0, du = 0.0;
+        for (int k = 0; k < d; ++k) {
+            u += args.rot[c * 3 + k] * a[k];
+            du += args.rot[c * 3 + k] * da[k];
         }
+        ct[1 + c] = c < d ? -(u / args.ell[c]) * du : 0.0;
+        for (int e = 0; e < 3; ++e) ct[4 + c * 3 + e] = (c < d && e < d) ? u * da[e] : 0.0;
     }
 }
 
 // Kernel 3: scalar gradients, one block, fixed-order reductions.
 __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
     __shared__ double red[256];
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kContrib; ++q) {
         double acc = 0.0;
         for (int m = threadIdx.x; m < args.n_pad; m += 256)
-            acc += args.contrib[static_cast<int64_t>(m) * 4 + q];
+            acc += args.contrib[static_cast<int64_t>(m) * kContrib + q];
         red[threadIdx.x] = acc;
         __syncthreads();
         for (int off = 128; off > 0; off >>= 1) {
@@ -315,10 +324,14 @@ __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            if (q == 0)
+            if (q == 0) {
                 args.g.dsigma[0] = red[0];
-            else if (q - 1 < args.dim)
-                args.g.dell[q - 1] = red[0];
+            } else if (q < 4) {
+                if (q - 1 < args.dim) args.g.dell[q - 1] = red[0];
+            } else if (args.g.drot != nullptr) {
+                const int c = (q - 4) / 3, e = (q - 4) % 3;
+                if (c < args.dim && e < args.dim) args.g.drot[c * args.dim + e] = red[0];
+            }
         }
         __syncthreads();
     }
@@ -366,12 +379,13 @@ size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
     const int64_t n_pad = pad_modes(n_modes);
     const int64_t part = int64_t(kBwdMaxSplits) * n_pad * 5 * 8;
     const int64_t gpart = int64_t(kBwdMaxSplits) * 8;
-    const int64_t contrib = n_pad * 4 * 8;
+    const int64_t contrib = n_pad * kContrib * 8;
     return static_cast<size_t>(align256(part) + align256(gpart) + align256(contrib));
 }
 
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
-                     const double* ell, const float* xs, const float* ys, const float* zs,
+                     const double* ell, const double* rot, const float* xs, const float* ys,
+                     const float* zs,
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -387,6 +401,7 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.dim = dim;
     a.sigma = sigma;
     for (int c = 0; c < 3; ++c) a.ell[c] = c < dim ? ell[c] : 1.0;
+    for (int k = 0; k < 9; ++k) a.rot[k] = rot[k];
     a.xs = xs;
     a.ys = ys;
     a.zs = zs;

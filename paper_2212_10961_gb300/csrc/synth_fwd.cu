@@ -34,6 +34,7 @@ constexpr int kWChunk = 128;                 // modes per warp chunk
 constexpr int kWChunkBytes = kWChunk * 16;   // hot records only (16 B per mode)
 constexpr int kStages = 3;                   // chunk buffers per warp (prefetch distance 2)
 constexpr int kMaxSplit = 8;                 // most mode splits of one launch
+constexpr float kInvTwoPiF = 0.159154943091895335769f;
 static_assert(kChunk % kWChunk == 0, "table padding must be a multiple of the warp chunk");
 
 // Shared memory of one warp: a ring of hot-record chunks filled by bulk
@@ -92,7 +93,11 @@ __device__ __forceinline__ float warp_max(float v) {
 // tiles).  Returns false if a bounded wait expired (status bit 2 set).
 // With `partial` the TwoSum pair (s, e) of every cell is written to
 // partial[i] instead of the maps (mode split over blocks).
-template <int DIM, int C>
+// POLY: cells per lane whose cosine is evaluated on the FMA pipe (polynomial)
+// instead of the MUFU pipe in the light loop.  It pays only where the MUFU
+// pipe, not instruction issue, limits the kernel (the persistent batched
+// kernel); the single-realisation kernel uses 0.
+template <int DIM, int C, int POLY>
 __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase, int cb, int ce,
                                                 float2* partial, WarpSmem& ws, uint32_t (&uses)[kStages],
                                                 int32_t* status) {
@@ -237,6 +242,9 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
             fence_proxy_async_smem();
             issue_wchunk(d, ch + kStages - 1, ws, (ch - cb + kStages - 1) % kStages);
         }
+        // the hi/lo records of the next chunk (128 modes x 32 B = 32 lines,
+        // one per lane) are pulled into L1 while this chunk is summed
+        if (ch + 1 < ce) prefetch_l1(d.cold + 2 * ((ch + 1) * kWChunk + lane * (kWChunk / 32)));
         const uint32_t parity = uses[b] & 1u;
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ws.full[b], parity));
         uses[b] += 1;
@@ -259,7 +267,14 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
                     float th = fmaf(h.x, dx[c][0], t0);
                     if (DIM > 1) th = fmaf(h.y, dx[c][1], th);
                     if (DIM > 2) th = fmaf(h.z, dx[c][2], th);
-                    p[c] = fmaf(h.w, hw_cos(th), p[c]);
+                    float cv;
+                    if (c >= C - POLY) {
+                        const float u = th * kInvTwoPiF;
+                        cv = cos_turns_poly(u - ((u + kRoundMagic) - kRoundMagic));
+                    } else {
+                        cv = hw_cos(th);
+                    }
+                    p[c] = fmaf(h.w, cv, p[c]);
                 }
             }
 #pragma unroll
@@ -319,7 +334,7 @@ __global__ void __launch_bounds__(W * 32, 6) synth_fwd_kernel(FwdDesc d, float2*
     const int cb = static_cast<int>(static_cast<int64_t>(n_chunks) * split / n_split);
     const int ce = static_cast<int>(static_cast<int64_t>(n_chunks) * (split + 1) / n_split);
     float2* part = n_split > 1 ? partial + static_cast<int64_t>(split) * d.n_cells : nullptr;
-    synth_warp_tile<DIM, C>(d, wbase, cb, ce, part, ws, uses, status);
+    synth_warp_tile<DIM, C, 0>(d, wbase, cb, ce, part, ws, uses, status);
 }
 
 // Combine the per-split partials of every sorted cell in split order (a
@@ -369,7 +384,7 @@ __global__ void __launch_bounds__(W * 32, 5) synth_batched_kernel(const FwdDesc*
         }
         __syncwarp();
         const int64_t wbase = static_cast<int64_t>(it.t) * (32 * C);
-        if (!synth_warp_tile<DIM, C>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status)) break;
+        if (!synth_warp_tile<DIM, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status)) break;
         __syncwarp();  // every lane is done with the descriptor
     }
 }

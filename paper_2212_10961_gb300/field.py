@@ -59,6 +59,8 @@ class FieldParams:
     seed: int = 1
     nu: float = 1.5
     stream: int = 0
+    period: Sequence[float] = (0.0, 0.0, 0.0)  # Appendix B `periodic`: L_c > 0 per axis
+    rot: Optional[Sequence[Sequence[float]]] = None  # rows: principal axes of the anisotropy
 
     @property
     def sigma(self):
@@ -79,6 +81,14 @@ class FieldParams:
         p.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
         p.stream = int(self.stream)
         p.reserved = 0
+        per = list(self.period) + [0.0] * (3 - len(self.period))
+        for c in range(3):
+            p.period[c] = float(per[c])
+        if self.rot is not None:
+            R = np.asarray(self.rot, dtype=np.float64)
+            for i in range(R.shape[0]):
+                for k in range(R.shape[1]):
+                    p.rot[i * 3 + k] = float(R[i, k])
         return p
 
 
@@ -361,7 +371,7 @@ def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=
              workspace=None):
     """Gradients (device FP64) of a loss with dL/dY = gY (CUDA float32,
     original cell order): dA, dpsi, da (N, d) in the original mode order,
-    dmu, dsigma, dell (d)."""
+    dmu, dsigma, dell (d), drot (d, d; meaningful with a rotation)."""
     gY = _require_cuda(gY, torch.float32, "gY")
     dev = gY.device
     n, d = table.n_modes, table.dim
@@ -370,7 +380,8 @@ def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=
          "da": torch.empty((n, d), dtype=torch.float64, device=dev),
          "dmu": torch.empty(1, dtype=torch.float64, device=dev),
          "dsigma": torch.empty(1, dtype=torch.float64, device=dev),
-         "dell": torch.empty(d, dtype=torch.float64, device=dev)}
+         "dell": torch.empty(d, dtype=torch.float64, device=dev),
+         "drot": torch.empty((d, d), dtype=torch.float64, device=dev)}
     gs = _abi.grf_grads()
     for k in g:
         setattr(gs, k, g[k].data_ptr())

@@ -14,7 +14,7 @@ Uses torch.distributed (NCCL between GPUs, gloo on CPU for tests).
 import torch
 import torch.distributed as dist
 
-GRAD_KEYS = ("dA", "dpsi", "da", "dmu", "dsigma", "dell")
+GRAD_KEYS = ("dA", "dpsi", "da", "dmu", "dsigma", "dell", "drot")
 
 
 def shard_range(n, rank, world):

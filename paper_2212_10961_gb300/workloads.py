@@ -19,6 +19,12 @@ unstructured cell sets, Sec. 4.1; jittered lattices for unstructured meshes):
                 l = 0.1, sigma^2 = 1 (recipe seed 4).
 * diff128     : 128^3 unit cube, N = 2048, Gaussian l = 0.1, sigma^2 = 1; the
                 target K comes from seed 2, the trial field from seed 1.
+* hrl2d       : the Horton-Rogers-Lapwood example's field (Sec. 5): 2 x 1
+                domain, 1024 x 512 cells, lognormal with sigma^2 = 2,
+                l = (0.2, 0.05) (covariance family unstated: Gaussian taken),
+                N = 4096; thresholded variant with 4 facies at the Gaussian
+                quartiles whose permeabilities are the four values the paper
+                lists, in ascending order.
 """
 import math
 
@@ -56,6 +62,9 @@ WORKLOADS = {
     "jitter3d_2m": dict(shape=(252, 126, 63), h=1.0 / 126.0, jitter=0.4, jitter_seed=3, family="matern",
                         nu=1.5, ell=(0.1, 0.1, 0.1), sigma2=2.0, mean=0.0, n_modes=8192, seed=1,
                         quantiles=()),
+    "hrl2d": dict(shape=(1024, 512), extent=(2.0, 1.0), family="gaussian", ell=(0.2, 0.05), sigma2=2.0,
+                  mean=0.0, n_modes=4096, seed=1, quantiles=(0.25, 0.5, 0.75),
+                  values=(0.0183, 0.27, 3.99, 58.9)),
     "diff128": dict(shape=(128, 128, 128), family="gaussian", ell=(0.1, 0.1, 0.1), sigma2=1.0, mean=0.0,
                     n_modes=2048, seed=1, target_seed=2, quantiles=()),
 }
@@ -67,7 +76,7 @@ def workload_cells(name, scale=1):
     shape = tuple(max(1, s // scale) for s in w["shape"])
     if "h" in w:
         return jittered_lattice(shape, w["h"] * scale, w["jitter"], w["jitter_seed"])
-    return grid_centres(shape)
+    return grid_centres(shape, w.get("extent"))
 
 
 def ensemble_recipe(n_real=256, seed=4):

@@ -56,6 +56,19 @@ def test_gen_modes_matches_oracle(abi, family, nu, dim):
         np.testing.assert_allclose(got[k], want[k], rtol=4e-15, atol=1e-300, err_msg=k)
 
 
+def test_gen_modes_periodic_matches_oracle(abi):
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(family="exponential", sigma2=1.0, ell=(0.2, 0.1, 0.05), dim=3, n_modes=500, seed=77,
+                      period=(2.0, 1.0, 0.0))
+    got = F.gen_modes(p)
+    want = omodes.gen_modes(1, 1.0, (0.2, 0.1, 0.05), 3, 500, 77, period=(2.0, 1.0, 0.0))
+    np.testing.assert_array_equal(got["a"][:, :2], want["a"][:, :2])
+    np.testing.assert_allclose(got["a"][:, 2], want["a"][:, 2], rtol=4e-15)
+    p.period = (-1.0, 0.0, 0.0)
+    with pytest.raises(abi.GRFError):
+        F.gen_modes(p)
+
+
 def _params(abi, **kw):
     p = abi.grf_params()
     p.family, p.dim, p.nu, p.sigma2, p.mean = 0, 2, 1.5, 1.0, 0.0

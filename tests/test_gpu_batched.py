@@ -73,11 +73,9 @@ def test_batched_matches_single_and_oracle(env, tile_cells):
         torch.cuda.synchronize()
         yb = out["Y"].cpu().numpy()
         ys = single["Y"].cpu().numpy()
-        if tile_cells in (0, 256):
-            # same 256-cell warp tiles as the single-realisation kernel
-            assert np.array_equal(yb, ys)
-        else:
-            assert np.max(np.abs(yb - ys)) <= 2 * 1e-5 * p.sigma
+        # the batched kernel evaluates one cosine per lane on the FMA pipe, so
+        # it agrees with the single-realisation kernel to rounding
+        assert np.max(np.abs(yb - ys)) <= 2 * 1e-5 * p.sigma
         r = recipe[s]
         om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
         cells = W.grid_centres(r["shape"])

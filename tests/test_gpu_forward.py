@@ -240,3 +240,52 @@ def test_mode_split_matches_unsplit_and_oracle(env):
     check_lognormal(split["K"].cpu().numpy(), y_or, 2.0)
     check_facies(split["facies"].cpu().numpy(), y_or, (-0.5, 0.5), 2.0)
     assert plan.status() == 0
+
+
+def test_periodic_field_repeats(env):
+    # Appendix B `periodic`: with L = (1, 1) the field at x + (1, 0) and
+    # x + (0, 1) equals the field at x (frequencies on the reciprocal lattice)
+    torch, F, W = env
+    # dyadic centres, so that x + 1 and y + 1 are exact in FP32 (otherwise the
+    # shifted point itself moves, and high-frequency modes see it)
+    base = W.grid_centres((64, 32))
+    segs = [base, [base[0] + 1.0, base[1]], [base[0], base[1] + 1.0]]
+    for s_ in segs[1:]:
+        assert np.array_equal((s_[0].astype(np.float64) - base[0]) % 1.0, np.zeros(len(base[0])))
+        assert np.array_equal((s_[1].astype(np.float64) - base[1]) % 1.0, np.zeros(len(base[0])))
+    cells = [np.concatenate([s_[k] for s_ in segs]).astype(np.float32) for k in range(2)]
+    n = len(base[0])
+    plan = F.CellPlan(*to_dev(torch, cells), segments=[n, n, n])
+    p = F.FieldParams(family="exponential", sigma2=2.0, ell=(0.2, 0.1), dim=2, n_modes=800, seed=5,
+                      period=(1.0, 1.0))
+    gf = F.GaussianField(p)
+    ys = [gf.synth(plan, F.MapSpec(y=True), segment=k)["Y"].cpu().numpy() for k in range(3)]
+    torch.cuda.synchronize()
+    sig = math.sqrt(2.0)
+    assert np.max(np.abs(ys[1] - ys[0])) <= 2e-5 * sig
+    assert np.max(np.abs(ys[2] - ys[0])) <= 2e-5 * sig
+    from oracle import modes as om
+    m = om.gen_modes(1, 2.0, (0.2, 0.1), 2, 800, 5, period=(1.0, 1.0))
+    for k in range(3):
+        check_forward(ys[k], oracle_field(m, 0.0, segs[k]), sig, "periodic segment %d" % k)
+
+
+def test_hrl2d_workload_sampled(env):
+    torch, F, W = env
+    w = W.WORKLOADS["hrl2d"]
+    cells = W.workload_cells("hrl2d")
+    assert len(cells[0]) == 1024 * 512 and float(cells[0].max()) < 2.0 and float(cells[1].max()) < 1.0
+    sig = math.sqrt(w["sigma2"])
+    thr = W.quantile_thresholds(0.0, sig, w["quantiles"])
+    maps = F.MapSpec(y=True, lognormal=True, thresholds=thr, facies=True, values=w["values"])
+    out, p, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], maps=maps)
+    om = oracle_modes(w["family"], w["sigma2"], w["ell"], 2, w["n_modes"], w["seed"])
+    idx = np.random.default_rng(7).choice(len(cells[0]), 20000, replace=False)
+    y_or = oracle_field(om, 0.0, cells, idx)
+    check_forward(out["Y"][idx], y_or, sig, "hrl2d")
+    check_lognormal(out["K"][idx], y_or, sig)
+    check_facies(out["facies"][idx], y_or, thr, sig)
+    assert np.array_equal(out["prop"], np.asarray(w["values"], dtype=np.float32)[out["facies"]])
+    # quartile thresholds: each facies holds about a quarter of the cells
+    frac = np.bincount(out["facies"], minlength=4) / len(out["facies"])
+    assert np.all(np.abs(frac - 0.25) < 0.15)
