@@ -48,10 +48,10 @@ def hbm_peak():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd", "batched", "jitter"])
+    ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd", "batched", "jitter", "hrl"])
     ap.add_argument("--scale", type=int, default=1, help="shrink every grid axis by this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -209,7 +209,8 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     torch.cuda.synchronize()
-    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kev[warmup:]]))
+    kern_all = [a.elapsed_time(b) for a, b in kev[warmup:]]
+    kern_ms = float(np.mean(kern_all))
     assert plan.status() == 0
     # field of the workload's own seed, kept for the accuracy check of the CPU-baseline leg
     p0 = params_for(F, w, dim, w["seed"])
@@ -218,7 +219,9 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     y_seed = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True))["Y"].cpu().numpy()
     per_step = launches / float(steps + warmup)
     res = {"workload": name, "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
-           "kernel_ms": max_over_ranks(torch, world, kern_ms), "plan_ms": plan_ms,
+           "kernel_ms": max_over_ranks(torch, world, kern_ms),
+           "kernel_ms_median": max_over_ranks(torch, world, float(np.median(kern_all))),
+           "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
            "launches_per_step": per_step, "y_seed": y_seed}
     if with_e2e:
@@ -401,8 +404,20 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
             break
         n = int(min(len(c), n * max(2.0, min(16.0, target_s / 4 / max(dt, 1e-3)))))
     rate = len(idx) * float(w["n_modes"]) / dt
-    res = {"value": rate / 1e9, "unit": "Gcell.mode/s", "cores": native.threads(), "kind": "oracle",
+    cores = native.threads()
+    res = {"value": rate / 1e9, "unit": "Gcell.mode/s", "cores": cores, "kind": "oracle",
            "sample": "%d random cells of %s x %d modes, FP64 C + OpenMP, %.1f s" % (len(idx), name, w["n_modes"], dt)}
+    # the same oracle on one core, on a sample sized for about the same time per core
+    n1 = max(64, int(len(idx) / max(1, cores)))
+    native.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        native.synth(m["a"], m["amp"], m["psi"], w["mean"], c[idx[:n1]])
+        dt1 = time.perf_counter() - t0
+    finally:
+        native.set_threads(cores)
+    res["single_core"] = {"value": n1 * float(w["n_modes"]) / dt1 / 1e9, "unit": "Gcell.mode/s",
+                          "sample": "%d of those cells, %.1f s" % (n1, dt1)}
     if y_gpu is not None:
         err = float(np.max(np.abs(y_gpu[idx].astype(np.float64) - y_or)))
         res["gpu_max_abs_err_sigma"] = err / math.sqrt(w["sigma2"])
@@ -491,9 +506,10 @@ def main():
     if args.only in ("all", "jitter"):
         extra["jitter3d_2m"] = bench_forward(torch, F, W, "jitter3d_2m", rank, world, args.steps, args.warmup,
                                              args.scale, with_e2e=False)
-    if args.only == "all":
+    if args.only in ("all", "hrl"):
         extra["hrl2d"] = bench_forward(torch, F, W, "hrl2d", rank, world, args.steps, args.warmup, 1,
                                        with_e2e=False)
+    if args.only == "all":
         extra["grid2d_64"] = bench_forward(torch, F, W, "grid2d_64", rank, world, args.steps, args.warmup, 1,
                                            with_e2e=False)
     ck = clocks.stop()
@@ -526,7 +542,8 @@ def main():
         "config": dict(head_config(args.scale, head["cells"], head["modes"]),
                        plan_ms_once_per_mesh=head["plan_ms"]),
         "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms),
-        "kernel_ms": head["kernel_ms"],
+        "kernel_ms": head["kernel_ms"], "kernel_ms_median": head["kernel_ms_median"],
+        "kernel_ms_best": head["kernel_ms_best"],
         "gpu_launches": head["launches_in_timed_region"],
         "clocks": ck,
     }

@@ -381,8 +381,8 @@ size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells);
  * cost-ordered work list into `workspace` (H2D from host_staging, which
  * must hold grf_batch_workspace_bytes() bytes and stay valid until the copy
  * has run).  tile_cells selects the cells per work item, one warp's tile
- * (0 = library choice, otherwise 128 or 256: 4 or 8 cells per lane).  Call
- * once per batch layout.
+ * (0 = library choice, otherwise 128, 256 or 512: 4, 8 or 16 cells per
+ * lane).  Call once per batch layout.
  */
 int grf_batch_prepare(int32_t n_items, const grf_batch_item *items, const void *plan,
                       int32_t tile_cells, void *workspace, size_t ws_bytes, void *host_staging,
@@ -390,8 +390,8 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item *items, const void *
 
 /*
  * grf_batch_autotune -- choose the work-tile shape for a batch by timing it.
- * Every candidate (256 and 128 cells per warp tile: 8 or 4 cells per lane)
- * is prepared and launched twice on `stream` (the second
+ * Every candidate (256, 512 and 128 cells per warp tile: 8, 16 or 4 cells
+ * per lane) is prepared and launched twice on `stream` (the second
  * launch timed with CUDA events), the fastest is written to *tile_cells and
  * its time in milliseconds to *best_ms, and `workspace` is left prepared for
  * it.  Results are cached in the process by batch signature (item count,

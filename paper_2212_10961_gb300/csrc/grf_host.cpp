@@ -652,7 +652,8 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
         case 0:
         case 256: cfg = 0; break;
         case 128: cfg = 1; break;
-        default: return fail(GRF_EINVAL, "tile_cells must be 0, 128 or 256");
+        case 512: cfg = 2; break;
+        default: return fail(GRF_EINVAL, "tile_cells must be 0, 128, 256 or 512");
     }
     const int64_t tc = fwd_tile_cells(cfg);
     const size_t need = grf_batch_workspace_bytes(n_items, meta.offsets.back());
@@ -750,7 +751,7 @@ int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void*
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(GRF_ECUDA, "event creation failed");
-    const int32_t candidates[2] = {256, 128};
+    const int32_t candidates[3] = {256, 512, 128};
     int32_t best = 0;
     float best_t = 0.f;
     int rc = GRF_OK;

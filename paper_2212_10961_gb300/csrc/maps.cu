@@ -15,44 +15,63 @@ constexpr int kMapThreads = 256;
 constexpr int kLossThreads = 256;
 constexpr int kLossItems = 8;  // elements per thread per block pass
 
-// Four consecutive cells per thread: one 16-byte load of Y and, when the
-// outputs are 16-byte (4-byte for facies) aligned, vector stores.
+constexpr int kMapGroups = 2;  // 4-cell groups per thread, loaded before any is processed
+
+// One 4-cell group whose Y, K, P pointers are 16-byte and F 4-byte aligned;
+// streaming stores, since nothing reads the outputs back in this launch.
+__device__ __forceinline__ void map_store4(const MapDev& m, int64_t i0, float4 y) {
+    const float v[4] = {y.x, y.y, y.z, y.w};
+    const int bits = m.bits;
+    if (bits & GRF_MAP_LOGNORMAL)
+        __stcs(reinterpret_cast<float4*>(m.K + i0),
+               make_float4(m.k_ref * expf(v[0]), m.k_ref * expf(v[1]), m.k_ref * expf(v[2]),
+                           m.k_ref * expf(v[3])));
+    if (bits & (GRF_MAP_FACIES | GRF_MAP_VALUES | GRF_MAP_POROSITY)) {
+        int lab[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            lab[q] = 0;
+            for (int t = 0; t < m.n_thr; ++t) lab[q] += (v[q] > m.thr[t]) ? 1 : 0;
+        }
+        if (bits & GRF_MAP_FACIES)
+            *reinterpret_cast<uchar4*>(m.F + i0) = make_uchar4(lab[0], lab[1], lab[2], lab[3]);
+        if (bits & GRF_MAP_VALUES)
+            __stcs(reinterpret_cast<float4*>(m.P + i0),
+                   make_float4(m.values[lab[0]], m.values[lab[1]], m.values[lab[2]], m.values[lab[3]]));
+        if (bits & GRF_MAP_POROSITY) {
+            float ph[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                ph[q] = fminf(fmaxf(fmaf(m.phi1, (v[q] - m.mu) * m.sigma_inv, m.phi0), m.phi_min), m.phi_max);
+            __stcs(reinterpret_cast<float4*>(m.P + i0), make_float4(ph[0], ph[1], ph[2], ph[3]));
+        }
+    }
+    if (bits & GRF_MAP_Y) __stcs(reinterpret_cast<float4*>(m.Y + i0), y);
+}
+
+// kMapGroups groups of four consecutive cells per thread, the groups of a
+// block interleaved so that every load of a warp is one contiguous 512-byte
+// segment.  All loads of a thread are issued before the first store, which
+// doubles the bytes in flight per SM against one group per thread.  A thread
+// whose groups run past n, or every thread when a pointer is misaligned
+// (vec == 0), stores cell by cell.
 __global__ void __launch_bounds__(kMapThreads) map_kernel(MapDev m, int64_t n,
                                                           const float* __restrict__ Y, int vec) {
-    const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-    if (i0 >= n) return;
-    if (vec && i0 + 4 <= n) {
-        const float4 y = __ldg(reinterpret_cast<const float4*>(Y + i0));
-        const float v[4] = {y.x, y.y, y.z, y.w};
-        const int bits = m.bits;
-        if (bits & GRF_MAP_LOGNORMAL)
-            *reinterpret_cast<float4*>(m.K + i0) =
-                make_float4(m.k_ref * expf(v[0]), m.k_ref * expf(v[1]), m.k_ref * expf(v[2]),
-                            m.k_ref * expf(v[3]));
-        if (bits & (GRF_MAP_FACIES | GRF_MAP_VALUES | GRF_MAP_POROSITY)) {
-            int lab[4];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kMapThreads * kMapGroups) + threadIdx.x;
+    const int64_t last = (base + static_cast<int64_t>(kMapGroups - 1) * kMapThreads) * 4;
+    if (vec && last + 4 <= n) {
+        float4 y[kMapGroups];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                lab[q] = 0;
-                for (int t = 0; t < m.n_thr; ++t) lab[q] += (v[q] > m.thr[t]) ? 1 : 0;
-            }
-            if (bits & GRF_MAP_FACIES)
-                *reinterpret_cast<uchar4*>(m.F + i0) = make_uchar4(lab[0], lab[1], lab[2], lab[3]);
-            if (bits & GRF_MAP_VALUES)
-                *reinterpret_cast<float4*>(m.P + i0) =
-                    make_float4(m.values[lab[0]], m.values[lab[1]], m.values[lab[2]], m.values[lab[3]]);
-            if (bits & GRF_MAP_POROSITY) {
-                float ph[4];
+        for (int u = 0; u < kMapGroups; ++u)
+            y[u] = __ldg(reinterpret_cast<const float4*>(Y + (base + u * kMapThreads) * 4));
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    ph[q] = fminf(fmaxf(fmaf(m.phi1, (v[q] - m.mu) * m.sigma_inv, m.phi0), m.phi_min), m.phi_max);
-                *reinterpret_cast<float4*>(m.P + i0) = make_float4(ph[0], ph[1], ph[2], ph[3]);
-            }
-        }
-        if (bits & GRF_MAP_Y) *reinterpret_cast<float4*>(m.Y + i0) = y;
+        for (int u = 0; u < kMapGroups; ++u) map_store4(m, (base + u * kMapThreads) * 4, y[u]);
         return;
     }
-    for (int64_t i = i0; i < n && i < i0 + 4; ++i) map_store(m, i, Y[i]);
+    for (int u = 0; u < kMapGroups; ++u) {
+        const int64_t i0 = (base + static_cast<int64_t>(u) * kMapThreads) * 4;
+        for (int64_t i = i0; i < n && i < i0 + 4; ++i) map_store(m, i, Y[i]);
+    }
 }
 
 // Bitruncated truncation rule (Sec. 3.1): region (i, j) of the two fields,
@@ -159,8 +178,8 @@ int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream) {
     auto a16 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     auto a4 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 3u) == 0; };
     const int vec = a16(Y) && a16(m.Y) && a16(m.K) && a16(m.P) && a4(m.F) ? 1 : 0;
-    const int64_t threads = (n + 3) / 4;
-    const int64_t blocks = (threads + kMapThreads - 1) / kMapThreads;
+    const int64_t groups = (n + 3) / 4;
+    const int64_t blocks = (groups + kMapThreads * kMapGroups - 1) / (kMapThreads * kMapGroups);
     map_kernel<<<static_cast<unsigned>(blocks), kMapThreads, 0, st>>>(m, n, Y, vec);
     count_launches(1);
     return cudaGetLastError();

@@ -249,19 +249,11 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ws.full[b], parity));
         uses[b] += 1;
         if (!ok) break;
-        const float4* hotS = ws.buf[b];
+        float4* hotS = ws.buf[b];
         const int jbase = ch * kWChunk;
         if (jbase + kWChunk > k_med) {
             const int m0 = k_med > jbase ? k_med - jbase : 0;
-            for (int m = m0 + lane; m < kWChunk; m += 32) {
-                const int j = jbase + m;
-                ws.t0[m] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
-            }
-            __syncwarp();
-#pragma unroll 4
-            for (int m = m0; m < kWChunk; ++m) {
-                const float4 h = hotS[m];
-                const float t0 = ws.t0[m];
+            auto mode = [&](const float4 h, const float t0) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     float th = fmaf(h.x, dx[c][0], t0);
@@ -276,6 +268,38 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
                     }
                     p[c] = fmaf(h.w, cv, p[c]);
                 }
+            };
+            if constexpr (C >= 16) {
+                // groups of 4 modes share one 16-byte load of t0; the modes of
+                // the first group that belong to the medium class (summed
+                // already) get amplitude 0 in this warp's copy of the chunk
+                const int m0a = m0 & ~3;
+                for (int m = m0a + lane; m < kWChunk; m += 32) {
+                    const int j = jbase + m;
+                    float t = 0.0f;
+                    if (m >= m0)
+                        t = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
+                    else
+                        hotS[m].w = 0.0f;
+                    ws.t0[m] = t;
+                }
+                __syncwarp();
+#pragma unroll 2
+                for (int m = m0a; m < kWChunk; m += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(&ws.t0[m]);
+                    mode(hotS[m + 0], t4.x);
+                    mode(hotS[m + 1], t4.y);
+                    mode(hotS[m + 2], t4.z);
+                    mode(hotS[m + 3], t4.w);
+                }
+            } else {
+                for (int m = m0 + lane; m < kWChunk; m += 32) {
+                    const int j = jbase + m;
+                    ws.t0[m] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
+                }
+                __syncwarp();
+#pragma unroll 4
+                for (int m = m0; m < kWChunk; ++m) mode(hotS[m], ws.t0[m]);
             }
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -320,7 +344,7 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
 // warp-chunk range; with more than one split every warp writes its TwoSum
 // partial (s, e) per sorted cell to partial[split * n_cells + i]).
 template <int DIM, int C, int W>
-__global__ void __launch_bounds__(W * 32, 6) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
+__global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 6) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
     const int warp = threadIdx.x >> 5;
@@ -358,7 +382,7 @@ __global__ void __launch_bounds__(256) synth_split_finalize(FwdDesc d, const flo
 // dimension; a realisation of lower dimension has zero frequencies on the
 // extra axes.
 template <int DIM, int C, int W>
-__global__ void __launch_bounds__(W * 32, 5) synth_batched_kernel(const FwdDesc* __restrict__ descs,
+__global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 5) synth_batched_kernel(const FwdDesc* __restrict__ descs,
                                                                 const WorkItem* __restrict__ work,
                                                                 int32_t n_work, int32_t* counter,
                                                                 int32_t* status) {
@@ -454,6 +478,7 @@ int launch_batched_dim(int cfg, const FwdDesc* descs, const WorkItem* work, int3
     switch (cfg) {
         case 0: return launch_batched_cfg<DIM, 8, 4>(descs, work, n_work, counter, status, st);
         case 1: return launch_batched_cfg<DIM, 4, 4>(descs, work, n_work, counter, status, st);
+        case 2: return launch_batched_cfg<DIM, 16, 4>(descs, work, n_work, counter, status, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -465,6 +490,7 @@ int fwd_tile_cells(int cfg) {
     switch (cfg) {
         case 0: return 32 * 8;
         case 1: return 32 * 4;
+        case 2: return 32 * 16;
         default: return 0;
     }
 }
@@ -478,7 +504,7 @@ int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t
     switch (d.dim) {
         case 1: return launch_fwd_cfg<1, 8, 4>(d, workspace, ws_bytes, status, st);
         case 2: return launch_fwd_cfg<2, 8, 4>(d, workspace, ws_bytes, status, st);
-        case 3: return launch_fwd_cfg<3, 8, 4>(d, workspace, ws_bytes, status, st);
+        case 3: return launch_fwd_cfg<3, 16, 4>(d, workspace, ws_bytes, status, st);
         default: return cudaErrorInvalidValue;
     }
 }

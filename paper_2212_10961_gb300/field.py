@@ -501,7 +501,7 @@ class Batch:
     """Many realisations on the segments of one plan, one persistent launch.
 
     items: list of (table, params, segment, MapSpec, out dict).  tile_cells:
-    cells per warp work item (128 or 256), 0 for the library default, or
+    cells per warp work item (128, 256 or 512), 0 for the library default, or
     "auto" to time the candidates on this batch (grf_batch_autotune)."""
 
     def __init__(self, plan: CellPlan, items, tile_cells=0, stream=None):

@@ -61,7 +61,7 @@ def _recipe():
     return out
 
 
-@pytest.mark.parametrize("tile_cells", [0, 256, 128])
+@pytest.mark.parametrize("tile_cells", [0, 256, 128, 512])
 def test_batched_matches_single_and_oracle(env, tile_cells):
     torch, F, W = env
     recipe = _recipe()
@@ -122,7 +122,7 @@ def test_autotune_picks_a_candidate_and_stays_correct(env):
     torch, F, W = env
     recipe = _recipe()
     plan, batch, items, fields = _ensemble(env, recipe, tile_cells="auto")
-    assert batch.tile_cells in (128, 256) and batch.tuned_ms > 0
+    assert batch.tile_cells in (128, 256, 512) and batch.tuned_ms > 0
     batch.launch()
     torch.cuda.synchronize()
     for s_, (table, p, seg, maps, out) in enumerate(items):

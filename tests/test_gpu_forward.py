@@ -177,6 +177,24 @@ def test_maps_standalone_and_fused(env):
     check_facies(out["facies"], y_or, thr, math.sqrt(1.5))
 
 
+@pytest.mark.parametrize("off,n", [(0, 5000), (1, 4999), (0, 2051), (4, 4093), (3, 1)])
+def test_map_standalone_ragged_and_misaligned(env, off, n):
+    # offsets that break the 16-byte alignment of Y take the per-cell path;
+    # sizes that end inside a thread's groups take the ragged tail
+    torch, F, W = env
+    rng = np.random.default_rng(16)
+    cells = [rng.random(5000).astype(np.float32) for _ in range(2)]
+    thr = (-0.5, 0.25, 1.0)
+    maps = F.MapSpec(y=True, lognormal=True, k_ref=2.5, thresholds=thr, facies=True)
+    out, p, plan = run(env, cells, "gaussian", 1.0, (0.1, 0.1), 256, seed=4, maps=maps)
+    Yd = torch.from_numpy(out["Y"]).cuda()[off:off + n]
+    st = F.map_property(Yd, F.MapSpec(y=False, lognormal=True, k_ref=2.5, thresholds=thr, facies=True),
+                        0.0, 1.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(st["K"].cpu().numpy(), out["K"][off:off + n])
+    assert np.array_equal(st["facies"].cpu().numpy(), out["facies"][off:off + n])
+
+
 def test_segments_share_one_plan(env):
     torch, F, W = env
     a = W.grid_centres((40, 30))
