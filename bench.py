@@ -8,11 +8,14 @@ mode drawing (host C++), table packing and upload, and the fused synthesis
 kernel writing Y, K and facies.  Metric: Gcell.mode/s = cells x modes per
 second.  The same JSON line also reports the forward+backward step (128^3,
 N = 2048, mismatch loss and adjoint), the batched ensemble (256 realisations
-in one graph-replayed persistent launch), the unstructured 2M-cell workload
-and the 64^2 workload.
+in one graph-replayed persistent launch), the unstructured 2M-cell workload,
+the 1024 x 512 HRL-shaped workload and the 64^2 workload.  roofline.traffic
+is the DRAM bytes (read + written) of one headline kernel launch measured by
+ncu.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--only all|fwd|bwd|batched|jitter] [--scale S]
+                  [--only all|fwd|bwd|batched|jitter|hrl] [--scale S]
+                  [--batched-tile auto|128|256|512] [--no-cpu-baseline]
 
 Under torchrun each rank runs its own realisations (different seeds) of the
 same workloads: per-GPU work is fixed (weak scaling) and the forward path has
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd", "batched", "jitter", "hrl"])
     ap.add_argument("--scale", type=int, default=1, help="shrink every grid axis by this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-tile", default="auto", choices=["auto", "128", "256", "512"],
+                    help="cells per warp work item of the ensemble (default: autotuned)")
     return ap.parse_args()
 
 
@@ -348,7 +353,7 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
             "launches_per_step": launches / float(steps + warmup)}
 
 
-def bench_batched(torch, F, W, rank, world, steps, warmup, scale):
+def bench_batched(torch, F, W, rank, world, steps, warmup, scale, tile="auto"):
     recipe = W.ensemble_recipe(seed=4 + rank)
     segs, xs, ys, zs = [], [], [], []
     for r in recipe:
@@ -372,7 +377,7 @@ def bench_batched(torch, F, W, rank, world, steps, warmup, scale):
         out = maps.allocate(segs[s], torch.device("cuda"))
         items.append((gf.table, p, s, maps, out))
         cm += float(segs[s]) * r["n_modes"]
-    batch = F.Batch(plan, items, tile_cells="auto")
+    batch = F.Batch(plan, items, tile_cells=tile)
     batch.launch()
     batch.capture()
     l0 = F.launch_count()
@@ -425,11 +430,20 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
     return res
 
 
-def roofline(kern_ms, cell_modes, clocks, sms):
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
+# headline synthesis kernel (synth_fwd_kernel<3,16,4>, 256^3 cells, 4096 modes),
+# from one ncu capture of `bench.py --only fwd --steps 3 --warmup 3`:
+# 271.14 MB read + 116.61 MB written.  Algorithmic: 16 B read (sorted
+# coordinates, permutation) + 9 B written (Y, K, facies) per cell = 419 MB;
+# part of the writes was still in L2 when the launch ended.
+HEAD_TRAFFIC_BYTES = 271.138816e6 + 116.610816e6
+
+
+def roofline(kern_ms, cell_modes, clocks, sms, traffic=None):
     peak_max = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 1e9  # Gcell.mode/s at the maximum SM clock
     achieved = cell_modes / (kern_ms * 1e-3) / 1e9
     out = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "Gcell.mode/s",
-           "frac": achieved / peak_max, "traffic": None,
+           "frac": achieved / peak_max, "traffic": traffic,
            "peak_basis": "%d MUFU cos/clk/SM x %d SMs x 2070 MHz (1 MUFU per cell-mode)" % (MUFU_PER_CLK_PER_SM, sms)}
     if clocks.get("sm_mhz"):
         peak_meas = MUFU_PER_CLK_PER_SM * sms * clocks["sm_mhz"] * 1e6 / 1e9
@@ -502,7 +516,8 @@ def main():
     if args.only in ("all", "bwd"):
         extra["fwd_bwd"] = bench_fwd_bwd(torch, F, W, rank, world, args.steps, args.warmup, args.scale)
     if args.only in ("all", "batched"):
-        extra["batched"] = bench_batched(torch, F, W, rank, world, max(3, args.steps // 2), args.warmup, args.scale)
+        extra["batched"] = bench_batched(torch, F, W, rank, world, max(3, args.steps // 2), args.warmup, args.scale,
+                                         "auto" if args.batched_tile == "auto" else int(args.batched_tile))
     if args.only in ("all", "jitter"):
         extra["jitter3d_2m"] = bench_forward(torch, F, W, "jitter3d_2m", rank, world, args.steps, args.warmup,
                                              args.scale, with_e2e=False)
@@ -541,7 +556,8 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": dict(head_config(args.scale, head["cells"], head["modes"]),
                        plan_ms_once_per_mesh=head["plan_ms"]),
-        "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms),
+        "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms,
+                             HEAD_TRAFFIC_BYTES if args.scale == 1 else None),
         "kernel_ms": head["kernel_ms"], "kernel_ms_median": head["kernel_ms_median"],
         "kernel_ms_best": head["kernel_ms_best"],
         "gpu_launches": head["launches_in_timed_region"],
