@@ -435,6 +435,17 @@ int grf_device_info(int32_t *sm_count, int32_t *sm_clock_khz);
 int64_t grf_launch_count(void);
 
 /*
+ * grf_debug_inject_alloc_failures -- host-side fault injection for tests
+ * (the paper has no counterpart).  The next n host allocations made by the
+ * library's entry points fail as if the allocator had run out of memory: the
+ * entry point that meets one returns GRF_ENOMEM with grf_last_error() set,
+ * launches nothing after that point and leaves earlier plans, tables and
+ * batches usable.  n = 0 clears the injection.  Every entry point catches
+ * host exceptions, so none crosses this ABI.  Returns GRF_EINVAL for n < 0.
+ */
+int grf_debug_inject_alloc_failures(int32_t n);
+
+/*
  * grf_mufu_probe -- throughput probe of the hardware cosine: `iters`
  * dependent-free cos.approx evaluations per thread over a grid of
  * `blocks` x 256 threads; writes one float per thread to `sink` (device,

@@ -42,7 +42,31 @@ int cuda_fail(int err, const char* what) {
 }
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+std::atomic<int32_t> g_inject_alloc{0};  // host allocation failures still to inject
+
+// Maps an exception thrown below an ABI entry point to a status code: no
+// exception crosses the C ABI.
+int host_exception() {
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return fail(GRF_ENOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(GRF_EINVAL, "host exception: %s", e.what());
+    } catch (...) {
+        return fail(GRF_EINVAL, "unknown host exception");
+    }
+}
 }  // namespace
+
+// Every host allocation of the library passes here first.  With failures
+// injected (grf_debug_inject_alloc_failures) it fails as the allocator would.
+void alloc_point() {
+    int32_t v = g_inject_alloc.load();
+    while (v > 0)
+        if (g_inject_alloc.compare_exchange_weak(v, v - 1)) throw std::bad_alloc();
+}
 
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -181,6 +205,7 @@ bool lookup_plan(const void* plan, PlanMeta& out) {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     auto it = g_plans.find(plan);
     if (it == g_plans.end()) return false;
+    alloc_point();
     out = it->second;
     return true;
 }
@@ -249,10 +274,16 @@ const char* grf_version(void) { return "grf-gb300 1.0"; }
 
 int64_t grf_launch_count(void) { return g_launches.load(); }
 
+int grf_debug_inject_alloc_failures(int32_t n) {
+    if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
+    g_inject_alloc.store(n);
+    return GRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // S1: modes
 // ---------------------------------------------------------------------------
-int grf_gen_modes(const grf_params* p, grf_modes* out) {
+int grf_gen_modes(const grf_params* p, grf_modes* out) try {
     int rc = check_params(p);
     if (rc) return rc;
     if (!out) return fail(GRF_EINVAL, "modes output is NULL");
@@ -321,6 +352,8 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) {
         }
     }
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
@@ -331,7 +364,7 @@ size_t grf_table_bytes(int64_t n_modes) {
     return static_cast<size_t>(table_layout(n_modes).total);
 }
 
-int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
+int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
     if (!m || !host_table) return fail(GRF_EINVAL, "modes or table is NULL");
     if (m->n < 1 || m->n > GRF_MAX_MODES) return fail(GRF_EINVAL, "n_modes out of range");
     if (m->dim < 1 || m->dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
@@ -350,7 +383,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
                             (long long)j);
     }
     unsigned char* base = static_cast<unsigned char*>(host_table);
-    std::memset(base, 0, static_cast<size_t>(L.total));
+    alloc_point();
     std::vector<double> h(N);
     for (int64_t j = 0; j < N; ++j) {
         double s = 0.0;
@@ -360,6 +393,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
     std::vector<int64_t> ord(N);
     std::iota(ord.begin(), ord.end(), int64_t(0));
     std::stable_sort(ord.begin(), ord.end(), [&](int64_t u, int64_t v) { return h[u] > h[v]; });
+    std::memset(base, 0, static_cast<size_t>(L.total));
 
     TableHeader hd{};
     hd.magic = kTableMagic;
@@ -414,9 +448,11 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) {
         kpref[b] = static_cast<int32_t>(k);
     }
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
-int grf_upload_table(const void* host_table, void* dev_table, size_t bytes, void* stream) {
+int grf_upload_table(const void* host_table, void* dev_table, size_t bytes, void* stream) try {
     if (!host_table || !dev_table) return fail(GRF_EINVAL, "table pointer is NULL");
     if (!aligned256(dev_table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
     TableHeader hd;
@@ -428,6 +464,8 @@ int grf_upload_table(const void* host_table, void* dev_table, size_t bytes, void
                                     cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "table upload");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +477,7 @@ size_t grf_plan_bytes(int64_t n_cells, int32_t n_segments) {
 }
 
 int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t* seg_offsets, const float* x,
-                   const float* y, const float* z, void* plan, size_t plan_bytes, void* stream) {
+                   const float* y, const float* z, void* plan, size_t plan_bytes, void* stream) try {
     if (dim < 1 || dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
     if (n_segments < 1) return fail(GRF_EINVAL, "n_segments must be >= 1");
     if (!seg_offsets) return fail(GRF_EINVAL, "seg_offsets is NULL");
@@ -455,18 +493,21 @@ int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t* seg_offsets, 
     const PlanLayout L = plan_layout(n, n_segments);
     if (plan_bytes < static_cast<size_t>(L.total))
         return fail(GRF_EWORKSPACE, "plan buffer %zu bytes < %lld needed", plan_bytes, (long long)L.total);
-    const int err = launch_plan(dim, n_segments, seg_offsets, x, y, z, plan, L, stream);
-    if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
     PlanMeta meta;
     meta.dim = dim;
+    alloc_point();
     meta.offsets.assign(seg_offsets, seg_offsets + n_segments + 1);
     meta.layout = L;
+    const int err = launch_plan(dim, n_segments, seg_offsets, x, y, z, plan, L, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
     std::lock_guard<std::mutex> lk(g_reg_mu);
     g_plans[plan] = std::move(meta);
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
-int grf_read_status(const void* plan, int32_t* status_out, void* stream) {
+int grf_read_status(const void* plan, int32_t* status_out, void* stream) try {
     if (!plan || !status_out) return fail(GRF_EINVAL, "NULL argument");
     PlanMeta meta;
     if (!lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
@@ -476,6 +517,8 @@ int grf_read_status(const void* plan, int32_t* status_out, void* stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
@@ -517,7 +560,7 @@ size_t grf_synth_workspace_bytes(int64_t n_cells) {
 
 int grf_synth_field(const void* table, const grf_params* p, const void* plan, int32_t segment,
                     const grf_map* map, const grf_outputs* out, void* workspace, size_t ws_bytes,
-                    void* stream) {
+                    void* stream) try {
     int rc = check_params(p);
     if (rc) return rc;
     if (!table) return fail(GRF_EINVAL, "table is NULL");
@@ -535,10 +578,12 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     const int err = launch_synth_fwd(d, workspace, workspace ? ws_bytes : 0, status, stream);
     if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, const float* Y,
-                     const grf_outputs* out, void* stream) {
+                     const grf_outputs* out, void* stream) try {
     int rc = check_map(map, out);
     if (rc) return rc;
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
@@ -547,10 +592,12 @@ int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, c
     const int err = launch_map(make_map(map, out, mean, sigma), n, Y, stream);
     if (err != cudaSuccess) return cuda_fail(err, "map kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 int grf_map_bitruncated(const grf_bimap* map, int64_t n, const float* Y1, const float* Y2, uint8_t* facies,
-                        float* prop, void* stream) {
+                        float* prop, void* stream) try {
     if (!map) return fail(GRF_EINVAL, "map is NULL");
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
     if (n > 0 && (!Y1 || !Y2 || !facies)) return fail(GRF_EINVAL, "Y1, Y2 or facies is NULL");
@@ -565,6 +612,8 @@ int grf_map_bitruncated(const grf_bimap* map, int64_t n, const float* Y1, const 
     const int err = launch_bimap(*map, n, Y1, Y2, facies, prop, stream);
     if (err != cudaSuccess) return cuda_fail(err, "bitruncated map kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
@@ -577,7 +626,7 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
 
 int grf_synth_backward(const void* table, const grf_params* p, const void* plan, int32_t segment,
                        const float* gY, const grf_grads* g, void* workspace, size_t ws_bytes,
-                       void* stream) {
+                       void* stream) try {
     int rc = check_params(p);
     if (rc) return rc;
     if (!table || !g || !g->dA || !g->dpsi || !g->da || !g->dmu || !g->dsigma || !g->dell)
@@ -609,6 +658,8 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
         workspace, status, stream);
     if (err != cudaSuccess) return cuda_fail(err, "backward kernels");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 size_t grf_mismatch_workspace_bytes(int64_t n) {
@@ -617,7 +668,7 @@ size_t grf_mismatch_workspace_bytes(int64_t n) {
 }
 
 int grf_mismatch_grad(int64_t n, const float* K, const float* K_target, float* gY, double* loss,
-                      void* workspace, size_t ws_bytes, void* stream) {
+                      void* workspace, size_t ws_bytes, void* stream) try {
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
     if (n > 0 && (!K || !K_target || !gY)) return fail(GRF_EINVAL, "K, K_target or gY is NULL");
     if (!loss || !workspace) return fail(GRF_EINVAL, "loss or workspace is NULL");
@@ -626,6 +677,8 @@ int grf_mismatch_grad(int64_t n, const float* K, const float* K_target, float* g
     const int err = launch_mismatch(n, K, K_target, gY, loss, workspace, stream);
     if (err != cudaSuccess) return cuda_fail(err, "mismatch kernels");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +694,7 @@ size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells) {
 
 int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* plan,
                       int32_t tile_cells, void* workspace, size_t ws_bytes, void* host_staging,
-                      void* stream) {
+                      void* stream) try {
     if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
     if (!workspace || !host_staging) return fail(GRF_EINVAL, "workspace or staging is NULL");
     if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
@@ -668,6 +721,7 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
     h.off_work = h.off_desc + align256(int64_t(n_items) * int64_t(sizeof(FwdDesc)));
     unsigned char* hs = static_cast<unsigned char*>(host_staging);
     FwdDesc* descs = reinterpret_cast<FwdDesc*>(hs + h.off_desc);
+    alloc_point();
     std::vector<int64_t> order(n_items);
     for (int32_t r = 0; r < n_items; ++r) {
         const grf_batch_item& it = items[r];
@@ -712,11 +766,13 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
     std::lock_guard<std::mutex> lk(g_reg_mu);
     g_batches[workspace] = bm;
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void* plan, void* workspace,
                        size_t ws_bytes, void* host_staging, void* stream, int32_t* tile_cells,
-                       float* best_ms) {
+                       float* best_ms) try {
     if (!tile_cells || !best_ms) return fail(GRF_EINVAL, "tile_cells or best_ms is NULL");
     if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
     PlanMeta meta;
@@ -785,9 +841,11 @@ int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void*
     *tile_cells = best;
     *best_ms = best_t;
     return grf_batch_prepare(n_items, items, plan, best, workspace, ws_bytes, host_staging, stream);
+} catch (...) {
+    return host_exception();
 }
 
-int grf_batch_launch(void* workspace, void* stream) {
+int grf_batch_launch(void* workspace, void* stream) try {
     BatchMeta bm;
     {
         std::lock_guard<std::mutex> lk(g_reg_mu);
@@ -801,12 +859,14 @@ int grf_batch_launch(void* workspace, void* stream) {
     const int err = launch_synth_batched(workspace, bm.hdr, status, counter, stream);
     if (err != cudaSuccess) return cuda_fail(err, "batched kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 // ---------------------------------------------------------------------------
 // Measurement helpers
 // ---------------------------------------------------------------------------
-int grf_device_info(int32_t* sm_count, int32_t* sm_clock_khz) {
+int grf_device_info(int32_t* sm_count, int32_t* sm_clock_khz) try {
     if (!sm_count || !sm_clock_khz) return fail(GRF_EINVAL, "NULL argument");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -814,9 +874,11 @@ int grf_device_info(int32_t* sm_count, int32_t* sm_clock_khz) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(sm_clock_khz, cudaDevAttrClockRate, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device attributes");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
-int grf_selftest_wait(int32_t limit_us, int32_t* status_dev, void* stream) {
+int grf_selftest_wait(int32_t limit_us, int32_t* status_dev, void* stream) try {
     if (limit_us < 1 || limit_us > 2000000) return fail(GRF_EINVAL, "limit_us must be in [1, 2000000]");
     if (!status_dev) return fail(GRF_EINVAL, "status_dev is NULL");
     int err = launch_selftest_wait(static_cast<uint64_t>(limit_us) * 1000ull, status_dev, stream);
@@ -828,13 +890,17 @@ int grf_selftest_wait(int32_t limit_us, int32_t* status_dev, void* stream) {
     if (e != cudaSuccess) return cuda_fail(e, "self-test status read");
     if (st == 2) return fail(GRF_ETIMEOUT, "bounded device wait expired after %d us (expected)", limit_us);
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
-int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) {
+int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) try {
     if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
     const int err = launch_mufu_probe(blocks, iters, sink, stream);
     if (err != cudaSuccess) return cuda_fail(err, "probe kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
 }
 
 }  // extern "C"

@@ -27,8 +27,8 @@ namespace grf {
 constexpr int kChunk = 128;          // modes per shared-memory chunk
 constexpr int kBuckets = 160;        // extent buckets
 constexpr int kBucketBias = 100;     // E_b = 2^((b - kBucketBias) / 4)
-constexpr float kTauLight = 2.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
-constexpr float kTauMedium = 4.0f;   // lane-origin path iff h_j * E_lane <= tau2 (turns)
+constexpr float kTauLight = 8.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
+constexpr float kTauMedium = 16.0f;  // lane-origin path iff h_j * E_lane <= tau2 (turns)
 constexpr uint32_t kTableMagic = 0x54465247u;  // "GRFT"
 // Largest |a_c| (turns per unit length) accepted: with |x| < 2^16 the exact
 // phase split needs |a x| < 2^46.
@@ -209,5 +209,9 @@ int launch_selftest_wait(uint64_t limit_ns, int32_t* status, void* stream);
 void count_launches(int64_t n);
 // Record `message` as the calling thread's last error and return `code`.
 int set_error(int code, const char* message);
+// Allocation point of the host code: throws std::bad_alloc while injected
+// failures remain (grf_debug_inject_alloc_failures); ABI entry points turn
+// it into GRF_ENOMEM.
+void alloc_point();
 
 }  // namespace grf

@@ -388,6 +388,7 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     cudaError_t err = cudaMemcpyAsync(hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess) return err;
     // cudaMemcpyAsync from pageable memory returns once the source is staged.
+    alloc_point();
     SegInfo* hseg = new (std::nothrow) SegInfo[n_segments];
     if (!hseg) return cudaErrorMemoryAllocation;
     for (int s = 0; s < n_segments; ++s) {

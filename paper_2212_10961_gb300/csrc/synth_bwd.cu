@@ -31,7 +31,7 @@ namespace {
 constexpr int kBwdThreads = 128;
 constexpr int kBwdTile = 256;
 constexpr int kBwdMaxSplits = 256;
-constexpr int kMPT = 2;  // modes per thread
+constexpr int kMPT = 4;  // modes per thread
 constexpr int kContrib = 13;  // per-mode terms of the scalar gradients
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 

@@ -169,6 +169,30 @@ def test_pack_and_sizes_reject(abi):
     assert abi.lib().grf_batch_workspace_bytes(0, 10) == 0
 
 
+def test_injected_host_allocation_failure(abi):
+    # host-side fault injection: the entry point reports GRF_ENOMEM instead of
+    # letting the allocation failure escape, and the next call succeeds
+    from paper_2212_10961_gb300 import field as F
+    L = abi.lib()
+    p = F.FieldParams(n_modes=300, dim=3, ell=(0.1, 0.2, 0.3), seed=11)
+    md = F.gen_modes(p)
+    m = F._modes_struct(300, 3, md)
+    nb = L.grf_table_bytes(300)
+    ref = (ctypes.c_uint8 * nb)()
+    assert L.grf_pack_table(ctypes.byref(m), ref, nb) == 0
+    buf = (ctypes.c_uint8 * nb)()
+    assert L.grf_debug_inject_alloc_failures(1) == 0
+    try:
+        assert L.grf_pack_table(ctypes.byref(m), buf, nb) == abi.GRF_ENOMEM
+        assert b"allocation" in L.grf_last_error()
+        assert not any(bytes(buf))  # nothing written before the failure
+        assert L.grf_pack_table(ctypes.byref(m), buf, nb) == 0  # the injection was used up
+        assert bytes(buf) == bytes(ref)
+    finally:
+        L.grf_debug_inject_alloc_failures(0)
+    assert L.grf_debug_inject_alloc_failures(-1) == abi.GRF_EINVAL
+
+
 def test_null_and_unknown_handles_rejected(abi):
     L = abi.lib()
     p = _params(abi)

@@ -35,3 +35,34 @@ def test_bounded_wait_expires_and_context_survives():
     torch.cuda.synchronize()
     assert plan.status() == 0
     assert np.all(np.isfinite(out["Y"].cpu().numpy()))
+
+
+def test_injected_allocation_failure_in_plan_and_synthesis():
+    # host-side injection: the failing call raises GRF_ENOMEM, launches nothing
+    # after the failure point, and the same objects work on the next call
+    torch = gpu_env()
+    from paper_2212_10961_gb300 import _abi
+    from paper_2212_10961_gb300 import field as F
+    from paper_2212_10961_gb300 import workloads as W
+    L = _abi.lib()
+    cells = to_dev(torch, W.grid_centres((48, 40)))
+    p = F.FieldParams(family="exponential", sigma2=1.0, ell=(0.1, 0.2), dim=2, n_modes=300, seed=4)
+    gf = F.GaussianField(p)
+    try:
+        L.grf_debug_inject_alloc_failures(1)
+        with pytest.raises(_abi.GRFError) as e:
+            F.CellPlan(*cells)
+        assert e.value.code == _abi.GRF_ENOMEM
+        plan = F.CellPlan(*cells)
+        want = gf.synth(plan)["Y"].clone()
+        L.grf_debug_inject_alloc_failures(1)
+        n0 = F.launch_count()
+        with pytest.raises(_abi.GRFError) as e:
+            gf.synth(plan)
+        assert e.value.code == _abi.GRF_ENOMEM and F.launch_count() == n0
+    finally:
+        L.grf_debug_inject_alloc_failures(0)
+    got = gf.synth(plan)["Y"]
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(got, want)
