@@ -264,9 +264,11 @@ def bench_map(torch, F, maps, Y, w, steps):
     for _ in range(3):
         F.map_property(Y, m2, w["mean"], sig, out)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=Y.device)  # larger than L2
+    clean = torch.zeros(256 << 20, dtype=torch.uint8, device=Y.device)
     times = []
     for _ in range(max(5, steps)):
-        flush.zero_()
+        flush.zero_()  # evicts the map's data from L2 ...
+        clean.max()  # ... and reading another buffer writes the flush's dirty lines back before the timed launch
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
@@ -280,37 +282,60 @@ def bench_map(torch, F, maps, Y, w, steps):
     peak, kind = hbm_peak()
     return {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
             "frac": gbs / peak, "bound": "hbm",
-            "note": "L2 flushed (256 MB write) before every launch; median of launches"}
+            "note": "L2 flushed before every launch (256 MB write, then a 256 MB read so that no dirty "
+                    "line of the flush is written back inside the timed launch); median of launches"}
 
 
 def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps):
     """Same step through the public API with host buffers: pinned host cell
-    centres copied in, plan, modes, synthesis, outputs copied back."""
+    centres copied in, plan, modes, synthesis, outputs copied back.
+
+    Two slots of device buffers alternate between steps: the copy-in and the
+    plan of step i + 1 run on a side stream while step i synthesises on the
+    main stream, and a slot is reused only after its previous step's outputs
+    have reached the host (events)."""
     M = len(cells[0])
     host_cells = [torch.from_numpy(c).pin_memory() for c in cells]
-    dev_cells = [torch.empty(M, dtype=torch.float32, device="cuda") for _ in cells]
-    host_out = {k: torch.empty(M, dtype=v, pin_memory=True)
-                for k, v in (("Y", torch.float32), ("K", torch.float32), ("facies", torch.uint8))
-                if (k == "Y" and maps.y) or (k == "K" and maps.lognormal) or (k == "facies" and maps.facies)}
-    dev_out = maps.allocate(M, torch.device("cuda"))
-    tab = F.ModeTable.from_modes(F.gen_modes(params_for(F, w, dim, base_seed)))
+    keys = [k for k in ("Y", "K", "facies")
+            if (k == "Y" and maps.y) or (k == "K" and maps.lognormal) or (k == "facies" and maps.facies)]
+    dtypes = {"Y": torch.float32, "K": torch.float32, "facies": torch.uint8}
+    slots = []
+    for _ in range(2):
+        slots.append({
+            "cells": [torch.empty(M, dtype=torch.float32, device="cuda") for _ in cells],
+            "host_out": {k: torch.empty(M, dtype=dtypes[k], pin_memory=True) for k in keys},
+            "dev_out": maps.allocate(M, torch.device("cuda")),
+            "tab": F.ModeTable.from_modes(F.gen_modes(params_for(F, w, dim, base_seed))),
+            "plan": None, "planned": torch.cuda.Event(), "done": torch.cuda.Event()})
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    for sl in slots:
+        sl["done"].record(main)
 
     def step(i):
-        for h, d in zip(host_cells, dev_cells):
-            d.copy_(h, non_blocking=True)
-        plan = F.CellPlan(*dev_cells)
+        sl = slots[i % 2]
+        side.wait_event(sl["done"])  # the slot's previous step has finished on the device
+        with torch.cuda.stream(side):
+            for h, d in zip(host_cells, sl["cells"]):
+                d.copy_(h, non_blocking=True)
+            sl["plan"] = F.CellPlan(*sl["cells"], stream=side)
+            sl["planned"].record(side)
         p = params_for(F, w, dim, base_seed + i)
         m = F.gen_modes(p)
-        tab.update(m["amp"], m["psi"], m["a"])
-        F.synth(tab, p, plan, 0, maps, dev_out)
-        for k, h in host_out.items():
-            h.copy_(dev_out[k], non_blocking=True)
-        step.plan = plan
+        sl["tab"].update(m["amp"], m["psi"], m["a"], stream=main)
+        main.wait_event(sl["planned"])
+        F.synth(sl["tab"], p, sl["plan"], 0, maps, sl["dev_out"], stream=main)
+        for k, h in sl["host_out"].items():
+            h.copy_(sl["dev_out"][k], non_blocking=True)
+        sl["done"].record(main)
 
-    ms = timed_steps(torch, world, steps, 1, step)
+    ms = timed_steps(torch, world, steps, 2, step)
+    for sl in slots:
+        assert sl["plan"].status() == 0
     h2d = 4 * M * len(cells)
-    d2h = sum(M * (1 if k == "facies" else 4) for k in host_out)
-    return {"ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    d2h = sum(M * (1 if k == "facies" else 4) for k in keys)
+    return {"ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "pipelined": "copy-in and plan of step i+1 on a side stream during step i's synthesis"}
 
 
 def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
@@ -433,10 +458,10 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
 # headline synthesis kernel (synth_fwd_kernel<3,16,4>, 256^3 cells, 4096 modes),
 # from one ncu capture of `bench.py --only fwd --steps 3 --warmup 3`:
-# 271.14 MB read + 116.61 MB written.  Algorithmic: 16 B read (sorted
+# 271.06 MB read + 116.38 MB written.  Algorithmic: 16 B read (sorted
 # coordinates, permutation) + 9 B written (Y, K, facies) per cell = 419 MB;
 # part of the writes was still in L2 when the launch ended.
-HEAD_TRAFFIC_BYTES = 271.138816e6 + 116.610816e6
+HEAD_TRAFFIC_BYTES = 271.062272e6 + 116.384000e6
 
 
 def roofline(kern_ms, cell_modes, clocks, sms, traffic=None):

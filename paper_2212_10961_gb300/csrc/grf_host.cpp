@@ -16,6 +16,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "grf_internal.h"
 
 namespace grf {
@@ -59,6 +61,15 @@ int host_exception() {
     }
 }
 }  // namespace
+
+// NVTX range around one ABI call (visible in Nsight tools and usable as an
+// ncu filter; a no-op when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Every host allocation of the library passes here first.  With failures
 // injected (grf_debug_inject_alloc_failures) it fails as the allocator would.
@@ -284,6 +295,7 @@ int grf_debug_inject_alloc_failures(int32_t n) {
 // S1: modes
 // ---------------------------------------------------------------------------
 int grf_gen_modes(const grf_params* p, grf_modes* out) try {
+    TraceRange trace_("grf_gen_modes");
     int rc = check_params(p);
     if (rc) return rc;
     if (!out) return fail(GRF_EINVAL, "modes output is NULL");
@@ -365,6 +377,7 @@ size_t grf_table_bytes(int64_t n_modes) {
 }
 
 int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
+    TraceRange trace_("grf_pack_table");
     if (!m || !host_table) return fail(GRF_EINVAL, "modes or table is NULL");
     if (m->n < 1 || m->n > GRF_MAX_MODES) return fail(GRF_EINVAL, "n_modes out of range");
     if (m->dim < 1 || m->dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
@@ -453,6 +466,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
 }
 
 int grf_upload_table(const void* host_table, void* dev_table, size_t bytes, void* stream) try {
+    TraceRange trace_("grf_upload_table");
     if (!host_table || !dev_table) return fail(GRF_EINVAL, "table pointer is NULL");
     if (!aligned256(dev_table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
     TableHeader hd;
@@ -478,6 +492,7 @@ size_t grf_plan_bytes(int64_t n_cells, int32_t n_segments) {
 
 int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t* seg_offsets, const float* x,
                    const float* y, const float* z, void* plan, size_t plan_bytes, void* stream) try {
+    TraceRange trace_("grf_plan_cells");
     if (dim < 1 || dim > 3) return fail(GRF_EINVAL, "dim must be 1, 2 or 3");
     if (n_segments < 1) return fail(GRF_EINVAL, "n_segments must be >= 1");
     if (!seg_offsets) return fail(GRF_EINVAL, "seg_offsets is NULL");
@@ -539,7 +554,7 @@ int fwd_desc(const void* table, int64_t n_modes, int32_t dim, const void* plan,
     d.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
     d.kpref = reinterpret_cast<const int32_t*>(tb + TL.off_kpref);
     d.n_pad = static_cast<int32_t>(TL.n_pad);
-    d.dim = meta.dim;
+    d.dim = dim;  // the field's own dimension: coordinates beyond it do not enter the phase
     d.inv_tau1 = 1.0f / kTauLight;
     d.inv_tau2 = 1.0f / kTauMedium;
     d.xs = reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin;
@@ -561,6 +576,7 @@ size_t grf_synth_workspace_bytes(int64_t n_cells) {
 int grf_synth_field(const void* table, const grf_params* p, const void* plan, int32_t segment,
                     const grf_map* map, const grf_outputs* out, void* workspace, size_t ws_bytes,
                     void* stream) try {
+    TraceRange trace_("grf_synth_field");
     int rc = check_params(p);
     if (rc) return rc;
     if (!table) return fail(GRF_EINVAL, "table is NULL");
@@ -584,6 +600,7 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
 
 int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, const float* Y,
                      const grf_outputs* out, void* stream) try {
+    TraceRange trace_("grf_map_property");
     int rc = check_map(map, out);
     if (rc) return rc;
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
@@ -598,6 +615,7 @@ int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, c
 
 int grf_map_bitruncated(const grf_bimap* map, int64_t n, const float* Y1, const float* Y2, uint8_t* facies,
                         float* prop, void* stream) try {
+    TraceRange trace_("grf_map_bitruncated");
     if (!map) return fail(GRF_EINVAL, "map is NULL");
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
     if (n > 0 && (!Y1 || !Y2 || !facies)) return fail(GRF_EINVAL, "Y1, Y2 or facies is NULL");
@@ -627,6 +645,7 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
 int grf_synth_backward(const void* table, const grf_params* p, const void* plan, int32_t segment,
                        const float* gY, const grf_grads* g, void* workspace, size_t ws_bytes,
                        void* stream) try {
+    TraceRange trace_("grf_synth_backward");
     int rc = check_params(p);
     if (rc) return rc;
     if (!table || !g || !g->dA || !g->dpsi || !g->da || !g->dmu || !g->dsigma || !g->dell)
@@ -669,6 +688,7 @@ size_t grf_mismatch_workspace_bytes(int64_t n) {
 
 int grf_mismatch_grad(int64_t n, const float* K, const float* K_target, float* gY, double* loss,
                       void* workspace, size_t ws_bytes, void* stream) try {
+    TraceRange trace_("grf_mismatch_grad");
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
     if (n > 0 && (!K || !K_target || !gY)) return fail(GRF_EINVAL, "K, K_target or gY is NULL");
     if (!loss || !workspace) return fail(GRF_EINVAL, "loss or workspace is NULL");
@@ -695,6 +715,7 @@ size_t grf_batch_workspace_bytes(int32_t n_items, int64_t n_cells) {
 int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* plan,
                       int32_t tile_cells, void* workspace, size_t ws_bytes, void* host_staging,
                       void* stream) try {
+    TraceRange trace_("grf_batch_prepare");
     if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
     if (!workspace || !host_staging) return fail(GRF_EINVAL, "workspace or staging is NULL");
     if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
@@ -773,6 +794,7 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
 int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void* plan, void* workspace,
                        size_t ws_bytes, void* host_staging, void* stream, int32_t* tile_cells,
                        float* best_ms) try {
+    TraceRange trace_("grf_batch_autotune");
     if (!tile_cells || !best_ms) return fail(GRF_EINVAL, "tile_cells or best_ms is NULL");
     if (n_items < 1 || !items) return fail(GRF_EINVAL, "no batch items");
     PlanMeta meta;
@@ -846,6 +868,7 @@ int grf_batch_autotune(int32_t n_items, const grf_batch_item* items, const void*
 }
 
 int grf_batch_launch(void* workspace, void* stream) try {
+    TraceRange trace_("grf_batch_launch");
     BatchMeta bm;
     {
         std::lock_guard<std::mutex> lk(g_reg_mu);

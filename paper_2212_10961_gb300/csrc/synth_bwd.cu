@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
 #pragma unroll
         for (int q = 0; q < 5; ++q) sm.acc[lane * MPT + k][q] = make_float2(0.f, 0.f);
     }
-    double gsum = 0.0;
+    DF gsum{0.f, 0.f};  // compensated FP32 pair instead of FP64 adds (slow pipe on this GPU)
     const bool count_g = blockIdx.x == 0 && warp == 0;  // one warp per split sums g
 
     const int64_t n = args.n_cells;
@@ -165,7 +165,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
         for (int q = 0; q < kPer; ++q) {
             const int idx = q * 32 + lane;
             sm.cd[idx] = make_float4(xv[q][0] - x0[0], xv[q][1] - x0[1], xv[q][2] - x0[2], gv[q]);
-            if (count_g) gsum += static_cast<double>(gv[q]);
+        }
+        if (count_g) {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) gsum.add(gv[q]);  // cascaded sum: TwoSum per value
         }
         __syncwarp();
         if (t + 1 < t_end) load_tile(t + 1);  // overlaps with the sums below
@@ -259,8 +262,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
             o[q] = q < 2 + DIM ? static_cast<double>(a[q].x) + static_cast<double>(a[q].y) : 0.0;
     }
     if (count_g) {
-        for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
-        if (lane == 0) args.gpart[blockIdx.y] = gsum;
+        double gs = gsum.value();
+        for (int off = 16; off > 0; off >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, off);
+        if (lane == 0) args.gpart[blockIdx.y] = gs;
     }
     (void)status;
 }

@@ -408,7 +408,17 @@ __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 5) synth_batched_kernel(
         }
         __syncwarp();
         const int64_t wbase = static_cast<int64_t>(it.t) * (32 * C);
-        if (!synth_warp_tile<DIM, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status)) break;
+        // a realisation of lower dimension than the plan (e.g. 2-D fields on a
+        // plan whose third coordinate is 0) runs the tile of its own dimension
+        bool ok;
+        if (DIM > 1 && d.dim == 1)
+            ok = synth_warp_tile<1, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status);
+        else if (DIM > 2 && d.dim == 2)
+            ok = synth_warp_tile<(DIM > 2 ? 2 : DIM), C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses,
+                                                             status);
+        else
+            ok = synth_warp_tile<DIM, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status);
+        if (!ok) break;
         __syncwarp();  // every lane is done with the descriptor
     }
 }
