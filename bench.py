@@ -264,11 +264,9 @@ def bench_map(torch, F, maps, Y, w, steps):
     for _ in range(3):
         F.map_property(Y, m2, w["mean"], sig, out)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=Y.device)  # larger than L2
-    clean = torch.zeros(256 << 20, dtype=torch.uint8, device=Y.device)
     times = []
     for _ in range(max(5, steps)):
-        flush.zero_()  # evicts the map's data from L2 ...
-        clean.max()  # ... and reading another buffer writes the flush's dirty lines back before the timed launch
+        flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
@@ -282,8 +280,7 @@ def bench_map(torch, F, maps, Y, w, steps):
     peak, kind = hbm_peak()
     return {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
             "frac": gbs / peak, "bound": "hbm",
-            "note": "L2 flushed before every launch (256 MB write, then a 256 MB read so that no dirty "
-                    "line of the flush is written back inside the timed launch); median of launches"}
+            "note": "L2 flushed (256 MB write) before every launch; median of launches"}
 
 
 def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps):
@@ -291,9 +288,9 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
     centres copied in, plan, modes, synthesis, outputs copied back.
 
     Two slots of device buffers alternate between steps: the copy-in and the
-    plan of step i + 1 run on a side stream while step i synthesises on the
-    main stream, and a slot is reused only after its previous step's outputs
-    have reached the host (events)."""
+    plan of step i + 1 run on a side stream and the copy-back of step i - 1 on
+    another while step i synthesises on the main stream; a slot is reused only
+    after its previous step's outputs have reached the host (events)."""
     M = len(cells[0])
     host_cells = [torch.from_numpy(c).pin_memory() for c in cells]
     keys = [k for k in ("Y", "K", "facies")
@@ -308,9 +305,11 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
             "tab": F.ModeTable.from_modes(F.gen_modes(params_for(F, w, dim, base_seed))),
             "plan": None, "planned": torch.cuda.Event(), "done": torch.cuda.Event()})
     main = torch.cuda.current_stream()
-    side = torch.cuda.Stream()
+    side = torch.cuda.Stream()  # copy-in and planning of the next step
+    back = torch.cuda.Stream()  # copy-back of the previous step
     for sl in slots:
         sl["done"].record(main)
+        sl["synthesised"] = torch.cuda.Event()
 
     def step(i):
         sl = slots[i % 2]
@@ -325,9 +324,12 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
         sl["tab"].update(m["amp"], m["psi"], m["a"], stream=main)
         main.wait_event(sl["planned"])
         F.synth(sl["tab"], p, sl["plan"], 0, maps, sl["dev_out"], stream=main)
-        for k, h in sl["host_out"].items():
-            h.copy_(sl["dev_out"][k], non_blocking=True)
-        sl["done"].record(main)
+        sl["synthesised"].record(main)
+        back.wait_event(sl["synthesised"])
+        with torch.cuda.stream(back):
+            for k, h in sl["host_out"].items():
+                h.copy_(sl["dev_out"][k], non_blocking=True)
+        sl["done"].record(back)
 
     ms = timed_steps(torch, world, steps, 2, step)
     for sl in slots:
@@ -335,7 +337,8 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
     h2d = 4 * M * len(cells)
     d2h = sum(M * (1 if k == "facies" else 4) for k in keys)
     return {"ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "pipelined": "copy-in and plan of step i+1 on a side stream during step i's synthesis"}
+            "pipelined": "copy-in and plan of step i+1 and copy-back of step i-1 on side streams during "
+                         "step i's synthesis"}
 
 
 def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):

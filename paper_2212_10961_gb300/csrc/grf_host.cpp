@@ -13,6 +13,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -311,58 +312,86 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) try {
     const double dof = 2.0 * nu;
     const bool sum_sq = (p->family != GRF_GAUSSIAN) && dof == std::round(dof) && dof >= 1.0 && dof <= 32.0;
     const bool rotated = has_rotation(p);
-    for (int64_t j = 0; j < N; ++j) {
-        const ModeStream g(p->seed, p->stream, static_cast<uint64_t>(j));
-        const double W = g.normal(0);
-        const double Wp = g.normal(1);
-        double z[3];
-        for (int c = 0; c < d; ++c) z[c] = g.normal(2u + c);
-        double scale;
-        if (p->family == GRF_GAUSSIAN) {
-            scale = std::sqrt(0.5 * M_PI);
-        } else {
-            double w = 0.0;
-            if (sum_sq) {
-                const int m = static_cast<int>(dof);
-                for (int i = 0; i < m; ++i) {
-                    const double v = g.normal(static_cast<uint32_t>(2 + d + i));
-                    w += v * v;
-                }
+    // Modes are independent draws: ranges of j run on host threads.  A worker
+    // records the first mode whose gamma sampler failed (errors are reported
+    // by the calling thread).
+    auto draw_range = [&](int64_t j0, int64_t j1, int64_t* bad) {
+        for (int64_t j = j0; j < j1; ++j) {
+            const ModeStream g(p->seed, p->stream, static_cast<uint64_t>(j));
+            const double W = g.normal(0);
+            const double Wp = g.normal(1);
+            double z[3];
+            for (int c = 0; c < d; ++c) z[c] = g.normal(2u + c);
+            double scale;
+            if (p->family == GRF_GAUSSIAN) {
+                scale = std::sqrt(0.5 * M_PI);
             } else {
-                double G;
-                const double alpha = nu >= 1.0 ? nu : nu + 1.0;
-                if (!gamma_mt(g, alpha, G))
-                    return fail(GRF_EINVAL, "gamma sampler did not accept for mode %lld", (long long)j);
-                if (nu < 1.0) {
-                    double ub, unused;
-                    g.uniforms(63u, ub, unused);
-                    G *= std::pow(ub, 1.0 / nu);
+                double w = 0.0;
+                if (sum_sq) {
+                    const int m = static_cast<int>(dof);
+                    for (int i = 0; i < m; ++i) {
+                        const double v = g.normal(static_cast<uint32_t>(2 + d + i));
+                        w += v * v;
+                    }
+                } else {
+                    double G;
+                    const double alpha = nu >= 1.0 ? nu : nu + 1.0;
+                    if (!gamma_mt(g, alpha, G)) {
+                        *bad = j;
+                        return;
+                    }
+                    if (nu < 1.0) {
+                        double ub, unused;
+                        g.uniforms(63u, ub, unused);
+                        G *= std::pow(ub, 1.0 / nu);
+                    }
+                    w = 2.0 * G;
                 }
-                w = 2.0 * G;
+                scale = std::sqrt(dof / w);
             }
-            scale = std::sqrt(dof / w);
-        }
-        const double rho = std::sqrt((W * W + Wp * Wp) / static_cast<double>(N));
-        out->rho[j] = rho;
-        out->amp[j] = sigma * rho;
-        out->psi[j] = -std::atan2(Wp, W) / (2.0 * M_PI);
-        double u[3] = {0.0, 0.0, 0.0};
-        for (int c = 0; c < d; ++c) {
-            const double kap = z[c] * scale;
-            out->kappa[j * d + c] = kap;
-            u[c] = kap / (2.0 * M_PI * p->ell[c]);
-        }
-        for (int c = 0; c < d; ++c) {
-            double a = u[c];
-            if (rotated) {  // a = R^T u
-                a = 0.0;
-                for (int k = 0; k < d; ++k) a += p->rot[k * 3 + c] * u[k];
+            const double rho = std::sqrt((W * W + Wp * Wp) / static_cast<double>(N));
+            out->rho[j] = rho;
+            out->amp[j] = sigma * rho;
+            out->psi[j] = -std::atan2(Wp, W) / (2.0 * M_PI);
+            double u[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < d; ++c) {
+                const double kap = z[c] * scale;
+                out->kappa[j * d + c] = kap;
+                u[c] = kap / (2.0 * M_PI * p->ell[c]);
             }
-            const double L = p->period[c];
-            if (L > 0.0) a = std::floor(a * L + 0.5) / L;  // periodic axis: multiple of 1/L
-            out->a[j * d + c] = a;
+            for (int c = 0; c < d; ++c) {
+                double a = u[c];
+                if (rotated) {  // a = R^T u
+                    a = 0.0;
+                    for (int k = 0; k < d; ++k) a += p->rot[k * 3 + c] * u[k];
+                }
+                const double L = p->period[c];
+                if (L > 0.0) a = std::floor(a * L + 0.5) / L;  // periodic axis: multiple of 1/L
+                out->a[j * d + c] = a;
+            }
         }
+    };
+    constexpr int64_t kModesPerThread = 1024;
+    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>(hw, (N + kModesPerThread - 1) / kModesPerThread);
+    alloc_point();
+    std::vector<int64_t> bad(static_cast<size_t>(nt), -1);
+    if (nt <= 1) {
+        draw_range(0, N, &bad[0]);
+    } else {
+        std::vector<std::thread> pool;
+        pool.reserve(static_cast<size_t>(nt));
+        try {
+            for (int64_t t = 0; t < nt; ++t)
+                pool.emplace_back(draw_range, N * t / nt, N * (t + 1) / nt, &bad[static_cast<size_t>(t)]);
+        } catch (...) {
+            for (auto& th : pool) th.join();  // never destroy a joinable thread
+            throw;
+        }
+        for (auto& th : pool) th.join();
     }
+    for (int64_t b : bad)
+        if (b >= 0) return fail(GRF_EINVAL, "gamma sampler did not accept for mode %lld", (long long)b);
     return GRF_OK;
 } catch (...) {
     return host_exception();
@@ -403,9 +432,29 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
         for (int c = 0; c < d; ++c) s += std::fabs(m->a[j * d + c]);
         h[j] = s;
     }
-    std::vector<int64_t> ord(N);
-    std::iota(ord.begin(), ord.end(), int64_t(0));
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t u, int64_t v) { return h[u] > h[v]; });
+    // order by |a|_1 descending, ties by original index: stable LSD radix sort
+    // (8-bit digits) of the complemented bit patterns (h >= 0, so the bits
+    // order as the values do)
+    std::vector<int64_t> ord(N), tmp(N);
+    std::vector<uint64_t> kb(N), kt(N);
+    for (int64_t j = 0; j < N; ++j) {
+        uint64_t u;
+        std::memcpy(&u, &h[j], sizeof(u));
+        kb[j] = ~u;
+        ord[j] = j;
+    }
+    for (int shift = 0; shift < 64; shift += 8) {
+        int64_t count[257] = {0};
+        for (int64_t j = 0; j < N; ++j) ++count[((kb[j] >> shift) & 0xFF) + 1];
+        for (int q = 0; q < 256; ++q) count[q + 1] += count[q];
+        for (int64_t j = 0; j < N; ++j) {
+            const int64_t dst = count[(kb[j] >> shift) & 0xFF]++;
+            kt[dst] = kb[j];
+            tmp[dst] = ord[j];
+        }
+        kb.swap(kt);
+        ord.swap(tmp);
+    }
     std::memset(base, 0, static_cast<size_t>(L.total));
 
     TableHeader hd{};
@@ -454,9 +503,10 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
         c0[7] = pl;
     }
     // kpref[b] = #{s : h_s * E_b > 1}, E_b = 2^((b - bias) / 4)
+    // (E_b grows with b, so the count only grows: one pass over the sorted modes)
+    int64_t k = 0;
     for (int b = 0; b < kBuckets; ++b) {
         const double Eb = std::pow(2.0, (b - kBucketBias) / 4.0);
-        int64_t k = 0;
         while (k < N && h[ord[k]] * Eb > 1.0) ++k;
         kpref[b] = static_cast<int32_t>(k);
     }

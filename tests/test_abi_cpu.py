@@ -56,6 +56,18 @@ def test_gen_modes_matches_oracle(abi, family, nu, dim):
         np.testing.assert_allclose(got[k], want[k], rtol=4e-15, atol=1e-300, err_msg=k)
 
 
+@pytest.mark.parametrize("family,nu", [(1, 0.0), (2, 1.3)])
+def test_gen_modes_threaded_ranges_match_oracle(abi, family, nu):
+    # more modes than one host thread draws: ranges of j run on several threads
+    from paper_2212_10961_gb300 import field as F
+    n = 4099
+    p = F.FieldParams(family=family, sigma2=1.0, ell=(0.2, 0.1, 0.05), dim=3, n_modes=n, seed=31, nu=nu)
+    got = F.gen_modes(p)
+    want = omodes.gen_modes(family, 1.0, (0.2, 0.1, 0.05), 3, n, 31, nu=nu)
+    for k in ("kappa", "rho", "psi", "a", "amp"):
+        np.testing.assert_allclose(got[k], want[k], rtol=4e-15, atol=1e-300, err_msg=k)
+
+
 def test_gen_modes_periodic_matches_oracle(abi):
     from paper_2212_10961_gb300 import field as F
     p = F.FieldParams(family="exponential", sigma2=1.0, ell=(0.2, 0.1, 0.05), dim=3, n_modes=500, seed=77,
