@@ -79,6 +79,7 @@ struct DF {  // double-float accumulator
 template <int MPT>
 struct BwdWarpSmem {
     float4 cd[kBwdTile];           // (x - x0, y - y0, z - z0, g)
+    float4 gd[kBwdTile];           // g (x - x0, y - y0, z - z0), 0: one FFMA per sum below
     float2 acc[32 * MPT][5];       // per mode: cos, sin, sin*x, sin*y, sin*z
 };
 
@@ -87,9 +88,12 @@ struct BwdWarpSmem {
 // tile in its own shared memory (no block-wide barrier).  The next tile's
 // coordinates and gradients are loaded into registers while the current
 // tile is being summed.
+constexpr int kBwdSmemBytes = static_cast<int>((kBwdThreads / 32) * sizeof(BwdWarpSmem<kMPT>));
+
 template <int DIM, int MPT>
 __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs args, int32_t* status) {
-    __shared__ BwdWarpSmem<MPT> wsm[kBwdThreads / 32];
+    extern __shared__ __align__(16) unsigned char bwd_raw[];
+    BwdWarpSmem<MPT>* wsm = reinterpret_cast<BwdWarpSmem<MPT>*>(bwd_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     BwdWarpSmem<MPT>& sm = wsm[warp];
@@ -164,7 +168,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int idx = q * 32 + lane;
-            sm.cd[idx] = make_float4(xv[q][0] - x0[0], xv[q][1] - x0[1], xv[q][2] - x0[2], gv[q]);
+            const float dx = xv[q][0] - x0[0], dy = xv[q][1] - x0[1], dz = xv[q][2] - x0[2];
+            sm.cd[idx] = make_float4(dx, dy, dz, gv[q]);
+            sm.gd[idx] = make_float4(gv[q] * dx, gv[q] * dy, gv[q] * dz, 0.f);
         }
         if (count_g) {
 #pragma unroll
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
 #pragma unroll 4
             for (int i = 0; i < kBwdTile; ++i) {
                 const float4 c = sm.cd[i];
+                const float4 gq = sm.gd[i];
 #pragma unroll
                 for (int k = 0; k < MPT; ++k) {
                     float th = fmaf(hot[k].x, c.x, t0[k]);
@@ -196,12 +203,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
                     if (DIM > 2) th = fmaf(hot[k].z, c.z, th);
                     const float cs = hw_cos(th);
                     const float sn = hw_sin(th);
-                    const float gs = c.w * sn;
                     sc[k] = fmaf(c.w, cs, sc[k]);
-                    ss[k] += gs;
-                    sx[k][0] = fmaf(gs, c.x, sx[k][0]);
-                    if (DIM > 1) sx[k][1] = fmaf(gs, c.y, sx[k][1]);
-                    if (DIM > 2) sx[k][2] = fmaf(gs, c.z, sx[k][2]);
+                    ss[k] = fmaf(c.w, sn, ss[k]);
+                    sx[k][0] = fmaf(gq.x, sn, sx[k][0]);
+                    if (DIM > 1) sx[k][1] = fmaf(gq.y, sn, sx[k][1]);
+                    if (DIM > 2) sx[k][2] = fmaf(gq.z, sn, sx[k][2]);
                 }
             }
         } else {
@@ -348,12 +354,24 @@ __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
 
 // Cell splits: the grid (mode_blocks x splits) should be a whole number of
 // waves of resident blocks, so that no SM idles in a partial last wave.
+// The per-warp tiles need more than the default 48 KB of shared memory per block.
+int bwd_allow_smem(int dim) {
+    cudaError_t e;
+    switch (dim) {
+        case 1: e = cudaFuncSetAttribute(bwd_partial_kernel<1, kMPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmemBytes); break;
+        case 2: e = cudaFuncSetAttribute(bwd_partial_kernel<2, kMPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmemBytes); break;
+        default: e = cudaFuncSetAttribute(bwd_partial_kernel<3, kMPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmemBytes); break;
+    }
+    return e;
+}
+
 template <int DIM>
 int choose_splits(int64_t n_cells, int mode_blocks) {
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_partial_kernel<DIM, kMPT>, kBwdThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_partial_kernel<DIM, kMPT>, kBwdThreads,
+                                                  kBwdSmemBytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t resident = static_cast<int64_t>(sms) * per_sm;
     const int64_t tiles = (n_cells + kBwdTile - 1) / kBwdTile;
@@ -393,6 +411,7 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (const int e = bwd_allow_smem(dim)) return e;
     const TableLayout TL = table_layout(n_modes);
     const unsigned char* tb = static_cast<const unsigned char*>(table);
     BwdArgs a{};
@@ -437,9 +456,9 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     } else {
         dim3 grid(mode_blocks, a.splits);
         switch (dim) {
-            case 1: bwd_partial_kernel<1, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
-            case 2: bwd_partial_kernel<2, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
-            case 3: bwd_partial_kernel<3, kMPT><<<grid, kBwdThreads, 0, st>>>(a, status); break;
+            case 1: bwd_partial_kernel<1, kMPT><<<grid, kBwdThreads, kBwdSmemBytes, st>>>(a, status); break;
+            case 2: bwd_partial_kernel<2, kMPT><<<grid, kBwdThreads, kBwdSmemBytes, st>>>(a, status); break;
+            case 3: bwd_partial_kernel<3, kMPT><<<grid, kBwdThreads, kBwdSmemBytes, st>>>(a, status); break;
             default: return cudaErrorInvalidValue;
         }
         count_launches(1);
