@@ -195,6 +195,17 @@ int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t *seg_offsets,
                    const float *x, const float *y, const float *z, void *plan,
                    size_t plan_bytes, void *stream);
 
+/*
+ * grf_release -- drop the library's host-side record of a plan (built by
+ * grf_plan_cells) or of a batch workspace (prepared by grf_batch_prepare).
+ * The library keeps one small record per such buffer for the life of the
+ * process; release it before the caller frees or reuses the buffer, so that
+ * a stale pointer passed later is rejected (GRF_EINVAL) instead of being
+ * read as a plan.  The device buffer itself is untouched.  Pointers the
+ * library does not know are ignored.  Returns GRF_OK.
+ */
+int grf_release(const void *buffer);
+
 /* Device status word of a plan (0 = no device-side error).  Synchronises
  * the stream.  Bits: 1 = non-finite coordinate, 2 = bounded wait expired,
  * 4 = table/plan mismatch detected on the device. */

@@ -286,6 +286,13 @@ const char* grf_version(void) { return "grf-gb300 1.0"; }
 
 int64_t grf_launch_count(void) { return g_launches.load(); }
 
+int grf_release(const void* buffer) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_plans.erase(buffer);
+    g_batches.erase(buffer);
+    return GRF_OK;
+}
+
 int grf_debug_inject_alloc_failures(int32_t n) {
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
     g_inject_alloc.store(n);

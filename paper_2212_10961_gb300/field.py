@@ -185,6 +185,15 @@ class CellPlan:
                                    _ptr(x), _ptr(y), _ptr(z), _ptr(self.buf), self.nbytes,
                                    _stream_handle(stream)))
 
+    def __del__(self):
+        # the library forgets this buffer before torch can hand its memory to another tensor
+        buf = getattr(self, "buf", None)
+        if buf is not None:
+            try:
+                lib().grf_release(_ptr(buf))
+            except Exception:  # interpreter shutdown
+                pass
+
     def segment_size(self, s):
         """Cells in segment s (0 for an out-of-range index; the C ABI rejects it)."""
         if not 0 <= s < self.n_segments:
@@ -536,6 +545,14 @@ class Batch:
                                           _ptr(self.host), _stream_handle(stream)))
             self.tile_cells = int(tile_cells)
         self.graph = None
+
+    def __del__(self):
+        ws = getattr(self, "ws", None)
+        if ws is not None:
+            try:
+                lib().grf_release(_ptr(ws))
+            except Exception:  # interpreter shutdown
+                pass
 
     def launch(self, stream=None):
         check(lib().grf_batch_launch(_ptr(self.ws), _stream_handle(stream)))

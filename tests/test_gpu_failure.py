@@ -66,3 +66,21 @@ def test_injected_allocation_failure_in_plan_and_synthesis():
     torch.cuda.synchronize()
     assert plan.status() == 0
     assert torch.equal(got, want)
+
+
+def test_released_plan_is_rejected():
+    # after grf_release the library no longer accepts the buffer as a plan
+    torch = gpu_env()
+    from paper_2212_10961_gb300 import _abi
+    from paper_2212_10961_gb300 import field as F
+    from paper_2212_10961_gb300 import workloads as W
+    plan = F.CellPlan(*to_dev(torch, W.grid_centres((20, 16))))
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=128, seed=2)
+    gf = F.GaussianField(p)
+    gf.synth(plan)
+    assert _abi.lib().grf_release(plan.ptr) == 0
+    with pytest.raises(_abi.GRFError) as e:
+        gf.synth(plan)
+    assert e.value.code == _abi.GRF_EINVAL
+    assert _abi.lib().grf_release(plan.ptr) == 0  # unknown pointers are ignored
+    torch.cuda.synchronize()
