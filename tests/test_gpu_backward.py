@@ -127,6 +127,37 @@ def test_diff128_full_size_identities(env):
     assert np.array_equal(gr2["dA"].cpu().numpy(), dA)
 
 
+@pytest.mark.slow
+def test_diff128_full_size_against_oracle(env):
+    # the 128^3 forward + adjoint workload on all 2,097,152 cells: the GPU field,
+    # loss and every gradient against the FP64 oracle's own (C, OpenMP)
+    torch, F, W = env
+    w = W.WORKLOADS["diff128"]
+    cells = W.workload_cells("diff128")
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=1)
+    pt = F.FieldParams(family="gaussian", sigma2=1.0, ell=w["ell"], dim=3, n_modes=w["n_modes"], seed=2)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    gf = F.GaussianField(p)
+    out = gf.synth(plan, F.MapSpec(y=True, lognormal=True))
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    loss, gY = F.mismatch_grad(out["K"], T)
+    gr = F.backward(gf.table, p, plan, gY)
+    torch.cuda.synchronize()
+    from oracle import field as of
+    om = oracle_modes("gaussian", 1.0, w["ell"], 3, w["n_modes"], 1)
+    omt = oracle_modes("gaussian", 1.0, w["ell"], 3, w["n_modes"], 2)
+    y_or = oracle_field(om, 0.0, cells)
+    assert np.max(np.abs(out["Y"].cpu().numpy().astype(np.float64) - y_or)) <= 1e-5
+    l_or, g_or = of.mismatch_loss(np.exp(y_or), np.exp(oracle_field(omt, 0.0, cells)))
+    assert loss.item() == pytest.approx(l_or, rel=1e-4)
+    ref = _oracle_grads(om, cells, g_or, 1.0, w["ell"])
+    errs = {k: _check(gr[k].cpu().numpy(), ref[k], k) for k in ("dA", "dpsi", "da")}
+    assert abs(gr["dmu"].item() - ref["dmu"]) <= GRAD_TOL * abs(ref["dmu"]) + 1e-12
+    assert abs(gr["dsigma"].item() - ref["dsigma"]) <= GRAD_TOL * abs(ref["dsigma"]) + GRAD_TOL * np.max(np.abs(ref["dA"]))
+    np.testing.assert_allclose(gr["dell"].cpu().numpy(), ref["dell"], rtol=1e-3)
+    print("diff 128^3 gradient errors (relative to max):", errs)
+
+
 def test_autograd_wrappers(env):
     torch, F, W = env
     cells = W.grid_centres((30, 30, 12))

@@ -101,7 +101,8 @@ def test_grid3d_256_full_size_sampled(env):
     out, p, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], maps=maps)
     om = oracle_modes(w["family"], w["sigma2"], w["ell"], 3, w["n_modes"], w["seed"])
     rng = np.random.default_rng(1)
-    idx = np.concatenate([rng.choice(len(cells[0]), 30000, replace=False),
+    # one million sampled cells (plus the first and last ones) against the FP64 oracle
+    idx = np.concatenate([rng.choice(len(cells[0]), 1000000, replace=False),
                           np.arange(256), len(cells[0]) - 1 - np.arange(256)])
     y_or = oracle_field(om, 0.0, cells, idx)
     err = check_forward(out["Y"][idx], y_or, sig, "grid3d 256^3")
@@ -121,7 +122,7 @@ def test_jitter3d_reduced_and_full_sampled(env):
     cells = W.workload_cells("jitter3d_2m")
     assert len(cells[0]) == 2000376
     out, _, _ = run(env, cells, w["family"], w["sigma2"], w["ell"], w["n_modes"], w["seed"], nu=w["nu"])
-    idx = np.random.default_rng(2).choice(len(cells[0]), 20000, replace=False)
+    idx = np.random.default_rng(2).choice(len(cells[0]), 1000000, replace=False)
     err = check_forward(out["Y"][idx], oracle_field(om, 0.0, cells, idx), sig, "jitter full")
     print("jitter3d full sampled max err %.3e sigma" % err)
 
