@@ -196,6 +196,19 @@ def test_map_standalone_ragged_and_misaligned(env, off, n):
     assert np.array_equal(st["facies"].cpu().numpy(), out["facies"][off:off + n])
 
 
+def test_lognormal_map_exponential_accuracy(env):
+    # K = k_ref exp(Y) over a wide range of Y, against FP64 exp of the same FP32 values
+    torch, F, W = env
+    y = np.concatenate([np.linspace(-80.0, 80.0, 200001), np.random.default_rng(3).normal(0.0, 3.0, 100000)])
+    y = y.astype(np.float32)
+    st = F.map_property(torch.from_numpy(y).cuda(), F.MapSpec(y=False, lognormal=True, k_ref=1.0), 0.0, 1.0)
+    torch.cuda.synchronize()
+    k = st["K"].cpu().numpy().astype(np.float64)
+    want = np.exp(y.astype(np.float64))
+    rel = np.abs(k - want) / want
+    assert np.max(rel) <= 2.0 ** -20, "max relative error %.3e" % np.max(rel)
+
+
 def test_segments_share_one_plan(env):
     torch, F, W = env
     a = W.grid_centres((40, 30))
