@@ -5,14 +5,16 @@
 // split each phase at a per-warp origin, which is accurate and cheap only when
 // a warp's cells are close together.  The plan provides that locality:
 //   1. bounding box of every segment (ordered-int atomics, warp-aggregated);
-//   2. an isotropic quantisation grid of 2^10 levels along the longest axis;
-//   3. 64-bit keys (segment << 30 | Morton code of the quantised position);
+//   2. an isotropic quantisation grid along the longest axis, about one
+//      level per cell spacing of the largest segment (at most 2^10 levels);
+//   3. 64-bit keys (segment above the Morton code of the quantised position);
 //   4. stable LSD radix sort of (key, original index), 8-bit digits;
 //   5. gather of the sorted SoA coordinates.
 // Everything runs on the stream without host synchronisation and is
 // deterministic (the sort is stable, so equal keys keep the input order).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <new>
 
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kBoxThreads)
 // (L_max = largest bounding-box extent), so that the Morton (Z-order) code
 // of the quantised position orders cells along a space-filling curve and
 // every aligned run of 2^k sorted cells is a compact, roughly cubic block.
-__global__ void brick_kernel(SegInfo* segs, int n_segments, int dim) {
+__global__ void brick_kernel(SegInfo* segs, int n_segments, int dim, int level_bits) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_segments) return;
     SegInfo& g = segs[s];
@@ -159,7 +161,7 @@ __global__ void brick_kernel(SegInfo* segs, int n_segments, int dim) {
         L[k] = hi - lo;
         Lmax = fmaxf(Lmax, L[k]);
     }
-    const double levels = double(1 << kMortonBits);
+    const double levels = double(1 << level_bits);
     for (int k = 0; k < 3; ++k) {
         int nb = 1;
         float inv = 0.f;
@@ -194,7 +196,7 @@ __device__ __forceinline__ uint32_t spread_bits2(uint32_t v) {  // 10 bits -> ev
 __global__ void key_kernel(const float* __restrict__ x, const float* __restrict__ y,
                            const float* __restrict__ z, int dim, int64_t n,
                            const SegInfo* __restrict__ segs, int n_segments,
-                           uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+                           uint64_t* __restrict__ keys, int32_t* __restrict__ vals, int morton_bits) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = find_segment(segs, n_segments, i);
@@ -214,7 +216,7 @@ __global__ void key_kernel(const float* __restrict__ x, const float* __restrict_
         morton = spread_bits2(b[0]) | (spread_bits2(b[1]) << 1);
     else
         morton = b[0];
-    keys[i] = (static_cast<uint64_t>(s) << 30) | morton;
+    keys[i] = (static_cast<uint64_t>(s) << morton_bits) | morton;
     vals[i] = static_cast<int32_t>(i);
 }
 
@@ -407,17 +409,29 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     const unsigned grid = static_cast<unsigned>((n + tpb - 1) / tpb);
     bbox_kernel<<<static_cast<unsigned>((n + kBoxItems - 1) / kBoxItems), kBoxThreads, 0, st>>>(
         x, y, z, dim, n, segs, n_segments, &hdr->status);
-    brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim);
-    key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, perm);
+    // Quantisation levels along the longest axis: about one level per cell
+    // spacing of the largest segment (n^(1/dim) rounded up to a power of
+    // two, 16 .. 2^kMortonBits), so that no sort pass is spent on key bits
+    // finer than the cells.
+    int64_t n_max = 0;
+    for (int s = 0; s < n_segments; ++s) {
+        const int64_t c = seg_offsets_host[s + 1] - seg_offsets_host[s];
+        if (c > n_max) n_max = c;
+    }
+    int level_bits = 4;
+    while (level_bits < kMortonBits &&
+           std::pow(2.0, static_cast<double>(level_bits * dim)) < static_cast<double>(n_max))
+        ++level_bits;
+    const int morton_bits = dim * level_bits;
+    brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim, level_bits);
+    key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, perm, morton_bits);
     count_launches(3);
 
-    int key_bits = 30;
+    int key_bits = morton_bits;
     if (n_segments > 1) {
         int sb = 0;
         while ((1 << sb) < n_segments) ++sb;
         key_bits += sb;
-    } else {
-        key_bits = dim * kMortonBits;
     }
     const int passes = (key_bits + 7) / 8;
     const int64_t nblk = sort_blocks(n);
