@@ -94,8 +94,29 @@ __global__ void __launch_bounds__(kBoxThreads)
     int seg = s_first;
     int64_t seg_end = s_first + 1 < n_segments ? segs[s_first + 1].begin : n;
     bool bad = false;
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += kBoxThreads) {
-        if (!single && i >= seg_end) {
+    if (single) {
+        // one segment: every coordinate load of the thread issued before its reductions
+        constexpr int kPer = kBoxItems / kBoxThreads;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k >= dim) break;
+            float v[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int64_t i = c0 + threadIdx.x + static_cast<int64_t>(q) * kBoxThreads;
+                v[q] = i < c1 ? src[k][i] : src[k][c0];
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                bad |= !isfinite(v[q]);
+                const int32_t o = float_to_ordered(v[q]);
+                lo[k] = min(lo[k], o);
+                hi[k] = max(hi[k], o);
+            }
+        }
+    }
+    for (int64_t i = c0 + threadIdx.x; !single && i < c1; i += kBoxThreads) {
+        if (i >= seg_end) {
             box_flush(segs, seg, dim, lo, hi);
             for (int k = 0; k < 3; ++k) {
                 lo[k] = float_to_ordered(INFINITY);
@@ -229,10 +250,15 @@ __global__ void __launch_bounds__(kSortThreads)
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d] = 0u;
     __syncthreads();
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 0xffu], 1u);
+    uint64_t k[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {  // loads first, all in flight together
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        k[r] = i < n ? keys[i] : 0ull;
     }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r)
+        if (base + r * kSortThreads + threadIdx.x < n) atomicAdd(&hist[(k[r] >> shift) & 0xffu], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
         counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
