@@ -92,6 +92,46 @@ class FieldParams:
         return p
 
 
+def from_dictionary(d, seed=1):
+    """Configuration from the keys of the paper's setRandomField dictionary
+    (Appendix B): returns {"type", "params", "maps", "thresholds2"}.
+
+    type         "truncated" (one field) or "bitruncated" (two fields on
+                 generator streams 0 and 1, the second thresholded by
+                 thresholds2; see PluriGaussianField)
+    correlation  "gaussian", "exponential" or "matern"
+    Kmean, Ksigma  mean and variance of the Gaussian field Y
+    Lcorr        correlation lengths (x, y, z)
+    nu           Matern smoothness (the paper's rho is not used)
+    nfreq        number of modes N
+    disableY, disableZ  drop an axis: the field's dimension is 3 minus the
+                 disabled axes, and the coordinates passed are the enabled
+                 ones in (x, y, z) order
+    periodic     per-axis domain lengths (0 = not periodic)
+    values, thresholds  facies values and thresholds (Y units)
+    The seed is not a dictionary key of the paper; it is the second argument.
+    """
+    keep = [True, not d.get("disableY", False), not d.get("disableZ", False)]
+    axes = [c for c in range(3) if keep[c]]
+    lcorr = list(d.get("Lcorr", (1.0, 1.0, 1.0)))
+    lcorr += [lcorr[-1]] * (3 - len(lcorr))
+    per = list(d.get("periodic", (0.0, 0.0, 0.0)) or (0.0, 0.0, 0.0))
+    per += [0.0] * (3 - len(per))
+    params = FieldParams(family=str(d.get("correlation", "gaussian")).lower(), sigma2=float(d.get("Ksigma", 1.0)),
+                         mean=float(d.get("Kmean", 0.0)), ell=tuple(float(lcorr[c]) for c in axes),
+                         dim=len(axes), n_modes=int(d.get("nfreq", 1000)), seed=int(seed),
+                         nu=float(d.get("nu", 1.5)), period=tuple(float(per[c]) for c in axes))
+    thr = tuple(float(t) for t in d.get("thresholds", ()))
+    vals = d.get("values")
+    kind = str(d.get("type", "truncated")).lower()
+    if kind not in ("truncated", "bitruncated"):
+        raise ValueError("type must be truncated or bitruncated")
+    maps = MapSpec(y=True, lognormal=False, thresholds=thr, facies=len(thr) > 0,
+                   values=tuple(float(v) for v in vals) if (vals is not None and kind == "truncated") else None)
+    return {"type": kind, "params": params, "maps": maps,
+            "thresholds2": tuple(float(t) for t in d.get("thresholds2", ()))}
+
+
 def _modes_struct(n, dim, arrays):
     m = _abi.grf_modes()
     m.n = n

@@ -226,3 +226,26 @@ def test_null_and_unknown_handles_rejected(abi):
     offs = (ctypes.c_int64 * 2)(5, 10)
     assert L.grf_plan_cells(3, 1, offs, None, None, None, ctypes.c_void_p(1 << 12), 1 << 20,
                             None) == abi.GRF_EINVAL
+
+
+def test_from_dictionary_maps_appendix_b_keys(abi):
+    # the setRandomField dictionary keys of Appendix B map onto FieldParams and
+    # MapSpec; the modes drawn equal those of the explicit parameters
+    from paper_2212_10961_gb300 import field as F
+    d = {"type": "truncated", "correlation": "matern", "Kmean": 0.3, "Ksigma": 2.0,
+         "Lcorr": [0.2, 0.1, 0.05], "nu": 1.5, "rho": 7.0, "nfreq": 300, "disableY": True,
+         "thresholds": [-0.5, 0.5], "values": [1.0, 10.0, 100.0], "periodic": [2.0, 0.0, 0.0]}
+    cfg = F.from_dictionary(d, seed=42)
+    p = cfg["params"]
+    assert (p.family, p.mean, p.sigma2, p.dim, p.n_modes, p.seed, p.nu) == ("matern", 0.3, 2.0, 2, 300, 42, 1.5)
+    assert tuple(p.ell) == (0.2, 0.05) and tuple(p.period) == (2.0, 0.0)
+    assert cfg["maps"].thresholds == (-0.5, 0.5) and cfg["maps"].facies and cfg["maps"].values == (1.0, 10.0, 100.0)
+    explicit = F.FieldParams(family="matern", sigma2=2.0, mean=0.3, ell=(0.2, 0.05), dim=2, n_modes=300, seed=42,
+                             nu=1.5, period=(2.0, 0.0))
+    a, b = F.gen_modes(p), F.gen_modes(explicit)
+    for k in ("a", "amp", "psi"):
+        np.testing.assert_array_equal(a[k], b[k])
+    cfg2 = F.from_dictionary({"type": "bitruncated", "disableZ": True, "thresholds2": [0.1]})
+    assert cfg2["type"] == "bitruncated" and cfg2["params"].dim == 2 and cfg2["thresholds2"] == (0.1,)
+    with pytest.raises(ValueError):
+        F.from_dictionary({"type": "other"})
