@@ -449,10 +449,6 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
            std::pow(2.0, static_cast<double>(level_bits * dim)) < static_cast<double>(n_max))
         ++level_bits;
     const int morton_bits = dim * level_bits;
-    brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim, level_bits);
-    key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, perm, morton_bits);
-    count_launches(3);
-
     int key_bits = morton_bits;
     if (n_segments > 1) {
         int sb = 0;
@@ -461,10 +457,15 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     }
     const int passes = (key_bits + 7) / 8;
     const int64_t nblk = sort_blocks(n);
+    // the index array ping-pongs between perm and vals_b: start where an odd
+    // number of passes ends in perm
+    int32_t* vin = passes % 2 == 1 ? vals_b : perm;
+    int32_t* vout = passes % 2 == 1 ? perm : vals_b;
+    brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim, level_bits);
+    key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, vin, morton_bits);
+    count_launches(3);
     uint64_t* kin = keys_a;
     uint64_t* kout = keys_b;
-    int32_t* vin = perm;
-    int32_t* vout = vals_b;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         radix_hist_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(kin, n, shift, counts,
