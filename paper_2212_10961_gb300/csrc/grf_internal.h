@@ -76,7 +76,7 @@ inline TableLayout table_layout(int64_t n_modes) {
 //   segs    : SegInfo[n_segments]
 //   xs,ys,zs: float[n_cells] sorted coordinates
 //   perm    : int32[n_cells] original (plan-global) index of sorted cell i
-//   keys_in, keys_out : uint64[n_cells]   (planning scratch)
+//   keys_in, keys_out : uint32[n_cells]   (planning scratch)
 //   vals_in           : int32[n_cells]    (planning scratch)
 //   sort_tmp          : radix-sort temporary storage
 // ---------------------------------------------------------------------------
@@ -120,8 +120,8 @@ inline PlanLayout plan_layout(int64_t n_cells, int32_t n_segments) {
     L.off_zs = L.off_ys + align256(n_cells * 4);
     L.off_perm = L.off_zs + align256(n_cells * 4);
     L.off_keys_in = L.off_perm + align256(n_cells * 4);
-    L.off_keys_out = L.off_keys_in + align256(n_cells * 8);
-    L.off_vals_in = L.off_keys_out + align256(n_cells * 8);
+    L.off_keys_out = L.off_keys_in + align256(n_cells * 4);
+    L.off_vals_in = L.off_keys_out + align256(n_cells * 4);
     L.off_sort_tmp = L.off_vals_in + align256(n_cells * 4);
     L.sort_tmp_bytes = int64_t(radix_sort_temp_bytes(n_cells));
     L.total = L.off_sort_tmp + align256(L.sort_tmp_bytes);

@@ -6,8 +6,9 @@
 // a warp's cells are close together.  The plan provides that locality:
 //   1. bounding box of every segment (ordered-int atomics, warp-aggregated);
 //   2. an isotropic quantisation grid along the longest axis, about one
-//      level per cell spacing of the largest segment (at most 2^10 levels);
-//   3. 64-bit keys (segment above the Morton code of the quantised position);
+//      level per four cell spacings of the largest segment (at most 2^10);
+//   3. 32-bit keys, the segment index above the Morton code of the quantised
+//      position, the first digit counted as they are made;
 //   4. stable LSD radix sort of (key, original index), 8-bit digits;
 //   5. gather of the sorted SoA coordinates.
 // Everything runs on the stream without host synchronisation and is
@@ -67,9 +68,11 @@ __global__ void seg_init_kernel(SegInfo* segs, int n_segments) {
 constexpr int kBoxThreads = 256;
 constexpr int kBoxItems = kBoxThreads * 16;
 
-__device__ __forceinline__ void box_flush(SegInfo* segs, int seg, int dim, const int32_t* lo,
-                                          const int32_t* hi) {
-    for (int k = 0; k < dim; ++k) {
+__device__ __forceinline__ void box_flush(SegInfo* segs, int seg, int dim, const int32_t (&lo)[3],
+                                          const int32_t (&hi)[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= dim) break;
         atomicMin(reinterpret_cast<int32_t*>(segs[seg].lo) + k, lo[k]);
         atomicMax(reinterpret_cast<int32_t*>(segs[seg].hi) + k, hi[k]);
     }
@@ -97,23 +100,23 @@ __global__ void __launch_bounds__(kBoxThreads)
     if (single) {
         // one segment: every coordinate load of the thread issued before its reductions
         constexpr int kPer = kBoxItems / kBoxThreads;
+        float v[3][kPer];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (k >= dim) break;
-            float v[kPer];
+        for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const int64_t i = c0 + threadIdx.x + static_cast<int64_t>(q) * kBoxThreads;
-                v[q] = i < c1 ? src[k][i] : src[k][c0];
+                v[k][q] = k < dim ? src[k][i < c1 ? i : c0] : 0.f;
             }
 #pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
             for (int q = 0; q < kPer; ++q) {
-                bad |= !isfinite(v[q]);
-                const int32_t o = float_to_ordered(v[q]);
+                bad |= !isfinite(v[k][q]);
+                const int32_t o = float_to_ordered(v[k][q]);
                 lo[k] = min(lo[k], o);
                 hi[k] = max(hi[k], o);
             }
-        }
     }
     for (int64_t i = c0 + threadIdx.x; !single && i < c1; i += kBoxThreads) {
         if (i >= seg_end) {
@@ -125,7 +128,9 @@ __global__ void __launch_bounds__(kBoxThreads)
             seg = find_segment(segs, n_segments, i);
             seg_end = seg + 1 < n_segments ? segs[seg + 1].begin : n;
         }
-        for (int k = 0; k < dim; ++k) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k >= dim) break;
             const float v = src[k][i];
             bad |= !isfinite(v);
             const int32_t o = float_to_ordered(v);
@@ -139,7 +144,9 @@ __global__ void __launch_bounds__(kBoxThreads)
         return;
     }
     const int warp = threadIdx.x >> 5;
-    for (int k = 0; k < dim; ++k) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= dim) break;
         for (int off = 16; off > 0; off >>= 1) {
             lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
             hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
@@ -152,7 +159,9 @@ __global__ void __launch_bounds__(kBoxThreads)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < kBoxThreads / 32; ++w)
-            for (int k = 0; k < dim; ++k) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k >= dim) break;
                 lo[k] = min(lo[k], red_lo[w][k]);
                 hi[k] = max(hi[k], red_hi[w][k]);
             }
@@ -214,51 +223,82 @@ __device__ __forceinline__ uint32_t spread_bits2(uint32_t v) {  // 10 bits -> ev
     return v;
 }
 
-__global__ void key_kernel(const float* __restrict__ x, const float* __restrict__ y,
-                           const float* __restrict__ z, int dim, int64_t n,
-                           const SegInfo* __restrict__ segs, int n_segments,
-                           uint64_t* __restrict__ keys, int32_t* __restrict__ vals, int morton_bits) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int s = find_segment(segs, n_segments, i);
-    const SegInfo& g = segs[s];
-    float v[3] = {x[i], dim > 1 ? y[i] : 0.f, dim > 2 ? z[i] : 0.f};
+__device__ __forceinline__ uint32_t morton_code(const float (&v)[3], const SegInfo& g, int dim) {
     uint32_t b[3] = {0u, 0u, 0u};
-    for (int k = 0; k < dim; ++k) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k >= dim) break;
         float f = (v[k] - g.lo[k]) * g.inv_brick[k];
         int q = isfinite(f) ? static_cast<int>(floorf(f)) : 0;
         q = q < 0 ? 0 : (q >= g.nb[k] ? g.nb[k] - 1 : q);
         b[k] = static_cast<uint32_t>(q);
     }
-    uint32_t morton;
-    if (dim == 3)
-        morton = spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
-    else if (dim == 2)
-        morton = spread_bits2(b[0]) | (spread_bits2(b[1]) << 1);
-    else
-        morton = b[0];
-    keys[i] = (static_cast<uint64_t>(s) << morton_bits) | morton;
-    vals[i] = static_cast<int32_t>(i);
+    if (dim == 3) return spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
+    if (dim == 2) return spread_bits2(b[0]) | (spread_bits2(b[1]) << 1);
+    return b[0];
+}
+
+// Sort keys (segment index above the Morton code), one sort tile per block,
+// fused with the digit-0 histogram of the tile (the first radix pass needs no
+// separate counting kernel).  The values of the first pass are the input
+// indices themselves, so none are stored here.
+__global__ void __launch_bounds__(kSortThreads)
+    key_kernel(const float* __restrict__ x, const float* __restrict__ y, const float* __restrict__ z,
+               int dim, int64_t n, const SegInfo* __restrict__ segs, int n_segments,
+               uint32_t* __restrict__ keys, int morton_bits, uint32_t* __restrict__ counts, int nblk) {
+    __shared__ uint32_t hist[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d] = 0u;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
+    const int64_t c1 = base + kSortTile < n ? base + kSortTile : n;
+    const int s_first = find_segment(segs, n_segments, base);
+    const bool single = s_first == find_segment(segs, n_segments, c1 - 1);
+    __syncthreads();
+    constexpr int kGroup = 8;  // cells whose loads are in flight together
+#pragma unroll 1
+    for (int r0 = 0; r0 < kSortItems; r0 += kGroup) {
+        float v[kGroup][3];
+#pragma unroll
+        for (int r = 0; r < kGroup; ++r) {
+            const int64_t i = base + (r0 + r) * kSortThreads + threadIdx.x;
+            const int64_t j = i < n ? i : base;
+            v[r][0] = x[j];
+            v[r][1] = dim > 1 ? y[j] : 0.f;
+            v[r][2] = dim > 2 ? z[j] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < kGroup; ++r) {
+            const int64_t i = base + (r0 + r) * kSortThreads + threadIdx.x;
+            if (i >= n) continue;
+            const int s = single ? s_first : find_segment(segs, n_segments, i);
+            const uint32_t key = (static_cast<uint32_t>(s) << morton_bits) | morton_code(v[r], segs[s], dim);
+            keys[i] = key;
+            atomicAdd(&hist[key & 0xffu], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
 }
 
 // ---- stable LSD radix sort, 8-bit digits -----------------------------------------
 
 __global__ void __launch_bounds__(kSortThreads)
-    radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
+    radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
                       uint32_t* __restrict__ counts, int nblk) {
     __shared__ uint32_t hist[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d] = 0u;
     __syncthreads();
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
-    uint64_t k[kSortItems];
+    uint32_t k[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {  // loads first, all in flight together
         const int64_t i = base + r * kSortThreads + threadIdx.x;
-        k[r] = i < n ? keys[i] : 0ull;
+        k[r] = i < n ? keys[i] : uint32_t(0);
     }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r)
-        if (base + r * kSortThreads + threadIdx.x < n) atomicAdd(&hist[(k[r] >> shift) & 0xffu], 1u);
+        if (base + r * kSortThreads + threadIdx.x < n)
+            atomicAdd(&hist[(k[r] >> shift) & 0xffu], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
         counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
@@ -293,81 +333,121 @@ __global__ void __launch_bounds__(kScanThreads)
     if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = part[kScanThreads - 1];
 }
 
-// Stable scatter: item order inside a tile is (round, warp, lane), which is
-// the input order; ranks are counted in that order.
-__global__ void __launch_bounds__(kSortThreads)
-    radix_scatter_kernel(const uint64_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
-                         uint64_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
-                         int64_t n, int shift, const uint32_t* __restrict__ offsets,
+// Stable scatter.  Warp w owns items [512 w, 512 (w + 1)) of the tile, in
+// 16 rounds of 32 consecutive items, so (warp, round, lane) is the input
+// order.  Each warp ranks its items per digit on its own (match_any within a
+// round, a warp-private running count across rounds); one block barrier then
+// turns the per-warp counts into offsets, and every item is stored at the
+// digit's global start + its warp's offset + its rank within the warp.
+// kFirst: the values are the input indices (nothing to read); kLast: only
+// the values are stored.
+template <bool kFirst, bool kLast>
+__global__ void __launch_bounds__(kSortThreads, kFirst || kLast ? 3 : 2)
+    radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+                         uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
+                         int64_t n64, int shift, const uint32_t* __restrict__ offsets,
                          const uint32_t* __restrict__ totals, int nblk) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t base[kRadix];           // global start of each digit for this tile
-    __shared__ uint32_t running[kRadix];        // items of each digit placed so far
-    __shared__ uint32_t warp_cnt[kWarps][kRadix];
-    __shared__ uint32_t warp_off[kWarps][kRadix];
+    constexpr int kRounds = kSortTile / kSortThreads;  // rounds of 32 items per warp
+    static_assert(kRounds % 2 == 0 && kRounds * 32 <= 65536, "ranks are packed two per register");
+    __shared__ uint32_t scan[kRadix];
+    __shared__ uint32_t warp_cnt[kWarps][kRadix];  // per-warp digit counts, then offsets
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    // digit offsets: exclusive scan of the digit totals (kRadix == blockDim.x)
-    {
-        const int d = threadIdx.x;
-        running[d] = totals[d];
-        __syncthreads();
-        for (int off = 1; off < kRadix; off <<= 1) {
-            const uint32_t v = d >= off ? running[d - off] : 0u;
-            __syncthreads();
-            running[d] += v;
-            __syncthreads();
-        }
-        const uint32_t excl = running[d] - totals[d];
-        __syncthreads();
-        base[d] = excl + offsets[static_cast<int64_t>(d) * nblk + blockIdx.x];
-        running[d] = 0u;
+    // plans hold at most 2^31 - 1 cells, so item indices fit in 32 bits
+    const uint32_t n = static_cast<uint32_t>(n64);
+    const uint32_t i0 = blockIdx.x * static_cast<uint32_t>(kSortTile) + warp * (kRounds * 32) + lane;
+    uint32_t key[kRounds];
+    int32_t val[kFirst ? 1 : kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {  // loads first, all in flight together
+        const uint32_t i = i0 + r * 32;
+        key[r] = i < n ? keys_in[i] : 0u;
+        if (!kFirst) val[r] = i < n ? vals_in[i] : 0;
     }
     for (int k = threadIdx.x; k < kWarps * kRadix; k += blockDim.x) (&warp_cnt[0][0])[k] = 0u;
+    // digit starts: exclusive scan of the digit totals (kRadix == blockDim.x)
+    const int d0 = threadIdx.x;
+    scan[d0] = totals[d0];
     __syncthreads();
-    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * kSortTile;
+    for (int off = 1; off < kRadix; off <<= 1) {
+        const uint32_t v = d0 >= off ? scan[d0 - off] : 0u;
+        __syncthreads();
+        scan[d0] += v;
+        __syncthreads();
+    }
+    const uint32_t digit_base = scan[d0] - totals[d0] + offsets[static_cast<int64_t>(d0) * nblk + blockIdx.x];
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t i = tbase + r * kSortThreads + threadIdx.x;
-        const bool in = i < n;
-        uint64_t key = in ? keys_in[i] : 0ull;
-        int32_t val = in ? vals_in[i] : 0;
-        // out-of-range items get a digit of their own (never stored)
-        const int digit = in ? static_cast<int>((key >> shift) & 0xffu) : kRadix;
+    uint32_t loc[kRounds / 2];  // rank of each item among its warp's items of the same digit
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const bool in = i0 + r * 32 < n;
+        // out-of-range items get a digit of their own (never counted or stored)
+        const int digit = in ? static_cast<int>((key[r] >> shift) & 0xffu) : kRadix;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
-        const int rank = __popc(peers & lt_mask);
-        const bool leader = (peers & lt_mask) == 0u;
-        if (leader && in) warp_cnt[warp][digit] = __popc(peers);
-        __syncthreads();
-        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-            uint32_t run = running[d];
-            for (int w = 0; w < kWarps; ++w) {
-                warp_off[w][d] = run;
-                run += warp_cnt[w][d];
-                warp_cnt[w][d] = 0u;
-            }
-            running[d] = run;
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0u;
+        if (lane == leader && in) {
+            before = warp_cnt[warp][digit];
+            warp_cnt[warp][digit] = before + static_cast<uint32_t>(__popc(peers));
         }
-        __syncthreads();
-        if (in) {
-            const uint32_t pos = base[digit] + warp_off[warp][digit] + static_cast<uint32_t>(rank);
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+        before = __shfl_sync(0xffffffffu, before, leader);
+        const uint32_t rank = before + static_cast<uint32_t>(__popc(peers & lt_mask));
+        if (r % 2 == 0)
+            loc[r / 2] = rank;
+        else
+            loc[r / 2] |= rank << 16;
+    }
+    __syncthreads();
+    {
+        uint32_t run = digit_base;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = warp_cnt[w][d0];
+            warp_cnt[w][d0] = run;
+            run += c;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const uint32_t i = i0 + r * 32;
+        if (i >= n) continue;
+        const uint32_t rank = r % 2 == 0 ? (loc[r / 2] & 0xffffu) : (loc[r / 2] >> 16);
+        const uint32_t pos = warp_cnt[warp][(key[r] >> shift) & 0xffu] + rank;
+        if (!kLast) keys_out[pos] = key[r];
+        vals_out[pos] = kFirst ? static_cast<int32_t>(i) : val[r];
     }
 }
 
+// Sorted coordinates: four cells per thread, index and coordinate loads
+// issued before the stores.
+constexpr int kGatherPer = 4;
 __global__ void gather_kernel(const float* __restrict__ x, const float* __restrict__ y,
                               const float* __restrict__ z, int dim, int64_t n,
                               const int32_t* __restrict__ perm, float* __restrict__ xs,
                               float* __restrict__ ys, float* __restrict__ zs) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t o = perm[i];
-    xs[i] = x[o];
-    if (dim > 1) ys[i] = y[o];
-    if (dim > 2) zs[i] = z[o];
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * kGatherPer + threadIdx.x;
+    int64_t o[kGatherPer];
+#pragma unroll
+    for (int q = 0; q < kGatherPer; ++q) {
+        const int64_t i = i0 + static_cast<int64_t>(q) * blockDim.x;
+        o[q] = i < n ? perm[i] : 0;
+    }
+    float v[kGatherPer][3];
+#pragma unroll
+    for (int q = 0; q < kGatherPer; ++q) {
+        v[q][0] = x[o[q]];
+        v[q][1] = dim > 1 ? y[o[q]] : 0.f;
+        v[q][2] = dim > 2 ? z[o[q]] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kGatherPer; ++q) {
+        const int64_t i = i0 + static_cast<int64_t>(q) * blockDim.x;
+        if (i >= n) continue;
+        xs[i] = v[q][0];
+        if (dim > 1) ys[i] = v[q][1];
+        if (dim > 2) zs[i] = v[q][2];
+    }
 }
 
 int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
@@ -377,6 +457,52 @@ int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 size_t radix_sort_temp_bytes(int64_t n_cells) {
     return static_cast<size_t>(sort_blocks(n_cells) + 1) * kRadix * sizeof(uint32_t);
 }
+
+namespace {
+
+// Keys of the sort tiles (first digit counted on the fly), then one
+// histogram / scan / scatter triple per further 8-bit digit.  The index array
+// ping-pongs between vals_b and perm so that the last pass writes perm.
+void run_sort(const float* x, const float* y, const float* z, int dim, int64_t n, const SegInfo* segs,
+              int n_segments, int morton_bits, int passes, int64_t nblk, uint32_t* keys_a, uint32_t* keys_b,
+              int32_t* vals_b, int32_t* perm, uint32_t* counts, uint32_t* totals, cudaStream_t st) {
+    uint32_t* kin = keys_a;
+    uint32_t* kout = keys_b;
+    const unsigned grid = static_cast<unsigned>(nblk);
+    key_kernel<<<grid, kSortThreads, 0, st>>>(x, y, z, dim, n, segs, n_segments, kin, morton_bits, counts,
+                                              static_cast<int>(nblk));
+    count_launches(1);
+    const int32_t* vin = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        if (p > 0) {
+            radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, shift, counts, static_cast<int>(nblk));
+            count_launches(1);
+        }
+        scan_rows_kernel<<<kRadix, kScanThreads, 0, st>>>(counts, static_cast<int>(nblk), totals);
+        int32_t* vout = (passes - 1 - p) % 2 == 0 ? perm : vals_b;
+        const bool first = p == 0, last = p == passes - 1;
+        if (first && last)
+            radix_scatter_kernel<true, true><<<grid, kSortThreads, 0, st>>>(
+                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+        else if (first)
+            radix_scatter_kernel<true, false><<<grid, kSortThreads, 0, st>>>(
+                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+        else if (last)
+            radix_scatter_kernel<false, true><<<grid, kSortThreads, 0, st>>>(
+                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+        else
+            radix_scatter_kernel<false, false><<<grid, kSortThreads, 0, st>>>(
+                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+        count_launches(2);
+        uint32_t* tk = kin;
+        kin = kout;
+        kout = tk;
+        vin = vout;
+    }
+}
+
+}  // namespace
 
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
                 const float* y, const float* z, void* plan, const PlanLayout& L, void* stream) {
@@ -389,8 +515,8 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     float* ys = reinterpret_cast<float*>(base + L.off_ys);
     float* zs = reinterpret_cast<float*>(base + L.off_zs);
     int32_t* perm = reinterpret_cast<int32_t*>(base + L.off_perm);
-    uint64_t* keys_a = reinterpret_cast<uint64_t*>(base + L.off_keys_in);
-    uint64_t* keys_b = reinterpret_cast<uint64_t*>(base + L.off_keys_out);
+    uint32_t* keys_a = reinterpret_cast<uint32_t*>(base + L.off_keys_in);
+    uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + L.off_keys_out);
     int32_t* vals_b = reinterpret_cast<int32_t*>(base + L.off_vals_in);
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_sort_tmp);
     uint32_t* totals = counts + sort_blocks(n) * kRadix;  // kRadix digit totals
@@ -431,14 +557,14 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     seg_init_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments);
     count_launches(1);
     if (n == 0) return cudaGetLastError();
-    const int tpb = 256;
-    const unsigned grid = static_cast<unsigned>((n + tpb - 1) / tpb);
     bbox_kernel<<<static_cast<unsigned>((n + kBoxItems - 1) / kBoxItems), kBoxThreads, 0, st>>>(
         x, y, z, dim, n, segs, n_segments, &hdr->status);
-    // Quantisation levels along the longest axis: about one level per cell
-    // spacing of the largest segment (n^(1/dim) rounded up to a power of
-    // two, 16 .. 2^kMortonBits), so that no sort pass is spent on key bits
-    // finer than the cells.
+    count_launches(1);
+    // Quantisation levels along the longest axis: about one level per four
+    // cell spacings of the largest segment (n^(1/dim) / 4 rounded up to a
+    // power of two, 16 .. 2^kMortonBits), so that no sort pass is spent on
+    // key bits finer than a lane's group of cells; cells that share a level
+    // keep their input order (the sort is stable).
     int64_t n_max = 0;
     for (int s = 0; s < n_segments; ++s) {
         const int64_t c = seg_offsets_host[s + 1] - seg_offsets_host[s];
@@ -446,46 +572,24 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     }
     int level_bits = 4;
     while (level_bits < kMortonBits &&
-           std::pow(2.0, static_cast<double>(level_bits * dim)) < static_cast<double>(n_max))
+           std::pow(2.0, static_cast<double>(level_bits * dim)) * std::pow(4.0, dim) < static_cast<double>(n_max))
         ++level_bits;
+    // 32-bit keys: with very many segments (more than 2^(32 - 4 dim)) the
+    // grid is made coarser so that the segment index still fits above it.
+    int sb = 0;
+    while ((int64_t(1) << sb) < n_segments) ++sb;
+    if (level_bits * dim + sb > 32) level_bits = (32 - sb) / dim;
     const int morton_bits = dim * level_bits;
-    int key_bits = morton_bits;
-    if (n_segments > 1) {
-        int sb = 0;
-        while ((1 << sb) < n_segments) ++sb;
-        key_bits += sb;
-    }
-    const int passes = (key_bits + 7) / 8;
+    const int key_bits = morton_bits + sb;
+    const int passes = key_bits > 8 ? (key_bits + 7) / 8 : 1;
     const int64_t nblk = sort_blocks(n);
-    // the index array ping-pongs between perm and vals_b: start where an odd
-    // number of passes ends in perm
-    int32_t* vin = passes % 2 == 1 ? vals_b : perm;
-    int32_t* vout = passes % 2 == 1 ? perm : vals_b;
     brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim, level_bits);
-    key_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, segs, n_segments, keys_a, vin, morton_bits);
-    count_launches(3);
-    uint64_t* kin = keys_a;
-    uint64_t* kout = keys_b;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        radix_hist_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(kin, n, shift, counts,
-                                                                                  static_cast<int>(nblk));
-        scan_rows_kernel<<<kRadix, kScanThreads, 0, st>>>(counts, static_cast<int>(nblk), totals);
-        radix_scatter_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(
-            kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
-        count_launches(3);
-        uint64_t* tk = kin;
-        kin = kout;
-        kout = tk;
-        int32_t* tv = vin;
-        vin = vout;
-        vout = tv;
-    }
-    if (vin != perm) {
-        err = cudaMemcpyAsync(perm, vin, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
-        if (err != cudaSuccess) return err;
-    }
-    gather_kernel<<<grid, tpb, 0, st>>>(x, y, z, dim, n, perm, xs, ys, zs);
+    count_launches(1);
+    run_sort(x, y, z, dim, n, segs, n_segments, morton_bits, passes, nblk, keys_a, keys_b, vals_b, perm, counts,
+             totals, st);
+    const int gtpb = 256;
+    const unsigned ggrid = static_cast<unsigned>((n + gtpb * kGatherPer - 1) / (gtpb * kGatherPer));
+    gather_kernel<<<ggrid, gtpb, 0, st>>>(x, y, z, dim, n, perm, xs, ys, zs);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -249,3 +249,24 @@ def test_from_dictionary_maps_appendix_b_keys(abi):
     assert cfg2["type"] == "bitruncated" and cfg2["params"].dim == 2 and cfg2["thresholds2"] == (0.1,)
     with pytest.raises(ValueError):
         F.from_dictionary({"type": "other"})
+
+
+def test_fma_pipe_cosine_polynomial_matches_its_fit():
+    # The FP32 coefficients compiled into the kernels are the ones the committed
+    # generator fits, and their FP32 Horner evaluation stays within the stated
+    # 4.0e-7 of cos(2 pi f) on [-1/2, 1/2].
+    import importlib.util
+    import pathlib
+    csrc = pathlib.Path(__file__).resolve().parents[1] / "paper_2212_10961_gb300" / "csrc"
+    spec = importlib.util.spec_from_file_location("gen_cos_poly", csrc / "gen_cos_poly.py")
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    text = (csrc / "device_common.cuh").read_text()
+    body = text[text.index("cos_turns_poly(float f)"):]
+    body = body[:body.index("\n}")]
+    lits = [float(v) for v in re.findall(r"[-+]?\d\.\d+e[-+]\d+(?=f)", body)]
+    compiled = np.array(lits[::-1], dtype=np.float32)  # Horner lists the highest degree first
+    assert np.array_equal(compiled, gen.fit().astype(np.float32))
+    f = np.linspace(-0.5, 0.5, 400_001)
+    err = np.max(np.abs(gen.horner_fp32(compiled, f).astype(np.float64) - np.cos(2 * np.pi * f)))
+    assert err <= 4.0e-7, err

@@ -224,6 +224,33 @@ def test_segments_share_one_plan(env):
         check_forward(out["Y"].cpu().numpy(), oracle_field(om, 0.0, c), 1.0, "segment %d" % s)
 
 
+def test_many_segments_coarsen_the_sort_grid(env):
+    # 2^17 one-cell segments after a 2M-cell one: the segment index takes 18
+    # key bits, so the quantisation grid of the large segment is made coarser
+    # (4 bits per axis instead of 6) to keep 32-bit sort keys.
+    torch, F, W = env
+    big = W.jittered_lattice((160, 128, 104), 1.0 / 128, 0.3, seed=5)
+    n_small = 1 << 17
+    rng = np.random.default_rng(6)
+    small = [rng.uniform(-2.0, 2.0, n_small).astype(np.float32) for _ in range(3)]
+    cells = [np.concatenate([big[k], small[k]]) for k in range(3)]
+    sizes = [len(big[0])] + [1] * n_small
+    plan = F.CellPlan(*to_dev(torch, cells), segments=sizes)
+    p = F.FieldParams(family="exponential", sigma2=2.0, ell=(0.2, 0.15, 0.1), dim=3, n_modes=1024, seed=31)
+    gf = F.GaussianField(p)
+    om = oracle_modes("exponential", 2.0, (0.2, 0.15, 0.1), 3, 1024, 31)
+    sig = math.sqrt(2.0)
+    y = gf.synth(plan, F.MapSpec(y=True), segment=0)["Y"].cpu().numpy()
+    idx = np.random.default_rng(7).choice(len(y), 20000, replace=False)
+    check_forward(y[idx], oracle_field(om, 0.0, big, idx), sig, "large segment")
+    for s in (1, 2, 777, n_small):
+        ys = gf.synth(plan, F.MapSpec(y=True), segment=s)["Y"].cpu().numpy()
+        c = [small[k][s - 1:s] for k in range(3)]
+        check_forward(ys, oracle_field(om, 0.0, c), sig, "one-cell segment %d" % s)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+
+
 def test_rejects_bad_calls(env):
     torch, F, W = env
     from paper_2212_10961_gb300 import _abi
