@@ -8,8 +8,9 @@ mode drawing (host C++), table packing and upload, and the fused synthesis
 kernel writing Y, K and facies.  Metric: Gcell.mode/s = cells x modes per
 second.  The same JSON line also reports the forward+backward step (128^3,
 N = 2048, mismatch loss and adjoint), the batched ensemble (256 realisations
-in one graph-replayed persistent launch), the unstructured 2M-cell workload,
-the 1024 x 512 HRL-shaped workload and the 64^2 workload.  roofline.traffic
+in one graph-replayed persistent launch), the unstructured 2M-cell workload
+(in lattice order and in a seeded random order), the 1024 x 512 HRL-shaped
+workload and the 64^2 workload.  roofline.traffic
 is the DRAM bytes (read + written) of one headline kernel launch measured by
 ncu.
 
@@ -177,10 +178,14 @@ def timed_steps(torch, world, steps, warmup, step_fn, kernel_events=None):
     return max_over_ranks(torch, world, ms)
 
 
-def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e=True):
-    """Headline forward step on one workload; returns dict of measurements."""
+def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e=True, shuffle_seed=None):
+    """Headline forward step on one workload; returns dict of measurements.
+    shuffle_seed: cells handed to the plan in a seeded random order (the
+    plan must recover the spatial locality itself)."""
     w = W.WORKLOADS[name]
     cells = W.workload_cells(name, scale)
+    if shuffle_seed is not None:
+        cells, _ = W.shuffled(cells, shuffle_seed)
     dim = len(cells)
     M = len(cells[0])
     N = w["n_modes"]
@@ -223,7 +228,8 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     ring[0].update(m0["amp"], m0["psi"], m0["a"])
     y_seed = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True))["Y"].cpu().numpy()
     per_step = launches / float(steps + warmup)
-    res = {"workload": name, "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
+    res = {"workload": name if shuffle_seed is None else "%s, cells in seeded random order (seed %d)"
+           % (name, shuffle_seed), "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
            "kernel_ms": max_over_ranks(torch, world, kern_ms),
            "kernel_ms_median": max_over_ranks(torch, world, float(np.median(kern_all))),
            "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
@@ -549,6 +555,8 @@ def main():
     if args.only in ("all", "jitter"):
         extra["jitter3d_2m"] = bench_forward(torch, F, W, "jitter3d_2m", rank, world, args.steps, args.warmup,
                                              args.scale, with_e2e=False)
+        extra["jitter3d_2m_shuffled"] = bench_forward(torch, F, W, "jitter3d_2m", rank, world, args.steps,
+                                                      args.warmup, args.scale, with_e2e=False, shuffle_seed=5)
     if args.only in ("all", "hrl"):
         extra["hrl2d"] = bench_forward(torch, F, W, "hrl2d", rank, world, args.steps, args.warmup, 1,
                                        with_e2e=False)

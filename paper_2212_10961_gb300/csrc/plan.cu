@@ -9,7 +9,8 @@
 //      level per four cell spacings of the largest segment (at most 2^10);
 //   3. 32-bit keys, the segment index above the Morton code of the quantised
 //      position, the first digit counted as they are made;
-//   4. stable LSD radix sort of (key, original index), 8-bit digits;
+//   4. stable LSD radix sort of (key, original index) in the fewest passes
+//      with digits of at most 10 bits;
 //   5. gather of the sorted SoA coordinates.
 // Everything runs on the stream without host synchronisation and is
 // deterministic (the sort is stable, so equal keys keep the input order).
@@ -28,8 +29,9 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
-constexpr int kRadix = 256;
-static_assert(kRadix == kSortThreads, "the scatter kernel scans digit totals with one thread per digit");
+constexpr int kMaxDigitBits = 10;  // radix passes use digits of up to 10 bits
+constexpr int kMaxRadix = 1 << kMaxDigitBits;
+static_assert(kMaxRadix % kSortThreads == 0, "digits are spread evenly over the threads");
 
 __device__ __forceinline__ int32_t float_to_ordered(float f) {
     int32_t b = __float_as_int(f);
@@ -245,9 +247,12 @@ __device__ __forceinline__ uint32_t morton_code(const float (&v)[3], const SegIn
 __global__ void __launch_bounds__(kSortThreads)
     key_kernel(const float* __restrict__ x, const float* __restrict__ y, const float* __restrict__ z,
                int dim, int64_t n, const SegInfo* __restrict__ segs, int n_segments,
-               uint32_t* __restrict__ keys, int morton_bits, uint32_t* __restrict__ counts, int nblk) {
-    __shared__ uint32_t hist[kRadix];
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d] = 0u;
+               uint32_t* __restrict__ keys, int morton_bits, int digit_bits, uint32_t* __restrict__ counts,
+               int nblk) {
+    __shared__ uint32_t hist[kMaxRadix];
+    const int radix = 1 << digit_bits;
+    const uint32_t mask = static_cast<uint32_t>(radix - 1);
+    for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[d] = 0u;
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
     const int64_t c1 = base + kSortTile < n ? base + kSortTile : n;
     const int s_first = find_segment(segs, n_segments, base);
@@ -272,21 +277,23 @@ __global__ void __launch_bounds__(kSortThreads)
             const int s = single ? s_first : find_segment(segs, n_segments, i);
             const uint32_t key = (static_cast<uint32_t>(s) << morton_bits) | morton_code(v[r], segs[s], dim);
             keys[i] = key;
-            atomicAdd(&hist[key & 0xffu], 1u);
+            atomicAdd(&hist[key & mask], 1u);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    for (int d = threadIdx.x; d < radix; d += blockDim.x)
         counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
 }
 
-// ---- stable LSD radix sort, 8-bit digits -----------------------------------------
+// ---- stable LSD radix sort, digits of up to kMaxDigitBits bits ---------------------
 
 __global__ void __launch_bounds__(kSortThreads)
-    radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
+    radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, int digit_bits,
                       uint32_t* __restrict__ counts, int nblk) {
-    __shared__ uint32_t hist[kRadix];
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d] = 0u;
+    __shared__ uint32_t hist[kMaxRadix];
+    const int radix = 1 << digit_bits;
+    const uint32_t mask = static_cast<uint32_t>(radix - 1);
+    for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[d] = 0u;
     __syncthreads();
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
     uint32_t k[kSortItems];
@@ -298,39 +305,77 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r)
         if (base + r * kSortThreads + threadIdx.x < n)
-            atomicAdd(&hist[(k[r] >> shift) & 0xffu], 1u);
+            atomicAdd(&hist[(k[r] >> shift) & mask], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    for (int d = threadIdx.x; d < radix; d += blockDim.x)
         counts[static_cast<int64_t>(d) * nblk + blockIdx.x] = hist[d];
+}
+
+// Exclusive scan over the block of one value per thread (kSortThreads
+// threads), also returning the block total; `warp_tot` is kSortThreads / 32
+// words of shared scratch.  Contains block barriers.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0u;
+    total = 0u;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t t = warp_tot[w];
+        before += w < warp ? t : 0u;
+        total += t;
+    }
+    __syncthreads();  // warp_tot may be reused after the return
+    return before + incl - v;
 }
 
 // Exclusive scan of each digit's row of per-block counts, one block per
 // digit (rows are counts[d * nblk .. (d + 1) * nblk)), plus the row total.
-constexpr int kScanThreads = 256;
+// The row goes through shared memory in chunks of 4096 so that the global
+// loads and stores are coalesced while each thread scans 16 consecutive
+// counts.
+constexpr int kScanThreads = kSortThreads;
+constexpr int kScanPer = 16;
+constexpr int kScanChunk = kScanThreads * kScanPer;
 __global__ void __launch_bounds__(kScanThreads)
     scan_rows_kernel(uint32_t* __restrict__ counts, int nblk, uint32_t* __restrict__ totals) {
-    __shared__ uint32_t part[kScanThreads];
+    __shared__ uint32_t buf[kScanChunk + kScanChunk / 32];  // one pad word per 32
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
     uint32_t* row = counts + static_cast<int64_t>(blockIdx.x) * nblk;
-    const int per = (nblk + kScanThreads - 1) / kScanThreads;
-    const int b = threadIdx.x * per;
-    const int e = b + per < nblk ? b + per : nblk;
-    uint32_t sum = 0u;
-    for (int k = b; k < e; ++k) sum += row[k];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    const auto at = [](int k) { return k + (k >> 5); };
+    uint32_t carry = 0u;
+    for (int c0 = 0; c0 < nblk; c0 += kScanChunk) {
+        const int m = nblk - c0 < kScanChunk ? nblk - c0 : kScanChunk;
+        for (int k = threadIdx.x; k < kScanChunk; k += kScanThreads) buf[at(k)] = k < m ? row[c0 + k] : 0u;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t v[kScanPer];
+        uint32_t sum = 0u;
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            v[q] = buf[at(threadIdx.x * kScanPer + q)];
+            sum += v[q];
+        }
+        uint32_t chunk = 0u;
+        uint32_t run = carry + block_exclusive_scan(sum, warp_tot, chunk);
+#pragma unroll
+        for (int q = 0; q < kScanPer; ++q) {
+            buf[at(threadIdx.x * kScanPer + q)] = run;
+            run += v[q];
+        }
         __syncthreads();
+        for (int k = threadIdx.x; k < m; k += kScanThreads) row[c0 + k] = buf[at(k)];
+        __syncthreads();  // buf is refilled by the next chunk
+        carry += chunk;
     }
-    uint32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0u;
-    for (int k = b; k < e; ++k) {
-        const uint32_t v = row[k];
-        row[k] = run;
-        run += v;
-    }
-    if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = part[kScanThreads - 1];
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 // Stable scatter.  Warp w owns items [512 w, 512 (w + 1)) of the tile, in
@@ -342,18 +387,21 @@ __global__ void __launch_bounds__(kScanThreads)
 // kFirst: the values are the input indices (nothing to read); kLast: only
 // the values are stored.
 template <bool kFirst, bool kLast>
-__global__ void __launch_bounds__(kSortThreads, kFirst || kLast ? 3 : 2)
+__global__ void __launch_bounds__(kSortThreads, kFirst ? 3 : 2)
     radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
                          uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
-                         int64_t n64, int shift, const uint32_t* __restrict__ offsets,
+                         int64_t n64, int shift, int digit_bits, const uint32_t* __restrict__ offsets,
                          const uint32_t* __restrict__ totals, int nblk) {
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kRounds = kSortTile / kSortThreads;  // rounds of 32 items per warp
     static_assert(kRounds % 2 == 0 && kRounds * 32 <= 65536, "ranks are packed two per register");
-    __shared__ uint32_t scan[kRadix];
-    __shared__ uint32_t warp_cnt[kWarps][kRadix];  // per-warp digit counts, then offsets
+    __shared__ uint32_t warp_cnt[kWarps][kMaxRadix];  // per-warp digit counts, then offsets
+    __shared__ uint32_t digit_start[kMaxRadix];       // global start of each digit for this tile
+    __shared__ uint32_t warp_tot[kWarps];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const int radix = 1 << digit_bits;
+    const uint32_t mask = static_cast<uint32_t>(radix - 1);
     // plans hold at most 2^31 - 1 cells, so item indices fit in 32 bits
     const uint32_t n = static_cast<uint32_t>(n64);
     const uint32_t i0 = blockIdx.x * static_cast<uint32_t>(kSortTile) + warp * (kRounds * 32) + lane;
@@ -365,25 +413,28 @@ __global__ void __launch_bounds__(kSortThreads, kFirst || kLast ? 3 : 2)
         key[r] = i < n ? keys_in[i] : 0u;
         if (!kFirst) val[r] = i < n ? vals_in[i] : 0;
     }
-    for (int k = threadIdx.x; k < kWarps * kRadix; k += blockDim.x) (&warp_cnt[0][0])[k] = 0u;
-    // digit starts: exclusive scan of the digit totals (kRadix == blockDim.x)
-    const int d0 = threadIdx.x;
-    scan[d0] = totals[d0];
-    __syncthreads();
-    for (int off = 1; off < kRadix; off <<= 1) {
-        const uint32_t v = d0 >= off ? scan[d0 - off] : 0u;
-        __syncthreads();
-        scan[d0] += v;
-        __syncthreads();
+    for (int w = 0; w < kWarps; ++w)
+        for (int d = threadIdx.x; d < radix; d += kSortThreads) warp_cnt[w][d] = 0u;
+    // digit starts: exclusive scan of the digit totals in slabs of kSortThreads
+    // digits (the slab loop is uniform over the block)
+    {
+        uint32_t carry = 0u;
+        for (int d0 = 0; d0 < radix; d0 += kSortThreads) {
+            const int d = d0 + threadIdx.x;
+            const uint32_t t = d < radix ? totals[d] : 0u;
+            uint32_t slab = 0u;
+            const uint32_t ex = block_exclusive_scan(t, warp_tot, slab);
+            if (d < radix) digit_start[d] = carry + ex + offsets[static_cast<int64_t>(d) * nblk + blockIdx.x];
+            carry += slab;
+        }
     }
-    const uint32_t digit_base = scan[d0] - totals[d0] + offsets[static_cast<int64_t>(d0) * nblk + blockIdx.x];
     const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t loc[kRounds / 2];  // rank of each item among its warp's items of the same digit
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const bool in = i0 + r * 32 < n;
         // out-of-range items get a digit of their own (never counted or stored)
-        const int digit = in ? static_cast<int>((key[r] >> shift) & 0xffu) : kRadix;
+        const int digit = in ? static_cast<int>((key[r] >> shift) & mask) : kMaxRadix;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0u;
@@ -399,11 +450,12 @@ __global__ void __launch_bounds__(kSortThreads, kFirst || kLast ? 3 : 2)
             loc[r / 2] |= rank << 16;
     }
     __syncthreads();
-    {
-        uint32_t run = digit_base;
+    for (int d = threadIdx.x; d < radix; d += kSortThreads) {
+        uint32_t run = digit_start[d];
+#pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = warp_cnt[w][d0];
-            warp_cnt[w][d0] = run;
+            const uint32_t c = warp_cnt[w][d];
+            warp_cnt[w][d] = run;
             run += c;
         }
     }
@@ -413,7 +465,7 @@ __global__ void __launch_bounds__(kSortThreads, kFirst || kLast ? 3 : 2)
         const uint32_t i = i0 + r * 32;
         if (i >= n) continue;
         const uint32_t rank = r % 2 == 0 ? (loc[r / 2] & 0xffffu) : (loc[r / 2] >> 16);
-        const uint32_t pos = warp_cnt[warp][(key[r] >> shift) & 0xffu] + rank;
+        const uint32_t pos = warp_cnt[warp][(key[r] >> shift) & mask] + rank;
         if (!kLast) keys_out[pos] = key[r];
         vals_out[pos] = kFirst ? static_cast<int32_t>(i) : val[r];
     }
@@ -455,45 +507,47 @@ int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 }  // namespace
 
 size_t radix_sort_temp_bytes(int64_t n_cells) {
-    return static_cast<size_t>(sort_blocks(n_cells) + 1) * kRadix * sizeof(uint32_t);
+    return static_cast<size_t>(sort_blocks(n_cells) + 1) * kMaxRadix * sizeof(uint32_t);
 }
 
 namespace {
 
 // Keys of the sort tiles (first digit counted on the fly), then one
-// histogram / scan / scatter triple per further 8-bit digit.  The index array
+// histogram / scan / scatter triple per further digit.  The index array
 // ping-pongs between vals_b and perm so that the last pass writes perm.
 void run_sort(const float* x, const float* y, const float* z, int dim, int64_t n, const SegInfo* segs,
-              int n_segments, int morton_bits, int passes, int64_t nblk, uint32_t* keys_a, uint32_t* keys_b,
-              int32_t* vals_b, int32_t* perm, uint32_t* counts, uint32_t* totals, cudaStream_t st) {
+              int n_segments, int morton_bits, int passes, int digit_bits, int64_t nblk, uint32_t* keys_a,
+              uint32_t* keys_b, int32_t* vals_b, int32_t* perm, uint32_t* counts, uint32_t* totals,
+              cudaStream_t st) {
     uint32_t* kin = keys_a;
     uint32_t* kout = keys_b;
     const unsigned grid = static_cast<unsigned>(nblk);
-    key_kernel<<<grid, kSortThreads, 0, st>>>(x, y, z, dim, n, segs, n_segments, kin, morton_bits, counts,
-                                              static_cast<int>(nblk));
+    const int nb = static_cast<int>(nblk);
+    key_kernel<<<grid, kSortThreads, 0, st>>>(x, y, z, dim, n, segs, n_segments, kin, morton_bits, digit_bits,
+                                              counts, nb);
     count_launches(1);
     const int32_t* vin = nullptr;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
+        const int shift = digit_bits * p;
         if (p > 0) {
-            radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, shift, counts, static_cast<int>(nblk));
+            radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, shift, digit_bits, counts, nb);
             count_launches(1);
         }
-        scan_rows_kernel<<<kRadix, kScanThreads, 0, st>>>(counts, static_cast<int>(nblk), totals);
+        scan_rows_kernel<<<1u << digit_bits, kScanThreads, 0, st>>>(counts, nb, totals);
         int32_t* vout = (passes - 1 - p) % 2 == 0 ? perm : vals_b;
         const bool first = p == 0, last = p == passes - 1;
         if (first && last)
-            radix_scatter_kernel<true, true><<<grid, kSortThreads, 0, st>>>(
-                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+            radix_scatter_kernel<true, true><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift,
+                                                                            digit_bits, counts, totals, nb);
         else if (first)
-            radix_scatter_kernel<true, false><<<grid, kSortThreads, 0, st>>>(
-                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+            radix_scatter_kernel<true, false><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift,
+                                                                             digit_bits, counts, totals, nb);
         else if (last)
-            radix_scatter_kernel<false, true><<<grid, kSortThreads, 0, st>>>(
-                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+            radix_scatter_kernel<false, true><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift,
+                                                                             digit_bits, counts, totals, nb);
         else
-            radix_scatter_kernel<false, false><<<grid, kSortThreads, 0, st>>>(
-                kin, vin, kout, vout, n, shift, counts, totals, static_cast<int>(nblk));
+            radix_scatter_kernel<false, false><<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift,
+                                                                              digit_bits, counts, totals, nb);
         count_launches(2);
         uint32_t* tk = kin;
         kin = kout;
@@ -519,7 +573,7 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + L.off_keys_out);
     int32_t* vals_b = reinterpret_cast<int32_t*>(base + L.off_vals_in);
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_sort_tmp);
-    uint32_t* totals = counts + sort_blocks(n) * kRadix;  // kRadix digit totals
+    uint32_t* totals = counts + sort_blocks(n) * kMaxRadix;  // digit totals
 
     // header and segment table from the host (small synchronous-staging copies)
     PlanHeader h{};
@@ -581,12 +635,15 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     if (level_bits * dim + sb > 32) level_bits = (32 - sb) / dim;
     const int morton_bits = dim * level_bits;
     const int key_bits = morton_bits + sb;
-    const int passes = key_bits > 8 ? (key_bits + 7) / 8 : 1;
+    // fewest passes with digits of at most kMaxDigitBits bits, the bits spread
+    // evenly over them (18-bit keys: two passes of 9 bits)
+    const int passes = key_bits > kMaxDigitBits ? (key_bits + kMaxDigitBits - 1) / kMaxDigitBits : 1;
+    const int digit_bits = key_bits > 0 ? (key_bits + passes - 1) / passes : 1;
     const int64_t nblk = sort_blocks(n);
     brick_kernel<<<(n_segments + 127) / 128, 128, 0, st>>>(segs, n_segments, dim, level_bits);
     count_launches(1);
-    run_sort(x, y, z, dim, n, segs, n_segments, morton_bits, passes, nblk, keys_a, keys_b, vals_b, perm, counts,
-             totals, st);
+    run_sort(x, y, z, dim, n, segs, n_segments, morton_bits, passes, digit_bits, nblk, keys_a, keys_b, vals_b,
+             perm, counts, totals, st);
     const int gtpb = 256;
     const unsigned ggrid = static_cast<unsigned>((n + gtpb * kGatherPer - 1) / (gtpb * kGatherPer));
     gather_kernel<<<ggrid, gtpb, 0, st>>>(x, y, z, dim, n, perm, xs, ys, zs);
