@@ -435,6 +435,25 @@ int grf_batch_launch(void *workspace, void *stream);
  */
 int grf_selftest_wait(int32_t limit_us, int32_t *status_dev, void *stream);
 
+/*
+ * Checked builds (the stand-in for a memory sanitizer).  The same sources
+ * compiled with -DGRF_CHECKED=1 give libgrf_checked.so, with the same entry
+ * points: before a kernel uses an index it read from device memory as an
+ * address (an entry of a plan's permutation, a radix-sort scatter position),
+ * it tests the index against the array it addresses; an index out of range
+ * is counted and its access skipped instead of reading or writing out of
+ * bounds.  Nothing else changes.
+ *
+ * grf_checked_build -- 1 for the checked library, 0 for the release one.
+ *
+ * grf_take_index_faults -- the number of accesses skipped since the last
+ * call (and resets the count).  Synchronises the device; *count_out is
+ * always 0 in the release library.  GRF_EINVAL for a NULL pointer,
+ * GRF_ECUDA if the device counter cannot be read.
+ */
+int grf_checked_build(void);
+int grf_take_index_faults(int64_t *count_out);
+
 /* ------------------------------------------------------------------ */
 /* Measurement helpers                                                  */
 /* ------------------------------------------------------------------ */

@@ -8,7 +8,10 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgrf.so")
+# GRF_LIBRARY=checked selects the build with device-side index checks
+# (libgrf_checked.so, same entry points); anything else the release build.
+CHECKED = os.environ.get("GRF_LIBRARY", "") == "checked"
+LIB_PATH = os.path.join(_HERE, "libgrf_checked.so" if CHECKED else "libgrf.so")
 
 GRF_OK = 0
 GRF_EINVAL = -1
@@ -125,6 +128,8 @@ _SIGS = {
     "grf_release": (ctypes.c_int, [ctypes.c_void_p]),
     "grf_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_mufu_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "grf_checked_build": (ctypes.c_int, []),
+    "grf_take_index_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
 }
 
 _lib = None
@@ -137,11 +142,12 @@ class GRFError(RuntimeError):
 
 
 def lib():
-    """The loaded libgrf.so (raises if it was not built)."""
+    """The loaded library (libgrf.so, or libgrf_checked.so under
+    GRF_LIBRARY=checked); raises if it was not built."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libgrf.so not found at %s: build it with __graft_entry__.build()" % LIB_PATH)
+            raise ImportError("%s not found: build it with __graft_entry__.build()" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)

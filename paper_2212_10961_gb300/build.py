@@ -1,8 +1,11 @@
-"""Build the CUDA library ``libgrf.so`` in-tree for sm_103a (GB300).
+"""Build the CUDA library in-tree for sm_103a (GB300), in two flavours:
+``libgrf.so`` (release) and ``libgrf_checked.so`` (the same sources with
+-DGRF_CHECKED=1: device-side index checks that count and skip out-of-range
+accesses, selected at run time with GRF_LIBRARY=checked).
 
-Each translation unit is compiled by nvcc in parallel and linked into one
-shared library next to this file.  Host code uses portable flags only, so the
-same command builds on x86-64 and on Arm hosts.
+Every translation unit of both flavours is compiled by nvcc in parallel and
+linked into one shared library per flavour next to this file.  Host code uses
+portable flags only, so the same command builds on x86-64 and on Arm hosts.
 """
 import os
 import subprocess
@@ -15,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgrf.so")
+FLAVOURS = {"release": (LIB, os.path.join(BUILD, "release"), []),
+            "checked": (os.path.join(PKG, "libgrf_checked.so"), os.path.join(BUILD, "checked"),
+                        ["-DGRF_CHECKED=1"])}
 SOURCES = ["synth_fwd.cu", "synth_bwd.cu", "plan.cu", "maps.cu", "grf_host.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -24,49 +30,57 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _compile(src, verbose_ptxas=False):
-    out = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src, out_dir, defines, verbose_ptxas=False):
+    out = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", out]
+           "-I", INCLUDE, "-I", CSRC] + defines + ["-c", os.path.join(CSRC, src), "-o", out]
     if src.endswith(".cu"):
         cmd += ["-Xptxas", "-warn-spills"]
         if verbose_ptxas:
             cmd += ["-Xptxas", "-v"]
     else:
-        cmd = [nvcc(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-               "-x", "c++", "-c", os.path.join(CSRC, src), "-o", out]
+        cmd = [nvcc(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + defines + \
+              ["-x", "c++", "-c", os.path.join(CSRC, src), "-o", out]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, res.stdout, res.stderr))
     return out, res.stderr
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "grf.h"), __file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force=False, verbose_ptxas=False):
-    """Compile and link libgrf.so if any source is newer than the library."""
-    if not force and not _stale():
+def build(force=False, verbose_ptxas=False, flavours=("release", "checked")):
+    """Compile and link each flavour whose library is older than a source;
+    returns the release library's path."""
+    todo = [f for f in flavours if force or _stale(FLAVOURS[f][0])]
+    if not todo:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
+    jobs = []
+    for f in todo:
+        _, out_dir, defines = FLAVOURS[f]
+        os.makedirs(out_dir, exist_ok=True)
+        jobs += [(f, src, out_dir, defines) for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        results = list(ex.map(lambda j: (j[0],) + _compile(j[1], j[2], j[3], verbose_ptxas), jobs))
     if verbose_ptxas:
-        for _, log in results:
+        for _, _, log in results:
             if log:
                 sys.stderr.write(log)
-    objs = [o for o, _ in results]
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), ARCH, "-shared", "-cudart", "shared", "-o", tmp] + objs
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
-    os.replace(tmp, LIB)
+    for f in todo:
+        lib = FLAVOURS[f][0]
+        objs = [o for g, o, _ in results if g == f]
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [nvcc(), ARCH, "-shared", "-cudart", "shared", "-o", tmp] + objs
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -162,6 +162,43 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// ---- checked builds --------------------------------------------------------
+// Compiled with -DGRF_CHECKED=1 (libgrf_checked.so), every index that a kernel
+// reads from device memory before using it as an address (a permutation
+// entry, a scatter position) is tested first: an index out of range is
+// counted in this translation unit's g_index_faults and its access skipped,
+// instead of reading or writing out of bounds.  The release build compiles
+// the tests out (GRF_CHECKED is set in grf_internal.h).
+#if GRF_CHECKED
+static __device__ unsigned long long g_index_faults;
+#endif
+
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n) {
+#if GRF_CHECKED
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&g_index_faults, 1ull);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    return true;
+#endif
+}
+
+// Host side: this translation unit's count since the last call, then reset
+// (synchronous; 0 without a checked build).
+static inline unsigned long long take_tu_index_faults() {
+#if GRF_CHECKED
+    unsigned long long v = 0ull;
+    const unsigned long long zero = 0ull;
+    if (cudaMemcpyFromSymbol(&v, g_index_faults, sizeof(v)) != cudaSuccess) return ~0ull;
+    if (cudaMemcpyToSymbol(g_index_faults, &zero, sizeof(zero)) != cudaSuccess) return ~0ull;
+    return v;
+#else
+    return 0ull;
+#endif
+}
+
 // Map epilogue of one cell (Sec. 3.1 truncation rule, Sec. 4.1 lognormal).
 __device__ __forceinline__ void map_store(const MapDev& m, int64_t o, float y) {
     const int bits = m.bits;

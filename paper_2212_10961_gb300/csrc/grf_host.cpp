@@ -974,6 +974,24 @@ int grf_selftest_wait(int32_t limit_us, int32_t* status_dev, void* stream) try {
     return host_exception();
 }
 
+int grf_checked_build(void) { return GRF_CHECKED ? 1 : 0; }
+
+int grf_take_index_faults(int64_t* count_out) try {
+    if (!count_out) return fail(GRF_EINVAL, "count_out is NULL");
+    *count_out = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the index-fault counters");
+    unsigned long long total = 0ull;
+    for (unsigned long long v : {take_index_faults_fwd(), take_index_faults_bwd(), take_index_faults_plan()}) {
+        if (v == ~0ull) return fail(GRF_ECUDA, "index-fault counter not readable");
+        total += v;
+    }
+    *count_out = static_cast<int64_t>(total);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
 int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) try {
     if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
     const int err = launch_mufu_probe(blocks, iters, sink, stream);

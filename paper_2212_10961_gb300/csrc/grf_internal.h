@@ -7,6 +7,10 @@
 
 #include "grf.h"
 
+#ifndef GRF_CHECKED
+#define GRF_CHECKED 0  // 1 in the checked build (libgrf_checked.so)
+#endif
+
 namespace grf {
 
 // ---------------------------------------------------------------------------
@@ -186,6 +190,14 @@ constexpr uint32_t kBatchMagic = 0x48435442u;  // "BTCH"
 // Return cudaError_t as int.
 // ---------------------------------------------------------------------------
 int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream);
+
+// Checked builds (-DGRF_CHECKED=1): device accesses skipped since the last
+// call because an index read from device memory was out of range, per
+// translation unit, then reset; ~0 if the counter cannot be read; always 0
+// in release builds.
+unsigned long long take_index_faults_fwd();
+unsigned long long take_index_faults_bwd();
+unsigned long long take_index_faults_plan();
 size_t synth_workspace_bytes(int64_t n_cells);
 int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
                          int32_t* counter, void* stream);

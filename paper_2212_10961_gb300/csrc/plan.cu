@@ -466,6 +466,7 @@ __global__ void __launch_bounds__(kSortThreads, kFirst ? 3 : 2)
         if (i >= n) continue;
         const uint32_t rank = r % 2 == 0 ? (loc[r / 2] & 0xffffu) : (loc[r / 2] >> 16);
         const uint32_t pos = warp_cnt[warp][(key[r] >> shift) & mask] + rank;
+        if (!index_ok(pos, n)) continue;
         if (!kLast) keys_out[pos] = key[r];
         vals_out[pos] = kFirst ? static_cast<int32_t>(i) : val[r];
     }
@@ -484,6 +485,7 @@ __global__ void gather_kernel(const float* __restrict__ x, const float* __restri
     for (int q = 0; q < kGatherPer; ++q) {
         const int64_t i = i0 + static_cast<int64_t>(q) * blockDim.x;
         o[q] = i < n ? perm[i] : 0;
+        if (!index_ok(o[q], n)) o[q] = 0;  // checked builds: read a valid cell instead
     }
     float v[kGatherPer][3];
 #pragma unroll
@@ -650,5 +652,7 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     count_launches(1);
     return cudaGetLastError();
 }
+
+unsigned long long take_index_faults_plan() { return take_tu_index_faults(); }
 
 }  // namespace grf

@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
             xv[q][0] = __ldg(args.xs + ii);
             xv[q][1] = DIM > 1 ? __ldg(args.ys + ii) : 0.f;
             xv[q][2] = DIM > 2 ? __ldg(args.zs + ii) : 0.f;
-            gv[q] = in ? __ldg(args.gY + (static_cast<int64_t>(__ldg(args.perm + i)) - args.perm_base)) : 0.f;
+            const int64_t o = in ? static_cast<int64_t>(__ldg(args.perm + i)) - args.perm_base : 0;
+            gv[q] = in && index_ok(o, n) ? __ldg(args.gY + o) : 0.f;
         }
     };
     if (t_begin < t_end) load_tile(t_begin);
@@ -468,5 +469,7 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     count_launches(2);
     return cudaGetLastError();
 }
+
+unsigned long long take_index_faults_bwd() { return take_tu_index_faults(); }
 
 }  // namespace grf

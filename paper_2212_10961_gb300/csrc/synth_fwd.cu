@@ -333,7 +333,8 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
                 partial[i] = make_float2(s[c], e[c]);
             } else {
                 const float y = (s[c] + e[c]) + d.map.mu;
-                map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
+                const int64_t o = static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base;
+                if (index_ok(o, d.n_cells)) map_store(d.map, o, y);
             }
         }
     }
@@ -374,7 +375,8 @@ __global__ void __launch_bounds__(256) synth_split_finalize(FwdDesc d, const flo
         e += v.y;
     }
     const float y = (s + e) + d.map.mu;
-    map_store(d.map, static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base, y);
+    const int64_t o = static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base;
+    if (index_ok(o, d.n_cells)) map_store(d.map, o, y);
 }
 
 // Persistent batched kernel: every warp pulls (realisation, warp tile) work
@@ -534,5 +536,7 @@ int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* s
         default: return cudaErrorInvalidValue;
     }
 }
+
+unsigned long long take_index_faults_fwd() { return take_tu_index_faults(); }
 
 }  // namespace grf

@@ -11,6 +11,8 @@ spectra), Sec. 3.1 / Appendix B (thresholds, facies values, lognormal
 scaling).
 """
 import ctypes
+import dataclasses
+import json
 import math
 from dataclasses import dataclass, field as dc_field
 from typing import Optional, Sequence
@@ -149,6 +151,40 @@ def gen_modes(params: FieldParams):
     m = _modes_struct(n, d, arrays)
     check(lib().grf_gen_modes(ctypes.byref(params.to_c()), ctypes.byref(m)))
     return arrays
+
+
+_MODE_KEYS = ("kappa", "rho", "psi", "a", "amp")
+
+
+def save_realisation(path, params: FieldParams, modes=None):
+    """Record of one realisation for audit or restart, as one numpy .npz file:
+    the parameters (with the seed they determine the field exactly, at any
+    cell centres: Sec. 4.1) and the drawn modes (drawn here if not given)."""
+    modes = gen_modes(params) if modes is None else modes
+    rec = dataclasses.asdict(params)
+    rec["ell"], rec["period"] = list(rec["ell"]), list(rec["period"])
+    if rec["rot"] is not None:
+        rec["rot"] = np.asarray(rec["rot"], dtype=np.float64).tolist()
+    np.savez(path, params=np.array(json.dumps(rec)), **{k: np.asarray(modes[k]) for k in _MODE_KEYS})
+
+
+def load_realisation(path, verify=True):
+    """(params, modes) from a save_realisation file.  verify=True draws the
+    modes again from the stored parameters and requires them to be
+    bit-identical to the stored ones (the record is then self-consistent)."""
+    with np.load(path, allow_pickle=False) as z:
+        rec = json.loads(str(z["params"]))
+        modes = {k: z[k].copy() for k in _MODE_KEYS}
+    rec["ell"], rec["period"] = tuple(rec["ell"]), tuple(rec["period"])
+    if rec["rot"] is not None:
+        rec["rot"] = tuple(tuple(r) for r in rec["rot"])
+    params = FieldParams(**rec)
+    if verify:
+        again = gen_modes(params)
+        for k in _MODE_KEYS:
+            if not np.array_equal(again[k], modes[k]):
+                raise ValueError("stored %s differs from the modes its parameters draw" % k)
+    return params, modes
 
 
 class ModeTable:

@@ -38,6 +38,18 @@ def test_exports_every_declared_symbol(abi):
     assert sorted(abi.exported_symbols()) == names
 
 
+def test_checked_library_exports_the_same_symbols(abi):
+    # the checked flavour (device-side index checks) is a drop-in replacement
+    names = header_functions()
+    path = os.path.join(ROOT, "paper_2212_10961_gb300", "libgrf_checked.so")
+    C = ctypes.CDLL(path)
+    for n in names:
+        assert hasattr(C, n), n
+    assert C.grf_checked_build() == 1
+    assert abi.lib().grf_checked_build() == 0
+    assert C.grf_take_index_faults(None) == abi.GRF_EINVAL
+
+
 def test_version_and_launch_count(abi):
     assert abi.lib().grf_version().decode().startswith("grf-gb300")
     assert abi.lib().grf_launch_count() >= 0
@@ -249,6 +261,31 @@ def test_from_dictionary_maps_appendix_b_keys(abi):
     assert cfg2["type"] == "bitruncated" and cfg2["params"].dim == 2 and cfg2["thresholds2"] == (0.1,)
     with pytest.raises(ValueError):
         F.from_dictionary({"type": "other"})
+
+
+@pytest.mark.parametrize("rot", [None, ((0.0, 1.0, 0.0), (-1.0, 0.0, 0.0), (0.0, 0.0, 1.0))])
+def test_realisation_record_round_trip(abi, tmp_path, rot):
+    # the saved record reproduces the parameters and the modes bit for bit, and
+    # a record whose modes do not follow from its parameters is rejected
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(family="exponential", sigma2=2.5, mean=-0.25, ell=(0.3, 0.2, 0.1), dim=3, n_modes=257,
+                      seed=2 ** 40 + 3, stream=1, period=(2.0, 0.0, 0.0), rot=rot)
+    path = tmp_path / "real.npz"
+    F.save_realisation(path, p)
+    q, modes = F.load_realisation(path)
+    assert bytes(q.to_c()) == bytes(p.to_c())
+    want = omodes.gen_modes(omodes.EXPONENTIAL, 2.5, (0.3, 0.2, 0.1), 3, 257, 2 ** 40 + 3, stream=1,
+                            period=(2.0, 0.0, 0.0), rot=None if rot is None else np.array(rot))
+    for k in ("kappa", "rho", "psi", "a", "amp"):
+        np.testing.assert_allclose(modes[k], want[k], rtol=4e-15, atol=1e-300, err_msg=k)
+    bad = dict(modes)
+    bad["psi"] = modes["psi"].copy()
+    bad["psi"][7] += 1e-12
+    F.save_realisation(tmp_path / "bad.npz", p, bad)
+    with pytest.raises(ValueError):
+        F.load_realisation(tmp_path / "bad.npz")
+    q2, m2 = F.load_realisation(tmp_path / "bad.npz", verify=False)
+    assert m2["psi"][7] == bad["psi"][7]
 
 
 def test_fma_pipe_cosine_polynomial_matches_its_fit():
