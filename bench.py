@@ -236,7 +236,7 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
            "launches_per_step": per_step, "y_seed": y_seed}
     if with_e2e:
-        res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(2, steps // 3))
+        res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(5, steps))
         res["s1_host"] = bench_gen_modes(F, w, dim, base_seed)
         res["map_standalone"] = bench_map(torch, F, maps, out["Y"], w, steps)
     return res
@@ -337,7 +337,7 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
                 h.copy_(sl["dev_out"][k], non_blocking=True)
         sl["done"].record(back)
 
-    ms = timed_steps(torch, world, steps, 2, step)
+    ms = timed_steps(torch, world, steps, 3, step)
     for sl in slots:
         assert sl["plan"].status() == 0
     h2d = 4 * M * len(cells)
