@@ -10,12 +10,13 @@ second.  The same JSON line also reports the forward+backward step (128^3,
 N = 2048, mismatch loss and adjoint), the batched ensemble (256 realisations
 in one graph-replayed persistent launch), the unstructured 2M-cell workload
 (in lattice order and in a seeded random order), the 1024 x 512 HRL-shaped
-workload and the 64^2 workload.  roofline.traffic
+workload, the bitruncated two-field facies and the periodic, rotated field on
+the 256^3 cube, and the 64^2 workload.  roofline.traffic
 is the DRAM bytes (read + written) of one headline kernel launch measured by
 ncu.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--only all|fwd|bwd|batched|jitter|hrl] [--scale S]
+                  [--only all|fwd|bwd|batched|jitter|hrl|next] [--scale S]
                   [--batched-tile auto|128|256|512] [--no-cpu-baseline]
 
 Under torchrun each rank runs its own realisations (different seeds) of the
@@ -55,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd", "batched", "jitter", "hrl"])
+    ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd", "batched", "jitter", "hrl", "next"])
     ap.add_argument("--scale", type=int, default=1, help="shrink every grid axis by this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-tile", default="auto", choices=["auto", "128", "256", "512"],
@@ -156,7 +157,8 @@ def max_over_ranks(torch, world, v):
 # ---------------------------------------------------------------------------
 def params_for(F, w, dim, seed):
     return F.FieldParams(family=w["family"], sigma2=w["sigma2"], mean=w["mean"], ell=w["ell"], dim=dim,
-                         n_modes=w["n_modes"], seed=seed, nu=w.get("nu", 1.5))
+                         n_modes=w["n_modes"], seed=seed, nu=w.get("nu", 1.5), period=w.get("period", (0.0,) * 3),
+                         rot=w.get("rot"))
 
 
 def timed_steps(torch, world, steps, warmup, step_fn, kernel_events=None):
@@ -178,11 +180,13 @@ def timed_steps(torch, world, steps, warmup, step_fn, kernel_events=None):
     return max_over_ranks(torch, world, ms)
 
 
-def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e=True, shuffle_seed=None):
+def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e=True, shuffle_seed=None,
+                  override=None, label=None):
     """Headline forward step on one workload; returns dict of measurements.
     shuffle_seed: cells handed to the plan in a seeded random order (the
-    plan must recover the spatial locality itself)."""
-    w = W.WORKLOADS[name]
+    plan must recover the spatial locality itself).  override: workload
+    keys replaced (e.g. period, rot), reported under `label`."""
+    w = dict(W.WORKLOADS[name], **(override or {}))
     cells = W.workload_cells(name, scale)
     if shuffle_seed is not None:
         cells, _ = W.shuffled(cells, shuffle_seed)
@@ -228,8 +232,8 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     ring[0].update(m0["amp"], m0["psi"], m0["a"])
     y_seed = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True))["Y"].cpu().numpy()
     per_step = launches / float(steps + warmup)
-    res = {"workload": name if shuffle_seed is None else "%s, cells in seeded random order (seed %d)"
-           % (name, shuffle_seed), "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
+    res = {"workload": label or (name if shuffle_seed is None else "%s, cells in seeded random order (seed %d)"
+                                 % (name, shuffle_seed)), "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
            "kernel_ms": max_over_ranks(torch, world, kern_ms),
            "kernel_ms_median": max_over_ranks(torch, world, float(np.median(kern_all))),
            "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
@@ -385,6 +389,31 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
     return {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
             "ms_per_step": ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "cell_modes_per_step": float(M) * N,
             "launches_per_step": launches / float(steps + warmup)}
+
+
+def bench_bitruncated(torch, F, W, rank, world, steps, warmup, scale):
+    """Bitruncated pluri-Gaussian facies (Sec. 3.1, Appendix B) on the 256^3
+    cube: two fields of 4096 modes on generator streams 0 and 1 (the
+    headline's exponential field and a Gaussian one), a 3 x 2 truncation
+    rule and per-facies values; per step both syntheses and the rule map
+    (tables fixed; events on the stream around the whole step)."""
+    w = W.WORKLOADS["grid3d_256"]
+    cells = W.workload_cells("grid3d_256", scale)
+    M, N = len(cells[0]), w["n_modes"]
+    plan = F.CellPlan(*[torch.from_numpy(c).cuda() for c in cells])
+    seed = w["seed"] + 1000 * rank
+    p1 = F.FieldParams(family=w["family"], sigma2=w["sigma2"], ell=w["ell"], dim=3, n_modes=N, seed=seed)
+    p2 = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1, 0.1), dim=3, n_modes=N, seed=seed)
+    pg = F.PluriGaussianField(p1, p2)
+    t = W.quantile_thresholds(0.0, math.sqrt(w["sigma2"]), (1.0 / 3.0, 2.0 / 3.0))
+    rule = [[0, 1], [2, 3], [4, 5]]
+    values = [0.01, 0.1, 1.0, 10.0, 100.0, 1000.0]
+    l0 = F.launch_count()
+    ms = timed_steps(torch, world, steps, warmup, lambda i: pg.synth(plan, t, (0.0,), rule, values))
+    launches = F.launch_count() - l0
+    return {"workload": "grid3d_256 bitruncated: exponential l=(0.2,0.2,0.05) x Gaussian l=0.1, 3 x 2 rule",
+            "cells": M, "modes_per_field": N, "ms_per_step": ms, "cell_modes_per_step": 2.0 * M * N,
+            "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms}
 
 
 def bench_batched(torch, F, W, rank, world, steps, warmup, scale, tile="auto"):
@@ -560,6 +589,15 @@ def main():
     if args.only in ("all", "hrl"):
         extra["hrl2d"] = bench_forward(torch, F, W, "hrl2d", rank, world, args.steps, args.warmup, 1,
                                        with_e2e=False)
+    if args.only in ("all", "next"):
+        extra["bitruncated_256"] = bench_bitruncated(torch, F, W, rank, world, max(3, args.steps // 2), args.warmup,
+                                                     args.scale)
+        c30, s30 = math.cos(math.pi / 6), math.sin(math.pi / 6)
+        extra["periodic_rotated_256"] = bench_forward(
+            torch, F, W, "grid3d_256", rank, world, max(3, args.steps // 2), args.warmup, args.scale,
+            with_e2e=False, override={"period": (1.0, 1.0, 1.0), "rot": ((c30, s30, 0.0), (-s30, c30, 0.0),
+                                                                        (0.0, 0.0, 1.0))},
+            label="grid3d_256 with periodic = (1, 1, 1) and the anisotropy rotated 30 degrees about z")
     if args.only == "all":
         extra["grid2d_64"] = bench_forward(torch, F, W, "grid2d_64", rank, world, args.steps, args.warmup, 1,
                                            with_e2e=False)
