@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(kBoxThreads)
     }
 }
 
-// Quantisation grid per segment: cubic cells of side L_max / 2^kMortonBits
-// (L_max = largest bounding-box extent), so that the Morton (Z-order) code
+// Quantisation grid per segment: cubic cells of side L_max / 2^level_bits
+// (L_max = largest bounding-box extent, level_bits <= kMortonBits chosen by
+// the host from the largest segment's size), so that the Morton (Z-order) code
 // of the quantised position orders cells along a space-filling curve and
 // every aligned run of 2^k sorted cells is a compact, roughly cubic block.
 __global__ void brick_kernel(SegInfo* segs, int n_segments, int dim, int level_bits) {
