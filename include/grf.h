@@ -154,7 +154,9 @@ int grf_gen_modes(const grf_params *p, grf_modes *out);
  * and phase as FP32 hi/lo pairs (for the compensated phase split), the
  * original mode index, and a per-extent table of how many modes need the
  * compensated path.  Modes are stored in decreasing order of |a|_1; the sum
- * is order independent.
+ * is order independent.  Every mode at an odd position is stored in the
+ * equivalent form (-A, psi + 1/2), so that a mean offset of the hardware
+ * cosine's error cancels over the sum instead of growing with sqrt(N).
  */
 size_t grf_table_bytes(int64_t n_modes);
 
@@ -234,7 +236,8 @@ typedef struct grf_map {
 } grf_map;
 
 /* Device outputs in the caller's original cell order; an output may be
- * NULL when its bit is not requested. */
+ * NULL when its bit is not requested, and every output may be NULL when
+ * there are no cells to write (an empty plan or segment, n = 0). */
 typedef struct grf_outputs {
     float *Y;         /* GRF_MAP_Y */
     float *K;         /* GRF_MAP_LOGNORMAL */

@@ -249,7 +249,8 @@ MapDev make_map(const grf_map* m, const grf_outputs* out, double mean, double si
     return d;
 }
 
-int check_map(const grf_map* m, const grf_outputs* out) {
+// Output pointers are required only when there are cells to write (n > 0).
+int check_map(const grf_map* m, const grf_outputs* out, int64_t n) {
     if (!m) return fail(GRF_EINVAL, "map is NULL");
     if (!out) return fail(GRF_EINVAL, "outputs is NULL");
     const int known = GRF_MAP_Y | GRF_MAP_LOGNORMAL | GRF_MAP_FACIES | GRF_MAP_VALUES | GRF_MAP_POROSITY;
@@ -263,10 +264,10 @@ int check_map(const grf_map* m, const grf_outputs* out) {
         if (t > 0 && !(m->thresholds[t] > m->thresholds[t - 1]))
             return fail(GRF_EINVAL, "thresholds must be strictly ascending");
     }
-    if ((m->bits & GRF_MAP_Y) && !out->Y) return fail(GRF_EINVAL, "Y output is NULL");
-    if ((m->bits & GRF_MAP_LOGNORMAL) && !out->K) return fail(GRF_EINVAL, "K output is NULL");
-    if ((m->bits & GRF_MAP_FACIES) && !out->facies) return fail(GRF_EINVAL, "facies output is NULL");
-    if ((m->bits & (GRF_MAP_VALUES | GRF_MAP_POROSITY)) && !out->prop)
+    if (n > 0 && (m->bits & GRF_MAP_Y) && !out->Y) return fail(GRF_EINVAL, "Y output is NULL");
+    if (n > 0 && (m->bits & GRF_MAP_LOGNORMAL) && !out->K) return fail(GRF_EINVAL, "K output is NULL");
+    if (n > 0 && (m->bits & GRF_MAP_FACIES) && !out->facies) return fail(GRF_EINVAL, "facies output is NULL");
+    if (n > 0 && (m->bits & (GRF_MAP_VALUES | GRF_MAP_POROSITY)) && !out->prop)
         return fail(GRF_EINVAL, "prop output is NULL");
     if ((m->bits & GRF_MAP_POROSITY) && !(m->phi_min <= m->phi_max))
         return fail(GRF_EINVAL, "phi_min must not exceed phi_max");
@@ -491,14 +492,17 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
         double a[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < d; ++c) a[c] = m->a[j * d + c];
         for (int c = 0; c < 3; ++c) hot[s * 4 + c] = static_cast<float>(2.0 * M_PI * a[c]);
-        hot[s * 4 + 3] = static_cast<float>(m->amp[j]);
+        // (-A, psi + 1/2) at odd positions: see mode_flipped
+        const bool flip = mode_flipped(s);
+        hot[s * 4 + 3] = static_cast<float>(flip ? -m->amp[j] : m->amp[j]);
+        const double psi = flip ? (m->psi[j] <= 0.0 ? m->psi[j] + 0.5 : m->psi[j] - 0.5) : m->psi[j];
         float ah[3], al[3];
         for (int c = 0; c < 3; ++c) {
             ah[c] = static_cast<float>(a[c]);
             al[c] = static_cast<float>(a[c] - static_cast<double>(ah[c]));
         }
-        const float ph = static_cast<float>(m->psi[j]);
-        const float pl = static_cast<float>(m->psi[j] - static_cast<double>(ph));
+        const float ph = static_cast<float>(psi);
+        const float pl = static_cast<float>(psi - static_cast<double>(ph));
         float* c0 = cold + s * 8;
         c0[0] = ah[0];
         c0[1] = al[0];
@@ -637,11 +641,13 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     int rc = check_params(p);
     if (rc) return rc;
     if (!table) return fail(GRF_EINVAL, "table is NULL");
-    rc = check_map(map, out);
-    if (rc) return rc;
-    if (map->bits == 0) return fail(GRF_EINVAL, "no output requested");
     PlanMeta meta;
     if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    const int32_t n_seg = static_cast<int32_t>(meta.offsets.size()) - 1;
+    const int64_t n = segment >= 0 && segment < n_seg ? meta.offsets[segment + 1] - meta.offsets[segment] : 0;
+    rc = check_map(map, out, n);
+    if (rc) return rc;
+    if (map->bits == 0) return fail(GRF_EINVAL, "no output requested");
     FwdDesc d{};
     rc = fwd_desc(table, p->n_modes, p->dim, plan, meta, segment,
                   make_map(map, out, p->mean, std::sqrt(p->sigma2)), d);
@@ -658,9 +664,9 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
 int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, const float* Y,
                      const grf_outputs* out, void* stream) try {
     TraceRange trace_("grf_map_property");
-    int rc = check_map(map, out);
-    if (rc) return rc;
     if (n < 0) return fail(GRF_EINVAL, "n must be >= 0");
+    int rc = check_map(map, out, n);
+    if (rc) return rc;
     if (n > 0 && !Y) return fail(GRF_EINVAL, "Y is NULL");
     if (!(sigma > 0.0)) return fail(GRF_EINVAL, "sigma must be > 0");
     const int err = launch_map(make_map(map, out, mean, sigma), n, Y, stream);
@@ -807,7 +813,11 @@ int grf_batch_prepare(int32_t n_items, const grf_batch_item* items, const void* 
         if (it.n_modes < 1 || it.n_modes > GRF_MAX_MODES) return fail(GRF_EINVAL, "item %d: n_modes", r);
         if (it.dim < 1 || it.dim > 3) return fail(GRF_EINVAL, "item %d: dim", r);
         if (!(it.sigma > 0.0) || !std::isfinite(it.mean)) return fail(GRF_EINVAL, "item %d: sigma/mean", r);
-        int rc = check_map(&it.map, &it.out);
+        const int32_t n_seg = static_cast<int32_t>(meta.offsets.size()) - 1;
+        const int64_t n_it = it.segment >= 0 && it.segment < n_seg
+                                 ? meta.offsets[it.segment + 1] - meta.offsets[it.segment]
+                                 : 0;
+        int rc = check_map(&it.map, &it.out, n_it);
         if (rc) return fail(rc, "item %d: %s", r, g_last_error.c_str());
         if (it.map.bits == 0) return fail(GRF_EINVAL, "item %d: no output requested", r);
         FwdDesc d{};

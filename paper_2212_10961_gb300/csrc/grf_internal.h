@@ -27,6 +27,13 @@ namespace grf {
 //   kpref: int32[kBuckets] kpref[b] = #{j : h_j * 2^((b - bias)/4) > 1}, the
 //          length of the prefix of modes whose phase span over a box of
 //          half-extent E exceeds tau turns is read at bucket(E / tau)
+// Every mode at an odd sorted position is stored in the equivalent form
+// (-A, psi + 1/2): A cos(2 pi (a.x + psi)) = -A cos(2 pi (a.x + psi + 1/2)).
+// Half of the terms then evaluate the hardware cosine half a turn away with
+// the opposite sign, so a mean offset of its error over the phases cancels
+// between the two halves instead of adding up over all N terms (it would
+// otherwise grow like c * sum_j A_j ~ sqrt(N)).  Only the adjoint's dA_j
+// changes sign with the form (dpsi, da and the chain rule are invariant).
 // ---------------------------------------------------------------------------
 constexpr int kChunk = 128;          // modes per shared-memory chunk
 constexpr int kBuckets = 160;        // extent buckets
@@ -34,6 +41,12 @@ constexpr int kBucketBias = 100;     // E_b = 2^((b - kBucketBias) / 4)
 constexpr float kTauLight = 8.0f;    // warp-origin path iff h_j * E_warp <= tau1 (turns)
 constexpr float kTauMedium = 16.0f;  // lane-origin path iff h_j * E_lane <= tau2 (turns)
 constexpr uint32_t kTableMagic = 0x54465247u;  // "GRFT"
+
+// Sorted position s holds its mode in the form (-A, psi + 1/2).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr bool mode_flipped(int64_t s) { return (s & 1) != 0; }
 // Largest |a_c| (turns per unit length) accepted: with |x| < 2^16 the exact
 // phase split needs |a x| < 2^46.
 constexpr double kMaxFrequency = 1073741824.0;  // 2^30

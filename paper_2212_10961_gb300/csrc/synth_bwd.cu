@@ -300,7 +300,9 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
     const double a[3] = {static_cast<double>(q0.x) + static_cast<double>(q0.y),
                          static_cast<double>(q0.z) + static_cast<double>(q0.w),
                          static_cast<double>(q1.x) + static_cast<double>(q1.y)};
-    args.g.dA[j] = v[0];
+    // the table holds the mode as (-A, psi + 1/2) at odd positions, where the
+    // cosine sum v[0] has the opposite sign; A * v[1] and A * v[2..] do not
+    args.g.dA[j] = mode_flipped(m) ? -v[0] : v[0];
     args.g.dpsi[j] = -kTwoPi * A * v[1];
     ct[0] = (A / args.sigma) * v[0];
     const int d = args.dim;

@@ -113,8 +113,8 @@ def _modes_for(abi, n, dim):
 
 
 @pytest.mark.parametrize("bad", [dict(family=5), dict(dim=0), dict(dim=4), dict(sigma2=0.0),
-                                 dict(sigma2=float("nan")), dict(n_modes=0), dict(reserved=1),
-                                 dict(family=2, nu=-1.0)])
+                                 dict(sigma2=float("nan")), dict(n_modes=0), dict(n_modes=(1 << 24) + 1),
+                                 dict(reserved=1), dict(family=2, nu=-1.0)])
 def test_gen_modes_rejects_bad_params(abi, bad):
     p = _params(abi, **bad)
     m, _ = _modes_for(abi, 10, 2)
@@ -164,12 +164,20 @@ def test_pack_table_layout(abi, n, dim):
     h = np.sum(np.abs(a), axis=1)
     assert np.all(np.diff(h) <= 0)  # sorted by |a|_1, descending
     np.testing.assert_array_equal(t["hot"][:n, :dim], (2 * math.pi * a).astype(np.float32))
-    np.testing.assert_array_equal(t["hot"][:n, 3], md["amp"][order[:n]].astype(np.float32))
+    # odd sorted positions hold the equivalent form (-A, psi + 1/2)
+    sgn = np.where(np.arange(n) % 2 == 1, -1.0, 1.0)
+    np.testing.assert_array_equal(t["hot"][:n, 3], (sgn * md["amp"][order[:n]]).astype(np.float32))
     assert np.all(t["hot"][n:] == 0) and np.all(t["cold"][n:] == 0)
     c = t["cold"][:n].astype(np.float64)
     rec = np.stack([c[:, 0] + c[:, 1], c[:, 2] + c[:, 3], c[:, 4] + c[:, 5]], axis=1)[:, :dim]
     np.testing.assert_allclose(rec, a, rtol=2.0 ** -46, atol=0)
-    np.testing.assert_allclose(c[:, 6] + c[:, 7], md["psi"][order[:n]], rtol=0, atol=1e-15)
+    psi = md["psi"][order[:n]]
+    want = np.where(sgn < 0, np.where(psi <= 0.0, psi + 0.5, psi - 0.5), psi)
+    np.testing.assert_allclose(c[:, 6] + c[:, 7], want, rtol=0, atol=1e-15)
+    # the stored form is the same term: A cos(2 pi t) = -A cos(2 pi (t + 1/2))
+    tt = np.random.default_rng(n).random(n)
+    np.testing.assert_allclose(sgn * md["amp"][order[:n]] * np.cos(2 * math.pi * (tt + want)),
+                               md["amp"][order[:n]] * np.cos(2 * math.pi * (tt + psi)), rtol=0, atol=1e-12)
     for b in range(160):
         Eb = 2.0 ** ((b - 100) / 4.0)
         assert t["kpref"][b] == int(np.sum(h * Eb > 1.0))
@@ -187,7 +195,12 @@ def test_pack_and_sizes_reject(abi):
     buf = (ctypes.c_uint8 * nb)()
     assert abi.lib().grf_pack_table(ctypes.byref(m), buf, nb) == abi.GRF_EINVAL
     assert abi.lib().grf_table_bytes(0) == 0
+    assert abi.lib().grf_table_bytes(abi.GRF_MAX_MODES) > 48 * abi.GRF_MAX_MODES
+    assert abi.lib().grf_table_bytes(abi.GRF_MAX_MODES + 1) == 0
     assert abi.lib().grf_plan_bytes(100, 0) == 0
+    # plans index cells with int32: 2^31 - 1 cells at most
+    assert abi.lib().grf_plan_bytes((1 << 31) - 1, 1) > 0
+    assert abi.lib().grf_plan_bytes(1 << 31, 1) == 0
     assert abi.lib().grf_plan_bytes(1000, 1) > 1000 * 16
     assert abi.lib().grf_backward_workspace_bytes(1000, 0, 3) == 0
     assert abi.lib().grf_batch_workspace_bytes(0, 10) == 0

@@ -251,6 +251,48 @@ def test_many_segments_coarsen_the_sort_grid(env):
     assert plan.status() == 0
 
 
+def test_empty_plan_and_empty_segment(env):
+    # no cells at all, and an empty segment between two others: nothing to
+    # compute, no error, and the neighbouring segments are unaffected
+    torch, F, W = env
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    plan0 = F.CellPlan(e, e, e)
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1, 0.1), dim=3, n_modes=300, seed=4)
+    gf = F.GaussianField(p)
+    out = gf.synth(plan0, F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True))
+    assert all(v.numel() == 0 for v in out.values())
+    g0 = F.backward(gf.table, p, plan0, torch.empty(0, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    assert plan0.status() == 0
+    assert float(g0["dA"].abs().max()) == 0.0 and float(g0["dmu"].abs().max()) == 0.0
+    rng = np.random.default_rng(5)
+    a = [rng.random(100).astype(np.float32) for _ in range(3)]
+    b = [rng.random(57).astype(np.float32) + 2.0 for _ in range(3)]
+    cells = [np.concatenate([a[k], b[k]]) for k in range(3)]
+    plan = F.CellPlan(*to_dev(torch, cells), segments=[100, 0, 57])
+    om = oracle_modes("gaussian", 1.0, (0.1, 0.1, 0.1), 3, 300, 4)
+    assert gf.synth(plan, F.MapSpec(y=True), segment=1)["Y"].numel() == 0
+    for s, c in ((0, a), (2, b)):
+        y = gf.synth(plan, F.MapSpec(y=True), segment=s)["Y"].cpu().numpy()
+        check_forward(y, oracle_field(om, 0.0, c), 1.0, "segment %d" % s)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+
+
+def test_maximum_mode_count(env):
+    # N = GRF_MAX_MODES = 2^24 modes (131,072 chunks of 128) on a few hundred
+    # cells, checked against the oracle on a sample of them
+    torch, F, W = env
+    from paper_2212_10961_gb300 import _abi
+    n_modes = _abi.GRF_MAX_MODES
+    rng = np.random.default_rng(8)
+    cells = [rng.random(300).astype(np.float32) for _ in range(3)]
+    out, p, plan = run(env, cells, "gaussian", 1.0, (0.3, 0.2, 0.1), n_modes, seed=6)
+    om = oracle_modes("gaussian", 1.0, (0.3, 0.2, 0.1), 3, n_modes, 6)
+    idx = np.arange(0, 300, 15)
+    check_forward(out["Y"][idx], oracle_field(om, 0.0, cells, idx), 1.0, "2^24 modes")
+
+
 def test_rejects_bad_calls(env):
     torch, F, W = env
     from paper_2212_10961_gb300 import _abi
