@@ -290,7 +290,8 @@ def test_maximum_mode_count(env):
     out, p, plan = run(env, cells, "gaussian", 1.0, (0.3, 0.2, 0.1), n_modes, seed=6)
     om = oracle_modes("gaussian", 1.0, (0.3, 0.2, 0.1), 3, n_modes, 6)
     idx = np.arange(0, 300, 15)
-    check_forward(out["Y"][idx], oracle_field(om, 0.0, cells, idx), 1.0, "2^24 modes")
+    err = check_forward(out["Y"][idx], oracle_field(om, 0.0, cells, idx), 1.0, "2^24 modes")
+    print("max-abs field error with 2^24 modes: %.3e sigma" % err)
 
 
 def test_rejects_bad_calls(env):
