@@ -17,7 +17,7 @@ ncu.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--only all|fwd|bwd|batched|jitter|hrl|next] [--scale S]
-                  [--batched-tile auto|128|256|512] [--no-cpu-baseline]
+                  [--batched-tile auto|128|256|512] [--no-cpu-baseline] [--jsonl PATH]
 
 Under torchrun each rank runs its own realisations (different seeds) of the
 same workloads: per-GPU work is fixed (weak scaling) and the forward path has
@@ -61,7 +61,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-tile", default="auto", choices=["auto", "128", "256", "512"],
                     help="cells per warp work item of the ensemble (default: autotuned)")
+    ap.add_argument("--jsonl", default=None,
+                    help="also append the result line to this JSON-lines run log (with a UTC timestamp)")
     return ap.parse_args()
+
+
+def emit(args, line):
+    """Print the one result line; with --jsonl also append it to the run log."""
+    print(json.dumps(line))
+    if args.jsonl:
+        rec = dict(line, logged_utc=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()))
+        with open(args.jsonl, "a") as f:
+            f.write(json.dumps(rec) + "\n")
 
 
 # ---------------------------------------------------------------------------
@@ -551,7 +562,7 @@ def run_reference(args):
             "cpu_baseline": {"value": val, "unit": "Gcell.mode/s", "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": val, "unit": "Gcell.mode/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    emit(args, line)
 
 
 def main():
@@ -619,7 +630,7 @@ def main():
         k_fb["roofline_fwd_bwd"]["frac"] = k_fb["roofline_fwd_bwd"]["achieved"] / k_fb["roofline_fwd_bwd"]["peak"]
     if head is None:
         head = next(iter(extra.values()))
-        print(json.dumps({"partial": args.only, "results": extra, "clocks": ck}))
+        emit(args, {"partial": args.only, "results": extra, "clocks": ck})
         return
     value = head["cell_modes_per_step"] * world / (head["ms_per_step"] * 1e-3) / 1e9
     e2e = head.get("e2e")
@@ -649,7 +660,7 @@ def main():
         from oracle import native
         native.build()
         line["cpu_baseline"] = cpu_baseline(W, "grid3d_256", args.scale, y_gpu=y_seed_head)
-    print(json.dumps(line))
+    emit(args, line)
 
 
 if __name__ == "__main__":
