@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(kSortThreads, kFirst ? 3 : 2)
             loc[r / 2] = rank;
         else
             loc[r / 2] |= rank << 16;
+        __syncwarp();  // this round's counts are visible to the next round's leaders
     }
     __syncthreads();
     for (int d = threadIdx.x; d < radix; d += kSortThreads) {
