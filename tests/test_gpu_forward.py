@@ -149,6 +149,21 @@ def test_large_coordinates_exact_path(env):
     check_forward(out["Y"], oracle_field(om, 0.0, cells), 1.0, "far cells")
 
 
+def test_rough_field_medium_and_super_classes(env):
+    # correlation length five times smaller than the cell spacing, exponential
+    # (Cauchy-like spectrum): most modes span more than the light-class limit
+    # over a warp tile, so the lane-origin and per-cell exact paths carry much
+    # of the sum; every cell against the oracle
+    torch, F, W = env
+    cells = W.grid_centres((64, 64, 64))
+    ell = (0.003, 0.003, 0.003)
+    out, p, _ = run(env, cells, "exponential", 2.0, ell, 1500, seed=13)
+    om = oracle_modes("exponential", 2.0, ell, 3, 1500, 13)
+    span = np.sum(np.abs(om["a"]), axis=1) * (4.0 / 64.0)  # turns over a warp tile's half-extent
+    assert np.mean(span > 8.0) > 0.5  # the light class is the minority here
+    check_forward(out["Y"], oracle_field(om, 0.0, cells), math.sqrt(2.0), "rough field")
+
+
 def test_maps_standalone_and_fused(env):
     torch, F, W = env
     rng = np.random.default_rng(6)
