@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
                                                       __ldg(args.cold + 2 * mm[k] + 1));
         }
         if (!__any_sync(0xffffffffu, any_heavy)) {
-#pragma unroll 4
+#pragma unroll 8
             for (int i = 0; i < kBwdTile; ++i) {
                 const float4 c = sm.cd[i];
                 const float4 gq = sm.gd[i];
