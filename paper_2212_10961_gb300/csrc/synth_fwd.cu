@@ -298,7 +298,7 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
                     ws.t0[m] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
                 }
                 __syncwarp();
-#pragma unroll 4
+#pragma unroll 8
                 for (int m = m0; m < kWChunk; ++m) mode(hotS[m], ws.t0[m]);
             }
 #pragma unroll
