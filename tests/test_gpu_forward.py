@@ -359,10 +359,13 @@ def test_mode_split_matches_unsplit_and_oracle(env):
     assert plan.status() == 0
 
 
-def test_periodic_field_repeats(env):
+@pytest.mark.parametrize("angle", [None, 0.5])
+def test_periodic_field_repeats(env, angle):
     # Appendix B `periodic`: with L = (1, 1) the field at x + (1, 0) and
-    # x + (0, 1) equals the field at x (frequencies on the reciprocal lattice)
+    # x + (0, 1) equals the field at x (frequencies on the reciprocal lattice);
+    # also with the anisotropy axes rotated (the snapping follows the rotation)
     torch, F, W = env
+    rot = None if angle is None else ((math.cos(angle), math.sin(angle)), (-math.sin(angle), math.cos(angle)))
     # dyadic centres, so that x + 1 and y + 1 are exact in FP32 (otherwise the
     # shifted point itself moves, and high-frequency modes see it)
     base = W.grid_centres((64, 32))
@@ -374,7 +377,7 @@ def test_periodic_field_repeats(env):
     n = len(base[0])
     plan = F.CellPlan(*to_dev(torch, cells), segments=[n, n, n])
     p = F.FieldParams(family="exponential", sigma2=2.0, ell=(0.2, 0.1), dim=2, n_modes=800, seed=5,
-                      period=(1.0, 1.0))
+                      period=(1.0, 1.0), rot=rot)
     gf = F.GaussianField(p)
     ys = [gf.synth(plan, F.MapSpec(y=True), segment=k)["Y"].cpu().numpy() for k in range(3)]
     torch.cuda.synchronize()
@@ -382,7 +385,7 @@ def test_periodic_field_repeats(env):
     assert np.max(np.abs(ys[1] - ys[0])) <= 2e-5 * sig
     assert np.max(np.abs(ys[2] - ys[0])) <= 2e-5 * sig
     from oracle import modes as om
-    m = om.gen_modes(1, 2.0, (0.2, 0.1), 2, 800, 5, period=(1.0, 1.0))
+    m = om.gen_modes(1, 2.0, (0.2, 0.1), 2, 800, 5, period=(1.0, 1.0), rot=None if rot is None else np.array(rot))
     for k in range(3):
         check_forward(ys[k], oracle_field(m, 0.0, segs[k]), sig, "periodic segment %d" % k)
 
