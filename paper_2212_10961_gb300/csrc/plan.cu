@@ -226,19 +226,35 @@ __device__ __forceinline__ uint32_t spread_bits2(uint32_t v) {  // 10 bits -> ev
     return v;
 }
 
-__device__ __forceinline__ uint32_t morton_code(const float (&v)[3], const SegInfo& g, int dim) {
-    uint32_t b[3] = {0u, 0u, 0u};
+// Quantisation grid of one segment, held in registers.
+struct SegGrid {
+    float lo[3], inv[3];
+    int nb[3];
+};
+__device__ __forceinline__ SegGrid seg_grid(const SegInfo& g) {
+    SegGrid r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.lo[k] = g.lo[k];
+        r.inv[k] = g.inv_brick[k];
+        r.nb[k] = g.nb[k];
+    }
+    return r;
+}
+
+// spread[b] = the 10 bits of b moved to every dim-th bit (shared-memory table)
+__device__ __forceinline__ uint32_t morton_code(const float (&v)[3], const SegGrid& g, int dim,
+                                                const uint32_t* spread) {
+    uint32_t code = 0u;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (k >= dim) break;
-        float f = (v[k] - g.lo[k]) * g.inv_brick[k];
+        const float f = (v[k] - g.lo[k]) * g.inv[k];
         int q = isfinite(f) ? static_cast<int>(floorf(f)) : 0;
         q = q < 0 ? 0 : (q >= g.nb[k] ? g.nb[k] - 1 : q);
-        b[k] = static_cast<uint32_t>(q);
+        code |= spread[q] << k;
     }
-    if (dim == 3) return spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
-    if (dim == 2) return spread_bits2(b[0]) | (spread_bits2(b[1]) << 1);
-    return b[0];
+    return code;
 }
 
 // Sort keys (segment index above the Morton code), one sort tile per block,
@@ -251,13 +267,17 @@ __global__ void __launch_bounds__(kSortThreads)
                uint32_t* __restrict__ keys, int morton_bits, int digit_bits, uint32_t* __restrict__ counts,
                int nblk) {
     __shared__ uint32_t hist[kMaxRadix];
+    __shared__ uint32_t spread[1 << kMortonBits];
     const int radix = 1 << digit_bits;
     const uint32_t mask = static_cast<uint32_t>(radix - 1);
     for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[d] = 0u;
+    for (int b = threadIdx.x; b < (1 << kMortonBits); b += blockDim.x)
+        spread[b] = dim == 3 ? spread_bits3(b) : (dim == 2 ? spread_bits2(b) : static_cast<uint32_t>(b));
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
     const int64_t c1 = base + kSortTile < n ? base + kSortTile : n;
     const int s_first = find_segment(segs, n_segments, base);
     const bool single = s_first == find_segment(segs, n_segments, c1 - 1);
+    const SegGrid g_first = seg_grid(segs[s_first]);
     __syncthreads();
     constexpr int kGroup = 8;  // cells whose loads are in flight together
 #pragma unroll 1
@@ -275,8 +295,13 @@ __global__ void __launch_bounds__(kSortThreads)
         for (int r = 0; r < kGroup; ++r) {
             const int64_t i = base + (r0 + r) * kSortThreads + threadIdx.x;
             if (i >= n) continue;
-            const int s = single ? s_first : find_segment(segs, n_segments, i);
-            const uint32_t key = (static_cast<uint32_t>(s) << morton_bits) | morton_code(v[r], segs[s], dim);
+            uint32_t key;
+            if (single) {
+                key = (static_cast<uint32_t>(s_first) << morton_bits) | morton_code(v[r], g_first, dim, spread);
+            } else {
+                const int s = find_segment(segs, n_segments, i);
+                key = (static_cast<uint32_t>(s) << morton_bits) | morton_code(v[r], seg_grid(segs[s]), dim, spread);
+            }
             keys[i] = key;
             atomicAdd(&hist[key & mask], 1u);
         }
