@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(kScanThreads)
 // Stable scatter.  Warp w owns items [512 w, 512 (w + 1)) of the tile, in
 // 16 rounds of 32 consecutive items, so (warp, round, lane) is the input
 // order.  Each warp ranks its items per digit on its own (match_any within a
-// round, a warp-private running count across rounds); one block barrier then
+// round, all rounds' matches issued first; a warp-private running count
+// across rounds, advanced by one shared atomic per digit group); one block barrier then
 // turns the per-warp counts into offsets, and every item is stored at the
 // digit's global start + its warp's offset + its rank within the warp.
 // kFirst: the values are the input indices (nothing to read); kLast: only
@@ -456,18 +457,22 @@ __global__ void __launch_bounds__(kSortThreads, kFirst ? 3 : 2)
     }
     const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t loc[kRounds / 2];  // rank of each item among its warp's items of the same digit
+    unsigned peer[kRounds];
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
+    for (int r = 0; r < kRounds; ++r) {  // the rounds' matches are independent: all in flight
         const bool in = i0 + r * 32 < n;
         // out-of-range items get a digit of their own (never counted or stored)
         const int digit = in ? static_cast<int>((key[r] >> shift) & mask) : kMaxRadix;
-        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        peer[r] = __match_any_sync(0xffffffffu, digit);
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const bool in = i0 + r * 32 < n;
+        const unsigned peers = peer[r];
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0u;
-        if (lane == leader && in) {
-            before = warp_cnt[warp][digit];
-            warp_cnt[warp][digit] = before + static_cast<uint32_t>(__popc(peers));
-        }
+        if (lane == leader && in)
+            before = atomicAdd(&warp_cnt[warp][(key[r] >> shift) & mask], static_cast<uint32_t>(__popc(peers)));
         before = __shfl_sync(0xffffffffu, before, leader);
         const uint32_t rank = before + static_cast<uint32_t>(__popc(peers & lt_mask));
         if (r % 2 == 0)
