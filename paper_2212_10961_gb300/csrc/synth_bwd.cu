@@ -307,18 +307,24 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
     ct[0] = (A / args.sigma) * v[0];
     const int d = args.dim;
     double da[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < d; ++c) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c >= d) break;
         da[c] = -kTwoPi * A * v[2 + c];
         args.g.da[static_cast<int64_t>(j) * d + c] = da[c];
     }
     // u = R a (the unrotated frequencies), dL/du = R dL/da
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         double u = 0.0, du = 0.0;
-        for (int k = 0; k < d; ++k) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k >= d) break;
             u += args.rot[c * 3 + k] * a[k];
             du += args.rot[c * 3 + k] * da[k];
         }
         ct[1 + c] = c < d ? -(u / args.ell[c]) * du : 0.0;
+#pragma unroll
         for (int e = 0; e < 3; ++e) ct[4 + c * 3 + e] = (c < d && e < d) ? u * da[e] : 0.0;
     }
 }
