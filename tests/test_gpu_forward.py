@@ -193,6 +193,33 @@ def test_maps_standalone_and_fused(env):
     check_facies(out["facies"], y_or, thr, math.sqrt(1.5))
 
 
+def test_most_thresholds_and_fused_porosity(env):
+    # the largest truncation rule (GRF_MAX_THRESHOLDS thresholds, 16 facies with
+    # values) and the porosity map, both fused into the synthesis kernel
+    torch, F, W = env
+    from paper_2212_10961_gb300 import _abi
+    from oracle import field as of
+    rng = np.random.default_rng(17)
+    cells = [rng.random(3000).astype(np.float32) for _ in range(2)]
+    sig = math.sqrt(2.0)
+    q = (np.arange(_abi.GRF_MAX_THRESHOLDS) + 1.0) / (_abi.GRF_MAX_THRESHOLDS + 1.0)
+    thr = tuple(W.quantile_thresholds(-0.3, sig, q))
+    vals = tuple(float(v) for v in 10.0 ** np.arange(len(thr) + 1))
+    maps = F.MapSpec(y=True, thresholds=thr, facies=True, values=vals)
+    out, p, plan = run(env, cells, "gaussian", 2.0, (0.15, 0.1), 400, seed=23, mean=-0.3, maps=maps)
+    om = oracle_modes("gaussian", 2.0, (0.15, 0.1), 2, 400, 23)
+    y_or = oracle_field(om, -0.3, cells)
+    check_forward(out["Y"], y_or, sig, "16 facies")
+    check_facies(out["facies"], y_or, thr, sig)
+    assert np.array_equal(out["prop"], np.asarray(vals, dtype=np.float32)[out["facies"]])
+    assert len(np.unique(out["facies"])) == len(thr) + 1  # every facies occurs
+    pmap = F.MapSpec(y=False, porosity=(0.25, 0.05, 0.1, 0.35))
+    por, _, _ = run(env, cells, "gaussian", 2.0, (0.15, 0.1), 400, seed=23, mean=-0.3, maps=pmap, plan=plan)
+    want = of.porosity(y_or, -0.3, sig, 0.25, 0.05, 0.1, 0.35)
+    # porosity is affine in Y with slope 0.05 / sigma, then clamped
+    np.testing.assert_allclose(por["prop"], want, rtol=0, atol=0.05 / sig * 1e-5 * sig + 1e-6)
+
+
 @pytest.mark.parametrize("off,n", [(0, 5000), (1, 4999), (0, 2051), (4, 4093), (3, 1)])
 def test_map_standalone_ragged_and_misaligned(env, off, n):
     # offsets that break the 16-byte alignment of Y take the per-cell path;
