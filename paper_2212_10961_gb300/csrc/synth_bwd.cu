@@ -459,8 +459,9 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
                                           align256(int64_t(kBwdMaxSplits) * 8));
     if (n_cells == 0) {
         // no cells: all gradients are zero
-        cudaMemsetAsync(a.part, 0, sizeof(double) * n_pad * 5, st);
-        cudaMemsetAsync(a.gpart, 0, sizeof(double), st);
+        cudaError_t e = cudaMemsetAsync(a.part, 0, sizeof(double) * n_pad * 5, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.gpart, 0, sizeof(double), st);
+        if (e != cudaSuccess) return e;
         a.splits = 1;
     } else {
         dim3 grid(mode_blocks, a.splits);
