@@ -86,11 +86,12 @@ typedef struct grf_params {
     double period[3]; /* Appendix B `periodic`: L_c > 0 makes the field repeat with
                          period L_c along axis c (frequencies moved to the nearest
                          multiple of 1/L_c); 0 = not periodic */
-    double rot[9];    /* rotation of the anisotropy axes (Sec. 4.1: rescaling of
-                         frequency space "extended by including rotations"): row-major
-                         R whose rows are the principal axes, C(r) = sigma^2
-                         rho(|diag(1/l) R r|); the leading dim x dim block is used and
-                         must be orthonormal.  All zeros = no rotation. */
+    double rot[9];    /* transform of the anisotropy axes (Sec. 4.1: the per-axis
+                         rescaling of frequency space, extended to rotations and
+                         general transformation matrices): row-major R, C(r) = sigma^2
+                         rho(|diag(1/l) R r|).  A rotation (rows = principal axes) or
+                         any invertible matrix; the leading dim x dim block is used.
+                         All zeros = no transform. */
 } grf_params;
 
 #define GRF_MAX_MODES (1 << 24)

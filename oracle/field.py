@@ -145,7 +145,8 @@ def mode_sums(a, psi, cells, g):
 def grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g, rot=None):
     """Chain rule from per-mode sums to all parameter gradients.
 
-    With a rotation R (a = R^T u, u = kappa / (2 pi l)): dL/du = R dL/da,
+    With an axis transform R (a = R^T u, u = kappa / (2 pi l); a rotation or
+    any invertible matrix): u = R^-T a, dL/du = R dL/da,
     dL/dl_c = -sum_j (u_jc / l_c) (dL/du_j)_c, and for R as a free matrix
     dL/dR_cd = sum_j u_jc dL/da_jd (returned as "drot")."""
     amp = np.asarray(amp, dtype=np.float64)
@@ -157,7 +158,7 @@ def grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g, rot=None):
     da = -TWO_PI * amp[:, None] * s_sinx
     rho = amp / sigma
     R = np.eye(d) if rot is None else np.asarray(rot, dtype=np.float64)[:d, :d]
-    u = a @ R.T          # u_j = R a_j
+    u = np.linalg.solve(R.T, a.T).T  # a_j = R^T u_j, i.e. a = u R as rows: u = a R^-1
     du = da @ R.T        # dL/du_j = R dL/da_j
     return {
         "dA": dA,

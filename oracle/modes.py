@@ -17,9 +17,9 @@ Readings of Sec. 4.1, Eq. (DiscreteFT), taken here:
   length).
 * `disableY` / `disableZ` (Appendix B): kappa is drawn directly in d = dim
   dimensions.
-* "Kmean" and "Ksigma" (Appendix B) are the mean mu and the variance sigma^2
-  of the Gaussian field Y; "scaled to obtain the desired mean and variance"
-  (Sec. 4.1) is the theoretical scaling mu + sigma * (unit field).
+* `Kmean` and `Ksigma` (Appendix B) are the mean mu and the variance sigma^2
+  of the Gaussian field Y; the scaling to that mean and variance (Sec. 4.1)
+  is the theoretical one, mu + sigma * (unit field).
 
 Writing W cos(t) + W' sin(t) = R cos(t - atan2(W', W)) with R^2 = W^2 + W'^2:
 
@@ -95,9 +95,10 @@ def chi2_draw(seed, stream, j, d, nu):
 def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=None, rot=None):
     """Draw the N modes of one realisation.
 
-    rot: optional d x d rotation R whose rows are the principal axes of the
-    anisotropy (Sec. 4.1: the per-axis rescaling of frequency space extended
-    by a rotation).  The covariance is C(r) = sigma^2 rho(|diag(1/l) R r|), so
+    rot: optional d x d invertible axis transform R (a rotation whose rows are
+    the principal axes of the anisotropy, or a general matrix; Sec. 4.1: the
+    per-axis rescaling of frequency space extended to such transforms).  The
+    covariance is C(r) = sigma^2 rho(|diag(1/l) R r|), so
     with u = kappa / (2 pi l) the frequencies are a = R^T u (a = u without R).
 
     period: optional per-axis domain lengths L_c (0 = not periodic).  Along a

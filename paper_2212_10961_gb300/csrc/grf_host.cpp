@@ -189,14 +189,27 @@ int check_params(const grf_params* p) {
         if (!(p->period[c] >= 0.0) || !std::isfinite(p->period[c]))
             return fail(GRF_EINVAL, "period[%d] must be finite and >= 0", c);
     if (has_rotation(p)) {
+        // any invertible transform of the axes (a rotation, or a general matrix):
+        // finite entries and |det| not negligible against the row norms
         const int d = p->dim;
-        for (int i = 0; i < d; ++i)
+        double m[3][3], rn = 1.0;
+        for (int i = 0; i < d; ++i) {
+            double r2 = 0.0;
             for (int k = 0; k < d; ++k) {
-                double dot = 0.0;
-                for (int c = 0; c < d; ++c) dot += p->rot[i * 3 + c] * p->rot[k * 3 + c];
-                if (!std::isfinite(dot) || std::fabs(dot - (i == k ? 1.0 : 0.0)) > 1e-9)
-                    return fail(GRF_EINVAL, "rot: the leading %dx%d block must be orthonormal", d, d);
+                m[i][k] = p->rot[i * 3 + k];
+                if (!std::isfinite(m[i][k])) return fail(GRF_EINVAL, "rot has a non-finite entry");
+                r2 += m[i][k] * m[i][k];
             }
+            rn *= std::sqrt(r2);
+        }
+        double det = m[0][0];
+        if (d == 2) det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        if (d == 3)
+            det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                  m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                  m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+        if (!(std::fabs(det) > 1e-12 * rn))
+            return fail(GRF_EINVAL, "rot: the leading %dx%d block must be invertible", d, d);
     }
     return GRF_OK;
 }

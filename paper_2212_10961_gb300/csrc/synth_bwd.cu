@@ -46,7 +46,8 @@ struct BwdArgs {
     int32_t splits;
     double sigma;
     double ell[3];
-    double rot[9];    // row-major rotation of the anisotropy axes (identity: none)
+    double rot[9];    // row-major transform R of the anisotropy axes (identity: none)
+    double rot_it[9]; // R^-T, which maps a back to u = kappa / (2 pi l) (R itself for a rotation)
     const float* xs;
     const float* ys;
     const float* zs;
@@ -313,14 +314,14 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
         da[c] = -kTwoPi * A * v[2 + c];
         args.g.da[static_cast<int64_t>(j) * d + c] = da[c];
     }
-    // u = R a (the unrotated frequencies), dL/du = R dL/da
+    // u = R^-T a (the frequencies before the transform, a = R^T u), dL/du = R dL/da
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         double u = 0.0, du = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if (k >= d) break;
-            u += args.rot[c * 3 + k] * a[k];
+            u += args.rot_it[c * 3 + k] * a[k];
             du += args.rot[c * 3 + k] * da[k];
         }
         ct[1 + c] = c < d ? -(u / args.ell[c]) * du : 0.0;
@@ -434,6 +435,27 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.sigma = sigma;
     for (int c = 0; c < 3; ++c) a.ell[c] = c < dim ? ell[c] : 1.0;
     for (int k = 0; k < 9; ++k) a.rot[k] = rot[k];
+    // inverse transpose of the leading dim x dim block (adjugate / determinant;
+    // the host checks that the block is invertible)
+    {
+        double m[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int i = 0; i < dim; ++i)
+            for (int k = 0; k < dim; ++k) m[i][k] = rot[i * 3 + k];
+        const double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+        const double c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+        const double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+        const double c10 = m[0][2] * m[2][1] - m[0][1] * m[2][2];
+        const double c11 = m[0][0] * m[2][2] - m[0][2] * m[2][0];
+        const double c12 = m[0][1] * m[2][0] - m[0][0] * m[2][1];
+        const double c20 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+        const double c21 = m[0][2] * m[1][0] - m[0][0] * m[1][2];
+        const double c22 = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        const double det = m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02;
+        // (R^-1)^T = cofactor matrix / det
+        const double cof[3][3] = {{c00, c01, c02}, {c10, c11, c12}, {c20, c21, c22}};
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) a.rot_it[i * 3 + k] = cof[i][k] / det;
+    }
     a.xs = xs;
     a.ys = ys;
     a.zs = zs;

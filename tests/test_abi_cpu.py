@@ -123,6 +123,26 @@ def test_gen_modes_rejects_bad_params(abi, bad):
     assert len(abi.lib().grf_last_error()) > 0
 
 
+def test_gen_modes_general_transform_matches_oracle_and_singular_is_rejected(abi):
+    # Sec. 4.1: any invertible axis transform R, a = R^T kappa / (2 pi l)
+    from paper_2212_10961_gb300 import field as F
+    R = np.array([[1.1, 0.5, 0.0], [0.0, 0.8, 0.3], [0.2, 0.0, 1.3]])
+    p = F.FieldParams(family="matern", sigma2=1.5, ell=(0.2, 0.1, 0.05), dim=3, n_modes=300, seed=41, nu=1.5,
+                      rot=R.tolist())
+    got = F.gen_modes(p)
+    want = omodes.gen_modes(omodes.MATERN, 1.5, (0.2, 0.1, 0.05), 3, 300, 41, nu=1.5, rot=R)
+    # a = R^T u sums products of either sign: agreement to a few ulps of the largest term
+    scale = np.max(np.abs(want["a"]), axis=1, keepdims=True)
+    assert np.all(np.abs(got["a"] - want["a"]) <= 8e-16 * scale * np.max(np.abs(R)))
+    S = R.copy()
+    S[2] = S[0] + S[1]  # rank 2
+    ps = F.FieldParams(family="matern", sigma2=1.5, ell=(0.2, 0.1, 0.05), dim=3, n_modes=300, seed=41, nu=1.5,
+                       rot=S.tolist())
+    m, _ = _modes_for(abi, 300, 3)
+    assert abi.lib().grf_gen_modes(ctypes.byref(ps.to_c()), ctypes.byref(m)) == abi.GRF_EINVAL
+    assert "invertible" in abi.lib().grf_last_error().decode()
+
+
 def test_gen_modes_rejects_mismatched_output(abi):
     p = _params(abi)
     m, _ = _modes_for(abi, 9, 2)

@@ -194,15 +194,17 @@ def test_autograd_wrappers(env):
     _check(a.grad.cpu().numpy(), ref["da"], "da")
 
 
-def test_rotated_anisotropy_forward_and_adjoint(env):
-    # Sec. 4.1: anisotropy axes rotated by R (rows = principal axes); forward
-    # parity and the gradients with respect to l and R against the oracle
+@pytest.mark.parametrize("kind", ["rotation", "general"])
+def test_rotated_anisotropy_forward_and_adjoint(env, kind):
+    # Sec. 4.1: anisotropy axes transformed by R (a rotation with rows = principal
+    # axes, or a general invertible matrix); forward parity and the gradients
+    # with respect to l and R against the oracle
     torch, F, W = env
     from helpers import check_forward
     a_, b_ = 0.5, -0.3
     Rz = np.array([[math.cos(a_), -math.sin(a_), 0], [math.sin(a_), math.cos(a_), 0], [0, 0, 1.0]])
     Rx = np.array([[1.0, 0, 0], [0, math.cos(b_), -math.sin(b_)], [0, math.sin(b_), math.cos(b_)]])
-    R = Rz @ Rx
+    R = Rz @ Rx if kind == "rotation" else np.array([[1.1, 0.5, 0.0], [0.0, 0.8, 0.3], [0.2, 0.0, 1.3]])
     ell = (0.25, 0.12, 0.06)
     cells = W.grid_centres((28, 24, 20))
     p = F.FieldParams(family="matern", sigma2=1.4, ell=ell, dim=3, n_modes=700, seed=17, nu=1.5, rot=R.tolist())
@@ -212,7 +214,7 @@ def test_rotated_anisotropy_forward_and_adjoint(env):
     om = oracle_modes("matern", 1.4, ell, 3, 700, 17, nu=1.5)
     from oracle import modes as omod
     om = omod.gen_modes(2, 1.4, ell, 3, 700, 17, nu=1.5, rot=R)
-    check_forward(y.cpu().numpy(), oracle_field(om, 0.0, cells), math.sqrt(1.4), "rotated")
+    check_forward(y.cpu().numpy(), oracle_field(om, 0.0, cells), math.sqrt(1.4), kind)
     g = np.random.default_rng(11).standard_normal(len(cells[0])).astype(np.float32)
     gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()

@@ -297,7 +297,10 @@ def test_periodic_option_repeats_exactly():
     assert np.max(np.abs(ynp - y0)) > 1e-3  # not periodic along z
 
 
-def test_rotated_adjoint_against_finite_differences():
+@pytest.mark.parametrize("kind", ["rotation", "general"])
+def test_rotated_adjoint_against_finite_differences(kind):
+    # dL/dl and dL/dR of the transformed anisotropy a = R^T kappa / (2 pi l),
+    # for a rotation and for a general (sheared, scaled) invertible R
     from oracle import field as of
     n3 = 7
     c = (np.arange(n3) + 0.5) / n3
@@ -306,6 +309,8 @@ def test_rotated_adjoint_against_finite_differences():
     ell = np.array([0.3, 0.2, 0.25])
     th = 0.6
     R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    if kind == "general":
+        R = np.array([[1.1, 0.5, 0.0], [0.0, 0.8, 0.3], [0.2, 0.0, 1.3]])
     base = modes.gen_modes(spectra.GAUSSIAN, 1.0, ell, 3, 20, seed=3)
     u = base["a"]                     # kappa / (2 pi l)
     target = of.lognormal(of.synth(u @ R, base["amp"], base["psi"], 0.0, cells) * 0.8)

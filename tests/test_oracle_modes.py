@@ -131,12 +131,15 @@ def _rotation(alpha, beta, gamma):
     return Rz @ Ry @ Rx
 
 
-@pytest.mark.parametrize("family,nu", [(spectra.GAUSSIAN, 0.0), (spectra.MATERN, 1.5)])
-def test_rotated_anisotropy_characteristic_function(family, nu):
-    # covariance with principal axes given by the rows of R:
-    # C(r) = sigma^2 rho(|diag(1/l) R r|)  (Sec. 4.1, rotation of the rescaled frequency space)
+@pytest.mark.parametrize("family,nu,kind", [(spectra.GAUSSIAN, 0.0, "rotation"), (spectra.MATERN, 1.5, "rotation"),
+                                            (spectra.GAUSSIAN, 0.0, "general"), (spectra.MATERN, 1.5, "general")])
+def test_rotated_anisotropy_characteristic_function(family, nu, kind):
+    # covariance of the field Z(R x), Z with axis lengths l:
+    # C(r) = sigma^2 rho(|diag(1/l) R r|)  (Sec. 4.1, transform of the rescaled frequency
+    # space), for a rotation (rows = principal axes) and for a general invertible R
     n = 200000
-    R = _rotation(0.7, -0.4, 1.1)
+    R = _rotation(0.7, -0.4, 1.1) if kind == "rotation" else np.array([[1.2, 0.4, 0.0], [-0.3, 0.9, 0.2],
+                                                                          [0.1, 0.0, 0.7]])
     m = modes.gen_modes(family, 1.0, ELL3, 3, n, seed=1234, nu=nu, rot=R)
     rng = np.random.default_rng(8)
     lags = rng.standard_normal((12, 3)) * 0.1
