@@ -62,7 +62,9 @@ class FieldParams:
     nu: float = 1.5
     stream: int = 0
     period: Sequence[float] = (0.0, 0.0, 0.0)  # Appendix B `periodic`: L_c > 0 per axis
-    rot: Optional[Sequence[Sequence[float]]] = None  # rows: principal axes of the anisotropy
+    # axis transform R of the anisotropy: a rotation (rows = principal axes) or any
+    # invertible matrix; C(r) = sigma^2 rho(|diag(1/l) R r|)
+    rot: Optional[Sequence[Sequence[float]]] = None
 
     @property
     def sigma(self):
