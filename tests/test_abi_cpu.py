@@ -340,3 +340,21 @@ def test_fma_pipe_cosine_polynomial_matches_its_fit():
     f = np.linspace(-0.5, 0.5, 400_001)
     err = np.max(np.abs(gen.horner_fp32(compiled, f).astype(np.float64) - np.cos(2 * np.pi * f)))
     assert err <= 4.0e-7, err
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the product path has no CPU fallback: without the shared library the
+    # binding raises instead of computing anything another way
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2212_10961_gb300 import _abi\n"
+            "_abi.LIB_PATH = %r\n"
+            "_abi._lib = None\n"
+            "try:\n"
+            "    _abi.lib()\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n") % (ROOT, str(tmp_path / "absent.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "raised" in r.stdout and "absent.so" in r.stdout
