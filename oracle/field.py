@@ -34,6 +34,13 @@ Adjoint of the field sum with g_i = dL/dY_i and theta_ij = 2 pi (a_j.x_i + psi_j
 With a rotation R of the anisotropy axes (a = R^T u, u = kappa/(2 pi l)) the
 last line reads with u and R dL/da in place of a and dL/da; see
 grads_from_sums.
+
+Gradients with respect to the standardised draws themselves (rho, kappa) and
+with periodic axes: see grads_reparam.  Along a periodic axis the frequency
+is rounded to a multiple of 1/L_c, a step function of kappa, l and R whose
+derivative is zero wherever it is defined; so dL/da_c of a periodic axis
+reaches none of kappa, l, R (the reading taken: the paper gives no
+derivative of its `periodic` option).
 """
 import math
 
@@ -175,3 +182,54 @@ def backward(a, amp, psi, sigma, ell, cells, g, rot=None):
     """All gradients of a loss with dL/dY = g (see module docstring)."""
     s_cos, s_sin, s_sinx = mode_sums(a, psi, cells, g)
     return grads_from_sums(s_cos, s_sin, s_sinx, amp, a, sigma, ell, g, rot)
+
+
+def grads_reparam(s_cos, s_sin, s_sinx, kappa, rho, sigma, ell, g, rot=None, period=None):
+    """All gradients of a loss with respect to the parameters of the
+    reparameterised field of Sec. 4.1 (see modes.reparam):
+
+        Y = mu + sum_j sigma rho_j cos(2 pi (a_j . x + psi_j)),
+        a_j = P(R^T u_j),  u_j = kappa_j / (2 pi l),
+
+    P rounding the periodic components to multiples of 1/L_c.  From the
+    per-mode sums of mode_sums (taken with the frequencies a_j):
+
+        dA_j     = S_cos[j],   dpsi_j = -2 pi A_j S_sin[j],   da_j = -2 pi A_j S_sinx[j]
+        drho_j   = sigma dA_j,           dsigma = sum_j rho_j dA_j,
+        dsigma2  = dsigma / (2 sigma),   dmu = sum_i g_i,
+        e_j      = M da_j  (M zeroes the periodic components: dP = M almost everywhere)
+        du_j     = R e_j,                dkappa_jc = du_jc / (2 pi l_c),
+        dl_c     = -sum_j (u_jc / l_c) du_jc,
+        dR_cd    = sum_j u_jc e_jd       (R as a free matrix; R = I without a transform).
+    """
+    kappa = np.asarray(kappa, dtype=np.float64)
+    kappa = kappa.reshape(len(kappa), -1)
+    d = kappa.shape[1]
+    rho = np.asarray(rho, dtype=np.float64)
+    ell = np.asarray(ell, dtype=np.float64)[:d]
+    amp = sigma * rho
+    dA = np.asarray(s_cos, dtype=np.float64)
+    dpsi = -TWO_PI * amp * np.asarray(s_sin, dtype=np.float64)
+    da = -TWO_PI * amp[:, None] * np.asarray(s_sinx, dtype=np.float64).reshape(len(amp), d)
+    R = np.eye(d) if rot is None else np.asarray(rot, dtype=np.float64)[:d, :d]
+    mask = np.ones(d)
+    if period is not None:
+        for c in range(min(d, len(period))):
+            if float(period[c]) > 0.0:
+                mask[c] = 0.0
+    e = da * mask[None, :]
+    du = e @ R.T                       # row j: (R e_j)^T
+    u = kappa / (TWO_PI * ell[None, :])
+    dsigma = float(np.sum(rho * dA))
+    return {
+        "dA": dA,
+        "dpsi": dpsi,
+        "da": da,
+        "dmu": float(np.sum(np.asarray(g, dtype=np.float64))),
+        "dsigma": dsigma,
+        "dsigma2": dsigma / (2.0 * sigma),
+        "drho": sigma * dA,
+        "dkappa": du / (TWO_PI * ell[None, :]),
+        "dell": -np.sum(u * du, axis=0) / ell,
+        "drot": u.T @ e,
+    }

@@ -129,6 +129,32 @@ def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=
         kappa = z * np.sqrt(2.0 * nu_e / w)[:, None]
     rho = np.sqrt((W * W + Wp * Wp) / n_modes)
     sigma = math.sqrt(sigma2)
+    amp, a = reparam(kappa, rho, sigma, ell, rot=rot, period=period)
+    return {
+        "kappa": kappa,
+        "W": W,
+        "Wp": Wp,
+        "rho": rho,
+        "amp": amp,
+        "psi": -np.arctan2(Wp, W) / (2.0 * math.pi),
+        "a": a,
+        "sigma": sigma,
+        "ell": ell,
+    }
+
+
+def reparam(kappa, rho, sigma, ell, rot=None, period=None):
+    """Amplitudes and frequencies of the modes from their standardised draws
+    (Sec. 4.1: scaling to the variance and rescaling of frequency space).
+
+    A_j = sigma rho_j;  u_j = kappa_j / (2 pi l) per axis;  a_j = R^T u_j with
+    an axis transform R (a_j = u_j without one);  along a periodic axis c
+    (period[c] = L_c > 0) a_jc = floor(a_jc L_c + 1/2) / L_c.
+    kappa: (N, d); rho: (N,); ell: (d,) or longer.  Returns (amp, a)."""
+    kappa = np.asarray(kappa, dtype=np.float64)
+    kappa = kappa.reshape(len(kappa), -1)
+    dim = kappa.shape[1]
+    ell = np.asarray(ell, dtype=np.float64)[:dim]
     a = kappa / (2.0 * math.pi * ell[None, :])
     if rot is not None:
         R = np.asarray(rot, dtype=np.float64)[:dim, :dim]
@@ -138,14 +164,4 @@ def gen_modes(family, sigma2, ell, dim, n_modes, seed, nu=1.5, stream=0, period=
             L = float(period[c]) if c < len(period) else 0.0
             if L > 0.0:
                 a[:, c] = np.floor(a[:, c] * L + 0.5) / L
-    return {
-        "kappa": kappa,
-        "W": W,
-        "Wp": Wp,
-        "rho": rho,
-        "amp": sigma * rho,
-        "psi": -np.arctan2(Wp, W) / (2.0 * math.pi),
-        "a": a,
-        "sigma": sigma,
-        "ell": ell,
-    }
+    return sigma * np.asarray(rho, dtype=np.float64), a

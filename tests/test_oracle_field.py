@@ -335,3 +335,91 @@ def test_rotated_adjoint_against_finite_differences(kind):
         E[i, j] = 1.0
         num = fd(lambda s: loss(ell, R + s * E)[0])
         assert gr["drot"][i, j] == pytest.approx(num, rel=1e-5, abs=1e-9)
+
+
+@pytest.mark.parametrize("case", ["plain", "periodic2d", "rotated_periodic", "general_periodic"])
+def test_reparam_adjoint_against_finite_differences(case):
+    # Gradients with respect to the standardised draws and the covariance
+    # parameters of Sec. 4.1 (A = sigma rho, a = P(R^T kappa / (2 pi l))):
+    # Richardson central differences of the FP64 loss through modes.reparam.
+    # Along a periodic axis the rounding P is locally constant, so its
+    # frequency contributes nothing to dkappa, dl, dR (checked against the
+    # differences, which step through P itself).
+    from oracle import field as of
+    dim = 2 if case == "periodic2d" else 3
+    n1 = {2: 14, 3: 7}[dim]
+    c = (np.arange(n1) + 0.5) / n1
+    cells = np.stack([v.ravel() for v in np.meshgrid(*([c] * dim), indexing="ij")], axis=-1)
+    ell = np.array([0.3, 0.2, 0.25])[:dim]
+    th = 0.6
+    R = None
+    if case == "rotated_periodic":
+        R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    elif case == "general_periodic":
+        R = np.array([[1.1, 0.5, 0.0], [0.0, 0.8, 0.3], [0.2, 0.0, 1.3]])
+    period = None if case == "plain" else ([1.0, 0.0] if dim == 2 else [1.0, 0.0, 2.0])
+    m = modes.gen_modes(spectra.GAUSSIAN, 1.0, ell, dim, 20, seed=3)
+    kappa, rho, psi = m["kappa"], m["rho"], m["psi"]
+    mt = modes.gen_modes(spectra.GAUSSIAN, 1.0, ell, dim, 20, seed=4)
+    target = of.lognormal(of.synth(mt["a"], mt["amp"], mt["psi"], 0.0, cells))
+    p0 = {"mu": 0.1, "sigma2": 1.3, "ell": ell, "R": np.eye(dim) if R is None else R, "rho": rho, "psi": psi,
+          "kappa": kappa}
+
+    def frequencies(p):
+        return modes.reparam(p["kappa"], p["rho"], math.sqrt(p["sigma2"]), p["ell"], rot=p["R"], period=period)[1]
+
+    def loss(p):
+        amp, a = modes.reparam(p["kappa"], p["rho"], math.sqrt(p["sigma2"]), p["ell"], rot=p["R"], period=period)
+        return of.mismatch_loss(of.lognormal(of.synth(a, amp, p["psi"], p["mu"], cells)), target)
+
+    L0, g = loss(p0)
+    amp0, a0 = modes.reparam(kappa, rho, math.sqrt(1.3), ell, rot=p0["R"], period=period)
+    sums = of.mode_sums(a0, psi, cells, g)
+    gr = of.grads_reparam(*sums, kappa, rho, math.sqrt(1.3), ell, g, rot=p0["R"], period=period)
+    h = 1e-4
+
+    def moved(key, idx, step):
+        p = dict(p0)
+        v = np.array(p0[key], dtype=np.float64, copy=True)
+        if idx is None:
+            v = v + step
+        else:
+            v[idx] += step
+        p[key] = v if idx is not None else float(v)
+        return p
+
+    def fd(key, idx=None):
+        vals = {}
+        for s_ in (-2, -1, 1, 2):
+            p = moved(key, idx, s_ * h)
+            # the step must not cross a rounding boundary of a periodic axis
+            assert np.array_equal(frequencies(p)[:, [k for k in range(dim) if period is not None
+                                                     and period[k] > 0]],
+                                  a0[:, [k for k in range(dim) if period is not None and period[k] > 0]])
+            vals[s_] = loss(p)[0]
+        d1 = (vals[1] - vals[-1]) / (2 * h)
+        d2 = (vals[2] - vals[-2]) / (4 * h)
+        return (4.0 * d1 - d2) / 3.0
+
+    def close(x, y):
+        return abs(x - y) <= 1e-6 * max(abs(x), abs(y)) + 1e-11
+
+    assert close(gr["dmu"], fd("mu"))
+    assert close(gr["dsigma2"], fd("sigma2"))
+    for c_ in range(dim):
+        assert close(gr["dell"][c_], fd("ell", c_)), c_
+    for i in range(dim):
+        for k in range(dim):
+            assert close(gr["drot"][i, k], fd("R", (i, k))), (i, k)
+    for j in (0, 7, 19):
+        assert close(gr["drho"][j], fd("rho", j))
+        assert close(gr["dpsi"][j], fd("psi", j))
+        for c_ in range(dim):
+            assert close(gr["dkappa"][j, c_], fd("kappa", (j, c_))), (j, c_)
+    # the same sums give the plain frequency gradients of grads_from_sums
+    plain = of.grads_from_sums(*sums, amp0, a0, math.sqrt(1.3), ell, g, rot=p0["R"])
+    for k in ("dA", "dpsi", "da", "dmu", "dsigma"):
+        assert np.allclose(gr[k], plain[k], rtol=1e-13, atol=0)
+    if period is not None and R is None:
+        # no transform: a periodic axis's frequency moves with neither kappa nor l
+        assert gr["dell"][0] == 0.0 and np.all(gr["dkappa"][:, 0] == 0.0)
