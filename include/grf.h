@@ -145,6 +145,25 @@ typedef struct grf_modes {
  */
 int grf_gen_modes(const grf_params *p, grf_modes *out);
 
+/*
+ * grf_reparam_modes -- amplitudes and frequencies of given standardised modes.
+ * Sec. 4.1: the field is scaled to its variance (A_j = sigma rho_j) and the
+ * frequency space is rescaled per axis for anisotropy (u_jc = kappa_jc /
+ * (2 pi l_c)), extended to an axis transform R (a_j = R^T u_j, p->rot) and
+ * to the Appendix B `periodic` option (a_jc = floor(a_jc L_c + 1/2) / L_c on
+ * every axis with p->period[c] = L_c > 0, after the transform).  This is the
+ * second half of grf_gen_modes, for callers that hold kappa_j and rho_j as
+ * parameters of their own (calibration, inversion) instead of drawing them.
+ *
+ * Arguments: p (host, read: sigma2, ell, rot, period, n_modes, dim); m
+ * (host): m->kappa [n*dim] and m->rho [n] are read, m->amp [n] and m->a
+ * [n*dim] written, m->psi is not touched.  Returns GRF_EINVAL for bad
+ * parameters, mismatched m->n / m->dim, a NULL array or a non-finite kappa
+ * or rho; GRF_OK otherwise.  Same arithmetic as grf_gen_modes, so modes drawn
+ * there reparameterise to bit-identical amp and a.
+ */
+int grf_reparam_modes(const grf_params *p, grf_modes *m);
+
 /* ------------------------------------------------------------------ */
 /* Device mode table                                                    */
 /* ------------------------------------------------------------------ */
@@ -163,6 +182,8 @@ size_t grf_table_bytes(int64_t n_modes);
 
 /* Build the table image of modes m (A = m->amp, a = m->a, psi = m->psi)
  * into host memory `host_table` of `bytes` >= grf_table_bytes(m->n).
+ * m->kappa may be NULL; when given it is stored too, for the adjoint's
+ * chain rule to l, R and kappa (grf_synth_backward).  m->rho is not read.
  * GRF_EWORKSPACE if too small, GRF_EINVAL for NULL arrays or bad sizes. */
 int grf_pack_table(const grf_modes *m, void *host_table, size_t bytes);
 
@@ -307,17 +328,26 @@ int grf_map_bitruncated(const grf_bimap *map, int64_t n, const float *Y1, const 
 /* ------------------------------------------------------------------ */
 /* S5: adjoint                                                          */
 /* ------------------------------------------------------------------ */
-/* Device FP64 gradient outputs (original mode order j of grf_gen_modes). */
+/* Device FP64 gradient outputs (original mode order j of grf_gen_modes).
+ * With u_j = kappa_j / (2 pi l) the frequencies before the axis transform and
+ * e_j = M dL/da_j, where M zeroes the components of periodic axes (their
+ * rounded frequency is locally constant in kappa, l and R, so dL/da of a
+ * periodic axis reaches none of them; without periodic axes e_j = dL/da_j): */
 typedef struct grf_grads {
     double *dA;     /* [N]      dL/dA_j   = sum_i g_i cos theta_ij */
     double *dpsi;   /* [N]      dL/dpsi_j = -2 pi A_j sum_i g_i sin theta_ij */
     double *da;     /* [N*dim]  dL/da_jc  = -2 pi A_j sum_i g_i sin theta_ij x_ic */
     double *dmu;    /* [1]      sum_i g_i */
-    double *dsigma; /* [1]      sum_j (A_j / sigma) dL/dA_j */
-    double *dell;   /* [dim]    -sum_j (u_jc / l_c) (R dL/da_j)_c, u_j = R a_j (R = I
-                       without rotation) */
-    double *drot;   /* [dim*dim] or NULL: dL/dR_cd = sum_j u_jc dL/da_jd, R as a free
-                       row-major matrix (only meaningful with a rotation) */
+    double *dsigma; /* [1]      sum_j (A_j / sigma) dL/dA_j = sum_j rho_j dL/dA_j */
+    double *dell;   /* [dim]    -sum_j (u_jc / l_c) (R e_j)_c (R = I without a transform) */
+    double *drot;   /* [dim*dim] or NULL: dL/dR_cd = sum_j u_jc e_jd, R as a free
+                       row-major matrix (only meaningful with a transform) */
+    double *dsigma2;/* [1] or NULL: dL/d(sigma^2) = dsigma / (2 sigma) */
+    double *drho;   /* [N] or NULL:     dL/drho_j = sigma dL/dA_j */
+    double *dkappa; /* [N*dim] or NULL: dL/dkappa_jc = (R e_j)_c / (2 pi l_c) */
+    const double *gscale; /* [1] device, or NULL for 1: every output above is
+                       multiplied by *gscale (the gradient of gscale * L; an
+                       upstream factor read on the device, e.g. by autograd) */
 } grf_grads;
 
 /* Workspace for grf_synth_backward on n_cells cells and n_modes modes. */
@@ -328,14 +358,46 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
  * amplitudes, phases and frequencies, the mean, sigma and the correlation
  * lengths, given gY = dL/dY (device float32, original cell order, cells of
  * segment `segment` of `plan`).  Derivative of Eq. (DiscreteFT) with the
- * reparameterisation A = sigma rho, a = kappa / (2 pi l) of Sec. 4.1.
+ * reparameterisation of Sec. 4.1 (grf_reparam_modes): A = sigma rho,
+ * a = R^T kappa / (2 pi l), periodic axes rounded.  p gives sigma, l, R and
+ * the periodic axes of the chain rule.  u_j is read from the kappa the table
+ * was packed with; a table packed without kappa uses u_j = R^-T a_j instead,
+ * which is the same unless an axis is periodic.
  * The sines and cosines are recomputed, never stored.  Per-block FP64
  * partials go to `workspace` and are reduced in a fixed order, so results
- * are deterministic.  All outputs in `g` are written (device).
+ * are deterministic.  All non-optional outputs in `g` are written (device).
  */
 int grf_synth_backward(const void *table, const grf_params *p, const void *plan, int32_t segment,
                        const float *gY, const grf_grads *g, void *workspace, size_t ws_bytes,
                        void *stream);
+
+/*
+ * grf_synth_mismatch -- the forward half of a calibration step in one pass:
+ * the field Y (Eq. DiscreteFT, as grf_synth_field) at every cell of segment
+ * `segment` of `plan`, K = exp(Y), the field-mismatch loss
+ *     L = sum_i (K_i - T_i)^2 / n_mean
+ * against the target T = K_target, and its gradient gY_i = dL/dY_i =
+ * 2 (K_i - T_i) K_i / n_mean, formed in the synthesis kernel's epilogue
+ * (no K round trip through memory).  gY then feeds grf_synth_backward.
+ * n_mean: the number of cells of the mean; 0 means the segment's own count.
+ * A field sharded over processes passes the total over all shards, so that
+ * the shards' losses and gradients add up to those of the whole field.
+ *
+ * K_target, gY: device float32 in the caller's original cell order; loss:
+ * device double[1], reduced in a fixed order (deterministic).  Y_out, K_out:
+ * optional device float32 outputs of the field and of K (NULL: not written).
+ * workspace: device scratch of grf_synth_mismatch_workspace_bytes(n) bytes,
+ * 256-byte aligned (the loss partial sums first; a smaller buffer that still
+ * holds them disables the mode split).  Same arithmetic as grf_synth_field
+ * followed by grf_mismatch_grad with n = n_mean: gY is identical, the loss
+ * equal up to the order of the FP64 sum.  GRF_EINVAL for n_mean < the
+ * segment's cell count or NULL buffers, GRF_EWORKSPACE for a workspace too
+ * small for the loss partials.
+ */
+int grf_synth_mismatch(const void *table, const grf_params *p, const void *plan, int32_t segment,
+                       const float *K_target, int64_t n_mean, float *gY, double *loss, float *Y_out,
+                       float *K_out, void *workspace, size_t ws_bytes, void *stream);
+size_t grf_synth_mismatch_workspace_bytes(int64_t n_cells);
 
 /* Workspace for grf_mismatch_grad on n cells. */
 size_t grf_mismatch_workspace_bytes(int64_t n);
@@ -352,22 +414,29 @@ int grf_mismatch_grad(int64_t n, const float *K, const float *K_target, float *g
 /*
  * grf_mismatch_grad_noalloc -- the same loss and gradient as
  * grf_mismatch_grad, for callers that cannot allocate device memory at the
- * call site (for example code running inside a host callback, a plugin that
- * must not touch the caller's allocator, or a process whose memory budget is
- * fixed once at start-up).  No counterpart in the paper: it only changes
- * where the per-block partial sums live.
+ * call site: a plug-in that must not touch its host application's
+ * allocator, or a process whose device-memory budget is fixed once at
+ * start-up.  No counterpart in the paper: it only changes where the
+ * per-block partial sums live.
+ *
+ * The call itself makes CUDA runtime calls (it looks up the scratch array's
+ * address) and enqueues two kernels on `stream`; like any CUDA call it must
+ * not be made from inside a host callback (cudaLaunchHostFunc or a stream
+ * callback), where CUDA calls are not allowed.
  *
  * The partial sums go to a fixed array inside the library,
  * GRF_NOALLOC_MAX_BLOCKS doubles (512 KiB) in device memory, which every GPU
  * that loads the library keeps until the process exits.  n may therefore be
  * at most GRF_NOALLOC_MAX_CELLS (134,217,728); larger n returns GRF_EINVAL
- * before any device work.  The first call on a device looks up the array's
- * device address on that device (cudaGetSymbolAddress); make that first call
- * outside any CUDA-graph stream capture.  All calls share the one array, so
- * calls that can overlap on the GPU (different streams, no ordering between
- * them) race and may return wrong losses: order them on one stream.  Nothing
- * in the array needs to start at zero; every call writes all the entries it
- * reads.  Arguments and results are those of grf_mismatch_grad.
+ * before any device work.  Every call looks up the array's device address in
+ * the current device's context (cudaGetSymbolAddress), so a context reset
+ * between calls is harmless; a device's first call also loads the library's
+ * device code there: make that first call outside any CUDA-graph stream
+ * capture.  All calls share the one array, so calls that can overlap on the
+ * GPU (different streams, no ordering between them) race and may return
+ * wrong losses: order them on one stream.  Nothing in the array needs to
+ * start at zero; every call writes all the entries it reads.  Arguments and
+ * results are those of grf_mismatch_grad.
  */
 #define GRF_NOALLOC_MAX_BLOCKS 65536
 #define GRF_NOALLOC_MAX_CELLS (134217728LL)

@@ -66,7 +66,8 @@ class grf_outputs(ctypes.Structure):
 class grf_grads(ctypes.Structure):
     _fields_ = [("dA", ctypes.c_void_p), ("dpsi", ctypes.c_void_p), ("da", ctypes.c_void_p),
                 ("dmu", ctypes.c_void_p), ("dsigma", ctypes.c_void_p), ("dell", ctypes.c_void_p),
-                ("drot", ctypes.c_void_p)]
+                ("drot", ctypes.c_void_p), ("dsigma2", ctypes.c_void_p), ("drho", ctypes.c_void_p),
+                ("dkappa", ctypes.c_void_p), ("gscale", ctypes.c_void_p)]
 
 
 class grf_bimap(ctypes.Structure):
@@ -87,6 +88,7 @@ _SIGS = {
     "grf_last_error": (ctypes.c_char_p, []),
     "grf_version": (ctypes.c_char_p, []),
     "grf_gen_modes": (ctypes.c_int, [ctypes.POINTER(grf_params), ctypes.POINTER(grf_modes)]),
+    "grf_reparam_modes": (ctypes.c_int, [ctypes.POINTER(grf_params), ctypes.POINTER(grf_modes)]),
     "grf_table_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "grf_pack_table": (ctypes.c_int, [ctypes.POINTER(grf_modes), ctypes.c_void_p, ctypes.c_size_t]),
     "grf_upload_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -109,6 +111,11 @@ _SIGS = {
     "grf_synth_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grf_params), ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(grf_grads),
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "grf_synth_mismatch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grf_params), ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p]),
+    "grf_synth_mismatch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "grf_mismatch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "grf_mismatch_grad": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),

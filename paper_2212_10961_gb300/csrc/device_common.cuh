@@ -199,6 +199,16 @@ static inline unsigned long long take_tu_index_faults() {
 #endif
 }
 
+// Mismatch epilogue of one cell (kMapMismatch): K = exp(Y), gY = 2 (K - T) K
+// / n_mean with the same FP32 operations as the standalone loss kernel, and
+// the squared difference returned for the loss sum (FP64).
+__device__ __forceinline__ double mismatch_store(const MapDev& m, int64_t o, float y) {
+    const float k = expf(y);
+    const float d = k - __ldg(m.T + o);
+    m.G[o] = m.g_scale * d * k;
+    return static_cast<double>(d) * static_cast<double>(d);
+}
+
 // Map epilogue of one cell (Sec. 3.1 truncation rule, Sec. 4.1 lognormal).
 __device__ __forceinline__ void map_store(const MapDev& m, int64_t o, float y) {
     const int bits = m.bits;

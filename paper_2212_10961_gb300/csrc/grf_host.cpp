@@ -169,6 +169,27 @@ bool has_rotation(const grf_params* p) {
     return false;
 }
 
+// Sec. 4.1 reparameterisation of one mode from its standardised draws:
+// A = sigma rho, u = kappa / (2 pi l) per axis, a = R^T u with an axis
+// transform, then every periodic axis rounded to a multiple of 1/L_c.
+void reparam_one(const grf_params* p, bool rotated, double sigma, const double* kappa, double rho,
+                 double* amp, double* a_out) {
+    const int d = p->dim;
+    *amp = sigma * rho;
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < d; ++c) u[c] = kappa[c] / (2.0 * M_PI * p->ell[c]);
+    for (int c = 0; c < d; ++c) {
+        double a = u[c];
+        if (rotated) {  // a = R^T u
+            a = 0.0;
+            for (int k = 0; k < d; ++k) a += p->rot[k * 3 + c] * u[k];
+        }
+        const double L = p->period[c];
+        if (L > 0.0) a = std::floor(a * L + 0.5) / L;  // periodic axis: multiple of 1/L
+        a_out[c] = a;
+    }
+}
+
 int check_params(const grf_params* p) {
     if (!p) return fail(GRF_EINVAL, "params is NULL");
     if (p->family < GRF_GAUSSIAN || p->family > GRF_MATERN)
@@ -372,24 +393,9 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) try {
             }
             const double rho = std::sqrt((W * W + Wp * Wp) / static_cast<double>(N));
             out->rho[j] = rho;
-            out->amp[j] = sigma * rho;
             out->psi[j] = -std::atan2(Wp, W) / (2.0 * M_PI);
-            double u[3] = {0.0, 0.0, 0.0};
-            for (int c = 0; c < d; ++c) {
-                const double kap = z[c] * scale;
-                out->kappa[j * d + c] = kap;
-                u[c] = kap / (2.0 * M_PI * p->ell[c]);
-            }
-            for (int c = 0; c < d; ++c) {
-                double a = u[c];
-                if (rotated) {  // a = R^T u
-                    a = 0.0;
-                    for (int k = 0; k < d; ++k) a += p->rot[k * 3 + c] * u[k];
-                }
-                const double L = p->period[c];
-                if (L > 0.0) a = std::floor(a * L + 0.5) / L;  // periodic axis: multiple of 1/L
-                out->a[j * d + c] = a;
-            }
+            for (int c = 0; c < d; ++c) out->kappa[j * d + c] = z[c] * scale;
+            reparam_one(p, rotated, sigma, out->kappa + j * d, rho, out->amp + j, out->a + j * d);
         }
     };
     constexpr int64_t kModesPerThread = 1024;
@@ -418,6 +424,31 @@ int grf_gen_modes(const grf_params* p, grf_modes* out) try {
     return host_exception();
 }
 
+int grf_reparam_modes(const grf_params* p, grf_modes* m) try {
+    TraceRange trace_("grf_reparam_modes");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!m) return fail(GRF_EINVAL, "modes is NULL");
+    if (m->n != p->n_modes || m->dim != p->dim)
+        return fail(GRF_EINVAL, "modes arrays sized for n=%lld dim=%d, params say n=%lld dim=%d",
+                    (long long)m->n, m->dim, (long long)p->n_modes, p->dim);
+    if (!m->kappa || !m->rho || !m->a || !m->amp) return fail(GRF_EINVAL, "kappa, rho, a or amp is NULL");
+    const int64_t N = m->n;
+    const int d = m->dim;
+    for (int64_t j = 0; j < N; ++j) {
+        if (!std::isfinite(m->rho[j])) return fail(GRF_EINVAL, "rho[%lld] is not finite", (long long)j);
+        for (int c = 0; c < d; ++c)
+            if (!std::isfinite(m->kappa[j * d + c]))
+                return fail(GRF_EINVAL, "kappa of mode %lld is not finite", (long long)j);
+    }
+    const double sigma = std::sqrt(p->sigma2);
+    const bool rotated = has_rotation(p);
+    for (int64_t j = 0; j < N; ++j) reparam_one(p, rotated, sigma, m->kappa + j * d, m->rho[j], m->amp + j, m->a + j * d);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
 // ---------------------------------------------------------------------------
 // Device table
 // ---------------------------------------------------------------------------
@@ -440,10 +471,13 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
     for (int64_t j = 0; j < N; ++j) {
         if (!std::isfinite(m->amp[j]) || !std::isfinite(m->psi[j]))
             return fail(GRF_EINVAL, "mode %lld has a non-finite amplitude or phase", (long long)j);
-        for (int c = 0; c < d; ++c)
+        for (int c = 0; c < d; ++c) {
             if (!std::isfinite(m->a[j * d + c]) || std::fabs(m->a[j * d + c]) > kMaxFrequency)
                 return fail(GRF_EINVAL, "mode %lld has a frequency that is not finite or exceeds 2^30 turns per unit",
                             (long long)j);
+            if (m->kappa && !std::isfinite(m->kappa[j * d + c]))
+                return fail(GRF_EINVAL, "mode %lld has a non-finite kappa", (long long)j);
+        }
     }
     unsigned char* base = static_cast<unsigned char*>(host_table);
     alloc_point();
@@ -490,6 +524,8 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
     hd.off_cold = L.off_cold;
     hd.off_order = L.off_order;
     hd.off_kpref = L.off_kpref;
+    hd.off_kappa = L.off_kappa;
+    hd.has_kappa = m->kappa != nullptr ? 1 : 0;
     hd.total_bytes = L.total;
     std::memcpy(base, &hd, sizeof(hd));
 
@@ -497,11 +533,14 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
     float* cold = reinterpret_cast<float*>(base + L.off_cold);
     int32_t* order = reinterpret_cast<int32_t*>(base + L.off_order);
     int32_t* kpref = reinterpret_cast<int32_t*>(base + L.off_kpref);
+    double* kap = reinterpret_cast<double*>(base + L.off_kappa);
     for (int64_t s = 0; s < L.n_pad; ++s) {
         order[s] = -1;
         if (s >= N) continue;
         const int64_t j = ord[s];
         order[s] = static_cast<int32_t>(j);
+        if (m->kappa)
+            for (int c = 0; c < d; ++c) kap[s * 3 + c] = m->kappa[j * d + c];
         double a[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < d; ++c) a[c] = m->a[j * d + c];
         for (int c = 0; c < 3; ++c) hot[s * 4 + c] = static_cast<float>(2.0 * M_PI * a[c]);
@@ -674,6 +713,59 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     return host_exception();
 }
 
+size_t grf_synth_mismatch_workspace_bytes(int64_t n_cells) {
+    if (n_cells < 0) return 0;
+    return static_cast<size_t>(align256(mismatch_partials(n_cells) * 8)) + synth_workspace_bytes(n_cells);
+}
+
+int grf_synth_mismatch(const void* table, const grf_params* p, const void* plan, int32_t segment,
+                       const float* K_target, int64_t n_mean, float* gY, double* loss, float* Y_out,
+                       float* K_out, void* workspace, size_t ws_bytes, void* stream) try {
+    TraceRange trace_("grf_synth_mismatch");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!table) return fail(GRF_EINVAL, "table is NULL");
+    PlanMeta meta;
+    if (!plan || !lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    const int32_t n_seg = static_cast<int32_t>(meta.offsets.size()) - 1;
+    if (segment < 0 || segment >= n_seg) return fail(GRF_EINVAL, "segment %d out of range", segment);
+    const int64_t n = meta.offsets[segment + 1] - meta.offsets[segment];
+    if (n_mean == 0) n_mean = n;
+    if (n_mean < n) return fail(GRF_EINVAL, "n_mean (%lld) is smaller than the segment's %lld cells",
+                                (long long)n_mean, (long long)n);
+    if (n > 0 && (!K_target || !gY)) return fail(GRF_EINVAL, "K_target or gY is NULL");
+    if (!loss) return fail(GRF_EINVAL, "loss is NULL");
+    if (!workspace) return fail(GRF_EINVAL, "workspace is NULL");
+    if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
+    const size_t lbytes = static_cast<size_t>(align256(mismatch_partials(n) * 8));
+    if (ws_bytes < lbytes)
+        return fail(GRF_EWORKSPACE, "mismatch workspace %zu < %zu bytes", ws_bytes, lbytes);
+    grf_map m{};
+    m.bits = (Y_out ? GRF_MAP_Y : 0) | (K_out ? GRF_MAP_LOGNORMAL : 0);
+    m.k_ref = 1.0f;
+    grf_outputs o{};
+    o.Y = Y_out;
+    o.K = K_out;
+    MapDev md = make_map(&m, &o, p->mean, std::sqrt(p->sigma2));
+    md.bits |= kMapMismatch;
+    md.T = K_target;
+    md.G = gY;
+    md.lpart = static_cast<double*>(workspace);
+    md.loss = loss;
+    md.inv_n_mean = n_mean > 0 ? 1.0 / static_cast<double>(n_mean) : 0.0;
+    md.g_scale = n_mean > 0 ? 2.0f / static_cast<float>(n_mean) : 0.0f;
+    FwdDesc d{};
+    rc = fwd_desc(table, p->n_modes, p->dim, plan, meta, segment, md, d);
+    if (rc) return rc;
+    int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
+    unsigned char* split_ws = static_cast<unsigned char*>(workspace) + lbytes;
+    const int err = launch_synth_fwd(d, split_ws, ws_bytes - lbytes, status, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
 int grf_map_property(const grf_map* map, double mean, double sigma, int64_t n, const float* Y,
                      const grf_outputs* out, void* stream) try {
     TraceRange trace_("grf_map_property");
@@ -744,8 +836,11 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
     double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     if (has_rotation(p))
         for (int k = 0; k < 9; ++k) rot[k] = p->rot[k];
+    int32_t periodic = 0;
+    for (int c = 0; c < p->dim; ++c)
+        if (p->period[c] > 0.0) periodic |= 1 << c;
     const int err = launch_synth_bwd(
-        table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell, rot,
+        table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell, rot, periodic,
         reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin,
         reinterpret_cast<const float*>(pb + meta.layout.off_ys) + begin,
         reinterpret_cast<const float*>(pb + meta.layout.off_zs) + begin,

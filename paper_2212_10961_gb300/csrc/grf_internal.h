@@ -27,6 +27,11 @@ namespace grf {
 //   kpref: int32[kBuckets] kpref[b] = #{j : h_j * 2^((b - bias)/4) > 1}, the
 //          length of the prefix of modes whose phase span over a box of
 //          half-extent E exceeds tau turns is read at bucket(E / tau)
+//   kappa: double[3*n_pad] standardised wave-vector of the mode in the slot
+//          (zeros beyond dim and for padding); filled when the modes were
+//          packed with their kappa (header has_kappa = 1).  Only the adjoint
+//          reads it: the chain rule to l and R needs u = kappa / (2 pi l),
+//          which a periodic axis's rounded frequency no longer determines.
 // Every mode at an odd sorted position is stored in the equivalent form
 // (-A, psi + 1/2): A cos(2 pi (a.x + psi)) = -A cos(2 pi (a.x + psi + 1/2)).
 // Half of the terms then evaluate the hardware cosine half a turn away with
@@ -59,13 +64,14 @@ struct TableHeader {
     float tau;
     int32_t n_buckets;
     int32_t bucket_bias;
-    int32_t reserved0;
+    int32_t has_kappa;  // 1: the kappa section holds the modes' kappa
     int64_t off_hot;
     int64_t off_cold;
     int64_t off_order;
     int64_t off_kpref;
     int64_t total_bytes;
-    int64_t reserved[7];
+    int64_t off_kappa;
+    int64_t reserved[6];
 };
 static_assert(sizeof(TableHeader) <= 256, "table header must fit in 256 bytes");
 
@@ -73,7 +79,7 @@ inline int64_t align256(int64_t v) { return (v + 255) & ~int64_t(255); }
 inline int64_t pad_modes(int64_t n) { return (n + kChunk - 1) / kChunk * kChunk; }
 
 struct TableLayout {
-    int64_t n_pad, off_hot, off_cold, off_order, off_kpref, total;
+    int64_t n_pad, off_hot, off_cold, off_order, off_kpref, off_kappa, total;
 };
 
 inline TableLayout table_layout(int64_t n_modes) {
@@ -83,7 +89,8 @@ inline TableLayout table_layout(int64_t n_modes) {
     L.off_cold = L.off_hot + align256(L.n_pad * 16);
     L.off_order = L.off_cold + align256(L.n_pad * 32);
     L.off_kpref = L.off_order + align256(L.n_pad * 4);
-    L.total = L.off_kpref + align256(kBuckets * 4);
+    L.off_kappa = L.off_kpref + align256(kBuckets * 4);
+    L.total = L.off_kappa + align256(L.n_pad * 24);
     return L;
 }
 
@@ -148,6 +155,11 @@ inline PlanLayout plan_layout(int64_t n_cells, int32_t n_segments) {
 // ---------------------------------------------------------------------------
 // Map parameters as the kernels see them.
 // ---------------------------------------------------------------------------
+// Internal map bit, outside the public grf_map_bits: the field-mismatch loss
+// of the calibration step and its gradient (grf_synth_mismatch), fused into
+// the synthesis epilogue.
+constexpr int32_t kMapMismatch = 1 << 16;
+
 struct MapDev {
     int32_t bits;
     int32_t n_thr;
@@ -159,6 +171,16 @@ struct MapDev {
     float* K;
     uint8_t* F;
     float* P;
+    // kMapMismatch: K = exp(Y), gY = g_scale (K - T) K, and per-unit sums of
+    // (K - T)^2 in lpart (one entry per warp tile, or per block of the
+    // split finalize), reduced afterwards into *loss / n_mean
+    const float* T;
+    float* G;
+    double* lpart;
+    double* loss;
+    double inv_n_mean;
+    float g_scale;        // 2 / n_mean (FP32, as the standalone loss kernel forms it)
+    int32_t pad_;
 };
 
 // One realisation as the forward kernel sees it.
@@ -203,6 +225,8 @@ constexpr uint32_t kBatchMagic = 0x48435442u;  // "BTCH"
 // Return cudaError_t as int.
 // ---------------------------------------------------------------------------
 int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream);
+// Entries of MapDev::lpart a launch of n cells may write (kMapMismatch).
+int64_t mismatch_partials(int64_t n_cells);
 
 // Checked builds (-DGRF_CHECKED=1): device accesses skipped since the last
 // call because an index read from device memory was out of range, per
@@ -220,9 +244,11 @@ int launch_bimap(const grf_bimap& m, int64_t n, const float* Y1, const float* Y2
                  void* stream);
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
                 const float* y, const float* z, void* plan, const PlanLayout& L, void* stream);
+// periodic_mask: bit c set when axis c is periodic (its frequency is rounded,
+// so its dL/da reaches neither kappa, l nor R).
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
-                     const double* ell, const double* rot, const float* xs, const float* ys,
-                     const float* zs,
+                     const double* ell, const double* rot, int32_t periodic_mask, const float* xs,
+                     const float* ys, const float* zs,
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream);
 size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);

@@ -1,12 +1,15 @@
 // Adjoint of the spectral field sum (derivative of Eq. DiscreteFT, Sec. 4.1,
-// with the reparameterisation A = sigma rho, a = kappa / (2 pi l)).
+// with the reparameterisation A = sigma rho, a = R^T kappa / (2 pi l) and
+// periodic axes rounded to multiples of 1/L).
 //
 // Given g_i = dL/dY_i, per mode j (theta_ij = 2 pi (a_j . x_i + psi_j)):
 //     S_cos[j] = sum_i g_i cos theta_ij,  S_sin[j] = sum_i g_i sin theta_ij,
 //     S_x[j,c] = sum_i g_i sin theta_ij x_ic
 // and then dA = S_cos, dpsi = -2 pi A S_sin, da = -2 pi A S_x,
-// dsigma = sum_j (A_j / sigma) dA_j, dl_c = -sum_j (a_jc / l_c) da_jc,
-// dmu = sum_i g_i.
+// drho = sigma dA, dsigma = sum_j (A_j / sigma) dA_j, with e = da with the
+// periodic components zeroed and u = kappa / (2 pi l): dkappa_c =
+// (R e)_c / (2 pi l_c), dl_c = -sum_j (u_jc / l_c) (R e_j)_c,
+// dR_cd = sum_j u_jc e_jd, dmu = sum_i g_i.
 //
 // Kernel 1 (mode-stationary): a block owns kBwdThreads * MPT consecutive
 // modes (MPT per thread, registers) and a contiguous range of spatially
@@ -48,6 +51,9 @@ struct BwdArgs {
     double ell[3];
     double rot[9];    // row-major transform R of the anisotropy axes (identity: none)
     double rot_it[9]; // R^-T, which maps a back to u = kappa / (2 pi l) (R itself for a rotation)
+    int32_t periodic; // bit c: axis c is periodic (its dL/da reaches neither kappa, l nor R)
+    const double* kap;      // table's kappa section [n_pad][3] (sorted slots)
+    const int32_t* has_kap; // table header flag: 1 when kap holds the modes' kappa
     const float* xs;
     const float* ys;
     const float* zs;
@@ -301,38 +307,49 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
     const double a[3] = {static_cast<double>(q0.x) + static_cast<double>(q0.y),
                          static_cast<double>(q0.z) + static_cast<double>(q0.w),
                          static_cast<double>(q1.x) + static_cast<double>(q1.y)};
+    const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
     // the table holds the mode as (-A, psi + 1/2) at odd positions, where the
     // cosine sum v[0] has the opposite sign; A * v[1] and A * v[2..] do not
-    args.g.dA[j] = mode_flipped(m) ? -v[0] : v[0];
-    args.g.dpsi[j] = -kTwoPi * A * v[1];
+    const double dA = mode_flipped(m) ? -v[0] : v[0];
+    args.g.dA[j] = gs * dA;
+    args.g.dpsi[j] = gs * (-kTwoPi * A * v[1]);
+    if (args.g.drho != nullptr) args.g.drho[j] = gs * (args.sigma * dA);
     ct[0] = (A / args.sigma) * v[0];
     const int d = args.dim;
     double da[3] = {0.0, 0.0, 0.0};
+    double e[3] = {0.0, 0.0, 0.0};  // da with the periodic components zeroed
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (c >= d) break;
         da[c] = -kTwoPi * A * v[2 + c];
-        args.g.da[static_cast<int64_t>(j) * d + c] = da[c];
+        e[c] = (args.periodic >> c) & 1 ? 0.0 : da[c];
+        args.g.da[static_cast<int64_t>(j) * d + c] = gs * da[c];
     }
-    // u = R^-T a (the frequencies before the transform, a = R^T u), dL/du = R dL/da
+    // u = kappa / (2 pi l) from the table when it holds kappa, else R^-T a
+    // (the frequencies before the transform, a = R^T u); dL/du = R e
+    const bool from_kappa = *args.has_kap != 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         double u = 0.0, du = 0.0;
+        if (from_kappa) u = c < d ? args.kap[static_cast<int64_t>(m) * 3 + c] / (kTwoPi * args.ell[c]) : 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if (k >= d) break;
-            u += args.rot_it[c * 3 + k] * a[k];
-            du += args.rot[c * 3 + k] * da[k];
+            if (!from_kappa) u += args.rot_it[c * 3 + k] * a[k];
+            du += args.rot[c * 3 + k] * e[k];
         }
+        if (c < d && args.g.dkappa != nullptr)
+            args.g.dkappa[static_cast<int64_t>(j) * d + c] = gs * (du / (kTwoPi * args.ell[c]));
         ct[1 + c] = c < d ? -(u / args.ell[c]) * du : 0.0;
 #pragma unroll
-        for (int e = 0; e < 3; ++e) ct[4 + c * 3 + e] = (c < d && e < d) ? u * da[e] : 0.0;
+        for (int q = 0; q < 3; ++q) ct[4 + c * 3 + q] = (c < d && q < d) ? u * e[q] : 0.0;
     }
 }
 
 // Kernel 3: scalar gradients, one block, fixed-order reductions.
 __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
     __shared__ double red[256];
+    const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
     for (int q = 0; q < kContrib; ++q) {
         double acc = 0.0;
         for (int m = threadIdx.x; m < args.n_pad; m += 256)
@@ -345,12 +362,13 @@ __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
         }
         if (threadIdx.x == 0) {
             if (q == 0) {
-                args.g.dsigma[0] = red[0];
+                args.g.dsigma[0] = gs * red[0];
+                if (args.g.dsigma2 != nullptr) args.g.dsigma2[0] = gs * (red[0] / (2.0 * args.sigma));
             } else if (q < 4) {
-                if (q - 1 < args.dim) args.g.dell[q - 1] = red[0];
+                if (q - 1 < args.dim) args.g.dell[q - 1] = gs * red[0];
             } else if (args.g.drot != nullptr) {
                 const int c = (q - 4) / 3, e = (q - 4) % 3;
-                if (c < args.dim && e < args.dim) args.g.drot[c * args.dim + e] = red[0];
+                if (c < args.dim && e < args.dim) args.g.drot[c * args.dim + e] = gs * red[0];
             }
         }
         __syncthreads();
@@ -358,7 +376,7 @@ __global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int k = 0; k < args.splits; ++k) s += args.gpart[k];
-        args.g.dmu[0] = s;
+        args.g.dmu[0] = gs * s;
     }
 }
 
@@ -416,8 +434,8 @@ size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
 }
 
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
-                     const double* ell, const double* rot, const float* xs, const float* ys,
-                     const float* zs,
+                     const double* ell, const double* rot, int32_t periodic_mask, const float* xs,
+                     const float* ys, const float* zs,
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -429,6 +447,9 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
     a.order = reinterpret_cast<const int32_t*>(tb + TL.off_order);
     a.kpref = reinterpret_cast<const int32_t*>(tb + TL.off_kpref);
+    a.kap = reinterpret_cast<const double*>(tb + TL.off_kappa);
+    a.has_kap = &reinterpret_cast<const TableHeader*>(tb)->has_kappa;
+    a.periodic = periodic_mask;
     a.n_modes = static_cast<int32_t>(n_modes);
     a.n_pad = static_cast<int32_t>(TL.n_pad);
     a.dim = dim;

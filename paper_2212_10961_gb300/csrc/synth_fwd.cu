@@ -97,7 +97,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // instead of the MUFU pipe in the light loop.  It pays only where the MUFU
 // pipe, not instruction issue, limits the kernel (the persistent batched
 // kernel); the single-realisation kernel uses 0.
-template <int DIM, int C, int POLY>
+// MM: the epilogue also forms the mismatch gradient of every cell and writes
+// the warp's sum of (K - T)^2 to d.map.lpart[wbase / (32 C)] (kMapMismatch).
+template <int DIM, int C, int POLY, bool MM = false>
 __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase, int cb, int ce,
                                                 float2* partial, WarpSmem& ws, uint32_t (&uses)[kStages],
                                                 int32_t* status) {
@@ -324,6 +326,7 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
     }
 
     // ---- epilogue: field value and fused maps ------------------------------------
+    double lsum = 0.0;  // MM: this lane's sum of (K - T)^2
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         two_sum_acc(s[c], e[c], p[c]);
@@ -334,8 +337,19 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
             } else {
                 const float y = (s[c] + e[c]) + d.map.mu;
                 const int64_t o = static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base;
-                if (index_ok(o, d.n_cells)) map_store(d.map, o, y);
+                if (index_ok(o, d.n_cells)) {
+                    map_store(d.map, o, y);
+                    if constexpr (MM) lsum += mismatch_store(d.map, o, y);
+                }
             }
+        }
+    }
+    if constexpr (MM) {
+        if (partial == nullptr) {
+            // fixed butterfly order: the warp's sum does not depend on timing
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+            if (lane == 0) d.map.lpart[wbase / (32 * C)] = lsum;
         }
     }
     return true;
@@ -344,7 +358,7 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
 // blockIdx.x: W warp tiles; blockIdx.y: mode split (gridDim.y splits of the
 // warp-chunk range; with more than one split every warp writes its TwoSum
 // partial (s, e) per sorted cell to partial[split * n_cells + i]).
-template <int DIM, int C, int W>
+template <int DIM, int C, int W, bool MM>
 __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 6) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
@@ -359,24 +373,60 @@ __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 6) synth_fwd_kernel(FwdD
     const int cb = static_cast<int>(static_cast<int64_t>(n_chunks) * split / n_split);
     const int ce = static_cast<int>(static_cast<int64_t>(n_chunks) * (split + 1) / n_split);
     float2* part = n_split > 1 ? partial + static_cast<int64_t>(split) * d.n_cells : nullptr;
-    synth_warp_tile<DIM, C, 0>(d, wbase, cb, ce, part, ws, uses, status);
+    const bool ok = synth_warp_tile<DIM, C, 0, MM>(d, wbase, cb, ce, part, ws, uses, status);
+    if (MM && !ok && part == nullptr && (threadIdx.x & 31) == 0)
+        d.map.lpart[wbase / (32 * C)] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no loss
 }
 
 // Combine the per-split partials of every sorted cell in split order (a
-// fixed order, so results are deterministic) and apply the maps.
+// fixed order, so results are deterministic) and apply the maps; with the
+// mismatch bit every block also writes its sum of (K - T)^2 to lpart.
 __global__ void __launch_bounds__(256) synth_split_finalize(FwdDesc d, const float2* __restrict__ partial,
                                                             int n_split) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= d.n_cells) return;
-    float s = 0.0f, e = 0.0f;
-    for (int k = 0; k < n_split; ++k) {
-        const float2 v = partial[static_cast<int64_t>(k) * d.n_cells + i];
-        two_sum_acc(s, e, v.x);
-        e += v.y;
+    double l = 0.0;
+    if (i < d.n_cells) {
+        float s = 0.0f, e = 0.0f;
+        for (int k = 0; k < n_split; ++k) {
+            const float2 v = partial[static_cast<int64_t>(k) * d.n_cells + i];
+            two_sum_acc(s, e, v.x);
+            e += v.y;
+        }
+        const float y = (s + e) + d.map.mu;
+        const int64_t o = static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base;
+        if (index_ok(o, d.n_cells)) {
+            map_store(d.map, o, y);
+            if (d.map.bits & kMapMismatch) l = mismatch_store(d.map, o, y);
+        }
     }
-    const float y = (s + e) + d.map.mu;
-    const int64_t o = static_cast<int64_t>(__ldg(d.perm + i)) - d.perm_base;
-    if (index_ok(o, d.n_cells)) map_store(d.map, o, y);
+    if (d.map.bits & kMapMismatch) {
+        __shared__ double red[8];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[w];
+            d.map.lpart[blockIdx.x] = t;
+        }
+    }
+}
+
+// loss = (sum of the nb partial sums of (K - T)^2) / n_mean, one block,
+// fixed order.
+__global__ void __launch_bounds__(256) loss_sum_kernel(const double* __restrict__ part, int64_t nb,
+                                                       double inv_n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < nb; k += 256) acc += part[k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] * inv_n;
 }
 
 // Persistent batched kernel: every warp pulls (realisation, warp tile) work
@@ -441,13 +491,20 @@ int choose_split(int64_t tiles, int n_chunks, int resident, int64_t n_cells, siz
 template <int DIM, int C, int W>
 int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, cudaStream_t st) {
     const size_t smem = sizeof(FwdSmem<W>);
-    auto kern = synth_fwd_kernel<DIM, C, W>;
+    const bool mm = (d.map.bits & kMapMismatch) != 0;
+    auto kern = mm ? synth_fwd_kernel<DIM, C, W, true> : synth_fwd_kernel<DIM, C, W, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     const int64_t per_cta = int64_t(W) * 32 * C;
     const int64_t grid = (d.n_cells + per_cta - 1) / per_cta;
-    if (grid == 0) return cudaSuccess;
+    if (grid == 0) {
+        if (mm) {  // no cells: the loss is 0
+            loss_sum_kernel<<<1, 256, 0, st>>>(d.map.lpart, 0, 0.0, d.map.loss);
+            count_launches(1);
+        }
+        return cudaGetLastError();
+    }
     int n_split = 1;
     if (workspace != nullptr) {
         int dev = 0, sms = 0, per_sm = 0;
@@ -459,8 +516,14 @@ int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* 
     float2* partial = static_cast<float2*>(workspace);
     kern<<<dim3(static_cast<unsigned>(grid), n_split), W * 32, smem, st>>>(d, partial, status);
     count_launches(1);
+    const int64_t fin_blocks = (d.n_cells + 255) / 256;
     if (n_split > 1) {
-        synth_split_finalize<<<static_cast<unsigned>((d.n_cells + 255) / 256), 256, 0, st>>>(d, partial, n_split);
+        synth_split_finalize<<<static_cast<unsigned>(fin_blocks), 256, 0, st>>>(d, partial, n_split);
+        count_launches(1);
+    }
+    if (mm) {
+        const int64_t nb = n_split > 1 ? fin_blocks : (d.n_cells + 32 * C - 1) / (32 * C);
+        loss_sum_kernel<<<1, 256, 0, st>>>(d.map.lpart, nb, d.map.inv_n_mean, d.map.loss);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -510,6 +573,10 @@ int fwd_tile_cells(int cfg) {
 size_t synth_workspace_bytes(int64_t n_cells) {
     return static_cast<size_t>(align256(int64_t(kMaxSplit) * n_cells * int64_t(sizeof(float2))));
 }
+
+// One entry per warp tile of at least 128 cells, or per 256-cell block of the
+// split finalize, whichever is more.
+int64_t mismatch_partials(int64_t n_cells) { return (n_cells + 127) / 128 + 1; }
 
 int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);

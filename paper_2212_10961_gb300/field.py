@@ -137,12 +137,25 @@ def from_dictionary(d, seed=1):
 
 
 def _modes_struct(n, dim, arrays):
+    """grf_modes over the float64 numpy arrays present in `arrays` (NULL for
+    a missing key); the arrays must outlive the struct's use."""
     m = _abi.grf_modes()
     m.n = n
     m.dim = dim
     for k in ("kappa", "rho", "psi", "a", "amp"):
-        setattr(m, k, arrays[k].ctypes.data_as(_abi.c_dp))
+        if arrays.get(k) is not None:
+            setattr(m, k, arrays[k].ctypes.data_as(_abi.c_dp))
     return m
+
+
+def _host64(v, shape=None):
+    """Contiguous float64 numpy copy on the host of a tensor, array or list."""
+    if isinstance(v, torch.Tensor):
+        v = v.detach().to(device="cpu", dtype=torch.float64)
+        out = v.contiguous().numpy()
+    else:
+        out = np.ascontiguousarray(v, dtype=np.float64)
+    return out.reshape(shape) if shape is not None else out
 
 
 def gen_modes(params: FieldParams):
@@ -152,6 +165,19 @@ def gen_modes(params: FieldParams):
               "a": np.empty((n, d)), "amp": np.empty(n)}
     m = _modes_struct(n, d, arrays)
     check(lib().grf_gen_modes(ctypes.byref(params.to_c()), ctypes.byref(m)))
+    return arrays
+
+
+def reparam_modes(params: FieldParams, kappa, rho):
+    """Amplitudes and frequencies of given standardised modes (Sec. 4.1,
+    grf_reparam_modes): A = sigma rho and a = R^T kappa / (2 pi l) with the
+    periodic axes of `params` rounded.  kappa (N, d), rho (N,): arrays or
+    tensors.  Returns a dict with kappa, rho, a (N, d), amp (host FP64)."""
+    n, d = int(params.n_modes), int(params.dim)
+    arrays = {"kappa": _host64(kappa, (n, d)), "rho": _host64(rho, (n,)), "a": np.empty((n, d)),
+              "amp": np.empty(n)}
+    m = _modes_struct(n, d, arrays)
+    check(lib().grf_reparam_modes(ctypes.byref(params.to_c()), ctypes.byref(m)))
     return arrays
 
 
@@ -190,46 +216,49 @@ def load_realisation(path, verify=True):
 
 
 class ModeTable:
-    """Device mode table: packed on the host, copied to the device."""
+    """Device mode table: packed on the host, copied to the device.
 
-    def __init__(self, amp, psi, a, device=None, stream=None):
-        amp = np.ascontiguousarray(amp, dtype=np.float64)
-        psi = np.ascontiguousarray(psi, dtype=np.float64)
-        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(len(amp), -1))
+    kappa (optional, (N, d)) is stored with the table for the adjoint's chain
+    rule to kappa, l and R (grf_synth_backward)."""
+
+    def __init__(self, amp, psi, a, device=None, stream=None, kappa=None):
+        amp = _host64(amp)
+        a = _host64(a, (len(amp), -1))
         self.n_modes, self.dim = a.shape
         self.nbytes = int(lib().grf_table_bytes(self.n_modes))
         if self.nbytes == 0:
             raise ValueError("n_modes out of range")
-        arrays = {"kappa": a, "rho": amp, "psi": psi, "a": a, "amp": amp}
-        m = _modes_struct(self.n_modes, self.dim, arrays)
         self.host = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
-        check(lib().grf_pack_table(ctypes.byref(m), _ptr(self.host), self.nbytes))
+        self._pack(amp, psi, a, kappa)
         device = device or torch.device("cuda", torch.cuda.current_device())
         self.dev = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
         self._uploaded = torch.cuda.Event()
         self.upload(stream)
 
+    def _pack(self, amp, psi, a, kappa):
+        arrays = {"amp": amp, "psi": _host64(psi), "a": a,
+                  "kappa": None if kappa is None else _host64(kappa, a.shape)}
+        m = _modes_struct(self.n_modes, self.dim, arrays)
+        check(lib().grf_pack_table(ctypes.byref(m), _ptr(self.host), self.nbytes))
+
     def upload(self, stream=None):
         check(lib().grf_upload_table(_ptr(self.host), _ptr(self.dev), self.nbytes, _stream_handle(stream)))
         self._uploaded.record(stream if stream is not None else torch.cuda.current_stream())
 
-    def update(self, amp, psi, a, stream=None):
+    def update(self, amp, psi, a, stream=None, kappa=None):
         """Repack new modes (same N and dim) into this table and upload them.
         Waits for the previous upload from the pinned staging buffer first."""
-        amp = np.ascontiguousarray(amp, dtype=np.float64)
-        psi = np.ascontiguousarray(psi, dtype=np.float64)
-        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(len(amp), -1))
+        amp = _host64(amp)
+        a = _host64(a, (len(amp), -1))
         if a.shape != (self.n_modes, self.dim):
             raise ValueError("update needs the same number of modes and dimension")
         self._uploaded.synchronize()
-        arrays = {"kappa": a, "rho": amp, "psi": psi, "a": a, "amp": amp}
-        m = _modes_struct(self.n_modes, self.dim, arrays)
-        check(lib().grf_pack_table(ctypes.byref(m), _ptr(self.host), self.nbytes))
+        self._pack(amp, psi, a, kappa)
         self.upload(stream)
 
     @classmethod
     def from_modes(cls, modes, **kw):
-        return cls(modes["amp"], modes["psi"], modes["a"], **kw)
+        return cls(modes["amp"], modes["psi"], modes["a"], kappa=modes.get("kappa"), **kw)
 
     @property
     def ptr(self):
@@ -455,10 +484,12 @@ _ws_fwd = Workspace()
 
 
 def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=0, stream=None,
-             workspace=None):
+             workspace=None, gscale=None):
     """Gradients (device FP64) of a loss with dL/dY = gY (CUDA float32,
     original cell order): dA, dpsi, da (N, d) in the original mode order,
-    dmu, dsigma, dell (d), drot (d, d; meaningful with a rotation)."""
+    dmu, dsigma, dsigma2, dell (d), drot (d, d; meaningful with a transform),
+    drho (N) and dkappa (N, d).  gscale: optional CUDA float64 scalar that
+    multiplies every gradient (an upstream factor read on the device)."""
     gY = _require_cuda(gY, torch.float32, "gY")
     dev = gY.device
     n, d = table.n_modes, table.dim
@@ -468,10 +499,15 @@ def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=
          "dmu": torch.empty(1, dtype=torch.float64, device=dev),
          "dsigma": torch.empty(1, dtype=torch.float64, device=dev),
          "dell": torch.empty(d, dtype=torch.float64, device=dev),
-         "drot": torch.empty((d, d), dtype=torch.float64, device=dev)}
+         "drot": torch.empty((d, d), dtype=torch.float64, device=dev),
+         "dsigma2": torch.empty(1, dtype=torch.float64, device=dev),
+         "drho": torch.empty(n, dtype=torch.float64, device=dev),
+         "dkappa": torch.empty((n, d), dtype=torch.float64, device=dev)}
     gs = _abi.grf_grads()
     for k in g:
         setattr(gs, k, g[k].data_ptr())
+    if gscale is not None:
+        gs.gscale = _require_cuda(gscale, torch.float64, "gscale").data_ptr()
     nbytes = int(lib().grf_backward_workspace_bytes(plan.segment_size(segment), n, d))
     ws = (workspace or _ws_bwd).get(nbytes, dev)
     check(lib().grf_synth_backward(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
@@ -493,50 +529,122 @@ def mismatch_grad(K, K_target, stream=None, workspace=None):
     return loss, gY
 
 
+_ws_mm = Workspace()
+
+
+def synth_mismatch(table: ModeTable, params: FieldParams, plan: CellPlan, K_target, segment=0, n_mean=0,
+                   want_Y=False, want_K=False, stream=None, workspace=None):
+    """Forward half of a calibration step in one kernel (grf_synth_mismatch):
+    the field, K = exp(Y), L = sum (K - T)^2 / n_mean and gY = dL/dY.
+    n_mean: cells of the mean (0: this segment's count; the total over all
+    shards for a sharded field).  Returns (loss (1,) FP64, gY, outputs) with
+    outputs holding "Y" and/or "K" when asked for (original cell order)."""
+    n = plan.segment_size(segment)
+    dev = plan.buf.device
+    T = _require_cuda(K_target, torch.float32, "K_target")
+    if T.numel() != n:
+        raise ValueError("K_target has %d values for %d cells" % (T.numel(), n))
+    gY = torch.empty(n, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    out = {}
+    if want_Y:
+        out["Y"] = torch.empty(n, dtype=torch.float32, device=dev)
+    if want_K:
+        out["K"] = torch.empty(n, dtype=torch.float32, device=dev)
+    nbytes = int(lib().grf_synth_mismatch_workspace_bytes(n))
+    ws = (workspace or _ws_mm).get(nbytes, dev)
+    check(lib().grf_synth_mismatch(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment), _ptr(T),
+                                   int(n_mean), _ptr(gY), _ptr(loss), _ptr(out.get("Y")), _ptr(out.get("K")),
+                                   _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return loss, gY, out
+
+
 # ---------------------------------------------------------------------------
 # Autograd
 # ---------------------------------------------------------------------------
 class _SpectralFieldFn(torch.autograd.Function):
+    """Differentiable field of the reparameterised modes.  Marshalling only:
+    the library forms A = sigma rho and a = R^T kappa / (2 pi l) with the
+    periodic rounding (grf_reparam_modes), synthesises Y and, in backward,
+    returns every gradient of the parameters themselves (grf_synth_backward:
+    dmu, dsigma2, dell, drho, dpsi, dkappa, drot)."""
+
     @staticmethod
-    def forward(ctx, mu, sigma, ell, rho, psi, kappa, plan, segment, family):
-        d = kappa.shape[1]
-        s = float(sigma.detach().cpu())
-        ellv = ell.detach().cpu().double().numpy()
-        amp = s * rho.detach().cpu().double().numpy()
-        a = kappa.detach().cpu().double().numpy() / (2.0 * math.pi * ellv[None, :d])
-        table = ModeTable(amp, psi.detach().cpu().double().numpy(), a)
-        params = FieldParams(family=family, sigma2=s * s, mean=float(mu.detach().cpu()),
-                             ell=tuple(ellv[:d]), dim=d, n_modes=len(amp))
+    def forward(ctx, mu, sigma2, ell, rho, psi, kappa, rot, plan, segment, period):
+        params, table = _reparam_table(mu, sigma2, ell, rho, psi, kappa, rot, period, plan.buf.device)
         y = synth(table, params, plan, segment, MapSpec(y=True))["Y"]
         ctx.table, ctx.params, ctx.plan, ctx.segment = table, params, plan, segment
-        ctx.save_for_backward(sigma, ell, rho, kappa)
+        ctx.meta = [(t.shape, t.device, t.dtype) if t is not None else None
+                    for t in (mu, sigma2, ell, rho, psi, kappa, rot)]
         return y
 
     @staticmethod
     def backward(ctx, gY):
-        sigma, ell, rho, kappa = ctx.saved_tensors
         g = backward(ctx.table, ctx.params, ctx.plan, gY.contiguous().float(), ctx.segment)
-        d = kappa.shape[1]
-        dev_p = sigma.device
-        s = float(sigma.detach().cpu())
-        ellv = ell.detach().to(torch.float64)
-        dmu = g["dmu"].reshape(()).to(dev_p)
-        dsigma = g["dsigma"].reshape(()).to(dev_p)
-        dell = torch.zeros_like(ell, dtype=torch.float64)
-        dell[:d] = g["dell"].to(ell.device)
-        drho = (s * g["dA"]).to(rho.device)
-        dpsi = g["dpsi"].to(rho.device)
-        dkappa = (g["da"] / (2.0 * math.pi * ellv[:d].to(g["da"].device))).to(kappa.device)
-        return (dmu.to(torch.float64), dsigma.to(torch.float64), dell.to(ell.dtype),
-                drho.to(rho.dtype), dpsi.to(rho.dtype), dkappa.to(kappa.dtype), None, None, None)
+        out = tuple(None if m is None else g[k].reshape(m[0]).to(device=m[1], dtype=m[2])
+                    for k, m in zip(_REPARAM_GRADS, ctx.meta))
+        return out + (None, None, None)
 
 
-def spectral_field(mu, sigma, ell, rho, psi, kappa, plan: CellPlan, segment=0, family="gaussian"):
-    """Differentiable Y(x) = mu + sum_j sigma rho_j cos(2 pi (kappa_j/(2 pi l) . x + psi_j)).
+def spectral_field(mu, sigma2, ell, rho, psi, kappa, plan: CellPlan, segment=0, rot=None, period=None):
+    """Differentiable Y(x) = mu + sum_j sqrt(sigma2) rho_j cos(2 pi (a_j . x + psi_j)),
+    a_j = R^T kappa_j / (2 pi l) with periodic axes rounded (Sec. 4.1,
+    Appendix B `periodic`; grf_reparam_modes).
 
-    Gradients flow to mu, sigma, ell (correlation lengths) and the per-mode
-    rho, psi, kappa through the CUDA adjoint kernel."""
-    return _SpectralFieldFn.apply(mu, sigma, ell, rho, psi, kappa, plan, segment, family)
+    mu, sigma2: scalar tensors; ell (d,); rho, psi (N,); kappa (N, d); rot:
+    optional (d, d) axis transform; period: optional per-axis lengths (not
+    differentiable).  Gradients flow to all tensors through the CUDA adjoint.
+    Parameters on the CPU keep the forward free of device-to-host copies."""
+    return _SpectralFieldFn.apply(mu, sigma2, ell, rho, psi, kappa, rot, plan, segment, period)
+
+
+def _reparam_table(mu, sigma2, ell, rho, psi, kappa, rot, period, device):
+    """FieldParams and device table of the reparameterised modes (marshalling
+    of the parameters; the reparameterisation runs in grf_reparam_modes)."""
+    n, d = kappa.shape
+    rot_h = None if rot is None else _host64(rot, (d, d)).tolist()
+    params = FieldParams(sigma2=float(sigma2), mean=float(mu), ell=tuple(_host64(ell, (d,)).tolist()), dim=d,
+                         n_modes=n, period=tuple(period) if period is not None else (0.0,) * 3, rot=rot_h)
+    modes = reparam_modes(params, kappa, rho)
+    return params, ModeTable(modes["amp"], psi, modes["a"], kappa=modes["kappa"], device=device)
+
+
+_REPARAM_GRADS = ("dmu", "dsigma2", "dell", "drho", "dpsi", "dkappa", "drot")
+
+
+class _SpectralMismatchFn(torch.autograd.Function):
+    """Calibration objective L = mean (exp(Y) - T)^2 of the reparameterised
+    field, as one differentiable scalar: the forward is grf_synth_mismatch
+    (field, K, loss and dL/dY in one kernel), the backward grf_synth_backward
+    with the upstream gradient passed to the library as its device scale."""
+
+    @staticmethod
+    def forward(ctx, mu, sigma2, ell, rho, psi, kappa, rot, plan, K_target, segment, period, n_mean):
+        params, table = _reparam_table(mu, sigma2, ell, rho, psi, kappa, rot, period, plan.buf.device)
+        loss, gY, _ = synth_mismatch(table, params, plan, K_target, segment, n_mean)
+        ctx.table, ctx.params, ctx.plan, ctx.segment, ctx.gY = table, params, plan, segment, gY
+        ctx.meta = [(t.shape, t.device, t.dtype) if t is not None else None
+                    for t in (mu, sigma2, ell, rho, psi, kappa, rot)]
+        return loss.reshape(())
+
+    @staticmethod
+    def backward(ctx, gL):
+        gs = gL.detach().to(device=ctx.gY.device, dtype=torch.float64).contiguous()
+        g = backward(ctx.table, ctx.params, ctx.plan, ctx.gY, ctx.segment, gscale=gs)
+        out = tuple(None if m is None else g[k].reshape(m[0]).to(device=m[1], dtype=m[2])
+                    for k, m in zip(_REPARAM_GRADS, ctx.meta))
+        return out + (None,) * 5
+
+
+def spectral_mismatch(mu, sigma2, ell, rho, psi, kappa, plan: CellPlan, K_target, segment=0, rot=None, period=None,
+                      n_mean=0):
+    """Differentiable calibration loss L = sum_i (exp(Y_i) - T_i)^2 / n_mean of
+    the field of spectral_field (same parameters), K_target = T (CUDA float32,
+    original cell order).  n_mean: 0 for the plain mean over the segment.
+    Returns a 0-d CUDA float64 tensor; .backward() gives the gradients of all
+    parameter tensors through the CUDA adjoint."""
+    return _SpectralMismatchFn.apply(mu, sigma2, ell, rho, psi, kappa, rot, plan, K_target, segment, period,
+                                     n_mean)
 
 
 class _ModeSumFn(torch.autograd.Function):

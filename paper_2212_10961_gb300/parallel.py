@@ -6,15 +6,15 @@ rank plans and synthesises its own range with the same mode table (same seed).
 Every gradient of a loss that is a sum over cells is itself a sum over cells
 (dA, dpsi, da, dmu, and dsigma, dl which are linear in them), so the adjoint
 of a sharded field needs exactly one exchange: a sum over ranks of the
-per-rank gradients.  A mean-type loss is first rescaled from the local to the
-global cell count.
+per-rank gradients.  A mean-type loss divides by the global cell count
+from the start (grf_synth_mismatch's n_mean).
 
 Uses torch.distributed (NCCL between GPUs, gloo on CPU for tests).
 """
 import torch
 import torch.distributed as dist
 
-GRAD_KEYS = ("dA", "dpsi", "da", "dmu", "dsigma", "dell", "drot")
+GRAD_KEYS = ("dA", "dpsi", "da", "dmu", "dsigma", "dell", "drot", "dsigma2", "drho", "dkappa")
 
 
 def shard_range(n, rank, world):
@@ -26,13 +26,18 @@ def shard_range(n, rank, world):
     return begin, begin + base + (1 if rank < extra else 0)
 
 
-def global_scale(n_local, group=None):
-    """(n_total, n_local / n_total) for rescaling a per-rank mean-type loss."""
+def global_count(n_local, group=None):
+    """Total number of cells over the ranks of `group` (one all-reduce)."""
     t = torch.tensor([float(n_local)], dtype=torch.float64,
                      device="cuda" if dist.get_backend(group) == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    n_total = float(t.item())
-    return n_total, (float(n_local) / n_total if n_total > 0 else 0.0)
+    return int(round(float(t.item())))
+
+
+def global_scale(n_local, group=None):
+    """(n_total, n_local / n_total) for rescaling a per-rank mean-type loss."""
+    n_total = global_count(n_local, group)
+    return float(n_total), (float(n_local) / n_total if n_total > 0 else 0.0)
 
 
 def allreduce_grads(grads, group=None):
@@ -48,17 +53,18 @@ def allreduce_grads(grads, group=None):
     return grads
 
 
-def sharded_loss_and_backward(F, table, params, plan, K, K_target, group=None):
+def sharded_loss_and_backward(F, table, params, plan, K_target, segment=0, group=None):
     """Mean mismatch loss over all ranks' cells and its gradients.
 
-    F is the field module (paper_2212_10961_gb300.field); K and K_target are
-    this rank's lognormal field and target (CUDA float32, original order of
-    this rank's cells).  Returns (loss, grads) identical on every rank."""
-    loss_local, gY = F.mismatch_grad(K, K_target)
-    n_total, frac = global_scale(K.numel(), group)
-    gY.mul_(frac)  # d(global mean)/dY = (n_local / n_total) d(local mean)/dY
-    grads = F.backward(table, params, plan, gY)
-    loss = loss_local * frac
+    F is the field module (paper_2212_10961_gb300.field); plan holds this
+    rank's cells and K_target their target (CUDA float32, original order of
+    this rank's cells).  The forward kernel divides by the global cell count
+    (grf_synth_mismatch with n_mean = total), so the per-rank losses and
+    gradients are the rank's shares of the global ones and the exchange is
+    a plain sum.  Returns (loss, grads) identical on every rank."""
+    n_total = global_count(plan.segment_size(segment), group)
+    loss, gY, _ = F.synth_mismatch(table, params, plan, K_target, segment, n_mean=n_total)
+    grads = F.backward(table, params, plan, gY, segment)
     dist.all_reduce(loss, op=dist.ReduceOp.SUM, group=group)
     allreduce_grads(grads, group)
     return loss, grads

@@ -156,14 +156,16 @@ def _parse_table(buf, n, dim):
     b = np.frombuffer(buf, dtype=np.uint8)
     hdr = np.frombuffer(b[:256].tobytes(), dtype=np.int32)
     magic, n_modes, n_pad, d = hdr[0], hdr[1], hdr[2], hdr[3]
-    off = np.frombuffer(b[32:72].tobytes(), dtype=np.int64)
-    off_hot, off_cold, off_order, off_kpref, total = off
+    has_kappa = hdr[7]
+    off = np.frombuffer(b[32:80].tobytes(), dtype=np.int64)
+    off_hot, off_cold, off_order, off_kpref, total, off_kappa = off
     hot = np.frombuffer(b[off_hot:off_hot + n_pad * 16].tobytes(), dtype=np.float32).reshape(n_pad, 4)
     cold = np.frombuffer(b[off_cold:off_cold + n_pad * 32].tobytes(), dtype=np.float32).reshape(n_pad, 8)
     order = np.frombuffer(b[off_order:off_order + n_pad * 4].tobytes(), dtype=np.int32)
     kpref = np.frombuffer(b[off_kpref:off_kpref + 160 * 4].tobytes(), dtype=np.int32)
+    kappa = np.frombuffer(b[off_kappa:off_kappa + n_pad * 24].tobytes(), dtype=np.float64).reshape(n_pad, 3)
     return dict(magic=magic, n=n_modes, n_pad=n_pad, dim=d, hot=hot, cold=cold, order=order, kpref=kpref,
-                total=total)
+                total=total, has_kappa=has_kappa, kappa=kappa, off_kappa=off_kappa)
 
 
 @pytest.mark.parametrize("n,dim", [(1, 1), (130, 2), (1000, 3)])
@@ -201,6 +203,69 @@ def test_pack_table_layout(abi, n, dim):
     for b in range(160):
         Eb = 2.0 ** ((b - 100) / 4.0)
         assert t["kpref"][b] == int(np.sum(h * Eb > 1.0))
+    # the standardised wave-vectors ride along in sorted order, for the adjoint
+    assert t["has_kappa"] == 1 and t["off_kappa"] % 256 == 0 and t["off_kappa"] + t["n_pad"] * 24 <= nbytes
+    np.testing.assert_array_equal(t["kappa"][:n, :dim], md["kappa"][order[:n]])
+    assert np.all(t["kappa"][:n, dim:] == 0) and np.all(t["kappa"][n:] == 0)
+    # packed without kappa: the flag is 0 and the section stays zero
+    m0 = F._modes_struct(n, dim, {k: md[k] for k in ("amp", "psi", "a")})
+    assert abi.lib().grf_pack_table(ctypes.byref(m0), buf, nbytes) == 0
+    t0 = _parse_table(bytes(buf), n, dim)
+    assert t0["has_kappa"] == 0 and np.all(t0["kappa"] == 0)
+    np.testing.assert_array_equal(t0["hot"], t["hot"])
+
+
+@pytest.mark.parametrize("dim,rot,period", [(3, None, None), (3, "rotation", (1.0, 0.0, 2.0)),
+                                            (2, "general", (0.0, 1.5)), (1, None, (2.0,))])
+def test_reparam_modes_matches_oracle_and_gen_modes(abi, dim, rot, period):
+    # Sec. 4.1: A = sigma rho, a = R^T kappa / (2 pi l), periodic axes rounded
+    # (Appendix B); the same arithmetic as the second half of grf_gen_modes
+    from paper_2212_10961_gb300 import field as F
+    R = None
+    if rot == "rotation":
+        th = 0.7
+        R = [[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]]
+    elif rot == "general":
+        R = [[1.2, 0.4], [-0.3, 0.9]]
+    ell = (0.2, 0.1, 0.05)[:dim]
+    p = F.FieldParams(family="matern", nu=1.5, sigma2=2.3, ell=ell, dim=dim, n_modes=600, seed=41, rot=R,
+                      period=period or (0.0,) * 3)
+    drawn = F.gen_modes(p)
+    got = F.reparam_modes(p, drawn["kappa"], drawn["rho"])
+    np.testing.assert_array_equal(got["amp"], drawn["amp"])
+    np.testing.assert_array_equal(got["a"], drawn["a"])
+    amp_o, a_o = omodes.reparam(drawn["kappa"], drawn["rho"], math.sqrt(2.3), ell, rot=R, period=period)
+    np.testing.assert_allclose(got["amp"], amp_o, rtol=4e-16, atol=0)
+    per = [c for c in range(dim) if period is not None and period[c] > 0]
+    free = [c for c in range(dim) if c not in per]
+    np.testing.assert_array_equal(got["a"][:, per], a_o[:, per])
+    np.testing.assert_allclose(got["a"][:, free], a_o[:, free], rtol=4e-15, atol=1e-300)
+    # arbitrary (not drawn) kappa and rho
+    rng = np.random.default_rng(dim)
+    k2, r2 = rng.standard_normal((600, dim)), rng.random(600)
+    got2 = F.reparam_modes(p, k2, r2)
+    amp2, a2 = omodes.reparam(k2, r2, math.sqrt(2.3), ell, rot=R, period=period)
+    np.testing.assert_allclose(got2["amp"], amp2, rtol=4e-16, atol=0)
+    # a = R^T u sums terms of either sign: rounding is relative to sum_k |R_kc u_k|
+    mag = np.abs(k2 / (2 * math.pi * np.asarray(ell))) @ (np.abs(np.asarray(R)) if R is not None else np.eye(dim))
+    assert np.all(np.abs(got2["a"][:, free] - a2[:, free]) <= 8 * 2.0 ** -52 * mag[:, free])
+    np.testing.assert_array_equal(got2["a"][:, per], a2[:, per])
+
+
+def test_reparam_modes_rejects(abi):
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=10, seed=1)
+    k = np.zeros((10, 2))
+    k[3, 1] = np.nan
+    with pytest.raises(abi.GRFError):
+        F.reparam_modes(p, k, np.ones(10))
+    with pytest.raises(abi.GRFError):
+        F.reparam_modes(p, np.zeros((10, 2)), np.full(10, np.inf))
+    m, _ = _modes_for(abi, 9, 2)
+    assert abi.lib().grf_reparam_modes(ctypes.byref(p.to_c()), ctypes.byref(m)) == abi.GRF_EINVAL
+    m2, _ = _modes_for(abi, 10, 2)
+    m2.rho = None
+    assert abi.lib().grf_reparam_modes(ctypes.byref(p.to_c()), ctypes.byref(m2)) == abi.GRF_EINVAL
 
 
 def test_pack_and_sizes_reject(abi):

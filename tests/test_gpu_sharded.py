@@ -2,7 +2,8 @@
 shards (no collective): every shard plans and synthesises its own contiguous
 range of cells with the same mode table, and the adjoint of a mean-type loss
 is the sum over shards of the per-shard gradients of the rescaled local loss
-(the exchange `parallel.allreduce_grads` performs between ranks)."""
+(the exchange `parallel.allreduce_grads` performs between ranks).  The
+product function itself runs as two processes in test_gpu_calibration."""
 import math
 
 import numpy as np
@@ -32,7 +33,7 @@ def test_sharded_forward_and_adjoint_match_unsharded(world):
     plan = F.CellPlan(*dev)
     full = gf.synth(plan, maps)
     T = gt.synth(plan, maps)["K"]
-    loss_full, gY = F.mismatch_grad(full["K"], T)
+    loss_full, gY, _ = F.synth_mismatch(gf.table, p, plan, T)
     g_full = F.backward(gf.table, p, plan, gY)
 
     # shards
@@ -43,13 +44,12 @@ def test_sharded_forward_and_adjoint_match_unsharded(world):
         b, e = parallel.shard_range(n, r, world)
         plan_r = F.CellPlan(*[c[b:e] for c in dev])
         out_r = gf.synth(plan_r, maps)
-        loss_r, gY_r = F.mismatch_grad(out_r["K"], T[b:e])
-        frac = (e - b) / n  # global mean from the local mean
-        gY_r.mul_(frac)
+        # the shard's share of the global mean: divided by the global count
+        loss_r, gY_r, _ = F.synth_mismatch(gf.table, p, plan_r, T[b:e], n_mean=n)
         g_r = F.backward(gf.table, p, plan_r, gY_r)
         for k in parallel.GRAD_KEYS:
             acc[k] += g_r[k]
-        loss_sum += float(loss_r.item()) * frac
+        loss_sum += float(loss_r.item())
         y_parts.append(out_r["Y"].cpu().numpy())
     torch.cuda.synchronize()
 
@@ -61,7 +61,7 @@ def test_sharded_forward_and_adjoint_match_unsharded(world):
     idx = np.random.default_rng(3).choice(n, 4000, replace=False)
     check_forward(y_sh[idx], oracle_field(om, 0.0, cells, idx), sig, "sharded")
     assert abs(loss_sum - float(loss_full.item())) <= 1e-5 * abs(float(loss_full.item()))
-    for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dell"):
+    for k in parallel.GRAD_KEYS:
         want = g_full[k].cpu().numpy()
         got = acc[k].cpu().numpy()
         scale = np.max(np.abs(want))

@@ -56,7 +56,7 @@ def _worker(rank, world, port, out_path):
         loss_local, g_local = of.mismatch_loss(K, T)
         n_total, frac = parallel.global_scale(len(mine))
         g = g_local * frac
-        gr = of.backward(m["a"], m["amp"], m["psi"], 1.0, ell, mine, g)
+        gr = of.grads_reparam(*of.mode_sums(m["a"], m["psi"], mine, g), m["kappa"], m["rho"], 1.0, ell, g)
         grads = {k: torch.as_tensor(np.asarray(gr[k], dtype=np.float64)).reshape(-1) for k in parallel.GRAD_KEYS}
         parallel.allreduce_grads(grads)
         loss = torch.tensor([loss_local * frac], dtype=torch.float64)
@@ -85,7 +85,7 @@ def test_sharded_gradient_equals_unsharded(tmp_path):
     K = of.lognormal(of.synth(m["a"], m["amp"], m["psi"], 0.0, cells))
     T = of.lognormal(of.synth(mt["a"], mt["amp"], mt["psi"], 0.0, cells))
     loss, g = of.mismatch_loss(K, T)
-    ref = of.backward(m["a"], m["amp"], m["psi"], 1.0, ell, cells, g)
+    ref = of.grads_reparam(*of.mode_sums(m["a"], m["psi"], cells, g), m["kappa"], m["rho"], 1.0, ell, g)
     assert float(got["n_total"]) == len(cells)
     assert got["loss"][0] == pytest.approx(loss, rel=1e-12)
     for k in parallel.GRAD_KEYS:
