@@ -3,8 +3,6 @@
 // loss and its gradient, and a throughput probe of the hardware cosine.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "device_common.cuh"
 
 namespace grf {
@@ -230,26 +228,19 @@ static_assert(int64_t(GRF_NOALLOC_MAX_BLOCKS) * kLossThreads * kLossItems == GRF
 static __device__ __align__(256) double g_noalloc_partials[GRF_NOALLOC_MAX_BLOCKS];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol's own address: on the host it
-// names a stand-in, not the device memory).
+// Device address of the scratch array in the current device's context (host
+// code cannot use the symbol's own address: on the host it names a stand-in,
+// not the device memory).  Looked up on every call rather than cached: the
+// lookup is a host-side table search once the module is loaded, and a cached
+// address would outlive a context that cudaDeviceReset destroyed and
+// recreated (where the module, and the array, may load at a new address).
+// On a device's first call the lookup also loads the library's device code
+// into the context.
 int noalloc_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 }  // namespace

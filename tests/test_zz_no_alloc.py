@@ -58,6 +58,26 @@ def test_noalloc_matches_workspace_entry_point_twice(env):
         assert loss.item() == pytest.approx(float(np.mean((k64 - t64) ** 2)), rel=1e-6)
 
 
+def test_noalloc_at_its_largest_size(env):
+    # n = GRF_NOALLOC_MAX_CELLS fills every entry of the fixed array; it must
+    # agree with the workspace entry point (three 512 MiB float32 arrays)
+    torch, abi = env
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n = 134217728
+    g = torch.Generator(device="cuda").manual_seed(7)
+    K = torch.rand(n, generator=g, device="cuda") + 0.5
+    T = torch.rand(n, generator=g, device="cuda") + 0.5
+    loss_ref, g_ref = _reference(torch, abi, K, T)
+    gY = torch.empty_like(K)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    assert abi.lib().grf_mismatch_grad_noalloc(n, _p(K), _p(T), _p(gY), _p(loss), stream) == abi.GRF_OK
+    torch.cuda.synchronize()
+    assert loss.item() == pytest.approx(loss_ref.item(), rel=1e-12, abs=0.0)
+    assert torch.equal(gY, g_ref)
+    del K, T, gY, g_ref
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     torch, abi = env
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
