@@ -172,6 +172,43 @@ def params_for(F, w, dim, seed):
                          rot=w.get("rot"))
 
 
+ERR_SAMPLE_CELLS = 1 << 20  # cells of every workload checked against the FP64 oracle (all if fewer)
+
+
+def oracle_modes_for(w, dim, seed):
+    """The FP64 oracle's own draw of a workload's modes (never the library's)."""
+    from oracle import modes as om
+    fam = {"gaussian": 0, "exponential": 1, "matern": 2}[w["family"]]
+    return om.gen_modes(fam, w["sigma2"], list(w["ell"]) + [1.0] * (3 - len(w["ell"])), dim, w["n_modes"], seed,
+                        nu=w.get("nu", 1.5), period=w.get("period"),
+                        rot=None if w.get("rot") is None else np.asarray(w["rot"])[:dim, :dim])
+
+
+def fp64_check(cells, y_gpu, modes, mean, sigma, n_sample=ERR_SAMPLE_CELLS, seed=12345, thresholds=(),
+               facies=None):
+    """Max-abs error of a GPU field against the FP64 C oracle on a seeded
+    sample of its cells (all cells when there are fewer), in units of sigma;
+    with thresholds and facies also the facies labels outside the 2e-5 sigma
+    band that differ from the oracle's.  Runs outside every timed region."""
+    from oracle import native
+    n = len(cells[0])
+    idx = np.arange(n) if n <= n_sample else np.sort(np.random.default_rng(seed).choice(n, n_sample, replace=False))
+    c = np.stack([cc[idx] for cc in cells], axis=-1)
+    t0 = time.perf_counter()
+    y_or = native.synth(modes["a"], modes["amp"], modes["psi"], mean, c)
+    err = float(np.max(np.abs(y_gpu[idx].astype(np.float64) - y_or))) / sigma if n else 0.0
+    out = {"max_abs_err_sigma": err, "cells": int(len(idx)), "of_cells": int(n), "tol_sigma": 1e-5,
+           "within_tol": bool(err <= 1e-5), "oracle_s": time.perf_counter() - t0}
+    if len(thresholds) and facies is not None:
+        lab = np.zeros(len(idx), dtype=np.int64)
+        for t in thresholds:
+            lab += (y_or > t)
+        band = np.min(np.abs(y_or[:, None] - np.asarray(thresholds)[None, :]), axis=1) <= 2e-5 * sigma
+        out["facies_mismatch_outside_band"] = int(np.sum((facies[idx].astype(np.int64) != lab) & ~band))
+        out["facies_in_band"] = int(np.sum(band))
+    return out
+
+
 def timed_steps(torch, world, steps, warmup, step_fn, kernel_events=None):
     for i in range(warmup):
         step_fn(i)
@@ -192,7 +229,7 @@ def timed_steps(torch, world, steps, warmup, step_fn, kernel_events=None):
 
 
 def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e=True, shuffle_seed=None,
-                  override=None, label=None):
+                  override=None, label=None, check=True):
     """Headline forward step on one workload; returns dict of measurements.
     shuffle_seed: cells handed to the plan in a seeded random order (the
     plan must recover the spatial locality itself).  override: workload
@@ -237,11 +274,13 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     kern_all = [a.elapsed_time(b) for a, b in kev[warmup:]]
     kern_ms = float(np.mean(kern_all))
     assert plan.status() == 0
-    # field of the workload's own seed, kept for the accuracy check of the CPU-baseline leg
+    # field of the workload's own seed, for the accuracy check against the FP64 oracle
     p0 = params_for(F, w, dim, w["seed"])
     m0 = F.gen_modes(p0)
-    ring[0].update(m0["amp"], m0["psi"], m0["a"])
-    y_seed = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True))["Y"].cpu().numpy()
+    ring[0].update(m0["amp"], m0["psi"], m0["a"], kappa=m0["kappa"])
+    o0 = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True, thresholds=thr, facies=len(thr) > 0))
+    y_seed = o0["Y"].cpu().numpy()
+    fac_seed = o0["facies"].cpu().numpy() if "facies" in o0 else None
     per_step = launches / float(steps + warmup)
     res = {"workload": label or (name if shuffle_seed is None else "%s, cells in seeded random order (seed %d)"
                                  % (name, shuffle_seed)), "cells": M, "modes": N, "dim": dim, "ms_per_step": ms,
@@ -250,6 +289,9 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
            "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
            "launches_per_step": per_step, "y_seed": y_seed}
+    if check and rank == 0:
+        res["fp64_check"] = fp64_check(cells, y_seed, oracle_modes_for(w, dim, w["seed"]), w["mean"], sig,
+                                       thresholds=thr, facies=fac_seed)
     if with_e2e:
         res["e2e"] = bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, max(5, steps))
         res["s1_host"] = bench_gen_modes(F, w, dim, base_seed)
@@ -363,6 +405,10 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
 
 
 def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
+    """Forward + backward of the calibration loss on the 128^3 cube, N = 2048:
+    per step the fused forward (field, K = exp(Y), L = mean (K - T)^2 and
+    dL/dY in one kernel, grf_synth_mismatch) and the adjoint
+    (grf_synth_backward); tables fixed, events on the stream."""
     w = W.WORKLOADS["diff128"]
     cells = W.workload_cells("diff128", scale)
     M = len(cells[0])
@@ -371,8 +417,6 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
     pt = F.FieldParams(family=w["family"], sigma2=w["sigma2"], ell=w["ell"], dim=3, n_modes=N,
                        seed=w["target_seed"] + 1000 * rank)
     T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
-    maps = F.MapSpec(y=False, lognormal=True)
-    K = maps.allocate(M, torch.device("cuda"))
     base = w["seed"] + 1000 * rank
     ring = [F.ModeTable.from_modes(F.gen_modes(params_for(F, w, 3, base + k))) for k in range(2)]
     st = torch.cuda.current_stream()
@@ -385,8 +429,7 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
         b = torch.cuda.Event(enable_timing=True)
         c = torch.cuda.Event(enable_timing=True)
         a.record(st)
-        F.synth(tab, p, plan, 0, maps, K)
-        loss, gY = F.mismatch_grad(K["K"], T)
+        loss, gY, _ = F.synth_mismatch(tab, p, plan, T)
         b.record(st)
         F.backward(tab, p, plan, gY)
         c.record(st)
@@ -397,9 +440,82 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
     launches = F.launch_count() - l0
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, c in kev[warmup:]]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for a, b, c in kev[warmup:]]))
+    res = {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
+           "ms_per_step": ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "cell_modes_per_step": float(M) * N,
+           "launches_per_step": launches / float(steps + warmup),
+           "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)"}
+    if rank == 0:
+        res["fp64_check"] = grad_check_40(torch, F, W)
+    return res
+
+
+def grad_check_40(torch, F, W):
+    """Loss and per-family gradient errors of the fused forward + adjoint on a
+    40^3 grid with the 128^3 workload's parameters, against the FP64 oracle's
+    own loss gradient (relative to each family's largest oracle value)."""
+    from oracle import field as of
+    from oracle import native
+    w = W.WORKLOADS["diff128"]
+    cells = W.grid_centres((40, 40, 40))
+    c = np.stack(cells, axis=-1)
+    plan = F.CellPlan(*[torch.from_numpy(x).cuda() for x in cells])
+    p = params_for(F, w, 3, w["seed"])
+    pt = params_for(F, w, 3, w["target_seed"])
+    gf = F.GaussianField(p)
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True)
+    g = F.backward(gf.table, p, plan, gY)
+    torch.cuda.synchronize()
+    om = oracle_modes_for(w, 3, w["seed"])
+    y_or = native.synth(om["a"], om["amp"], om["psi"], w["mean"], c)
+    l_or, g_or = of.mismatch_loss(np.exp(y_or), T.cpu().numpy().astype(np.float64))
+    ref = of.grads_reparam(*native.mode_sums(om["a"], om["psi"], c, g_or), om["kappa"], om["rho"],
+                           math.sqrt(w["sigma2"]), w["ell"], g_or)
+    errs = {}
+    for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dsigma2", "dell", "drot", "drho", "dkappa"):
+        r = np.asarray(ref[k], dtype=np.float64)
+        errs[k] = float(np.max(np.abs(g[k].cpu().numpy().reshape(r.shape) - r)) / np.max(np.abs(r)))
+    return {"grid": "40^3 with the 128^3 parameters", "grad_err_rel": errs, "tol_rel": 1e-4,
+            "within_tol": bool(max(errs.values()) <= 1e-4),
+            "loss_err_rel": abs(loss.item() - l_or) / abs(l_or),
+            "max_abs_err_sigma": float(np.max(np.abs(out["Y"].cpu().numpy() - y_or))) / math.sqrt(w["sigma2"])}
+
+
+def bench_calibration_autograd(torch, F, W, rank, world, steps, warmup, scale):
+    """The calibration step as a user writes it: loss = spectral_mismatch(...)
+    (parameters mu, sigma^2, l, rho, psi, kappa as CPU float64 tensors that
+    require grad; Sec. 4.1 reparameterisation and packing in the library),
+    then loss.backward(), on the 128^3 workload.  Host work, the table
+    upload and the gradients' copy back to the parameters' device are inside
+    the step."""
+    w = W.WORKLOADS["diff128"]
+    cells = W.workload_cells("diff128", scale)
+    M, N = len(cells[0]), w["n_modes"]
+    plan = F.CellPlan(*[torch.from_numpy(c).cuda() for c in cells])
+    pt = params_for(F, w, 3, w["target_seed"] + 1000 * rank)
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    m = F.gen_modes(params_for(F, w, 3, w["seed"] + 1000 * rank))
+    dt = torch.float64
+    prm = [torch.tensor(w["mean"], dtype=dt), torch.tensor(w["sigma2"], dtype=dt), torch.tensor(w["ell"], dtype=dt),
+           torch.tensor(m["rho"]), torch.tensor(m["psi"]), torch.tensor(m["kappa"])]
+    for t in prm:
+        t.requires_grad_(True)
+    losses = []
+
+    def step(i):
+        for t in prm:
+            t.grad = None
+        loss = F.spectral_mismatch(*prm, plan, T)
+        loss.backward()
+        losses.append(loss.detach())
+
+    l0 = F.launch_count()
+    ms = timed_steps(torch, world, steps, warmup, step)
+    launches = F.launch_count() - l0
     return {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
-            "ms_per_step": ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "cell_modes_per_step": float(M) * N,
-            "launches_per_step": launches / float(steps + warmup)}
+            "ms_per_step": ms, "cell_modes_per_step": float(M) * N,
+            "launches_per_step": launches / float(steps + warmup),
+            "api": "F.spectral_mismatch(mu, sigma2, ell, rho, psi, kappa, plan, T).backward(), CPU parameters"}
 
 
 def bench_bitruncated(torch, F, W, rank, world, steps, warmup, scale):
@@ -422,9 +538,33 @@ def bench_bitruncated(torch, F, W, rank, world, steps, warmup, scale):
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: pg.synth(plan, t, (0.0,), rule, values))
     launches = F.launch_count() - l0
-    return {"workload": "grid3d_256 bitruncated: exponential l=(0.2,0.2,0.05) x Gaussian l=0.1, 3 x 2 rule",
-            "cells": M, "modes_per_field": N, "ms_per_step": ms, "cell_modes_per_step": 2.0 * M * N,
-            "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms}
+    res = {"workload": "grid3d_256 bitruncated: exponential l=(0.2,0.2,0.05) x Gaussian l=0.1, 3 x 2 rule",
+           "cells": M, "modes_per_field": N, "ms_per_step": ms, "cell_modes_per_step": 2.0 * M * N,
+           "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms}
+    if rank == 0:
+        # both fields against the oracle's own draws (streams 0 and 1), and the
+        # merged facies against the rule applied to the oracle fields
+        from oracle import field as of
+        from oracle import modes as om
+        from oracle import native
+        o = pg.synth(plan, t, (0.0,), rule, values)
+        y1, y2, fac = o["Y1"].cpu().numpy(), o["Y2"].cpu().numpy(), o["facies"].cpu().numpy()
+        idx = np.sort(np.random.default_rng(12345).choice(M, min(M, ERR_SAMPLE_CELLS), replace=False))
+        c = np.stack([cc[idx] for cc in cells], axis=-1)
+        m1 = om.gen_modes(1, w["sigma2"], w["ell"], 3, N, seed, stream=0)
+        m2 = om.gen_modes(0, 1.0, (0.1, 0.1, 0.1), 3, N, seed, stream=1)
+        o1 = native.synth(m1["a"], m1["amp"], m1["psi"], 0.0, c)
+        o2 = native.synth(m2["a"], m2["amp"], m2["psi"], 0.0, c)
+        lab = of.bitruncated(o1, o2, t, (0.0,), rule)
+        band = (np.min(np.abs(o1[:, None] - np.asarray(t)[None, :]), axis=1) <= 2e-5 * math.sqrt(w["sigma2"])) | \
+            (np.abs(o2) <= 2e-5)
+        res["fp64_check"] = {
+            "max_abs_err_sigma": max(float(np.max(np.abs(y1[idx] - o1))) / math.sqrt(w["sigma2"]),
+                                     float(np.max(np.abs(y2[idx] - o2)))),
+            "cells": int(len(idx)), "of_cells": int(M), "tol_sigma": 1e-5,
+            "facies_mismatch_outside_band": int(np.sum((fac[idx] != lab) & ~band)), "facies_in_band": int(band.sum())}
+        res["fp64_check"]["within_tol"] = bool(res["fp64_check"]["max_abs_err_sigma"] <= 1e-5)
+    return res
 
 
 def bench_batched(torch, F, W, rank, world, steps, warmup, scale, tile="auto"):
@@ -456,9 +596,33 @@ def bench_batched(torch, F, W, rank, world, steps, warmup, scale, tile="auto"):
     batch.capture()
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: batch.replay())
-    return {"workload": "ensemble256", "realisations": len(recipe), "cells": int(sum(segs)),
-            "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1,
-            "tile_cells": batch.tile_cells, "autotune_ms": batch.tuned_ms}
+    res = {"workload": "ensemble256", "realisations": len(recipe), "cells": int(sum(segs)),
+           "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1,
+           "tile_cells": batch.tile_cells, "autotune_ms": batch.tuned_ms,
+           # one cell per lane takes its cosine from the FMA-pipe polynomial
+           "mufu_share": 1.0 - 1.0 / (batch.tile_cells // 32)}
+    if rank == 0:
+        # every realisation on a seeded sample (about 2^20 cells in all), its
+        # Y against the oracle's own draw of its modes
+        from oracle import native
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(12345)
+        per = max(1, ERR_SAMPLE_CELLS // len(recipe))
+        err, checked, t0 = 0.0, 0, time.perf_counter()
+        off = 0
+        for s_, r in enumerate(recipe):
+            n = segs[s_]
+            idx = np.arange(n) if n <= per else np.sort(rng.choice(n, per, replace=False))
+            c = np.stack([cc[off + idx] for cc in cells[:r["dim"]]], axis=-1)
+            om = oracle_modes_for(dict(r, seed=r["seed"] + 100000 * rank), r["dim"], r["seed"] + 100000 * rank)
+            y = items[s_][4]["Y"].cpu().numpy()[idx]
+            err = max(err, float(np.max(np.abs(y - native.synth(om["a"], om["amp"], om["psi"], r["mean"], c))))
+                      / math.sqrt(r["sigma2"]))
+            checked += len(idx)
+            off += n
+        res["fp64_check"] = {"max_abs_err_sigma": err, "cells": checked, "of_cells": int(sum(segs)),
+                             "tol_sigma": 1e-5, "within_tol": bool(err <= 1e-5), "oracle_s": time.perf_counter() - t0}
+    return res
 
 
 def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
@@ -536,7 +700,12 @@ def head_config(scale, cells, modes):
 
 
 def run_reference(args):
-    """--impl reference: the FP64 CPU oracle timed on the host cores."""
+    """--impl reference: the FP64 CPU oracle timed on the host cores.
+
+    Every step evaluates the same seeded sample of the headline workload's
+    cells (sized once, during warm-up, for about one second of oracle work)
+    with the oracle's own modes; ms_per_step is the measured time of that
+    sample, and the rate is cells x modes of the sample per second."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -544,23 +713,40 @@ def run_reference(args):
     from oracle import native
     native.build()
     name = "grid3d_256"
-    steps = []
-    base = None
-    for i in range(args.warmup + args.steps):
-        r = cpu_baseline(W, name, args.scale, target_s=4.0)
-        if i >= args.warmup:
-            steps.append(r)
-        base = r
-    val = float(np.median([s["value"] for s in steps]))
     w = W.WORKLOADS[name]
-    cm = float(len(W.workload_cells(name, args.scale)[0])) * w["n_modes"]
+    cells = W.workload_cells(name, args.scale)
+    c_all = np.stack(cells, axis=-1)
+    M, N = len(c_all), w["n_modes"]
+    m = oracle_modes_for(w, 3, w["seed"])
+    rng = np.random.default_rng(12345)
+    # size the sample: grow until one evaluation takes about a second
+    n = 1024
+    while True:
+        idx = rng.choice(M, min(n, M), replace=False)
+        t0 = time.perf_counter()
+        native.synth(m["a"], m["amp"], m["psi"], w["mean"], c_all[idx])
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or n >= M:
+            break
+        n = int(min(M, n * max(2.0, min(16.0, 1.0 / max(dt, 1e-3)))))
+    sample = c_all[idx]
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        native.synth(m["a"], m["amp"], m["psi"], w["mean"], sample)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    val = len(sample) * float(N) / (ms * 1e-3) / 1e9
+    desc = "%d random cells of %s x %d modes per step, FP64 C + OpenMP" % (len(sample), name, N)
     line = {"impl": "reference", "metric": HEAD_METRIC, "value": val,
             "unit": "Gcell.mode/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": cm / (val * 1e9) * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": head_config(args.scale, int(cm / w["n_modes"]), w["n_modes"]),
-            "cpu_baseline": {"value": val, "unit": "Gcell.mode/s", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
+            "ms_per_step": ms, "sampled_cells": int(len(sample)),
+            "extrapolated_ms_full_size": ms * M / len(sample),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": head_config(args.scale, M, N),
+            "cpu_baseline": {"value": val, "unit": "Gcell.mode/s", "cores": native.threads(), "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": val, "unit": "Gcell.mode/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     emit(args, line)
 
@@ -579,6 +765,9 @@ def main():
     __graft_entry__.build()
     from paper_2212_10961_gb300 import field as F
     from paper_2212_10961_gb300 import workloads as W
+    if rank == 0:
+        from oracle import native
+        native.build()  # the FP64 accuracy checks run outside every timed region
 
     sms, _ = F.device_info()
     clocks = ClockSampler(local)
@@ -589,6 +778,8 @@ def main():
         head = bench_forward(torch, F, W, "grid3d_256", rank, world, args.steps, args.warmup, args.scale)
     if args.only in ("all", "bwd"):
         extra["fwd_bwd"] = bench_fwd_bwd(torch, F, W, rank, world, args.steps, args.warmup, args.scale)
+        extra["calibration_autograd"] = bench_calibration_autograd(torch, F, W, rank, world, args.steps,
+                                                                   args.warmup, args.scale)
     if args.only in ("all", "batched"):
         extra["batched"] = bench_batched(torch, F, W, rank, world, max(3, args.steps // 2), args.warmup, args.scale,
                                          "auto" if args.batched_tile == "auto" else int(args.batched_tile))
@@ -615,13 +806,22 @@ def main():
     ck = clocks.stop()
     if rank != 0:
         return
-    y_seed_head = head.pop("y_seed", None) if head is not None else None
+    if head is not None:
+        head.pop("y_seed", None)
     for v in extra.values():
         v.pop("y_seed", None)
     for k, v in extra.items():
         v["gcell_modes_per_s"] = v["cell_modes_per_step"] * world / (v["ms_per_step"] * 1e-3) / 1e9
         if "kernel_ms" in v:
             v["roofline"] = roofline(v["kernel_ms"], v["cell_modes_per_step"], ck, sms)
+    if k_b := extra.get("batched"):
+        # one cosine per lane comes from the FMA pipe: the MUFU pipe's share of the work
+        r = roofline(k_b["ms_per_step"], k_b["cell_modes_per_step"], ck, sms)
+        r["mufu_frac"] = r["frac"] * k_b["mufu_share"]
+        r["peak_basis"] += "; mufu_frac counts only the %.4f of the cosines on the MUFU pipe" % k_b["mufu_share"]
+        k_b["roofline"] = r
+    if (k_ca := extra.get("calibration_autograd")) and (k_fb := extra.get("fwd_bwd")):
+        k_ca["vs_fwd_bwd_device_ms"] = k_ca["ms_per_step"] / (k_fb["fwd_ms"] + k_fb["bwd_ms"])
     if k_fb := extra.get("fwd_bwd"):
         # forward+backward SFU roofline: 3 MUFU per cell-mode (cos; sin and cos)
         k_fb["roofline_fwd_bwd"] = {
@@ -639,8 +839,8 @@ def main():
         "value": value, "unit": "Gcell.mode/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": dict(head_config(args.scale, head["cells"], head["modes"]),
-                       plan_ms_once_per_mesh=head["plan_ms"]),
+        "config": head_config(args.scale, head["cells"], head["modes"]),
+        "plan_ms_once_per_mesh": head["plan_ms"],
         "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms,
                              HEAD_TRAFFIC_BYTES if args.scale == 1 else None),
         "kernel_ms": head["kernel_ms"], "kernel_ms_median": head["kernel_ms_median"],
@@ -648,7 +848,7 @@ def main():
         "gpu_launches": head["launches_in_timed_region"],
         "clocks": ck,
     }
-    for k in ("s1_host", "map_standalone"):
+    for k in ("s1_host", "map_standalone", "fp64_check"):
         if k in head:
             line[k] = head[k]
     if e2e:
@@ -659,7 +859,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         from oracle import native
         native.build()
-        line["cpu_baseline"] = cpu_baseline(W, "grid3d_256", args.scale, y_gpu=y_seed_head)
+        line["cpu_baseline"] = cpu_baseline(W, "grid3d_256", args.scale)
     emit(args, line)
 
 

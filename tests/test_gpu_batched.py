@@ -1,12 +1,13 @@
 """GPU checks of the batched ensemble path (S6): one persistent launch over
 realisations of uneven size, dimension, mode count and covariance, against
-the single-realisation path and the FP64 oracle; CUDA-graph replay."""
+the single-realisation path and the FP64 oracle (Y, lognormal K and the
+facies of every item); CUDA-graph replay."""
 import math
 
 import numpy as np
 import pytest
 
-from helpers import check_forward, gpu_env, oracle_field, oracle_modes, to_dev
+from helpers import check_facies, check_forward, check_lognormal, gpu_env, oracle_field, oracle_modes, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -79,9 +80,12 @@ def test_batched_matches_single_and_oracle(env, tile_cells):
         r = recipe[s]
         om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
         cells = W.grid_centres(r["shape"])
-        check_forward(yb, oracle_field(om, r["mean"], cells), p.sigma, "batch item %d" % s)
-        assert np.array_equal(out["facies"].cpu().numpy(), single["facies"].cpu().numpy()) or \
-            np.mean(out["facies"].cpu().numpy() != single["facies"].cpu().numpy()) < 1e-3
+        y_or = oracle_field(om, r["mean"], cells)
+        check_forward(yb, y_or, p.sigma, "batch item %d" % s)
+        # K and the facies of the persistent kernel against the oracle field
+        # (Sec. 3.1 truncation rule), with the band of the single path
+        check_lognormal(out["K"].cpu().numpy(), y_or, p.sigma)
+        check_facies(out["facies"].cpu().numpy(), y_or, (0.0,), p.sigma)
 
 
 def test_graph_replay(env):
@@ -116,8 +120,12 @@ def test_ensemble256_sampled(env):
         cells = W.grid_centres(r["shape"])
         idx = rng.choice(len(cells[0]), min(4000, len(cells[0])), replace=False)
         om = oracle_modes(r["family"], r["sigma2"], r["ell"], r["dim"], r["n_modes"], r["seed"])
-        yb = items[s][4]["Y"].cpu().numpy()[idx]
-        check_forward(yb, oracle_field(om, r["mean"], cells, idx), math.sqrt(r["sigma2"]), "ensemble %d" % s)
+        out = items[s][4]
+        y_or = oracle_field(om, r["mean"], cells, idx)
+        sig = math.sqrt(r["sigma2"])
+        check_forward(out["Y"].cpu().numpy()[idx], y_or, sig, "ensemble %d" % s)
+        check_lognormal(out["K"].cpu().numpy()[idx], y_or, sig)
+        check_facies(out["facies"].cpu().numpy()[idx], y_or, (0.0,), sig)
 
 
 def test_autotune_picks_a_candidate_and_stays_correct(env):
