@@ -63,7 +63,7 @@ struct BwdArgs {
     const float* gY;
     double* part;     // [splits][n_pad][5]
     double* gpart;    // [splits]
-    double* contrib;  // [n_pad][kContrib]: (A/sigma) dA, dl terms (3), dR terms (9)
+    double* contrib;  // [kContrib][n_pad]: (A/sigma) dA, dl terms (3), dR terms (9)
     grf_grads g;
 };
 
@@ -284,20 +284,38 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
 }
 
 // Kernel 2: per mode, fixed-order sum over splits, chain rule, scatter to the
-// original mode index.
-__global__ void bwd_reduce_kernel(BwdArgs args) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= args.n_pad) return;
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int s = 0; s < args.splits; ++s) {
-        const double* p = args.part + (static_cast<int64_t>(s) * args.n_pad + m) * 5;
+// original mode index.  A block owns 32 modes (one per lane); warp w sums
+// the splits w, w + 8, w + 16, ... in increasing order (coalesced rows of the
+// partials, many loads in flight), and warp 0 adds the 8 warp sums in warp
+// order: a fixed order, so the result does not depend on timing.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRedWarps) bwd_reduce_kernel(BwdArgs args) {
+    __shared__ double red[kRedWarps][32][5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = blockIdx.x * 32 + lane;  // n_pad is a multiple of 128
+    {
+        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int s = warp; s < args.splits; s += kRedWarps) {
+            const double* p = args.part + (static_cast<int64_t>(s) * args.n_pad + m) * 5;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) v[q] += p[q];
+            for (int q = 0; q < 5; ++q) v[q] += p[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) red[warp][lane][q] = v[q];
     }
+    __syncthreads();
+    if (warp != 0) return;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < kRedWarps; ++w)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] += red[w][lane][q];
     const int j = args.order[m];
-    double* ct = args.contrib + static_cast<int64_t>(m) * kContrib;
+    const int64_t np = args.n_pad;
+    double* ct = args.contrib + m;  // contrib[q * n_pad + m]
     if (j < 0) {
-        for (int q = 0; q < kContrib; ++q) ct[q] = 0.0;
+        for (int q = 0; q < kContrib; ++q) ct[q * np] = 0.0;
         return;
     }
     const float4 h = args.hot[m];
@@ -340,43 +358,54 @@ __global__ void bwd_reduce_kernel(BwdArgs args) {
         }
         if (c < d && args.g.dkappa != nullptr)
             args.g.dkappa[static_cast<int64_t>(j) * d + c] = gs * (du / (kTwoPi * args.ell[c]));
-        ct[1 + c] = c < d ? -(u / args.ell[c]) * du : 0.0;
+        ct[(1 + c) * np] = c < d ? -(u / args.ell[c]) * du : 0.0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) ct[4 + c * 3 + q] = (c < d && q < d) ? u * e[q] : 0.0;
+        for (int q = 0; q < 3; ++q) ct[(4 + c * 3 + q) * np] = (c < d && q < d) ? u * e[q] : 0.0;
     }
 }
 
-// Kernel 3: scalar gradients, one block, fixed-order reductions.
-__global__ void __launch_bounds__(256) bwd_scalar_kernel(BwdArgs args) {
-    __shared__ double red[256];
-    const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
-    for (int q = 0; q < kContrib; ++q) {
-        double acc = 0.0;
-        for (int m = threadIdx.x; m < args.n_pad; m += 256)
-            acc += args.contrib[static_cast<int64_t>(m) * kContrib + q];
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            if (q == 0) {
-                args.g.dsigma[0] = gs * red[0];
-                if (args.g.dsigma2 != nullptr) args.g.dsigma2[0] = gs * (red[0] / (2.0 * args.sigma));
-            } else if (q < 4) {
-                if (q - 1 < args.dim) args.g.dell[q - 1] = gs * red[0];
-            } else if (args.g.drot != nullptr) {
-                const int c = (q - 4) / 3, e = (q - 4) % 3;
-                if (c < args.dim && e < args.dim) args.g.drot[c * args.dim + e] = gs * red[0];
-            }
-        }
-        __syncthreads();
+// Kernel 3: scalar gradients, one block.  Every thread first sums its
+// strided share of all kContrib rows (and of the per-split sums of g) with
+// all loads in flight, then each row is reduced by warp butterflies and the
+// warp sums added in warp order: a fixed order throughout.
+constexpr int kScalarThreads = 512;
+
+__global__ void __launch_bounds__(kScalarThreads) bwd_scalar_kernel(BwdArgs args) {
+    constexpr int kRows = kContrib + 1;  // + the sum of g (dmu)
+    __shared__ double red[kScalarThreads / 32][kRows];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc[kRows];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) acc[q] = 0.0;
+    const int64_t np = args.n_pad;
+    for (int64_t m = threadIdx.x; m < np; m += kScalarThreads)
+#pragma unroll
+        for (int q = 0; q < kContrib; ++q) acc[q] += args.contrib[q * np + m];
+    for (int k = threadIdx.x; k < args.splits; k += kScalarThreads) acc[kContrib] += args.gpart[k];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        if (lane == 0) red[warp][q] = acc[q];
     }
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < args.splits; ++k) s += args.gpart[k];
-        args.g.dmu[0] = gs * s;
+    __syncthreads();
+    if (threadIdx.x >= kRows) return;
+    const int q = threadIdx.x;
+    double t = 0.0;
+    for (int w = 0; w < kScalarThreads / 32; ++w) t += red[w][q];
+    const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
+    if (q == 0) {
+        args.g.dsigma[0] = gs * t;
+        if (args.g.dsigma2 != nullptr) args.g.dsigma2[0] = gs * (t / (2.0 * args.sigma));
+    } else if (q < 4) {
+        if (q - 1 < args.dim) args.g.dell[q - 1] = gs * t;
+    } else if (q < kContrib) {
+        if (args.g.drot != nullptr) {
+            const int c = (q - 4) / 3, e = (q - 4) % 3;
+            if (c < args.dim && e < args.dim) args.g.drot[c * args.dim + e] = gs * t;
+        }
+    } else {
+        args.g.dmu[0] = gs * t;
     }
 }
 
@@ -516,8 +545,8 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
         }
         count_launches(1);
     }
-    bwd_reduce_kernel<<<static_cast<unsigned>((n_pad + 255) / 256), 256, 0, st>>>(a);
-    bwd_scalar_kernel<<<1, 256, 0, st>>>(a);
+    bwd_reduce_kernel<<<static_cast<unsigned>(n_pad / 32), 32 * kRedWarps, 0, st>>>(a);
+    bwd_scalar_kernel<<<1, kScalarThreads, 0, st>>>(a);
     count_launches(2);
     return cudaGetLastError();
 }
