@@ -4,7 +4,8 @@ Headline step (default): one realisation of the 3-D workload
   256^3 unit-cube cell centres (16,777,216 cells), N = 4096 modes,
   exponential covariance, l = (0.2, 0.2, 0.05), sigma^2 = 4, FP32 field,
   lognormal K and a 3-facies map at the Gaussian 1/3, 2/3 quantiles:
-mode drawing (host C++), table packing and upload, and the fused synthesis
+a new realisation per step (modes drawn and packed by the library's native
+prefetcher threads, table upload on a copy stream) and the fused synthesis
 kernel writing Y, K and facies.  Metric: Gcell.mode/s = cells x modes per
 second.  The same JSON line also reports the forward+backward step (128^3,
 N = 2048, mismatch loss and adjoint), the batched ensemble (256 realisations
@@ -249,35 +250,46 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     plan = F.CellPlan(*dev_cells)
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t0) * 1e3
-    out = maps.allocate(M, torch.device("cuda"))
     base_seed = w["seed"] + 1000 * rank
-    ring = [F.ModeTable.from_modes(F.gen_modes(params_for(F, w, dim, base_seed + k))) for k in range(2)]
+    # a new realisation every step: drawn and packed ahead by the native
+    # prefetcher's worker threads; its upload runs on a copy stream into one
+    # of two device tables while the previous synthesis runs
+    pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=4)
+    ps = F.PreparedSynth(params_for(F, w, dim, base_seed), plan, 0, maps)
+    out = ps.out
+    tabs = [F.ModeTable.device_only(N, dim) for _ in range(2)]
     st = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    used = [torch.cuda.Event(), torch.cuda.Event()]  # last synthesis reading tabs[k] has run
+    up = [torch.cuda.Event(), torch.cuda.Event()]
     kev = []  # (start, end) events around each synthesis kernel
 
     def step(i):
-        p = params_for(F, w, dim, base_seed + i)
-        m = F.gen_modes(p)
-        tab = ring[i % 2]
-        tab.update(m["amp"], m["psi"], m["a"])
+        k = i % 2
+        copy.wait_event(used[k])
+        pf.next(tabs[k], stream=copy)
+        up[k].record(copy)
+        st.wait_event(up[k])
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
-        F.synth(tab, p, plan, 0, maps, out)
+        ps(tabs[k])
         b.record(st)
+        used[k].record(st)
         kev.append((a, b))
 
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     torch.cuda.synchronize()
+    pf.close()
     kern_all = [a.elapsed_time(b) for a, b in kev[warmup:]]
     kern_ms = float(np.mean(kern_all))
     assert plan.status() == 0
     # field of the workload's own seed, for the accuracy check against the FP64 oracle
     p0 = params_for(F, w, dim, w["seed"])
     m0 = F.gen_modes(p0)
-    ring[0].update(m0["amp"], m0["psi"], m0["a"], kappa=m0["kappa"])
+    ring = [F.ModeTable.from_modes(m0)]
     o0 = F.synth(ring[0], p0, plan, 0, F.MapSpec(y=True, thresholds=thr, facies=len(thr) > 0))
     y_seed = o0["Y"].cpu().numpy()
     fac_seed = o0["facies"].cpu().numpy() if "facies" in o0 else None

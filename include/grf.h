@@ -193,6 +193,40 @@ int grf_pack_table(const grf_modes *m, void *host_table, size_t bytes);
 int grf_upload_table(const void *host_table, void *dev_table, size_t bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Mode prefetcher (many realisations of one parameter set)             */
+/* ------------------------------------------------------------------ */
+/*
+ * Monte-Carlo runs draw a new realisation of the same field many times
+ * (Sec. 4.1: a realisation is fixed by its parameters and seed).  The
+ * prefetcher draws (grf_gen_modes) and packs (grf_pack_table, with kappa)
+ * realisation k = 0, 1, 2, ... with seed p->seed + k on `threads` host
+ * worker threads of its own, up to `depth` realisations ahead of use, into a
+ * ring of `depth` caller-provided staging buffers (host_slots[s], slot_bytes
+ * >= grf_table_bytes(p->n_modes) each; pinned memory makes the uploads
+ * asynchronous).  The caller's thread then only enqueues uploads.
+ *
+ * grf_prefetch_create: p is copied; the current device is recorded and made
+ * current on the workers.  GRF_EINVAL for bad parameters, depth outside
+ * [2, 64], threads outside [1, 64] or a NULL slot; GRF_EWORKSPACE for slots
+ * too small; GRF_ECUDA if events cannot be created.
+ * grf_prefetch_next: waits (on the host) for the next realisation in order,
+ * enqueues its upload into dev_table (device, 256-byte aligned, bytes >=
+ * grf_table_bytes) on `stream` and returns its seed in *seed_out (may be
+ * NULL).  A slot is reused only after its upload has run (an event recorded
+ * on `stream`).  A worker's failure (e.g. a sampler that does not accept) is
+ * returned by the next call with its message.  Calls on one prefetcher must
+ * come from one thread at a time.
+ * grf_prefetch_destroy: stops and joins the workers, waits for uploads still
+ * pending from the staging buffers (the caller may free them afterwards) and
+ * frees the prefetcher.  NULL is ignored.
+ */
+typedef struct grf_prefetch grf_prefetch;
+int grf_prefetch_create(const grf_params *p, int32_t depth, int32_t threads, void *const *host_slots,
+                        size_t slot_bytes, grf_prefetch **out);
+int grf_prefetch_next(grf_prefetch *pf, void *dev_table, size_t bytes, void *stream, uint64_t *seed_out);
+int grf_prefetch_destroy(grf_prefetch *pf);
+
+/* ------------------------------------------------------------------ */
 /* Cell plan (spatial binning of arbitrary cell centres)                */
 /* ------------------------------------------------------------------ */
 /*

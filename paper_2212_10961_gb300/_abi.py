@@ -90,6 +90,12 @@ _SIGS = {
     "grf_gen_modes": (ctypes.c_int, [ctypes.POINTER(grf_params), ctypes.POINTER(grf_modes)]),
     "grf_reparam_modes": (ctypes.c_int, [ctypes.POINTER(grf_params), ctypes.POINTER(grf_modes)]),
     "grf_table_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "grf_prefetch_create": (ctypes.c_int, [ctypes.POINTER(grf_params), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "grf_prefetch_next": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "grf_prefetch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "grf_pack_table": (ctypes.c_int, [ctypes.POINTER(grf_modes), ctypes.c_void_p, ctypes.c_size_t]),
     "grf_upload_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "grf_plan_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),

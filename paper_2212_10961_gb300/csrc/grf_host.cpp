@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <condition_variable>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -1057,6 +1059,204 @@ int grf_batch_launch(void* workspace, void* stream) try {
     const int err = launch_synth_batched(workspace, bm.hdr, status, counter, stream);
     if (err != cudaSuccess) return cuda_fail(err, "batched kernel");
     return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+// ---------------------------------------------------------------------------
+// Mode prefetcher: realisations drawn and packed ahead of use on host threads
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct grf_prefetch {
+    enum State { kFree, kDrawing, kReady, kUploaded };
+    grf_params p{};
+    int32_t depth = 0;
+    int device = 0;
+    size_t table_bytes = 0;
+    std::vector<void*> slots;        // caller's pinned host staging buffers
+    std::vector<cudaEvent_t> events; // upload of each slot, recorded by grf_prefetch_next
+    std::vector<State> state;
+    std::vector<int64_t> index;      // realisation a ready slot holds
+    int64_t next_draw = 0;           // next realisation a worker claims
+    int64_t next_use = 0;            // next realisation grf_prefetch_next hands out
+    bool stop = false;
+    int error = GRF_OK;
+    std::string error_msg;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::thread> workers;
+
+    void fail_with(int code, const std::string& msg) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (error == GRF_OK) {
+            error = code;
+            error_msg = msg;
+        }
+        cv.notify_all();
+    }
+
+    // Worker: claim the next realisation k once slot k % depth is no longer
+    // needed (realisation k - depth handed out and its upload finished), draw
+    // its modes with seed p.seed + k, pack them into the slot, mark it ready.
+    void work() {
+        if (cudaSetDevice(device) != cudaSuccess) {
+            fail_with(GRF_ECUDA, "prefetch worker: cudaSetDevice failed");
+            return;
+        }
+        const int64_t N = p.n_modes;
+        const int d = p.dim;
+        std::vector<double> kappa, rho, psi, a, amp;
+        try {
+            kappa.resize(N * d);
+            rho.resize(N);
+            psi.resize(N);
+            a.resize(N * d);
+            amp.resize(N);
+        } catch (const std::bad_alloc&) {
+            fail_with(GRF_ENOMEM, "prefetch worker: host allocation failed");
+            return;
+        }
+        grf_modes m{};
+        m.n = N;
+        m.dim = d;
+        m.kappa = kappa.data();
+        m.rho = rho.data();
+        m.psi = psi.data();
+        m.a = a.data();
+        m.amp = amp.data();
+        for (;;) {
+            int64_t k;
+            int32_t s;
+            bool wait_upload;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || error != GRF_OK || next_draw - next_use < depth; });
+                if (stop || error != GRF_OK) return;
+                k = next_draw++;
+                s = static_cast<int32_t>(k % depth);
+                wait_upload = state[s] == kUploaded;
+                state[s] = kDrawing;
+            }
+            if (wait_upload && cudaEventSynchronize(events[s]) != cudaSuccess) {
+                fail_with(GRF_ECUDA, "prefetch worker: waiting for a staging slot's upload failed");
+                return;
+            }
+            grf_params pk = p;
+            pk.seed = p.seed + static_cast<uint64_t>(k);
+            int rc = grf_gen_modes(&pk, &m);
+            if (rc == GRF_OK) rc = grf_pack_table(&m, slots[s], table_bytes);
+            if (rc != GRF_OK) {
+                fail_with(rc, std::string("prefetch worker: ") + grf_last_error());
+                return;
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            state[s] = kReady;
+            index[s] = k;
+            cv.notify_all();
+        }
+    }
+};
+
+extern "C" {
+
+int grf_prefetch_create(const grf_params* p, int32_t depth, int32_t threads, void* const* host_slots,
+                        size_t slot_bytes, grf_prefetch** out) try {
+    TraceRange trace_("grf_prefetch_create");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!out) return fail(GRF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (depth < 2 || depth > 64) return fail(GRF_EINVAL, "depth must be in [2, 64]");
+    if (threads < 1 || threads > 64) return fail(GRF_EINVAL, "threads must be in [1, 64]");
+    if (!host_slots) return fail(GRF_EINVAL, "host_slots is NULL");
+    for (int32_t s = 0; s < depth; ++s)
+        if (!host_slots[s]) return fail(GRF_EINVAL, "host slot %d is NULL", s);
+    const size_t tb = grf_table_bytes(p->n_modes);
+    if (slot_bytes < tb) return fail(GRF_EWORKSPACE, "staging slots of %zu bytes < %zu needed", slot_bytes, tb);
+    alloc_point();
+    std::unique_ptr<grf_prefetch> pf(new grf_prefetch());
+    pf->p = *p;
+    pf->depth = depth;
+    pf->table_bytes = tb;
+    if (cudaGetDevice(&pf->device) != cudaSuccess) return fail(GRF_ECUDA, "cudaGetDevice failed");
+    pf->slots.assign(host_slots, host_slots + depth);
+    pf->state.assign(depth, grf_prefetch::kFree);
+    pf->index.assign(depth, -1);
+    for (int32_t s = 0; s < depth; ++s) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            for (cudaEvent_t x : pf->events) cudaEventDestroy(x);
+            return fail(GRF_ECUDA, "event creation failed");
+        }
+        pf->events.push_back(e);
+    }
+    try {
+        for (int32_t t = 0; t < threads; ++t) pf->workers.emplace_back(&grf_prefetch::work, pf.get());
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(pf->mu);
+            pf->stop = true;
+        }
+        pf->cv.notify_all();
+        for (auto& th : pf->workers) th.join();
+        for (cudaEvent_t x : pf->events) cudaEventDestroy(x);
+        throw;
+    }
+    *out = pf.release();
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+int grf_prefetch_next(grf_prefetch* pf, void* dev_table, size_t bytes, void* stream, uint64_t* seed_out) try {
+    TraceRange trace_("grf_prefetch_next");
+    if (!pf || !dev_table) return fail(GRF_EINVAL, "prefetcher or device table is NULL");
+    if (!aligned256(dev_table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
+    if (bytes < pf->table_bytes) return fail(GRF_EWORKSPACE, "device table %zu bytes < %zu needed", bytes,
+                                             pf->table_bytes);
+    std::unique_lock<std::mutex> lk(pf->mu);
+    const int64_t k = pf->next_use;
+    const int32_t s = static_cast<int32_t>(k % pf->depth);
+    pf->cv.wait(lk, [&] {
+        return pf->error != GRF_OK || (pf->state[s] == grf_prefetch::kReady && pf->index[s] == k);
+    });
+    if (pf->error != GRF_OK) return fail(pf->error, "%s", pf->error_msg.c_str());
+    lk.unlock();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(dev_table, pf->slots[s], pf->table_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(pf->events[s], st);
+    if (e != cudaSuccess) {
+        pf->fail_with(GRF_ECUDA, "prefetch: table upload failed");
+        return cuda_fail(e, "prefetch table upload");
+    }
+    lk.lock();
+    pf->state[s] = grf_prefetch::kUploaded;
+    pf->next_use = k + 1;
+    pf->cv.notify_all();
+    if (seed_out) *seed_out = pf->p.seed + static_cast<uint64_t>(k);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+int grf_prefetch_destroy(grf_prefetch* pf) try {
+    if (!pf) return GRF_OK;
+    {
+        std::lock_guard<std::mutex> lk(pf->mu);
+        pf->stop = true;
+    }
+    pf->cv.notify_all();
+    for (auto& th : pf->workers) th.join();
+    int rc = GRF_OK;
+    for (int32_t s = 0; s < pf->depth; ++s) {
+        // the caller may free the staging buffers once this returns
+        if (pf->state[s] == grf_prefetch::kUploaded && cudaEventSynchronize(pf->events[s]) != cudaSuccess)
+            rc = fail(GRF_ECUDA, "waiting for an upload from a staging slot failed");
+        cudaEventDestroy(pf->events[s]);
+    }
+    delete pf;
+    return rc;
 } catch (...) {
     return host_exception();
 }

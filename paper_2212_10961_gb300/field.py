@@ -14,6 +14,7 @@ import ctypes
 import dataclasses
 import json
 import math
+import os
 from dataclasses import dataclass, field as dc_field
 from typing import Optional, Sequence
 
@@ -260,9 +261,63 @@ class ModeTable:
     def from_modes(cls, modes, **kw):
         return cls(modes["amp"], modes["psi"], modes["a"], kappa=modes.get("kappa"), **kw)
 
+    @classmethod
+    def device_only(cls, n_modes, dim, device=None):
+        """A device table with no host copy, filled by ModePrefetcher.next."""
+        t = cls.__new__(cls)
+        t.n_modes, t.dim = int(n_modes), int(dim)
+        t.nbytes = int(lib().grf_table_bytes(t.n_modes))
+        if t.nbytes == 0:
+            raise ValueError("n_modes out of range")
+        t.host = None
+        t.dev = torch.empty(t.nbytes, dtype=torch.uint8,
+                            device=device or torch.device("cuda", torch.cuda.current_device()))
+        t._uploaded = torch.cuda.Event()
+        return t
+
     @property
     def ptr(self):
         return _ptr(self.dev)
+
+
+class ModePrefetcher:
+    """Realisations k = 0, 1, 2, ... of one parameter set (seed params.seed + k)
+    drawn and packed ahead of use by native worker threads into a ring of
+    pinned staging buffers (grf_prefetch_*); next() only enqueues the upload
+    of the next one into a device table.  For Monte-Carlo loops over many
+    realisations of small fields, where drawing on the launching thread would
+    leave the GPU idle."""
+
+    def __init__(self, params: FieldParams, depth=4, threads=None):
+        self.params = params
+        self.nbytes = int(lib().grf_table_bytes(int(params.n_modes)))
+        threads = int(threads or max(1, min(8, (os.cpu_count() or 2) // 2)))
+        self.host = [torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(depth)]
+        slots = (ctypes.c_void_p * depth)(*[h.data_ptr() for h in self.host])
+        h = ctypes.c_void_p()
+        check(lib().grf_prefetch_create(ctypes.byref(params.to_c()), int(depth), threads, slots, self.nbytes,
+                                        ctypes.byref(h)))
+        self._h = h
+
+    def next(self, table: ModeTable, stream=None):
+        """Upload the next realisation into `table` (ModeTable.device_only of
+        the same N and dim) on `stream`; returns its seed."""
+        seed = ctypes.c_uint64(0)
+        check(lib().grf_prefetch_next(self._h, table.ptr, table.nbytes, _stream_handle(stream),
+                                      ctypes.byref(seed)))
+        return seed.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._h = None
+            check(lib().grf_prefetch_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # interpreter shutdown
+            pass
 
 
 class CellPlan:
@@ -399,6 +454,31 @@ def synth(table: ModeTable, params: FieldParams, plan: CellPlan, segment=0, maps
                                 ctypes.byref(maps.to_c()), ctypes.byref(_outputs_struct(out)),
                                 _ptr(ws), nbytes, _stream_handle(stream)))
     return out
+
+
+class PreparedSynth:
+    """grf_synth_field with its argument structs, outputs and workspace built
+    once, for many realisations on the same cells (only the table changes
+    from call to call); returns the outputs dict, overwritten by each call."""
+
+    def __init__(self, params: FieldParams, plan: CellPlan, segment=0, maps=None, out=None, stream=None):
+        maps = maps or MapSpec()
+        n = plan.segment_size(segment)
+        self.out = out if out is not None else maps.allocate(n, plan.buf.device)
+        self.plan = plan
+        self._p = params.to_c()
+        self._m = maps.to_c()
+        self._o = _outputs_struct(self.out)
+        self._nbytes = int(lib().grf_synth_workspace_bytes(n))
+        self._ws = torch.empty(max(self._nbytes, 256), dtype=torch.uint8, device=plan.buf.device)
+        self._stream = None if stream is None else _stream_handle(stream)
+        self._args = (ctypes.byref(self._p), plan.ptr, int(segment), ctypes.byref(self._m), ctypes.byref(self._o),
+                      _ptr(self._ws), self._nbytes)
+
+    def __call__(self, table: ModeTable, stream=None):
+        st = _stream_handle(stream) if stream is not None else (self._stream or _stream_handle(None))
+        check(lib().grf_synth_field(table.ptr, *self._args, st))
+        return self.out
 
 
 def map_property(Y, maps: MapSpec, mean, sigma, out=None, stream=None):

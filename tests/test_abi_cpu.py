@@ -423,3 +423,24 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert "raised" in r.stdout and "absent.so" in r.stdout
+
+
+def test_prefetch_rejects_bad_arguments(abi):
+    # argument checks come before any CUDA call, so they run without a GPU
+    from paper_2212_10961_gb300 import field as F
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=100, seed=1)
+    L = abi.lib()
+    nb = L.grf_table_bytes(100)
+    bufs = [(ctypes.c_uint8 * nb)() for _ in range(3)]
+    slots = (ctypes.c_void_p * 3)(*[ctypes.addressof(b) for b in bufs])
+    h = ctypes.c_void_p()
+    pc = p.to_c()
+    assert L.grf_prefetch_create(ctypes.byref(pc), 1, 2, slots, nb, ctypes.byref(h)) == abi.GRF_EINVAL
+    assert L.grf_prefetch_create(ctypes.byref(pc), 65, 2, slots, nb, ctypes.byref(h)) == abi.GRF_EINVAL
+    assert L.grf_prefetch_create(ctypes.byref(pc), 3, 0, slots, nb, ctypes.byref(h)) == abi.GRF_EINVAL
+    assert L.grf_prefetch_create(ctypes.byref(pc), 3, 2, slots, nb - 1, ctypes.byref(h)) == abi.GRF_EWORKSPACE
+    assert L.grf_prefetch_create(ctypes.byref(pc), 3, 2, None, nb, ctypes.byref(h)) == abi.GRF_EINVAL
+    bad = _params(abi, sigma2=-1.0)
+    assert L.grf_prefetch_create(ctypes.byref(bad), 3, 2, slots, nb, ctypes.byref(h)) == abi.GRF_EINVAL
+    assert L.grf_prefetch_next(None, None, 0, None, None) == abi.GRF_EINVAL
+    assert L.grf_prefetch_destroy(None) == abi.GRF_OK

@@ -53,9 +53,12 @@ def test_fused_mismatch_equals_synthesis_then_loss(env, shape, dim, split):
         n = len(cells[0])
         small = torch.empty(int(F.lib().grf_synth_mismatch_workspace_bytes(n)) -
                             int(F.lib().grf_synth_workspace_bytes(n)), dtype=torch.uint8, device="cuda")
-        ws_small = F.Workspace()
-        ws_small.buf = small
-        loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True, want_K=True, workspace=ws_small)
+
+        class Fixed:  # hands out exactly this buffer (a Workspace would grow it)
+            def get(self, nbytes, device):
+                return small
+
+        loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True, want_K=True, workspace=Fixed())
         ref = F.synth(gf.table, p, plan, 0, F.MapSpec(y=True, lognormal=True), workspace=False)
         loss_u, gY_u = F.mismatch_grad(ref["K"], T)
     torch.cuda.synchronize()
