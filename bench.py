@@ -278,11 +278,13 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
         used[k].record(st)
         kev.append((a, b))
 
+    F.take_path_counts()  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     torch.cuda.synchronize()
     pf.close()
+    gen_w, lat_w = F.take_path_counts()
     kern_all = [a.elapsed_time(b) for a, b in kev[warmup:]]
     kern_ms = float(np.mean(kern_all))
     assert plan.status() == 0
@@ -300,7 +302,9 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
            "kernel_ms_median": max_over_ranks(torch, world, float(np.median(kern_all))),
            "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
-           "launches_per_step": per_step, "y_seed": y_seed}
+           "launches_per_step": per_step, "y_seed": y_seed,
+           "path_warps": {"general": gen_w, "lattice": lat_w},
+           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
     if check and rank == 0:
         res["fp64_check"] = fp64_check(cells, y_seed, oracle_modes_for(w, dim, w["seed"]), w["mean"], sig,
                                        thresholds=thr, facies=fac_seed)
@@ -447,15 +451,19 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
         c.record(st)
         kev.append((a, b, c))
 
+    F.take_path_counts()  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
+    gen_w, lat_w = F.take_path_counts()
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, c in kev[warmup:]]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for a, b, c in kev[warmup:]]))
     res = {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
            "ms_per_step": ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "cell_modes_per_step": float(M) * N,
            "launches_per_step": launches / float(steps + warmup),
-           "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)"}
+           "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)",
+           "path_warps": {"general": gen_w, "lattice": lat_w},
+           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
     if rank == 0:
         res["fp64_check"] = grad_check_40(torch, F, W)
     return res
@@ -547,12 +555,16 @@ def bench_bitruncated(torch, F, W, rank, world, steps, warmup, scale):
     t = W.quantile_thresholds(0.0, math.sqrt(w["sigma2"]), (1.0 / 3.0, 2.0 / 3.0))
     rule = [[0, 1], [2, 3], [4, 5]]
     values = [0.01, 0.1, 1.0, 10.0, 100.0, 1000.0]
+    F.take_path_counts()  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: pg.synth(plan, t, (0.0,), rule, values))
     launches = F.launch_count() - l0
+    gen_w, lat_w = F.take_path_counts()
     res = {"workload": "grid3d_256 bitruncated: exponential l=(0.2,0.2,0.05) x Gaussian l=0.1, 3 x 2 rule",
            "cells": M, "modes_per_field": N, "ms_per_step": ms, "cell_modes_per_step": 2.0 * M * N,
-           "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms}
+           "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms,
+           "path_warps": {"general": gen_w, "lattice": lat_w},
+           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
     if rank == 0:
         # both fields against the oracle's own draws (streams 0 and 1), and the
         # merged facies against the rule applied to the oracle fields
@@ -681,22 +693,45 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
-# headline synthesis kernel (synth_fwd_kernel<3,16,4>, 256^3 cells, 4096 modes),
-# from one ncu capture of `bench.py --only fwd --steps 3 --warmup 3`:
-# 271.06 MB read + 116.38 MB written.  Algorithmic: 16 B read (sorted
-# coordinates, permutation) + 9 B written (Y, K, facies) per cell = 419 MB;
-# part of the writes was still in L2 when the launch ended.
-HEAD_TRAFFIC_BYTES = 271.062272e6 + 116.384000e6
+# headline synthesis kernel (synth_fwd_kernel<3,16,4,0> on the lattice path,
+# 256^3 cells, 4096 modes), from one ncu capture of
+# `bench.py --only fwd --steps 3 --warmup 3 --no-cpu-baseline`: 269.62 MB read
+# + 115.69 MB written.  Algorithmic: 16 B read (sorted coordinates,
+# permutation) + 9 B written (Y, K, facies) per cell = 419 MB; part of the
+# writes was still in L2 when the launch ended.
+HEAD_TRAFFIC_BYTES = 269.623552e6 + 115.687168e6
 
 
-def roofline(kern_ms, cell_modes, clocks, sms, traffic=None):
-    peak_max = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 1e9  # Gcell.mode/s at the maximum SM clock
+# FP32 instructions per cell-mode of the lattice path (lanes of 4-cell grid
+# rows): per (lane, mode) the complex corner term (3 FFMA phase, 2 FMUL
+# radian scaling inside the hardware sine/cosine, 2 FMUL by A), the C/4 - 1
+# row phasors (4 each) and per cell 2 FFMA (1 FADD on the first of a row):
+# (7 + 12 + 28) / 16 = 2.94 in 3-D and (6 + 4 + 14) / 8 = 3.0 in 2-D.
+LATTICE_FP32_PER_CELL_MODE = 3.0
+FP32_PER_CLK_PER_SM = 128
+
+
+def roofline(kern_ms, cell_modes, clocks, sms, traffic=None, lattice_share=0.0):
+    """Roofline of a synthesis kernel.  General path: the MUFU pipe, 1
+    hardware cosine per cell-mode.  Lattice path (lattice_share >= 1/2 of the
+    warp tiles): the FP32 pipe at LATTICE_FP32_PER_CELL_MODE instructions per
+    cell-mode (1/8 MUFU per cell-mode); the MUFU fraction is kept beside it."""
+    mufu_peak = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 1e9  # Gcell.mode/s at the maximum SM clock
     achieved = cell_modes / (kern_ms * 1e-3) / 1e9
+    if lattice_share >= 0.5:
+        peak_max = FP32_PER_CLK_PER_SM * sms * 2070e6 / LATTICE_FP32_PER_CELL_MODE / 1e9
+        basis = ("lattice path (%.3f of the warp tiles): %d FP32 lanes/clk/SM x %d SMs x 2070 MHz / %.1f FP32 "
+                 "instructions per cell-mode" % (lattice_share, FP32_PER_CLK_PER_SM, sms, LATTICE_FP32_PER_CELL_MODE))
+        per_clk = FP32_PER_CLK_PER_SM / LATTICE_FP32_PER_CELL_MODE
+    else:
+        peak_max = mufu_peak
+        basis = "%d MUFU cos/clk/SM x %d SMs x 2070 MHz (1 MUFU per cell-mode)" % (MUFU_PER_CLK_PER_SM, sms)
+        per_clk = MUFU_PER_CLK_PER_SM
     out = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "Gcell.mode/s",
-           "frac": achieved / peak_max, "traffic": traffic,
-           "peak_basis": "%d MUFU cos/clk/SM x %d SMs x 2070 MHz (1 MUFU per cell-mode)" % (MUFU_PER_CLK_PER_SM, sms)}
+           "frac": achieved / peak_max, "traffic": traffic, "peak_basis": basis,
+           "frac_of_mufu_roofline": achieved / mufu_peak}
     if clocks.get("sm_mhz"):
-        peak_meas = MUFU_PER_CLK_PER_SM * sms * clocks["sm_mhz"] * 1e6 / 1e9
+        peak_meas = per_clk * sms * clocks["sm_mhz"] * 1e6 / 1e9
         out["frac_at_measured_clock"] = achieved / peak_meas
     return out
 
@@ -825,7 +860,8 @@ def main():
     for k, v in extra.items():
         v["gcell_modes_per_s"] = v["cell_modes_per_step"] * world / (v["ms_per_step"] * 1e-3) / 1e9
         if "kernel_ms" in v:
-            v["roofline"] = roofline(v["kernel_ms"], v["cell_modes_per_step"], ck, sms)
+            v["roofline"] = roofline(v["kernel_ms"], v["cell_modes_per_step"], ck, sms,
+                                     lattice_share=v.get("lattice_share", 0.0))
     if k_b := extra.get("batched"):
         # one cosine per lane comes from the FMA pipe: the MUFU pipe's share of the work
         r = roofline(k_b["ms_per_step"], k_b["cell_modes_per_step"], ck, sms)
@@ -840,6 +876,16 @@ def main():
             "achieved": k_fb["cell_modes_per_step"] / ((k_fb["fwd_ms"] + k_fb["bwd_ms"]) * 1e-3) / 1e9,
             "peak": MUFU_PER_CLK_PER_SM * sms * 2070e6 / 3 / 1e9, "unit": "Gcell.mode/s"}
         k_fb["roofline_fwd_bwd"]["frac"] = k_fb["roofline_fwd_bwd"]["achieved"] / k_fb["roofline_fwd_bwd"]["peak"]
+        k_fb["roofline_fwd_bwd"]["peak_basis"] = ("3 MUFU per cell-mode (1 forward cosine, adjoint sine and "
+                                                  "cosine); the forward's own bound is in fwd_roofline")
+        # each half against its own bound
+        k_fb["fwd_roofline"] = roofline(k_fb["fwd_ms"], k_fb["cell_modes_per_step"], ck, sms,
+                                        lattice_share=k_fb.get("lattice_share", 0.0))
+        bw = k_fb["cell_modes_per_step"] / (k_fb["bwd_ms"] * 1e-3) / 1e9
+        bpk = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 2 / 1e9
+        k_fb["bwd_roofline"] = {"bound": "alu", "achieved": bw, "peak": bpk, "unit": "Gcell.mode/s",
+                                "frac": bw / bpk, "peak_basis": "2 MUFU per cell-mode (sine and cosine)",
+                                "note": "adjoint kernel and its two reductions"}
     if head is None:
         head = next(iter(extra.values()))
         emit(args, {"partial": args.only, "results": extra, "clocks": ck})
@@ -854,7 +900,9 @@ def main():
         "config": head_config(args.scale, head["cells"], head["modes"]),
         "plan_ms_once_per_mesh": head["plan_ms"],
         "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms,
-                             HEAD_TRAFFIC_BYTES if args.scale == 1 else None),
+                             HEAD_TRAFFIC_BYTES if args.scale == 1 and HEAD_TRAFFIC_BYTES else None,
+                             head.get("lattice_share", 0.0)),
+        "path_warps": head.get("path_warps"),
         "kernel_ms": head["kernel_ms"], "kernel_ms_median": head["kernel_ms_median"],
         "kernel_ms_best": head["kernel_ms_best"],
         "gpu_launches": head["launches_in_timed_region"],

@@ -572,6 +572,16 @@ int grf_device_info(int32_t *sm_count, int32_t *sm_clock_khz);
 int64_t grf_launch_count(void);
 
 /*
+ * grf_take_path_counts -- warp tiles of 2-D and 3-D single-field syntheses
+ * (grf_synth_field, grf_synth_mismatch) since the last call that took the
+ * general path and the lattice path (lanes holding 4-cell rows of one
+ * Cartesian grid, see the synthesis kernel), then resets both.  A tile split
+ * over mode groups counts once per group.  Synchronises the device.
+ * GRF_EINVAL for NULL pointers, GRF_ECUDA if the counters cannot be read.
+ */
+int grf_take_path_counts(int64_t *general_warps, int64_t *lattice_warps);
+
+/*
  * grf_debug_inject_alloc_failures -- host-side fault injection for tests
  * (the paper has no counterpart).  The next n host allocations made by the
  * library's entry points fail as if the allocator had run out of memory: the

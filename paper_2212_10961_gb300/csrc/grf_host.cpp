@@ -1310,6 +1310,22 @@ int grf_take_index_faults(int64_t* count_out) try {
     return host_exception();
 }
 
+int grf_take_path_counts(int64_t* general_warps, int64_t* lattice_warps) try {
+    if (!general_warps || !lattice_warps) return fail(GRF_EINVAL, "NULL argument");
+    *general_warps = 0;
+    *lattice_warps = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the path counters");
+    unsigned long long g = 0ull, l = 0ull;
+    e = static_cast<cudaError_t>(take_path_counts(&g, &l));
+    if (e != cudaSuccess) return cuda_fail(e, "path counters");
+    *general_warps = static_cast<int64_t>(g);
+    *lattice_warps = static_cast<int64_t>(l);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
 int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) try {
     if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
     const int err = launch_mufu_probe(blocks, iters, sink, stream);

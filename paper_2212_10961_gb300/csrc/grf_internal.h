@@ -235,6 +235,9 @@ int64_t mismatch_partials(int64_t n_cells);
 unsigned long long take_index_faults_fwd();
 unsigned long long take_index_faults_bwd();
 unsigned long long take_index_faults_plan();
+// Warp tiles of single-field synthesis launches that took the general and the
+// lattice path since the last call, then reset (synchronous); cudaError_t.
+int take_path_counts(unsigned long long* general, unsigned long long* lattice);
 size_t synth_workspace_bytes(int64_t n_cells);
 int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
                          int32_t* counter, void* stream);

@@ -28,6 +28,10 @@
 
 namespace grf {
 
+// Warp tiles of single-field launches that took the general path [0] and the
+// lattice path [1] since the last grf_take_path_counts (diagnostics).
+static __device__ unsigned long long g_path_warps[2];
+
 namespace {
 
 constexpr int kWChunk = 128;                 // modes per warp chunk
@@ -46,11 +50,97 @@ struct WarpSmem {
     uint64_t full[kStages];
 };
 
-template <int W>
+// NS > 0 (lattice path enabled): per warp, NS step phasors per mode of the
+// current chunk (see lattice_chunk); NS = 0 keeps one unused entry.
+template <int W, int NS = 0>
 struct FwdSmem {
     WarpSmem w[W];
     FwdDesc desc[W];  // batched: each warp's current realisation
+    float4 stp[W][NS > 0 ? NS * kWChunk / 2 : 1];
 };
+
+// Phase a v in turns, reduced to [-1/2, 1/2], of a = ah + al (FP32 pair) at a
+// point v of one axis: the product ah v split exactly by an FMA, integer
+// parts removed exactly (as phase_exact_turns, without psi).
+__device__ __forceinline__ float axis_turns(float ah, float al, float v) {
+    const float pr = ah * v;
+    const float e = fmaf(ah, v, -pr);
+    return frac_turn(frac_turn(pr) + fmaf(al, v, e));
+}
+
+// Lattice lanes.  When every lane's C cells are the 4 x NY block
+//     (xl + i hx, yl + k hy, zl),  cell c = i + 4 k,
+// of one Cartesian grid (the same hx, hy in every lane of the warp), a term
+// of the sum at cell c is the real part of
+//     A e^{i theta(lane corner)} * e^{2 pi i a_x i hx} * e^{2 pi i a_y k hy},
+// so one hardware sine/cosine pair per (lane, mode) and two exact step
+// phasors per axis shared by the warp replace the per-cell phase and cosine:
+// per cell-mode two FFMA (one FADD for i = 0) and a quarter of a complex
+// product.  The step phasors come from exact reduced phases (axis_turns),
+// the corner phase as in the general path: from the warp-origin phase plus
+// the corner offset for light modes, exactly for the modes of the medium
+// and super classes (j < k_med).  Adds this chunk's terms to p[].
+template <int DIM, int C, int NS>
+__device__ __forceinline__ void lattice_chunk(const FwdDesc& d, int jbase, int k_med, const float (&x0)[DIM],
+                                              const float (&xl)[DIM], float hx, float hy, const float4* hotS,
+                                              float* t0s, float4* stp, float (&p)[C], int lane) {
+    constexpr int NY = C / 4;
+    static_assert(NS == NY + 2, "step phasors: 3 along x, NY - 1 along y");
+    for (int m = lane; m < kWChunk; m += 32) {
+        const int j = jbase + m;
+        const float4 c0 = __ldg(d.cold + 2 * j);
+        const float4 c1 = __ldg(d.cold + 2 * j + 1);
+        t0s[m] = kTwoPiF * phase_exact_turns<DIM>(x0, c0, c1);
+        float ph[NS];
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) ph[k - 1] = kTwoPiF * axis_turns(c0.x, c0.y, static_cast<float>(k) * hx);
+#pragma unroll
+        for (int k = 1; k < NY; ++k) ph[2 + k] = kTwoPiF * axis_turns(c0.z, c0.w, static_cast<float>(k) * hy);
+        float4* sm = stp + m * (NS / 2);
+#pragma unroll
+        for (int k = 0; k < NS / 2; ++k)
+            sm[k] = make_float4(hw_cos(ph[2 * k]), hw_sin(ph[2 * k]), hw_cos(ph[2 * k + 1]), hw_sin(ph[2 * k + 1]));
+    }
+    __syncwarp();
+    float dl[DIM];  // lane corner relative to the warp origin
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) dl[k] = xl[k] - x0[k];
+    auto mode = [&](const float4 h, const float th, const float4* sm) {
+        const float er = h.w * hw_cos(th);
+        const float ei = h.w * hw_sin(th);
+        const float4 s01 = sm[0];  // step x 1, step x 2
+        const float4 s23 = sm[1];  // step x 3, step y 1
+#pragma unroll
+        for (int k = 0; k < NY; ++k) {
+            float zr = er, zi = ei;
+            if (k > 0) {
+                const float4 q = k == 1 ? s23 : sm[1 + k / 2];
+                const float qr = (k == 1 || k == 3) ? q.z : q.x;
+                const float qi = (k == 1 || k == 3) ? q.w : q.y;
+                zr = fmaf(er, qr, -ei * qi);
+                zi = fmaf(er, qi, ei * qr);
+            }
+            p[4 * k + 0] += zr;
+            p[4 * k + 1] = fmaf(zr, s01.x, fmaf(-zi, s01.y, p[4 * k + 1]));
+            p[4 * k + 2] = fmaf(zr, s01.z, fmaf(-zi, s01.w, p[4 * k + 2]));
+            p[4 * k + 3] = fmaf(zr, s23.x, fmaf(-zi, s23.y, p[4 * k + 3]));
+        }
+    };
+    const int mh = min(max(k_med - jbase, 0), kWChunk);
+    for (int m = 0; m < mh; ++m) {
+        const int j = jbase + m;
+        const float th = kTwoPiF * phase_exact_turns<DIM>(xl, __ldg(d.cold + 2 * j), __ldg(d.cold + 2 * j + 1));
+        mode(hotS[m], th, stp + m * (NS / 2));
+    }
+#pragma unroll 2
+    for (int m = mh; m < kWChunk; ++m) {
+        const float4 h = hotS[m];
+        float th = fmaf(h.x, dl[0], t0s[m]);
+        if (DIM > 1) th = fmaf(h.y, dl[1], th);
+        if (DIM > 2) th = fmaf(h.z, dl[2], th);
+        mode(h, th, stp + m * (NS / 2));
+    }
+}
 
 __device__ __forceinline__ void warp_init_barriers(WarpSmem& ws) {
     if ((threadIdx.x & 31) == 0) {
@@ -99,10 +189,10 @@ __device__ __forceinline__ float warp_max(float v) {
 // kernel); the single-realisation kernel uses 0.
 // MM: the epilogue also forms the mismatch gradient of every cell and writes
 // the warp's sum of (K - T)^2 to d.map.lpart[wbase / (32 C)] (kMapMismatch).
-template <int DIM, int C, int POLY, bool MM = false>
+template <int DIM, int C, int POLY, bool MM = false, int NS = 0>
 __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase, int cb, int ce,
                                                 float2* partial, WarpSmem& ws, uint32_t (&uses)[kStages],
-                                                int32_t* status) {
+                                                int32_t* status, float4* stp = nullptr) {
     const int lane = threadIdx.x & 31;
     const int64_t n = d.n_cells;
     const int jlo = cb * kWChunk;
@@ -176,84 +266,143 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
         p[c] = 0.0f;
     }
 
-    // ---- super class: exact phase at every cell ---------------------------------
-    const int sup_end = min(k_sup, jhi);
-    for (int j = jlo; j < sup_end; ++j) {
-        const float4 c0 = __ldg(d.cold + 2 * j);
-        const float4 c1 = __ldg(d.cold + 2 * j + 1);
-        const float A = __ldg(&d.hot[j].w);
+    // ---- lattice lanes (see lattice_chunk): every lane's cells are the 4 x C/4
+    // block of one grid spacing (hx, hy), the same in the whole warp ----------------
+    bool lat = false;
+    float hx = 0.0f, hy = 0.0f;
+    float xl[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) xl[k] = x[0][k];
+    if constexpr (NS > 0) {
+        static_assert(DIM >= 2 && C >= 8 && C % 4 == 0, "lattice lanes are 4 x C/4 blocks");
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < C; ++c) ok = ok && valid[c];
+        hx = x[1][0] - x[0][0];
+        hy = x[4][1] - x[0][1];
+        ok = ok && hx > 0.0f && hy > 0.0f;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const float r = phase_exact_turns<DIM>(x[c], c0, c1);
-            p[c] = fmaf(A, hw_cos(kTwoPiF * r), p[c]);
+            const float ox = static_cast<float>(c & 3) * hx;
+            const float oy = static_cast<float>(c >> 2) * hy;
+            ok = ok && (x[c][0] - x[0][0] == ox) && (x[0][0] + ox == x[c][0]) && (x[c][1] - x[0][1] == oy) &&
+                 (x[0][1] + oy == x[c][1]);
+            if (DIM > 2) ok = ok && (x[c][2] == x[0][2]);
         }
-        if ((j & 63) == 63) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                two_sum_acc(s[c], e[c], p[c]);
-                p[c] = 0.0f;
-            }
-        }
+        // every lane takes part in the shuffles (no short-circuit around them)
+        const float hx0 = __shfl_sync(0xffffffffu, hx, 0);
+        const float hy0 = __shfl_sync(0xffffffffu, hy, 0);
+        ok = ok && hx == hx0 && hy == hy0;
+        lat = __all_sync(0xffffffffu, ok);
+        if (lane == 0) atomicAdd(&g_path_warps[lat ? 1 : 0], 1ull);
     }
 
-    // ---- medium class: exact phase at the lane origin -------------------------
-    float dx[C][DIM];  // offsets from the lane origin, then from the warp origin
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - xt[k];
-    const int med_end = min(k_med, jhi);
-    for (int j = max(k_sup, jlo); j < med_end; ++j) {
-        const float4 c0 = __ldg(d.cold + 2 * j);
-        const float4 c1 = __ldg(d.cold + 2 * j + 1);
-        const float4 h = __ldg(d.hot + j);
-        const float t0 = kTwoPiF * phase_exact_turns<DIM>(xt, c0, c1);
+    // Chunk pipeline: waits for each of this warp's chunks in turn, keeping
+    // kStages - 1 bulk copies in flight, and hands it to body(hotS, jbase).
+    // If a bounded wait expires it records that in the status word, gives the
+    // copies still in flight a bounded chance to land before this warp's
+    // shared memory is reused, and returns false.
+    auto run_chunks = [&](auto&& body) -> bool {
+        bool ok = true;
+        int ch = cb;
+        for (; ch < ce; ++ch) {
+            const int b = (ch - cb) % kStages;
+            // keep kStages - 1 chunks in flight: refill the buffer freed last
+            if (lane == 0 && ch + kStages - 1 < ce) {
+                fence_proxy_async_smem();
+                issue_wchunk(d, ch + kStages - 1, ws, (ch - cb + kStages - 1) % kStages);
+            }
+            // the hi/lo records of the next chunk (128 modes x 32 B = 32 lines,
+            // one per lane) are pulled into L1 while this chunk is summed
+            if (ch + 1 < ce) prefetch_l1(d.cold + 2 * ((ch + 1) * kWChunk + lane * (kWChunk / 32)));
+            const uint32_t parity = uses[b] & 1u;
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ws.full[b], parity));
+            uses[b] += 1;
+            if (!ok) break;
+            body(ws.buf[b], ch * kWChunk);
+            __syncwarp();  // every lane is done with buffer b and the chunk's tables
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(status, 2);
+                for (int q = 0; q < kStages && ch + q < ce; ++q) {
+                    const int bq = (ch - cb + q) % kStages;
+                    mbar_wait_bounded(&ws.full[bq], (q == 0 ? uses[bq] - 1u : uses[bq]) & 1u);
+                }
+            }
+            __syncwarp();
+        }
+        return ok;
+    };
+    auto fold = [&]() {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            float th = fmaf(h.x, dx[c][0], t0);
-            if (DIM > 1) th = fmaf(h.y, dx[c][1], th);
-            if (DIM > 2) th = fmaf(h.z, dx[c][2], th);
-            p[c] = fmaf(h.w, hw_cos(th), p[c]);
+            two_sum_acc(s[c], e[c], p[c]);
+            p[c] = 0.0f;
         }
-        if (((j - k_sup) & 63) == 63) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                two_sum_acc(s[c], e[c], p[c]);
-                p[c] = 0.0f;
-            }
+    };
+
+    bool handled = false;
+    if constexpr (NS > 0) {
+        if (lat) {
+            handled = true;
+            if (!run_chunks([&](float4* hotS, int jbase) {
+                    lattice_chunk<DIM, C, NS>(d, jbase, k_med, x0, xl, hx, hy, hotS, ws.t0, stp, p, lane);
+                    fold();
+                }))
+                return false;
         }
     }
-    // re-base the offsets on the warp origin: dx = (x - xt) + (xt - x0)
-    {
-        float D[DIM];
+    if (!handled) {
+        // ---- super class: exact phase at every cell -----------------------------
+        const int sup_end = min(k_sup, jhi);
+        for (int j = jlo; j < sup_end; ++j) {
+            const float4 c0 = __ldg(d.cold + 2 * j);
+            const float4 c1 = __ldg(d.cold + 2 * j + 1);
+            const float A = __ldg(&d.hot[j].w);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) D[k] = xt[k] - x0[k];
+            for (int c = 0; c < C; ++c) {
+                const float r = phase_exact_turns<DIM>(x[c], c0, c1);
+                p[c] = fmaf(A, hw_cos(kTwoPiF * r), p[c]);
+            }
+            if ((j & 63) == 63) fold();
+        }
+
+        // ---- medium class: exact phase at the lane origin ---------------------
+        float dx[C][DIM];  // offsets from the lane origin, then from the warp origin
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) dx[c][k] += D[k];
-    }
-
-    // ---- light class over this warp's staged chunks ------------------------------
-    bool ok = true;
-    int ch = cb;
-    for (; ch < ce; ++ch) {
-        const int b = (ch - cb) % kStages;
-        // keep kStages - 1 chunks in flight: refill the buffer freed last
-        if (lane == 0 && ch + kStages - 1 < ce) {
-            fence_proxy_async_smem();
-            issue_wchunk(d, ch + kStages - 1, ws, (ch - cb + kStages - 1) % kStages);
+            for (int k = 0; k < DIM; ++k) dx[c][k] = x[c][k] - xt[k];
+        const int med_end = min(k_med, jhi);
+        for (int j = max(k_sup, jlo); j < med_end; ++j) {
+            const float4 c0 = __ldg(d.cold + 2 * j);
+            const float4 c1 = __ldg(d.cold + 2 * j + 1);
+            const float4 h = __ldg(d.hot + j);
+            const float t0 = kTwoPiF * phase_exact_turns<DIM>(xt, c0, c1);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                float th = fmaf(h.x, dx[c][0], t0);
+                if (DIM > 1) th = fmaf(h.y, dx[c][1], th);
+                if (DIM > 2) th = fmaf(h.z, dx[c][2], th);
+                p[c] = fmaf(h.w, hw_cos(th), p[c]);
+            }
+            if (((j - k_sup) & 63) == 63) fold();
         }
-        // the hi/lo records of the next chunk (128 modes x 32 B = 32 lines,
-        // one per lane) are pulled into L1 while this chunk is summed
-        if (ch + 1 < ce) prefetch_l1(d.cold + 2 * ((ch + 1) * kWChunk + lane * (kWChunk / 32)));
-        const uint32_t parity = uses[b] & 1u;
-        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ws.full[b], parity));
-        uses[b] += 1;
-        if (!ok) break;
-        float4* hotS = ws.buf[b];
-        const int jbase = ch * kWChunk;
-        if (jbase + kWChunk > k_med) {
+        // re-base the offsets on the warp origin: dx = (x - xt) + (xt - x0)
+        {
+            float D[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) D[k] = xt[k] - x0[k];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) dx[c][k] += D[k];
+        }
+
+        // ---- light class over this warp's staged chunks --------------------------
+        const bool done = run_chunks([&](float4* hotS, int jbase) {
+            if (jbase + kWChunk <= k_med) return;
             const int m0 = k_med > jbase ? k_med - jbase : 0;
             auto mode = [&](const float4 h, const float t0) {
 #pragma unroll
@@ -303,26 +452,9 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
 #pragma unroll 8
                 for (int m = m0; m < kWChunk; ++m) mode(hotS[m], ws.t0[m]);
             }
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                two_sum_acc(s[c], e[c], p[c]);
-                p[c] = 0.0f;
-            }
-        }
-        __syncwarp();  // every lane is done with buffer b and t0
-    }
-    if (!ok) {
-        // Give the copies still in flight (chunks ch .. ch + kStages - 1) a
-        // bounded chance to land before this warp's shared memory is reused.
-        if (lane == 0) {
-            atomicOr(status, 2);
-            for (int q = 0; q < kStages && ch + q < ce; ++q) {
-                const int bq = (ch - cb + q) % kStages;
-                mbar_wait_bounded(&ws.full[bq], (q == 0 ? uses[bq] - 1u : uses[bq]) & 1u);
-            }
-        }
-        __syncwarp();
-        return false;
+            fold();
+        });
+        if (!done) return false;
     }
 
     // ---- epilogue: field value and fused maps ------------------------------------
@@ -358,10 +490,19 @@ __device__ __forceinline__ bool synth_warp_tile(const FwdDesc& d, int64_t wbase,
 // blockIdx.x: W warp tiles; blockIdx.y: mode split (gridDim.y splits of the
 // warp-chunk range; with more than one split every warp writes its TwoSum
 // partial (s, e) per sorted cell to partial[split * n_cells + i]).
+// Lattice path in the single-field kernel for 2-D and 3-D fields (NS step
+// phasors per mode); the 2-D kernel then holds 5 blocks per SM (shared memory).
+template <int DIM, int C>
+__host__ __device__ constexpr int lattice_ns() { return DIM >= 2 && C >= 8 ? C / 4 + 2 : 0; }
+template <int DIM, int C>
+__host__ __device__ constexpr int fwd_min_blocks() { return C >= 16 ? 4 : (lattice_ns<DIM, C>() > 0 ? 5 : 6); }
+
 template <int DIM, int C, int W, bool MM>
-__global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 6) synth_fwd_kernel(FwdDesc d, float2* partial, int32_t* status) {
+__global__ void __launch_bounds__(W * 32, (fwd_min_blocks<DIM, C>())) synth_fwd_kernel(FwdDesc d, float2* partial,
+                                                                                   int32_t* status) {
+    constexpr int NS = lattice_ns<DIM, C>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
+    auto& sm = *reinterpret_cast<FwdSmem<W, NS>*>(smem_raw);
     const int warp = threadIdx.x >> 5;
     WarpSmem& ws = sm.w[warp];
     warp_init_barriers(ws);
@@ -373,7 +514,7 @@ __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 6) synth_fwd_kernel(FwdD
     const int cb = static_cast<int>(static_cast<int64_t>(n_chunks) * split / n_split);
     const int ce = static_cast<int>(static_cast<int64_t>(n_chunks) * (split + 1) / n_split);
     float2* part = n_split > 1 ? partial + static_cast<int64_t>(split) * d.n_cells : nullptr;
-    const bool ok = synth_warp_tile<DIM, C, 0, MM>(d, wbase, cb, ce, part, ws, uses, status);
+    const bool ok = synth_warp_tile<DIM, C, 0, MM, NS>(d, wbase, cb, ce, part, ws, uses, status, sm.stp[warp]);
     if (MM && !ok && part == nullptr && (threadIdx.x & 31) == 0)
         d.map.lpart[wbase / (32 * C)] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no loss
 }
@@ -490,7 +631,7 @@ int choose_split(int64_t tiles, int n_chunks, int resident, int64_t n_cells, siz
 
 template <int DIM, int C, int W>
 int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, cudaStream_t st) {
-    const size_t smem = sizeof(FwdSmem<W>);
+    const size_t smem = sizeof(FwdSmem<W, lattice_ns<DIM, C>()>);
     const bool mm = (d.map.bits & kMapMismatch) != 0;
     auto kern = mm ? synth_fwd_kernel<DIM, C, W, true> : synth_fwd_kernel<DIM, C, W, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -605,5 +746,15 @@ int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* s
 }
 
 unsigned long long take_index_faults_fwd() { return take_tu_index_faults(); }
+
+int take_path_counts(unsigned long long* general, unsigned long long* lattice) {
+    unsigned long long v[2] = {0ull, 0ull};
+    const unsigned long long zero[2] = {0ull, 0ull};
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_path_warps, sizeof(v));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_path_warps, zero, sizeof(zero));
+    *general = v[0];
+    *lattice = v[1];
+    return e;
+}
 
 }  // namespace grf

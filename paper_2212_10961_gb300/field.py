@@ -852,6 +852,14 @@ def launch_count():
     return int(lib().grf_launch_count())
 
 
+def take_path_counts():
+    """(general, lattice) warp tiles of single-field syntheses since the last
+    call (grf_take_path_counts); synchronises the device."""
+    g, l_ = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().grf_take_path_counts(ctypes.byref(g), ctypes.byref(l_)))
+    return g.value, l_.value
+
+
 def mufu_probe(blocks, iters, stream=None):
     sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
     check(lib().grf_mufu_probe(int(blocks), int(iters), _ptr(sink), _stream_handle(stream)))

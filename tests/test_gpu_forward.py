@@ -436,3 +436,29 @@ def test_hrl2d_workload_sampled(env):
     # quartile thresholds: each facies holds about a quarter of the cells
     frac = np.bincount(out["facies"], minlength=4) / len(out["facies"])
     assert np.all(np.abs(frac - 0.25) < 0.15)
+
+
+@pytest.mark.parametrize("shape,family", [((64, 48), "gaussian"), ((128, 48), "exponential"), ((64, 40), "matern"),
+                                          ((64, 64), "gaussian"), ((32, 32, 32), "exponential"),
+                                          ((64, 40, 24), "gaussian"), ((64, 64, 8), "matern")])
+def test_lattice_lanes_against_oracle(env, shape, family):
+    # Cartesian grids in x-fastest order: warps whose lanes all hold 4 x C/4
+    # blocks of one spacing take the lattice path (step phasors), the others
+    # the general one; grids where only some lanes of a warp are such blocks
+    # (one grid spacing not a power of two) mix both kinds of lanes in a warp
+    torch, F, W = env
+    cells = W.grid_centres(shape)
+    d = len(shape)
+    ell = (0.13, 0.1, 0.07)[:d]
+    p = F.FieldParams(family=family, sigma2=1.6, mean=-0.2, ell=ell, dim=d, n_modes=700, seed=29, nu=1.5)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    gf = F.GaussianField(p)
+    y_or = oracle_field(oracle_modes(family, 1.6, ell, d, 700, 29), -0.2, cells)
+    for ws in (False, None):  # without and with the mode split
+        out = F.synth(gf.table, p, plan, 0, F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True),
+                      workspace=ws)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        check_forward(out["Y"].cpu().numpy(), y_or, math.sqrt(1.6), "%s %s" % (shape, family))
+        check_lognormal(out["K"].cpu().numpy(), y_or, math.sqrt(1.6))
+        check_facies(out["facies"].cpu().numpy(), y_or, (0.0,), math.sqrt(1.6))
