@@ -73,6 +73,14 @@ __device__ __forceinline__ int bucket_of_bwd(float E) {
     return b < 0 ? 0 : b;
 }
 
+// Phase a v in turns, reduced to [-1/2, 1/2], of a = ah + al (FP32 pair) at a
+// point v of one axis (the product split exactly by an FMA).
+__device__ __forceinline__ float axis_turns_bwd(float ah, float al, float v) {
+    const float pr = ah * v;
+    const float e = fmaf(ah, v, -pr);
+    return frac_turn(frac_turn(pr) + fmaf(al, v, e));
+}
+
 struct DF {  // double-float accumulator
     float hi, lo;
     __device__ __forceinline__ void add(float v) { two_sum_acc(hi, lo, v); }
@@ -89,6 +97,133 @@ struct BwdWarpSmem {
     float4 gd[kBwdTile];           // g (x - x0, y - y0, z - z0), 0: one FFMA per sum below
     float2 acc[32 * MPT][5];       // per mode: cos, sin, sin*x, sin*y, sin*z
 };
+
+// Per-mode sums over a lattice tile (see the check in bwd_partial_kernel): for
+// brick b with corner c_b, e^{i theta} of cell (i, j, k) is
+//     R_jk X^i,   R_jk = E_b Y^j Z^k,   E_b = e^{i theta(c_b)},
+//     X = e^{2 pi i a_x hx},  Y = e^{2 pi i a_y hy},  Z = e^{2 pi i a_z hz},
+// so every cell's phasor is one complex product of its row phasor and X^i
+// (X^2, X^3 formed once per tile), and with the gradients g and i g staged
+// per cell:
+//     sum g cos, sum g sin            = Re, Im of sum g R X^i,
+//     sum g sin (x - x0)              = (c_bx - x0) sum g sin + hx sum i g sin,
+//     sum g sin (y - y0), (z - z0)    likewise with the weights j, k.
+// No sine or cosine per cell: per (tile, mode) the exact step phasors
+// (exactly reduced phases, hardware sine/cosine) and per (brick, mode) the
+// corner phasor (warp-origin phase plus offset for light modes, the exact
+// compensated phase for the first k_heavy modes).  Adds to sc, ss, sx.
+template <int MPT, class SM>
+__device__ __forceinline__ void bwd_lattice_tile(const BwdArgs& args, const SM& sm, const float4 (&hot)[MPT],
+                                                 const int (&mm)[MPT], int m_base, int k_heavy, const float (&x0)[3],
+                                                 const float (&cbk)[4][3], const float (&hl)[3],
+                                                 const float (&t0)[MPT], float (&sc)[MPT], float (&ss)[MPT],
+                                                 float (&sx)[MPT][3]) {
+    constexpr int G = 2;  // modes per pass (the per-mode state of all MPT modes does not fit in registers)
+    static_assert(MPT % G == 0, "mode groups");
+    const float* gs = reinterpret_cast<const float*>(sm.cd);
+    const float* gi = gs + kBwdTile;
+#pragma unroll
+    for (int kg = 0; kg < MPT; kg += G) {
+        float X1r[G], X1i[G], X2r[G], X2i[G], X3r[G], X3i[G], Yr[G], Yi[G], Zr[G], Zi[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const float4 c0 = __ldg(args.cold + 2 * mm[kg + k]);
+            const float4 c1 = __ldg(args.cold + 2 * mm[kg + k] + 1);
+            const float tx = kTwoPiF * axis_turns_bwd(c0.x, c0.y, hl[0]);
+            const float tx2 = kTwoPiF * axis_turns_bwd(c0.x, c0.y, 2.0f * hl[0]);
+            const float tx3 = kTwoPiF * axis_turns_bwd(c0.x, c0.y, 3.0f * hl[0]);
+            const float ty = kTwoPiF * axis_turns_bwd(c0.z, c0.w, hl[1]);
+            const float tz = kTwoPiF * axis_turns_bwd(c1.x, c1.y, hl[2]);
+            X1r[k] = hw_cos(tx);
+            X1i[k] = hw_sin(tx);
+            X2r[k] = hw_cos(tx2);
+            X2i[k] = hw_sin(tx2);
+            X3r[k] = hw_cos(tx3);
+            X3i[k] = hw_sin(tx3);
+            Yr[k] = hw_cos(ty);
+            Yi[k] = hw_sin(ty);
+            Zr[k] = hw_cos(tz);
+            Zi[k] = hw_sin(tz);
+        }
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+            float Qr[G], Qi[G];  // plane phasor E_b Z^k
+            float Sr[G], Si[G], Sp[G], Sj[G], Sk[G];
+            const float dxb[3] = {cbk[b][0] - x0[0], cbk[b][1] - x0[1], cbk[b][2] - x0[2]};
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                float th;
+                if (m_base + kg + k < k_heavy) {
+                    th = kTwoPiF * phase_exact_turns<3>(cbk[b], __ldg(args.cold + 2 * mm[kg + k]),
+                                                        __ldg(args.cold + 2 * mm[kg + k] + 1));
+                } else {
+                    th = fmaf(hot[kg + k].x, dxb[0], t0[kg + k]);
+                    th = fmaf(hot[kg + k].y, dxb[1], th);
+                    th = fmaf(hot[kg + k].z, dxb[2], th);
+                }
+                Qr[k] = hw_cos(th);
+                Qi[k] = hw_sin(th);
+                Sr[k] = Si[k] = Sp[k] = Sj[k] = Sk[k] = 0.f;
+            }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float Rr[G], Ri[G], Tk[G];
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (kk > 0) {
+                        const float qr = fmaf(Qr[k], Zr[k], -Qi[k] * Zi[k]);
+                        Qi[k] = fmaf(Qr[k], Zi[k], Qi[k] * Zr[k]);
+                        Qr[k] = qr;
+                    }
+                    Rr[k] = Qr[k];
+                    Ri[k] = Qi[k];
+                    Tk[k] = 0.f;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int base = 64 * b + 16 * kk + 4 * jj;
+                    const float4 g4 = *reinterpret_cast<const float4*>(gs + base);
+                    const float4 c4 = *reinterpret_cast<const float4*>(gi + base);
+#pragma unroll
+                    for (int k = 0; k < G; ++k) {
+                        if (jj > 0) {
+                            const float rr = fmaf(Rr[k], Yr[k], -Ri[k] * Yi[k]);
+                            Ri[k] = fmaf(Rr[k], Yi[k], Ri[k] * Yr[k]);
+                            Rr[k] = rr;
+                        }
+                        // cell phasors R X^i (independent of one another)
+                        const float c1r = fmaf(Rr[k], X1r[k], -Ri[k] * X1i[k]);
+                        const float c1i = fmaf(Rr[k], X1i[k], Ri[k] * X1r[k]);
+                        const float c2r = fmaf(Rr[k], X2r[k], -Ri[k] * X2i[k]);
+                        const float c2i = fmaf(Rr[k], X2i[k], Ri[k] * X2r[k]);
+                        const float c3r = fmaf(Rr[k], X3r[k], -Ri[k] * X3i[k]);
+                        const float c3i = fmaf(Rr[k], X3i[k], Ri[k] * X3r[k]);
+                        // row sums in two chains each
+                        const float re = fmaf(g4.x, Rr[k], g4.y * c1r) + fmaf(g4.z, c2r, g4.w * c3r);
+                        const float im = fmaf(g4.x, Ri[k], g4.y * c1i) + fmaf(g4.z, c2i, g4.w * c3i);
+                        const float ip = fmaf(c4.y, c1i, fmaf(c4.z, c2i, c4.w * c3i));
+                        Sr[k] += re;
+                        Si[k] += im;
+                        Sp[k] += ip;
+                        if (jj > 0) Sj[k] = fmaf(static_cast<float>(jj), im, Sj[k]);
+                        Tk[k] += im;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (kk > 0) Sk[k] = fmaf(static_cast<float>(kk), Tk[k], Sk[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                sc[kg + k] += Sr[k];
+                ss[kg + k] += Si[k];
+                sx[kg + k][0] += fmaf(dxb[0], Si[k], hl[0] * Sp[k]);
+                sx[kg + k][1] += fmaf(dxb[1], Si[k], hl[1] * Sj[k]);
+                sx[kg + k][2] += fmaf(dxb[2], Si[k], hl[2] * Sk[k]);
+            }
+        }
+    }
+}
 
 // Every warp works on its own: it owns 32 * MPT consecutive modes (MPT per
 // lane, registers) and walks the block's range of cell tiles, staging each
@@ -172,20 +307,64 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
         }
         const int bk = bucket_of_bwd(E);
         const int k_heavy = bk >= kBuckets ? args.n_pad : __ldg(args.kpref + bk);
-        __syncwarp();  // the previous tile's shared data is no longer read
+
+        // ---- lattice tile (3-D): four 4 x 4 x 4 bricks of one grid spacing -----
+        // Cell idx = 64 b + 16 k + 4 j + i of the tile lies at the corner of its
+        // brick b (cell 64 b) plus (i hx, j hy, k hz), exactly in FP32 -- a
+        // Cartesian grid handed over x-fastest, as the plan keeps it.  Lane l's
+        // cell q (idx = 32 q + l) has b = q / 2, i = l % 4, j = (l / 4) % 4,
+        // k = 2 (q % 2) + l / 16.  Every lane takes part in every shuffle.
+        bool lat = false;
+        float cbk[4][3] = {};
+        float hl[3] = {0.f, 0.f, 0.f};
+        if constexpr (DIM == 3) {
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int idx = q * 32 + lane;
-            const float dx = xv[q][0] - x0[0], dy = xv[q][1] - x0[1], dz = xv[q][2] - x0[2];
-            sm.cd[idx] = make_float4(dx, dy, dz, gv[q]);
-            sm.gd[idx] = make_float4(gv[q] * dx, gv[q] * dy, gv[q] * dz, 0.f);
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cbk[b][c] = __shfl_sync(0xffffffffu, xv[2 * b][c], 0);
+            hl[0] = __shfl_sync(0xffffffffu, xv[0][0], 1) - cbk[0][0];
+            hl[1] = __shfl_sync(0xffffffffu, xv[0][1], 4) - cbk[0][1];
+            hl[2] = __shfl_sync(0xffffffffu, xv[0][2], 16) - cbk[0][2];
+            bool okl = t * kBwdTile + kBwdTile <= n && hl[0] > 0.f && hl[1] > 0.f && hl[2] > 0.f;
+            const float oi = static_cast<float>(lane & 3) * hl[0];
+            const float oj = static_cast<float>((lane >> 2) & 3) * hl[1];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int b = q >> 1;
+                const float ok_ = static_cast<float>(2 * (q & 1) + (lane >> 4)) * hl[2];
+                okl = okl && (xv[q][0] - cbk[b][0] == oi) && (cbk[b][0] + oi == xv[q][0]) &&
+                      (xv[q][1] - cbk[b][1] == oj) && (cbk[b][1] + oj == xv[q][1]) &&
+                      (xv[q][2] - cbk[b][2] == ok_) && (cbk[b][2] + ok_ == xv[q][2]);
+            }
+            lat = __all_sync(0xffffffffu, okl);
+        }
+        __syncwarp();  // the previous tile's shared data is no longer read
+        if (lat) {
+            // g and i g per cell (i the cell's x index in its brick)
+            float* gs = reinterpret_cast<float*>(sm.cd);
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int idx = q * 32 + lane;
+                gs[idx] = gv[q];
+                gs[kBwdTile + idx] = static_cast<float>(lane & 3) * gv[q];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int idx = q * 32 + lane;
+                const float dx = xv[q][0] - x0[0], dy = xv[q][1] - x0[1], dz = xv[q][2] - x0[2];
+                sm.cd[idx] = make_float4(dx, dy, dz, gv[q]);
+                sm.gd[idx] = make_float4(gv[q] * dx, gv[q] * dy, gv[q] * dz, 0.f);
+            }
         }
         if (count_g) {
 #pragma unroll
             for (int q = 0; q < kPer; ++q) gsum.add(gv[q]);  // cascaded sum: TwoSum per value
         }
         __syncwarp();
-        if (t + 1 < t_end) load_tile(t + 1);  // overlaps with the sums below
+        // overlaps with the sums below (a lattice tile loads it after its sums:
+        // its per-mode state needs the registers)
+        if (!lat && t + 1 < t_end) load_tile(t + 1);
 
         // ---- per-mode sums over the tile ------------------------------------------
         const bool any_heavy = m_base < k_heavy;
@@ -199,7 +378,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
             t0[k] = kTwoPiF * phase_exact_turns<DIM>(x0, __ldg(args.cold + 2 * mm[k]),
                                                       __ldg(args.cold + 2 * mm[k] + 1));
         }
-        if (!__any_sync(0xffffffffu, any_heavy)) {
+        if (lat) {
+            if constexpr (DIM == 3) bwd_lattice_tile<MPT>(args, sm, hot, mm, m_base, k_heavy, x0, cbk, hl, t0, sc, ss, sx);
+            if (t + 1 < t_end) load_tile(t + 1);
+        } else if (!__any_sync(0xffffffffu, any_heavy)) {
 #pragma unroll 8
             for (int i = 0; i < kBwdTile; ++i) {
                 const float4 c = sm.cd[i];

@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import GRAD_TOL, gpu_env, oracle_field, oracle_modes, to_dev
+from helpers import FAMILY_IDS, GRAD_TOL, gpu_env, oracle_field, oracle_modes, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -268,3 +268,41 @@ def test_rotated_anisotropy_forward_and_adjoint(env, kind):
                              rot=R)
     for k in ("dA", "dpsi", "da", "dsigma", "dell", "drot"):
         _check(gr[k].cpu().numpy(), ref[k], k)
+
+
+@pytest.mark.parametrize("shape,family,rotated", [((32, 32, 32), "gaussian", False),
+                                                  ((64, 32, 16), "exponential", False),
+                                                  ((32, 32, 32), "matern", True),
+                                                  ((64, 48, 16), "gaussian", False),
+                                                  ((40, 32, 24), "exponential", True)])
+def test_lattice_adjoint_against_oracle(env, shape, family, rotated):
+    # tiles of 256 cells that are four 4 x 4 x 4 bricks of one grid spacing
+    # (Cartesian grids handed over x-fastest) take the adjoint's lattice path
+    # (Horner sums of the rows' gradients, no sine or cosine per cell); the
+    # exponential spectrum brings modes of the exact (heavy) class, and grid
+    # spacings that are not powers of two mix lattice and general tiles
+    torch, F, W = env
+    cells = W.grid_centres(shape)
+    ell = (0.2, 0.11, 0.07)
+    R = None
+    if rotated:
+        a_ = 0.4
+        R = np.array([[math.cos(a_), -math.sin(a_), 0.0], [math.sin(a_), math.cos(a_), 0.0], [0.0, 0.0, 1.0]])
+    p = F.FieldParams(family=family, sigma2=1.3, mean=0.05, ell=ell, dim=3, n_modes=777, seed=61, nu=1.5,
+                      rot=None if R is None else R.tolist())
+    gf = F.GaussianField(p)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    g = np.random.default_rng(7).standard_normal(len(cells[0])).astype(np.float32)
+    gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    from oracle import field as of
+    from oracle import modes as omod
+    from oracle import native
+    om = omod.gen_modes(FAMILY_IDS[family], 1.3, ell, 3, 777, 61, nu=1.5, rot=R)
+    c = np.stack(cells, axis=-1)
+    ref = of.grads_reparam(*native.mode_sums(om["a"], om["psi"], c, g.astype(np.float64)), om["kappa"], om["rho"],
+                           math.sqrt(1.3), ell, g.astype(np.float64), rot=R)
+    errs = {k: _check(gr[k].cpu().numpy(), ref[k], k)
+            for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dsigma2", "dell", "drot", "drho", "dkappa")}
+    print(shape, family, "rotated" if rotated else "", "lattice adjoint errors:", errs)
