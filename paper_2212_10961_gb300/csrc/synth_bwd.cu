@@ -102,9 +102,9 @@ struct BwdWarpSmem {
 // brick b with corner c_b, e^{i theta} of cell (i, j, k) is
 //     R_jk X^i,   R_jk = E_b Y^j Z^k,   E_b = e^{i theta(c_b)},
 //     X = e^{2 pi i a_x hx},  Y = e^{2 pi i a_y hy},  Z = e^{2 pi i a_z hz},
-// so every cell's phasor is one complex product of its row phasor and X^i
-// (X^2, X^3 formed once per tile), and with the gradients g and i g staged
-// per cell:
+// so a row's terms are R_jk H with H = sum_i g_i X^i evaluated from the
+// powers X, X^2, X^3 (formed once per tile), and with the gradients g and
+// i g staged per cell:
 //     sum g cos, sum g sin            = Re, Im of sum g R X^i,
 //     sum g sin (x - x0)              = (c_bx - x0) sum g sin + hx sum i g sin,
 //     sum g sin (y - y0), (z - z0)    likewise with the weights j, k.
@@ -191,20 +191,18 @@ __device__ __forceinline__ void bwd_lattice_tile(const BwdArgs& args, const SM& 
                             Ri[k] = fmaf(Rr[k], Yi[k], Ri[k] * Yr[k]);
                             Rr[k] = rr;
                         }
-                        // cell phasors R X^i (independent of one another)
-                        const float c1r = fmaf(Rr[k], X1r[k], -Ri[k] * X1i[k]);
-                        const float c1i = fmaf(Rr[k], X1i[k], Ri[k] * X1r[k]);
-                        const float c2r = fmaf(Rr[k], X2r[k], -Ri[k] * X2i[k]);
-                        const float c2i = fmaf(Rr[k], X2i[k], Ri[k] * X2r[k]);
-                        const float c3r = fmaf(Rr[k], X3r[k], -Ri[k] * X3i[k]);
-                        const float c3i = fmaf(Rr[k], X3i[k], Ri[k] * X3r[k]);
-                        // row sums in two chains each
-                        const float re = fmaf(g4.x, Rr[k], g4.y * c1r) + fmaf(g4.z, c2r, g4.w * c3r);
-                        const float im = fmaf(g4.x, Ri[k], g4.y * c1i) + fmaf(g4.z, c2i, g4.w * c3i);
-                        const float ip = fmaf(c4.y, c1i, fmaf(c4.z, c2i, c4.w * c3i));
+                        // the row's sums H = sum_i g_i X^i and H' = sum_i i g_i X^i
+                        // from the precomputed powers (short, independent chains),
+                        // then R H and Im(R H')
+                        const float hr = fmaf(g4.w, X3r[k], fmaf(g4.z, X2r[k], fmaf(g4.y, X1r[k], g4.x)));
+                        const float hi = fmaf(g4.w, X3i[k], fmaf(g4.z, X2i[k], g4.y * X1i[k]));
+                        const float pr = fmaf(c4.w, X3r[k], fmaf(c4.z, X2r[k], c4.y * X1r[k]));
+                        const float pi = fmaf(c4.w, X3i[k], fmaf(c4.z, X2i[k], c4.y * X1i[k]));
+                        const float re = fmaf(Rr[k], hr, -Ri[k] * hi);
+                        const float im = fmaf(Rr[k], hi, Ri[k] * hr);
                         Sr[k] += re;
                         Si[k] += im;
-                        Sp[k] += ip;
+                        Sp[k] = fmaf(Rr[k], pi, fmaf(Ri[k], pr, Sp[k]));
                         if (jj > 0) Sj[k] = fmaf(static_cast<float>(jj), im, Sj[k]);
                         Tk[k] += im;
                     }
