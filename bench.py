@@ -452,10 +452,12 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
         kev.append((a, b, c))
 
     F.take_path_counts()  # reset
+    F.take_adjoint_path_counts()
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     gen_w, lat_w = F.take_path_counts()
+    bgen, blat = F.take_adjoint_path_counts()
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, c in kev[warmup:]]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for a, b, c in kev[warmup:]]))
     res = {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
@@ -463,7 +465,9 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
            "launches_per_step": launches / float(steps + warmup),
            "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)",
            "path_warps": {"general": gen_w, "lattice": lat_w},
-           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
+           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0,
+           "adjoint_path_tiles": {"general": bgen, "lattice": blat},
+           "adjoint_lattice_share": blat / float(bgen + blat) if bgen + blat else 0.0}
     if rank == 0:
         res["fp64_check"] = grad_check_40(torch, F, W)
     return res
@@ -709,6 +713,12 @@ HEAD_TRAFFIC_BYTES = 269.623552e6 + 115.687168e6
 # (7 + 12 + 28) / 16 = 2.94 in 3-D and (6 + 4 + 14) / 8 = 3.0 in 2-D.
 LATTICE_FP32_PER_CELL_MODE = 3.0
 FP32_PER_CLK_PER_SM = 128
+# FP32 instructions per cell-mode of the adjoint's lattice tiles: per (row of
+# 4 cells, mode) the row phasor (4, on 3 rows of 4), H and H' from the powers
+# (4 chains of 3), R H (4), Im(R H') (2), the sums (Sr, Si, the row weight,
+# the plane sum: 4): 25 per 4 cells, plus the plane phasors and the
+# per-brick and per-tile terms: 6.6.
+ADJOINT_LATTICE_FP32_PER_CELL_MODE = 6.6
 
 
 def roofline(kern_ms, cell_modes, clocks, sms, traffic=None, lattice_share=0.0):
@@ -882,9 +892,16 @@ def main():
         k_fb["fwd_roofline"] = roofline(k_fb["fwd_ms"], k_fb["cell_modes_per_step"], ck, sms,
                                         lattice_share=k_fb.get("lattice_share", 0.0))
         bw = k_fb["cell_modes_per_step"] / (k_fb["bwd_ms"] * 1e-3) / 1e9
-        bpk = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 2 / 1e9
+        bmufu = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 2 / 1e9
+        if k_fb.get("adjoint_lattice_share", 0.0) >= 0.5:
+            bpk = FP32_PER_CLK_PER_SM * sms * 2070e6 / ADJOINT_LATTICE_FP32_PER_CELL_MODE / 1e9
+            basis = ("lattice tiles (%.3f of the tiles): %d FP32 lanes/clk/SM x %d SMs x 2070 MHz / %.1f FP32 "
+                     "instructions per cell-mode" % (k_fb["adjoint_lattice_share"], FP32_PER_CLK_PER_SM, sms,
+                                                     ADJOINT_LATTICE_FP32_PER_CELL_MODE))
+        else:
+            bpk, basis = bmufu, "2 MUFU per cell-mode (sine and cosine)"
         k_fb["bwd_roofline"] = {"bound": "alu", "achieved": bw, "peak": bpk, "unit": "Gcell.mode/s",
-                                "frac": bw / bpk, "peak_basis": "2 MUFU per cell-mode (sine and cosine)",
+                                "frac": bw / bpk, "peak_basis": basis, "frac_of_mufu_roofline": bw / bmufu,
                                 "note": "adjoint kernel and its two reductions"}
     if head is None:
         head = next(iter(extra.values()))

@@ -582,6 +582,15 @@ int64_t grf_launch_count(void);
 int grf_take_path_counts(int64_t *general_warps, int64_t *lattice_warps);
 
 /*
+ * grf_take_adjoint_path_counts -- the same for the 3-D adjoint
+ * (grf_synth_backward): (warp, cell tile) pairs since the last call that took
+ * the general path and the lattice path (a 256-cell tile made of four
+ * 4 x 4 x 4 bricks of one Cartesian grid), then resets both.  Synchronises
+ * the device.  GRF_EINVAL for NULL pointers, GRF_ECUDA if unreadable.
+ */
+int grf_take_adjoint_path_counts(int64_t *general_tiles, int64_t *lattice_tiles);
+
+/*
  * grf_debug_inject_alloc_failures -- host-side fault injection for tests
  * (the paper has no counterpart).  The next n host allocations made by the
  * library's entry points fail as if the allocator had run out of memory: the

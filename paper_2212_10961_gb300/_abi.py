@@ -138,6 +138,8 @@ _SIGS = {
     "grf_device_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "grf_launch_count": (ctypes.c_int64, []),
     "grf_take_path_counts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "grf_take_adjoint_path_counts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64),
+                                                    ctypes.POINTER(ctypes.c_int64)]),
     "grf_debug_inject_alloc_failures": (ctypes.c_int, [ctypes.c_int32]),
     "grf_release": (ctypes.c_int, [ctypes.c_void_p]),
     "grf_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),

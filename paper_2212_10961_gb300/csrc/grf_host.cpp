@@ -1326,6 +1326,22 @@ int grf_take_path_counts(int64_t* general_warps, int64_t* lattice_warps) try {
     return host_exception();
 }
 
+int grf_take_adjoint_path_counts(int64_t* general_tiles, int64_t* lattice_tiles) try {
+    if (!general_tiles || !lattice_tiles) return fail(GRF_EINVAL, "NULL argument");
+    *general_tiles = 0;
+    *lattice_tiles = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the path counters");
+    unsigned long long g = 0ull, l = 0ull;
+    e = static_cast<cudaError_t>(take_bwd_path_counts(&g, &l));
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint path counters");
+    *general_tiles = static_cast<int64_t>(g);
+    *lattice_tiles = static_cast<int64_t>(l);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
 int grf_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream) try {
     if (blocks < 1 || iters < 1 || !sink) return fail(GRF_EINVAL, "bad probe arguments");
     const int err = launch_mufu_probe(blocks, iters, sink, stream);

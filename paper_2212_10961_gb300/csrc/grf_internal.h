@@ -238,6 +238,8 @@ unsigned long long take_index_faults_plan();
 // Warp tiles of single-field synthesis launches that took the general and the
 // lattice path since the last call, then reset (synchronous); cudaError_t.
 int take_path_counts(unsigned long long* general, unsigned long long* lattice);
+// The same for the 3-D adjoint's warp tiles (synth_bwd.cu).
+int take_bwd_path_counts(unsigned long long* general, unsigned long long* lattice);
 size_t synth_workspace_bytes(int64_t n_cells);
 int launch_synth_batched(const void* workspace, const BatchHeader& h, int32_t* status,
                          int32_t* counter, void* stream);

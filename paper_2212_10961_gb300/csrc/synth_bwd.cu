@@ -29,6 +29,10 @@
 
 namespace grf {
 
+// Warp tiles of the adjoint that took the general path [0] and the lattice
+// path [1] since the last grf_take_adjoint_path_counts (diagnostics).
+static __device__ unsigned long long g_bwd_path_tiles[2];
+
 namespace {
 
 constexpr int kBwdThreads = 128;
@@ -335,6 +339,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
                       (xv[q][2] - cbk[b][2] == ok_) && (cbk[b][2] + ok_ == xv[q][2]);
             }
             lat = __all_sync(0xffffffffu, okl);
+            if (lane == 0) atomicAdd(&g_bwd_path_tiles[lat ? 1 : 0], 1ull);
         }
         __syncwarp();  // the previous tile's shared data is no longer read
         if (lat) {
@@ -732,5 +737,15 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
 }
 
 unsigned long long take_index_faults_bwd() { return take_tu_index_faults(); }
+
+int take_bwd_path_counts(unsigned long long* general, unsigned long long* lattice) {
+    unsigned long long v[2] = {0ull, 0ull};
+    const unsigned long long zero[2] = {0ull, 0ull};
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_bwd_path_tiles, sizeof(v));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bwd_path_tiles, zero, sizeof(zero));
+    *general = v[0];
+    *lattice = v[1];
+    return e;
+}
 
 }  // namespace grf

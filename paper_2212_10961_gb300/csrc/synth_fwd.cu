@@ -579,8 +579,10 @@ __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 5) synth_batched_kernel(
                                                                 const WorkItem* __restrict__ work,
                                                                 int32_t n_work, int32_t* counter,
                                                                 int32_t* status) {
+    // lattice lanes (lattice_chunk) for the realisations of 2 or 3 dimensions
+    constexpr int NS = lattice_ns<2, C>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<FwdSmem<W>*>(smem_raw);
+    auto& sm = *reinterpret_cast<FwdSmem<W, NS>*>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     WarpSmem& ws = sm.w[warp];
@@ -604,13 +606,15 @@ __global__ void __launch_bounds__(W * 32, C >= 16 ? 4 : 5) synth_batched_kernel(
         // a realisation of lower dimension than the plan (e.g. 2-D fields on a
         // plan whose third coordinate is 0) runs the tile of its own dimension
         bool ok;
+        constexpr int NSD = DIM >= 2 ? NS : 0;
         if (DIM > 1 && d.dim == 1)
             ok = synth_warp_tile<1, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status);
         else if (DIM > 2 && d.dim == 2)
-            ok = synth_warp_tile<(DIM > 2 ? 2 : DIM), C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses,
-                                                             status);
+            ok = synth_warp_tile<(DIM > 2 ? 2 : DIM), C, 1, false, (DIM > 2 ? NS : 0)>(
+                d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status, sm.stp[warp]);
         else
-            ok = synth_warp_tile<DIM, C, 1>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status);
+            ok = synth_warp_tile<DIM, C, 1, false, NSD>(d, wbase, 0, d.n_pad / kWChunk, nullptr, ws, uses, status,
+                                                        sm.stp[warp]);
         if (!ok) break;
         __syncwarp();  // every lane is done with the descriptor
     }
@@ -673,7 +677,7 @@ int launch_fwd_cfg(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* 
 template <int DIM, int C, int W>
 int launch_batched_cfg(const FwdDesc* descs, const WorkItem* work, int32_t n_work, int32_t* counter,
                        int32_t* status, cudaStream_t st) {
-    const size_t smem = sizeof(FwdSmem<W>);
+    const size_t smem = sizeof(FwdSmem<W, lattice_ns<2, C>()>);
     auto kern = synth_batched_kernel<DIM, C, W>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));

@@ -860,6 +860,14 @@ def take_path_counts():
     return g.value, l_.value
 
 
+def take_adjoint_path_counts():
+    """(general, lattice) (warp, tile) pairs of 3-D adjoints since the last
+    call (grf_take_adjoint_path_counts); synchronises the device."""
+    g, l_ = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().grf_take_adjoint_path_counts(ctypes.byref(g), ctypes.byref(l_)))
+    return g.value, l_.value
+
+
 def mufu_probe(blocks, iters, stream=None):
     sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
     check(lib().grf_mufu_probe(int(blocks), int(iters), _ptr(sink), _stream_handle(stream)))
