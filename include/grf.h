@@ -572,8 +572,9 @@ int grf_device_info(int32_t *sm_count, int32_t *sm_clock_khz);
 int64_t grf_launch_count(void);
 
 /*
- * grf_take_path_counts -- warp tiles of 2-D and 3-D single-field syntheses
- * (grf_synth_field, grf_synth_mismatch) since the last call that took the
+ * grf_take_path_counts -- warp tiles of 2-D and 3-D syntheses
+ * (grf_synth_field, grf_synth_mismatch, grf_batch_launch) since the last
+ * call that took the
  * general path and the lattice path (lanes holding 4-cell rows of one
  * Cartesian grid, see the synthesis kernel), then resets both.  A tile split
  * over mode groups counts once per group.  Synchronises the device.

@@ -28,8 +28,9 @@
 
 namespace grf {
 
-// Warp tiles of single-field launches that took the general path [0] and the
-// lattice path [1] since the last grf_take_path_counts (diagnostics).
+// Warp tiles of 2-D and 3-D synthesis launches (single-field and batched)
+// that took the general path [0] and the lattice path [1] since the last
+// grf_take_path_counts (diagnostics).
 static __device__ unsigned long long g_path_warps[2];
 
 namespace {

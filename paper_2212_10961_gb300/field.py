@@ -853,7 +853,7 @@ def launch_count():
 
 
 def take_path_counts():
-    """(general, lattice) warp tiles of single-field syntheses since the last
+    """(general, lattice) warp tiles of 2-D and 3-D syntheses since the last
     call (grf_take_path_counts); synchronises the device."""
     g, l_ = ctypes.c_int64(0), ctypes.c_int64(0)
     check(lib().grf_take_path_counts(ctypes.byref(g), ctypes.byref(l_)))
