@@ -330,6 +330,37 @@ int grf_synth_field(const void *table, const grf_params *p, const void *plan, in
 size_t grf_synth_workspace_bytes(int64_t n_cells);
 
 /*
+ * Cartesian grids (tensor-core path).  When a single-segment 2-D or 3-D plan
+ * holds the cells of a Cartesian grid handed over x-fastest -- cell
+ * n = i + nx (k + ny l) at (X_i, Y_k, Z_l) for axes X, Y, Z of any spacing,
+ * with ny >= 2 -- grf_plan_cells records the grid (a check that runs with the
+ * planning kernels).  grf_synth_field on such a plan, with a field of the
+ * plan's dimension and a workspace of at least
+ * grf_synth_grid_workspace_bytes() bytes, then evaluates Eq. (DiscreteFT) as
+ * a matrix product on the tensor cores: every term factorises into an x
+ * phasor and a (y, z) phasor, so a block of 128 x-cells by 128 (y, z)-cells
+ * is a real product over K = 2N (Sec. 4.1 term by term, no approximation).
+ * Operands are split into FP16 hi + lo pairs (three products per term) and
+ * the FP32 partial sums of a few chunks of modes are folded into running
+ * sums: results agree with the FP64 definition to a few 1e-6 sigma, as on the
+ * general path.  Outputs
+ * and maps are those of the general path, in the caller's cell order.
+ *
+ * grf_synth_mismatch takes the same path on such a plan when the part of its
+ * workspace after the loss partials (grf_synth_mismatch_workspace_bytes(n) -
+ * grf_synth_workspace_bytes(n) bytes) holds grf_synth_grid_workspace_bytes().
+ *
+ * grf_synth_grid_workspace_bytes -- workspace bytes the grid path needs for
+ * `plan` (segment 0) and a table of n_modes modes, or 0 when the plan is not
+ * such a grid (or is unknown).  The first query (or synthesis) of a new plan
+ * waits on the host for that plan's own kernels to finish.
+ * grf_plan_grid_shape -- the plan's grid (nx, ny, nz), or zeros.  Same wait.
+ * GRF_EINVAL for NULL pointers or an unknown plan.
+ */
+size_t grf_synth_grid_workspace_bytes(const void *plan, int32_t segment, int64_t n_modes);
+int grf_plan_grid_shape(const void *plan, int32_t *nx, int32_t *ny, int32_t *nz);
+
+/*
  * grf_map_property -- the maps of grf_synth_field applied to an existing
  * field Y (device, n values), writing `out` in the same order.  Memory bound.
  * mean, sigma: the Gaussian field's mean and standard deviation (porosity).
@@ -590,6 +621,35 @@ int grf_take_path_counts(int64_t *general_warps, int64_t *lattice_warps);
  * the device.  GRF_EINVAL for NULL pointers, GRF_ECUDA if unreadable.
  */
 int grf_take_adjoint_path_counts(int64_t *general_tiles, int64_t *lattice_tiles);
+
+/*
+ * grf_take_grid_tiles -- tiles of 128 x 128 cells computed by the tensor-core
+ * grid path since the last call, then resets the count.  Synchronises the
+ * device.  GRF_EINVAL for NULL, GRF_ECUDA if the counter cannot be read.
+ */
+int grf_take_grid_tiles(int64_t *tiles);
+
+/*
+ * grf_debug_grid_path -- process-wide switch of the grid path (enable = 0:
+ * grid plans take the general path, for comparisons) and the number of
+ * 32-mode chunks the tensor-core accumulator sums before each fold into the
+ * running sum (fold_chunks = 1, 2, 4 or 8, lowered to a divisor of the
+ * table's chunk count; default 4).  GRF_EINVAL otherwise.
+ */
+int grf_debug_grid_path(int32_t enable, int32_t fold_chunks);
+
+/*
+ * grf_debug_mma_f16 -- self-test of the tensor-core path's operand layout,
+ * descriptors and accumulator read-back:
+ * D[r][c] = sum_k A[r][k] B[c][k] for r, c < 128 and k < 64 k_chunks, with
+ * A and B device arrays of 128 x (64 k_chunks) FP16 bit patterns (rows
+ * contiguous) and D a device array of 128 x 128 floats (row-major), summed in
+ * chunks of 64 into one FP32 accumulator.  status_dev: device int32 that gets
+ * bit 2 if a bounded wait expired.  GRF_EINVAL for NULL pointers or k_chunks
+ * outside [1, 4096].  Asynchronous on `stream`.
+ */
+int grf_debug_mma_f16(const uint16_t *A, const uint16_t *B, int32_t k_chunks, float *D, int32_t *status_dev,
+                      void *stream);
 
 /*
  * grf_debug_inject_alloc_failures -- host-side fault injection for tests

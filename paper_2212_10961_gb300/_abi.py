@@ -108,6 +108,9 @@ _SIGS = {
                                        ctypes.POINTER(grf_outputs), ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_void_p]),
     "grf_synth_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "grf_synth_grid_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    "grf_plan_grid_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "grf_map_property": (ctypes.c_int, [ctypes.POINTER(grf_map), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(grf_outputs),
                                         ctypes.c_void_p]),
@@ -144,6 +147,10 @@ _SIGS = {
     "grf_release": (ctypes.c_int, [ctypes.c_void_p]),
     "grf_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_mufu_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "grf_take_grid_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "grf_debug_grid_path": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "grf_debug_mma_f16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "grf_checked_build": (ctypes.c_int, []),
     "grf_take_index_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
 }

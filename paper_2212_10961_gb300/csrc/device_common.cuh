@@ -71,6 +71,15 @@ __device__ __forceinline__ float phase_exact_turns(const float* x, float4 c0, fl
     return frac_turn(hi + frac_turn(lo));
 }
 
+// Phase a v in turns, reduced to [-1/2, 1/2], of a = ah + al (FP32 pair) at a
+// point v of one axis: the product ah v split exactly by an FMA, integer
+// parts removed exactly (as phase_exact_turns, for one axis and no psi).
+__device__ __forceinline__ float turns_axis(float ah, float al, float v) {
+    const float pr = ah * v;
+    const float e = fmaf(ah, v, -pr);
+    return frac_turn(frac_turn(pr) + fmaf(al, v, e));
+}
+
 // Accumulate partial sum p into (s, e) with an exact TwoSum error term.
 __device__ __forceinline__ void two_sum_acc(float& s, float& e, float p) {
     float t = s + p;

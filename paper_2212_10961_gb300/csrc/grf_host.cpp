@@ -245,9 +245,93 @@ struct PlanMeta {
     int32_t dim;
     std::vector<int64_t> offsets;
     PlanLayout layout;
+    // Cartesian-grid check (single segment, 2-D / 3-D): 0 = not a grid,
+    // 1 = pending (its result lands in g_slots[slot] once `ev` completes),
+    // 2 = grid of gn[0] x gn[1] x gn[2] cells.
+    int32_t grid_state = 0;
+    int32_t gn[3] = {0, 0, 0};
+    uint64_t tag = 0;
+    int32_t slot = -1;
+    cudaEvent_t ev = nullptr;
 };
 std::mutex g_reg_mu;
 std::unordered_map<const void*, PlanMeta> g_plans;
+
+// Pinned ring that receives the grid checks of new plans (device -> host
+// copies ordered after the planning kernels); a slot reused before its plan
+// was first read is recognised by the tag and treated as "not a grid".
+constexpr int kGridSlots = 1024;
+GridCheck* g_slots = nullptr;
+int g_next_slot = 0;
+std::atomic<uint64_t> g_next_tag{1};
+std::atomic<int32_t> g_grid_enabled{1};  // grf_debug_grid_path
+std::atomic<int32_t> g_grid_fold{4};     // chunks of 32 modes per fold interval
+
+void drop_plan_event(PlanMeta& m) {
+    if (m.ev) cudaEventDestroy(m.ev);
+    m.ev = nullptr;
+}
+
+// The grid shape of `plan` (single segment), resolving a pending check by
+// waiting for the plan's own event (the planning kernels only).  Returns
+// false when the cells are not a Cartesian grid in x-fastest order.
+bool plan_grid(const void* plan, GridGeom* gg) {
+    PlanMeta m;
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        auto it = g_plans.find(plan);
+        if (it == g_plans.end()) return false;
+        m.grid_state = it->second.grid_state;
+        m.ev = it->second.ev;
+        m.slot = it->second.slot;
+        m.tag = it->second.tag;
+        m.dim = it->second.dim;
+        m.layout = it->second.layout;
+        m.offsets = it->second.offsets;
+        for (int c = 0; c < 3; ++c) m.gn[c] = it->second.gn[c];
+    }
+    if (m.grid_state == 0) return false;
+    if (m.grid_state == 1) {
+        int32_t st = 0, gn[3] = {0, 0, 0};
+        if (cudaEventSynchronize(m.ev) == cudaSuccess) {
+            GridCheck c;
+            {
+                std::lock_guard<std::mutex> lk(g_reg_mu);
+                c = g_slots[m.slot];
+            }
+            const int64_t n = m.offsets.back();
+            const int64_t nx = static_cast<int64_t>(c.c1);
+            const int64_t nxy = m.dim > 2 ? static_cast<int64_t>(c.c2) : n;
+            if (c.tag == m.tag && c.bad == 0 && nx >= 1 && nxy >= nx && nxy % nx == 0 && n % nxy == 0) {
+                const int64_t ny = nxy / nx, nz = n / nxy;
+                if (ny >= 2 && nx + ny + nz <= n && nx <= INT32_MAX) {
+                    st = 2;
+                    gn[0] = static_cast<int32_t>(nx);
+                    gn[1] = static_cast<int32_t>(ny);
+                    gn[2] = static_cast<int32_t>(nz);
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        auto it = g_plans.find(plan);
+        if (it != g_plans.end() && it->second.tag == m.tag) {
+            it->second.grid_state = st;
+            for (int c = 0; c < 3; ++c) it->second.gn[c] = gn[c];
+            drop_plan_event(it->second);
+        }
+        m.grid_state = st;
+        for (int c = 0; c < 3; ++c) m.gn[c] = gn[c];
+    }
+    if (m.grid_state != 2) return false;
+    const float* axes = reinterpret_cast<const float*>(static_cast<const unsigned char*>(plan) + m.layout.off_keys_in);
+    gg->nx = m.gn[0];
+    gg->ny = m.gn[1];
+    gg->nz = m.gn[2];
+    gg->X = axes;
+    gg->Y = axes + m.gn[0];
+    gg->Z = axes + m.gn[0] + m.gn[1];
+    return true;
+}
 
 bool lookup_plan(const void* plan, PlanMeta& out) {
     std::lock_guard<std::mutex> lk(g_reg_mu);
@@ -325,6 +409,8 @@ int64_t grf_launch_count(void) { return g_launches.load(); }
 
 int grf_release(const void* buffer) {
     std::lock_guard<std::mutex> lk(g_reg_mu);
+    auto it = g_plans.find(buffer);
+    if (it != g_plans.end()) drop_plan_event(it->second);
     g_plans.erase(buffer);
     g_batches.erase(buffer);
     return GRF_OK;
@@ -536,6 +622,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
     int32_t* order = reinterpret_cast<int32_t*>(base + L.off_order);
     int32_t* kpref = reinterpret_cast<int32_t*>(base + L.off_kpref);
     double* kap = reinterpret_cast<double*>(base + L.off_kappa);
+    float amp_max = 0.0f;
     for (int64_t s = 0; s < L.n_pad; ++s) {
         order[s] = -1;
         if (s >= N) continue;
@@ -549,6 +636,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
         // (-A, psi + 1/2) at odd positions: see mode_flipped
         const bool flip = mode_flipped(s);
         hot[s * 4 + 3] = static_cast<float>(flip ? -m->amp[j] : m->amp[j]);
+        amp_max = std::max(amp_max, std::fabs(hot[s * 4 + 3]));
         const double psi = flip ? (m->psi[j] <= 0.0 ? m->psi[j] + 0.5 : m->psi[j] - 0.5) : m->psi[j];
         float ah[3], al[3];
         for (int c = 0; c < 3; ++c) {
@@ -567,6 +655,7 @@ int grf_pack_table(const grf_modes* m, void* host_table, size_t bytes) try {
         c0[6] = ph;
         c0[7] = pl;
     }
+    reinterpret_cast<TableHeader*>(base)->amp_max = amp_max;
     // kpref[b] = #{s : h_s * E_b > 1}, E_b = 2^((b - bias) / 4)
     // (E_b grows with b, so the count only grows: one pass over the sorted modes)
     int64_t k = 0;
@@ -628,9 +717,33 @@ int grf_plan_cells(int32_t dim, int32_t n_segments, const int64_t* seg_offsets, 
     alloc_point();
     meta.offsets.assign(seg_offsets, seg_offsets + n_segments + 1);
     meta.layout = L;
-    const int err = launch_plan(dim, n_segments, seg_offsets, x, y, z, plan, L, stream);
+    meta.tag = g_next_tag.fetch_add(1);
+    const int err = launch_plan(dim, n_segments, seg_offsets, x, y, z, plan, L, meta.tag, stream);
     if (err != cudaSuccess) return cuda_fail(err, "plan kernels");
     std::lock_guard<std::mutex> lk(g_reg_mu);
+    if (n_segments == 1 && dim >= 2 && n >= 4) {
+        // the grid check's result, copied to a pinned slot after the planning
+        // kernels; read (once) by the first call that needs it
+        cudaError_t e = cudaSuccess;
+        if (!g_slots) e = cudaHostAlloc(reinterpret_cast<void**>(&g_slots), kGridSlots * sizeof(GridCheck),
+                                        cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&meta.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            meta.slot = g_next_slot;
+            g_next_slot = (g_next_slot + 1) % kGridSlots;
+            cudaStream_t st = static_cast<cudaStream_t>(stream);
+            e = cudaMemcpyAsync(&g_slots[meta.slot], &static_cast<PlanHeader*>(plan)->grid, sizeof(GridCheck),
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(meta.ev, st);
+        }
+        if (e != cudaSuccess) {
+            drop_plan_event(meta);
+            return cuda_fail(e, "grid check read-back");
+        }
+        meta.grid_state = 1;
+    }
+    auto it = g_plans.find(plan);
+    if (it != g_plans.end()) drop_plan_event(it->second);
     g_plans[plan] = std::move(meta);
     return GRF_OK;
 } catch (...) {
@@ -708,8 +821,44 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     if (rc) return rc;
     int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
     if (workspace && !aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
+    // Cartesian grid handed over x-fastest: tensor-core path when the
+    // workspace holds its tables
+    GridGeom gg{};
+    if (n > 0 && workspace && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim &&
+        plan_grid(plan, &gg) &&
+        ws_bytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
+        const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, workspace, g_grid_fold.load(), status,
+                                          stream);
+        if (err != cudaSuccess) return cuda_fail(err, "grid synth kernels");
+        return GRF_OK;
+    }
     const int err = launch_synth_fwd(d, workspace, workspace ? ws_bytes : 0, status, stream);
     if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+size_t grf_synth_grid_workspace_bytes(const void* plan, int32_t segment, int64_t n_modes) {
+    try {
+        if (!plan || segment != 0 || n_modes < 1 || n_modes > GRF_MAX_MODES) return 0;
+        GridGeom gg{};
+        if (!plan_grid(plan, &gg)) return 0;
+        return grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+    } catch (...) {
+        return 0;
+    }
+}
+
+int grf_plan_grid_shape(const void* plan, int32_t* nx, int32_t* ny, int32_t* nz) try {
+    if (!plan || !nx || !ny || !nz) return fail(GRF_EINVAL, "NULL argument");
+    PlanMeta meta;
+    if (!lookup_plan(plan, meta)) return fail(GRF_EINVAL, "unknown plan (not built by grf_plan_cells)");
+    GridGeom gg{};
+    const bool g = plan_grid(plan, &gg);
+    *nx = g ? gg.nx : 0;
+    *ny = g ? gg.ny : 0;
+    *nz = g ? gg.nz : 0;
     return GRF_OK;
 } catch (...) {
     return host_exception();
@@ -761,6 +910,17 @@ int grf_synth_mismatch(const void* table, const grf_params* p, const void* plan,
     if (rc) return rc;
     int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
     unsigned char* split_ws = static_cast<unsigned char*>(workspace) + lbytes;
+    // Cartesian grid: the tensor-core path when the rest of the workspace
+    // holds its tables and the loss partials fit
+    GridGeom gg{};
+    if (n > 0 && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim && plan_grid(plan, &gg) &&
+        ws_bytes - lbytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad) &&
+        grid_loss_partials(gg.nx, gg.ny, gg.nz) <= mismatch_partials(n)) {
+        const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, split_ws, g_grid_fold.load(),
+                                          status, stream);
+        if (err != cudaSuccess) return cuda_fail(err, "grid synth kernels");
+        return GRF_OK;
+    }
     const int err = launch_synth_fwd(d, split_ws, ws_bytes - lbytes, status, stream);
     if (err != cudaSuccess) return cuda_fail(err, "synth kernel");
     return GRF_OK;
@@ -1337,6 +1497,39 @@ int grf_take_adjoint_path_counts(int64_t* general_tiles, int64_t* lattice_tiles)
     if (e != cudaSuccess) return cuda_fail(e, "adjoint path counters");
     *general_tiles = static_cast<int64_t>(g);
     *lattice_tiles = static_cast<int64_t>(l);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+int grf_take_grid_tiles(int64_t* tiles) try {
+    if (!tiles) return fail(GRF_EINVAL, "NULL argument");
+    *tiles = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the grid tile counter");
+    unsigned long long v = 0ull;
+    e = static_cast<cudaError_t>(take_grid_tiles(&v));
+    if (e != cudaSuccess) return cuda_fail(e, "grid tile counter");
+    *tiles = static_cast<int64_t>(v);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+int grf_debug_grid_path(int32_t enable, int32_t fold_chunks) {
+    if (fold_chunks != 1 && fold_chunks != 2 && fold_chunks != 4 && fold_chunks != 8)
+        return fail(GRF_EINVAL, "fold_chunks must be 1, 2, 4 or 8");
+    g_grid_enabled.store(enable ? 1 : 0);
+    g_grid_fold.store(fold_chunks);
+    return GRF_OK;
+}
+
+int grf_debug_mma_f16(const uint16_t* A, const uint16_t* B, int32_t k_chunks, float* D, int32_t* status_dev,
+                      void* stream) try {
+    if (!A || !B || !D || !status_dev) return fail(GRF_EINVAL, "NULL argument");
+    if (k_chunks < 1 || k_chunks > 4096) return fail(GRF_EINVAL, "k_chunks must be in [1, 4096]");
+    const int err = launch_mma_probe(A, B, k_chunks, D, status_dev, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "MMA self-test kernel");
     return GRF_OK;
 } catch (...) {
     return host_exception();

@@ -71,7 +71,9 @@ struct TableHeader {
     int64_t off_kpref;
     int64_t total_bytes;
     int64_t off_kappa;
-    int64_t reserved[6];
+    float amp_max;      // largest |A_j| as stored (FP32): the grid path's operand scale
+    int32_t pad_;
+    int64_t reserved[5];
 };
 static_assert(sizeof(TableHeader) <= 256, "table header must fit in 256 bytes");
 
@@ -105,6 +107,14 @@ inline TableLayout table_layout(int64_t n_modes) {
 //   sort_tmp          : radix-sort temporary storage
 // ---------------------------------------------------------------------------
 constexpr uint32_t kPlanMagic = 0x4E4C5047u;  // "GPLN"
+
+struct GridCheck {
+    unsigned long long c1;  // min {n >= 1 : (y_n, z_n) != (y_0, z_0)}, n_cells if none
+    unsigned long long c2;  // min {n >= 1 : z_n != z_0}, n_cells if none (3-D)
+    int32_t bad;            // some cell is not at (X_i, Y_k, Z_l) of its index
+    int32_t pad_;
+    uint64_t tag;           // host-assigned plan number
+};
 constexpr int kMortonBits = 10;                // quantised coordinate bits per axis
 
 struct PlanHeader {
@@ -115,7 +125,12 @@ struct PlanHeader {
     int64_t n_cells;
     int64_t off_segs, off_xs, off_ys, off_zs, off_perm, off_keys_in, off_keys_out, off_vals_in,
         off_sort_tmp, sort_tmp_bytes, total_bytes;
-    int64_t reserved[14];
+    // Cartesian-grid check of a single-segment 2-D / 3-D plan (GridCheck):
+    // the first index whose (y, z) differs from cell 0's (= nx), the first
+    // whose z differs (= nx ny), a mismatch flag, and the plan's tag.  The
+    // axes X (nx), Y (ny), Z (nz) are written over the keys_in scratch.
+    GridCheck grid;
+    int64_t reserved[10];
 };
 static_assert(sizeof(PlanHeader) <= 256, "plan header must fit in 256 bytes");
 
@@ -201,6 +216,52 @@ struct FwdDesc {
     MapDev map;
 };
 
+// Cartesian grid of a plan: cell n = i + nx (k + ny l) at (X_i, Y_k, Z_l).
+struct GridGeom {
+    int32_t nx, ny, nz;
+    const float* X;
+    const float* Y;
+    const float* Z;
+};
+
+// Tables of one grid synthesis (workspace) as the prep kernel fills them.
+struct GridPrep {
+    const TableHeader* thdr;
+    const float4* hot;
+    const float4* cold;
+    const float* X;
+    const float* Y;
+    const float* Z;
+    int32_t nx, ny, nz, n_pad, nc, n_mt, n_kt, dim;
+    int32_t form;          // 1: 3-D (B formed from ytab, wztab), 0: B tabulated in btab
+    unsigned char* atab;   // x phasors: FP16 hi/lo tiles [n_mt][nc][2][128 x 64]
+    unsigned char* btab;   // 2-D: B tiles [n_kt][nc][2][128 x 64]
+    float2* ytab;          // 3-D: [nc][ny][32] y phasors
+    float2* wztab;         // 3-D: [nc][nz][32] (amplitude, psi, z) phasors
+};
+
+// One grid synthesis as the tensor-core kernel sees it.
+struct GridDesc {
+    const unsigned char* atab;
+    const unsigned char* btab;
+    const float2* ytab;
+    const float2* wztab;
+    const TableHeader* thdr;
+    int32_t nx, ny, nz, n_pad;
+    int32_t nc;       // chunks of 32 modes
+    int32_t fc;       // chunks per fold interval (1, 2 or 4)
+    int32_t n_mt, n_kt, n_lt;
+    int32_t pk_log2;  // (y, z) patch: 2^pk_log2 along y, 128 / 2^pk_log2 along z
+    int64_t n_tiles;
+    int32_t form;     // 1: B formed in shared memory from the staged table rows
+    int32_t sa;       // stages of the copy ring
+    int32_t a_stage;  // bytes per copy stage
+    int32_t off_b;    // formed B ring (form)
+    int32_t off_bar;  // barriers
+    int32_t pad_;
+    MapDev map;
+};
+
 // Work tile of the batched launch: realisation r, tile index t inside it.
 struct WorkItem {
     int32_t r;
@@ -227,6 +288,8 @@ constexpr uint32_t kBatchMagic = 0x48435442u;  // "BTCH"
 int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream);
 // Entries of MapDev::lpart a launch of n cells may write (kMapMismatch).
 int64_t mismatch_partials(int64_t n_cells);
+// loss = (sum of the nb partials, fixed order) * inv_n, one block.
+int launch_loss_sum(const double* part, int64_t nb, double inv_n, double* out, void* stream);
 
 // Checked builds (-DGRF_CHECKED=1): device accesses skipped since the last
 // call because an index read from device memory was out of range, per
@@ -247,8 +310,9 @@ int fwd_tile_cells(int cfg);
 int launch_map(const MapDev& m, int64_t n, const float* Y, void* stream);
 int launch_bimap(const grf_bimap& m, int64_t n, const float* Y1, const float* Y2, uint8_t* F, float* P,
                  void* stream);
+// tag: host-assigned plan number, stored with the grid check (GridCheck::tag)
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
-                const float* y, const float* z, void* plan, const PlanLayout& L, void* stream);
+                const float* y, const float* z, void* plan, const PlanLayout& L, uint64_t tag, void* stream);
 // periodic_mask: bit c set when axis c is periodic (its frequency is rounded,
 // so its dL/da reaches neither kappa, l nor R).
 int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
@@ -261,6 +325,19 @@ int launch_mismatch(int64_t n, const float* K, const float* T, float* gY, double
                     void* stream);
 size_t mismatch_workspace_bytes(int64_t n);
 int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream);
+// Grid path (synth_grid.cu): workspace bytes of the tables, the launch (prep
+// + tensor-core kernel), tiles computed since the last call (synchronous),
+// and the MMA self-test.
+size_t grid_ws_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad);
+// Loss partials (kMapMismatch) the grid path writes: one per epilogue warp per tile.
+int64_t grid_loss_partials(int32_t nx, int32_t ny, int32_t nz);
+int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const GridGeom& gg, const MapDev& map,
+                      void* ws, int32_t fc, int32_t* status, void* stream);
+int take_grid_tiles(unsigned long long* tiles);
+int launch_mma_probe(const uint16_t* A, const uint16_t* B, int32_t k_chunks, float* D, int32_t* status,
+                     void* stream);
+int launch_grid_check(int32_t dim, int64_t n, const float* x, const float* y, const float* z, void* plan,
+                      const PlanLayout& L, void* stream);
 int launch_selftest_wait(uint64_t limit_ns, int32_t* status, void* stream);
 void count_launches(int64_t n);
 // Record `message` as the calling thread's last error and return `code`.

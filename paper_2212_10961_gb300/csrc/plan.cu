@@ -16,6 +16,7 @@
 // deterministic (the sort is stable, so equal keys keep the input order).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <new>
@@ -590,10 +591,103 @@ void run_sort(const float* x, const float* y, const float* z, int dim, int64_t n
     }
 }
 
+// ---- Cartesian-grid check of a single-segment plan --------------------------
+// Cells given x-fastest on the tensor product of three axes, cell
+// n = i + nx (k + ny l) at (X_i, Y_k, Z_l), let the synthesis use the tensor-
+// core grid path.  Pass 1 finds nx (the first cell whose (y, z) differs from
+// cell 0's) and nx ny (the first whose z differs); pass 2 checks every cell
+// against those axes and writes X, Y, Z.  The host reads the result later.
+constexpr int kGridThreads = 256;
+constexpr int kGridPer = 16;
+
+__device__ __forceinline__ unsigned long long block_min_u64(unsigned long long v, unsigned long long* red) {
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o < v ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kGridThreads / 32; ++w) v = red[w] < v ? red[w] : v;
+    return v;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kGridThreads) grid_scan_kernel(const float* y, const float* z, int32_t dim,
+                                                                 int64_t n, GridCheck* gc) {
+    __shared__ unsigned long long red1[kGridThreads / 32], red2[kGridThreads / 32];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kGridThreads * kGridPer);
+    // blocks past the current candidates cannot lower them
+    const unsigned long long lim =
+        dim > 2 ? *reinterpret_cast<volatile unsigned long long*>(&gc->c2)
+                : *reinterpret_cast<volatile unsigned long long*>(&gc->c1);
+    if (static_cast<unsigned long long>(base) >= lim) return;
+    const float y0 = __ldg(y);
+    const float z0 = dim > 2 ? __ldg(z) : 0.0f;
+    unsigned long long m1 = ~0ull, m2 = ~0ull;
+#pragma unroll 4
+    for (int q = 0; q < kGridPer; ++q) {
+        const int64_t i = base + static_cast<int64_t>(q) * kGridThreads + threadIdx.x;
+        if (i >= 1 && i < n) {
+            const bool zd = dim > 2 && __ldg(z + i) != z0;
+            if (zd || __ldg(y + i) != y0) m1 = m1 < static_cast<unsigned long long>(i) ? m1 : i;
+            if (zd) m2 = m2 < static_cast<unsigned long long>(i) ? m2 : i;
+        }
+    }
+    m1 = block_min_u64(m1, red1);
+    m2 = block_min_u64(m2, red2);
+    if (threadIdx.x == 0) {
+        if (m1 != ~0ull) atomicMin(&gc->c1, m1);
+        if (m2 != ~0ull) atomicMin(&gc->c2, m2);
+    }
+}
+
+__global__ void __launch_bounds__(kGridThreads) grid_verify_kernel(const float* x, const float* y, const float* z,
+                                                                   int32_t dim, int64_t n, GridCheck* gc,
+                                                                   float* axes) {
+    const int64_t nx = static_cast<int64_t>(gc->c1);
+    const int64_t nxy = dim > 2 ? static_cast<int64_t>(gc->c2) : n;
+    // a shape that is not a tensor product is rejected on the host
+    if (nx < 1 || nxy < nx || nxy % nx != 0 || n % nxy != 0) return;
+    const int64_t ny = nxy / nx, nz = n / nxy;
+    const bool room = nx + ny + nz <= n;  // the axes go over the keys scratch (n floats)
+    bool ok = true;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t ix = i % nx;
+        const int64_t r = i / nx;
+        const int64_t k = r % ny;
+        const int64_t l = r / ny;
+        const float xv = __ldg(x + i), yv = __ldg(y + i);
+        const float zv = dim > 2 ? __ldg(z + i) : 0.0f;
+        ok = ok && xv == __ldg(x + ix) && yv == __ldg(y + k * nx);
+        if (dim > 2) ok = ok && zv == __ldg(z + l * nxy);
+        if (room) {
+            if (i < nx) axes[i] = xv;
+            if (ix == 0 && l == 0) axes[nx + k] = yv;
+            if (ix == 0 && k == 0) axes[nx + ny + l] = zv;
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicOr(&gc->bad, 1);
+}
+
 }  // namespace
 
+int launch_grid_check(int32_t dim, int64_t n, const float* x, const float* y, const float* z, void* plan,
+                      const PlanLayout& L, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(plan);
+    GridCheck* gc = &reinterpret_cast<PlanHeader*>(base)->grid;
+    float* axes = reinterpret_cast<float*>(base + L.off_keys_in);
+    const int64_t per = int64_t(kGridThreads) * kGridPer;
+    grid_scan_kernel<<<static_cast<unsigned>((n + per - 1) / per), kGridThreads, 0, st>>>(y, z, dim, n, gc);
+    const int64_t vb = std::min<int64_t>((n + kGridThreads - 1) / kGridThreads, 152 * 16);
+    grid_verify_kernel<<<static_cast<unsigned>(vb), kGridThreads, 0, st>>>(x, y, z, dim, n, gc, axes);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host, const float* x,
-                const float* y, const float* z, void* plan, const PlanLayout& L, void* stream) {
+                const float* y, const float* z, void* plan, const PlanLayout& L, uint64_t tag, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* base = static_cast<unsigned char*>(plan);
     const int64_t n = seg_offsets_host[n_segments];
@@ -627,6 +721,10 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     h.off_sort_tmp = L.off_sort_tmp;
     h.sort_tmp_bytes = L.sort_tmp_bytes;
     h.total_bytes = L.total;
+    h.grid.c1 = static_cast<unsigned long long>(n);
+    h.grid.c2 = static_cast<unsigned long long>(n);
+    h.grid.bad = (n_segments == 1 && dim >= 2 && n >= 4) ? 0 : 1;
+    h.grid.tag = tag;
     cudaError_t err = cudaMemcpyAsync(hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess) return err;
     // cudaMemcpyAsync from pageable memory returns once the source is staged.
@@ -682,6 +780,10 @@ int launch_plan(int32_t dim, int32_t n_segments, const int64_t* seg_offsets_host
     const unsigned ggrid = static_cast<unsigned>((n + gtpb * kGatherPer - 1) / (gtpb * kGatherPer));
     gather_kernel<<<ggrid, gtpb, 0, st>>>(x, y, z, dim, n, perm, xs, ys, zs);
     count_launches(1);
+    if (n_segments == 1 && dim >= 2 && n >= 4) {
+        const int e = launch_grid_check(dim, n, x, y, z, plan, L, st);
+        if (e != cudaSuccess) return static_cast<cudaError_t>(e);
+    }
     return cudaGetLastError();
 }
 

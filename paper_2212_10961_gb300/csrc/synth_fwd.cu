@@ -724,6 +724,12 @@ size_t synth_workspace_bytes(int64_t n_cells) {
 // split finalize, whichever is more.
 int64_t mismatch_partials(int64_t n_cells) { return (n_cells + 127) / 128 + 1; }
 
+int launch_loss_sum(const double* part, int64_t nb, double inv_n, double* out, void* stream) {
+    loss_sum_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(part, nb, inv_n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 int launch_synth_fwd(const FwdDesc& d, void* workspace, size_t ws_bytes, int32_t* status, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (d.dim) {

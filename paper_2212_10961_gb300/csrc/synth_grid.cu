@@ -1,0 +1,760 @@
+// Spectral synthesis on Cartesian grids with the fifth-generation tensor
+// cores (Icardi et al., arXiv 2212.10961, Sec. 4.1, Eq. DiscreteFT).
+//
+// When the cells are the tensor product of three axes -- cell (i, k, l) at
+// (X_i, Y_k, Z_l) -- every term of the sum factorises,
+//     A_j cos(2 pi (a_j . x + psi_j)) = Re[ Xp_ij W_jc ],
+//     Xp_ij = e^{2 pi i a_jx X_i},  W_jc = A_j e^{2 pi i (psi_j + a_jy Y_k + a_jz Z_l)},
+// so on a block of 128 x-cells (rows i) by 128 (y, z) cells (columns c) the
+// field is a real matrix product over K = 2N:
+//     Y[i, c] - mu = sum_j ( Re Xp_ij Re W_jc - Im Xp_ij Im W_jc ).
+// The x phasors (operand A) are the same for every block of one x range:
+// they are tabulated once per call, already in the tensor core's shared-
+// memory layout, and copied in chunk by chunk.  Operand B:
+//   * 3-D grids: a tile's columns are a patch of 2^p y-cells by 128 / 2^p
+//     z-cells; per chunk the loader copies the patch's y phasors and
+//     (amplitude, psi, z) phasors (tables stored chunk by chunk) next to A,
+//     and the epilogue warps form B = WZ * Yp in shared memory;
+//   * 2-D grids (and 3-D grids of one z layer): B = W * Yp is tabulated like
+//     A and copied in as well.
+// All phases are exactly reduced (hi/lo frequencies, FMA-split products)
+// before an accurate sincospi.
+//
+// Precision.  Each operand value v (|v| <= 1 after scaling the amplitudes
+// by a power of two S) is split into FP16 numbers hi + lo with
+// |v - hi - lo| <= 2^-24; a term costs three tensor-core products
+// hi.hi + hi.lo + lo.hi (the dropped lo.lo is below 2^-24).  The hi.hi
+// products go to an FP32 accumulator in TMEM that takes `fc` chunks of 32
+// modes and is then folded into a running FP32 sum (a few tens of folds per
+// cell), so the accumulator's own rounding acts on short partial sums only;
+// the two correction products, 2^-11 smaller, go to a second accumulator
+// that spans the whole tile.
+//
+// Kernel structure (one CTA per SM, persistent over tiles):
+//   warps 0-7 : form B for each chunk (3-D), fold the accumulator, write the maps;
+//   warp 8    : one thread issues the MMAs (tcgen05.mma kind::f16, M = N = 128);
+//   warp 9    : one thread issues the bulk copies; the warp owns TMEM.
+// A ring of `sa` stages (A hi/lo and the chunk's tables, or A and B) and,
+// in 3-D, a ring of 2 formed B stages.  TMEM (512 columns): the hi.hi
+// accumulator double-buffered (2 x 128), the correction accumulator (128) and
+// the running sums (128).  Every mbarrier wait is bounded and reports through
+// the status word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "device_common.cuh"
+#include "tcgen05.cuh"
+
+namespace grf {
+
+// Tiles computed by the grid path since the last grf_take_grid_tiles.
+static __device__ unsigned long long g_grid_tiles;
+
+namespace {
+
+constexpr int kGM = 128;                    // x cells per tile (TMEM lanes)
+constexpr int kGN = 128;                    // (y, z) cells per tile (accumulator columns)
+constexpr int kGModes = 32;                 // modes per chunk
+constexpr int kGK = 2 * kGModes;            // K elements per chunk (re, im)
+constexpr int kGOpBytes = kGM * kGK * 2;    // one FP16 operand tile (128 x 64): 16 KB
+constexpr int kGPair = 2 * kGOpBytes;       // hi and lo tiles of one operand
+constexpr int kGRowBytes = kGModes * 8 + 16;  // one table row of a chunk: 32 float2 + 16 bytes of padding
+                                              // (consecutive rows start in different shared-memory banks)
+constexpr int kGMaxSA = 4;
+constexpr int kGSB = 2;                     // formed B stages (3-D)
+constexpr int kGEpiWarps = 8;
+constexpr int kGThreads = 32 * (kGEpiWarps + 2);
+constexpr uint32_t kGLbo = 128;             // core matrices adjacent along K: contiguous
+constexpr uint32_t kGSbo = 1024;            // 8-row groups: 8 core matrices of K apart
+constexpr uint32_t kGTmemCols = 512;
+constexpr uint32_t kGCorrCol = 256;         // hi.lo + lo.hi accumulator of the tile
+constexpr uint32_t kGSumCol = 384;          // running FP32 sum of the folded hi.hi intervals
+constexpr int kGBarBytes = 256;
+constexpr int kGSmemMax = 232448;           // dynamic shared memory per CTA (227 KB)
+static_assert(kGM == 128 && kGN == 128, "tile shape is fixed by the TMEM layout");
+
+// Amplitude scale: the smallest power of two S >= max |A_j| (1 when all
+// amplitudes vanish), so that |W| <= 1.
+__device__ __forceinline__ float grid_scale(const TableHeader* h) {
+    const float m = h->amp_max;
+    if (!(m > 0.0f)) return 1.0f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.0f, e);
+}
+
+// Bounded wait that also gives up once another role has set the abort flag.
+__device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int32_t* abort, int32_t* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t round = 0; round < kWaitMaxRounds; ++round) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitLimitNs) break;
+    }
+    *abort = 1;
+    atomicOr(status, 2);
+    return false;
+}
+
+// Byte offset of the 16-byte row segment (row r, K elements 8 kk8 .. 8 kk8 + 7)
+// in a 128 x 64 K-major FP16 tile: element (r, kk) lives at
+// (r / 8) * 1024 + (kk / 8) * 128 + (r % 8) * 16 + (kk % 8) * 2.
+__host__ __device__ __forceinline__ uint32_t tile_off(int r, int kk8) {
+    return static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(kk8) * kGLbo +
+           static_cast<uint32_t>(r & 7) * 16u;
+}
+
+// B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the 16 modes
+// 16 hm .. 16 hm + 15 of the chunk, from the staged table rows ty (y) and tw
+// (amplitude, psi, z), written as (re, im) FP16 pairs into the hi and lo
+// tiles at boff.
+__device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw, uint32_t boff) {
+#pragma unroll
+    for (int g4 = 0; g4 < 4; ++g4) {
+        const float4 ya = ty[2 * g4], yb = ty[2 * g4 + 1];
+        const float4 wa = tw[2 * g4], wb = tw[2 * g4 + 1];
+        const float r0 = fmaf(wa.x, ya.x, -wa.y * ya.y), i0 = fmaf(wa.x, ya.y, wa.y * ya.x);
+        const float r1 = fmaf(wa.z, ya.z, -wa.w * ya.w), i1 = fmaf(wa.z, ya.w, wa.w * ya.z);
+        const float r2 = fmaf(wb.x, yb.x, -wb.y * yb.y), i2 = fmaf(wb.x, yb.y, wb.y * yb.x);
+        const float r3 = fmaf(wb.z, yb.z, -wb.w * yb.w), i3 = fmaf(wb.z, yb.w, wb.w * yb.z);
+        uint4 H, L;
+        tc::split_f16x2(r0, i0, H.x, L.x);
+        tc::split_f16x2(r1, i1, H.y, L.y);
+        tc::split_f16x2(r2, i2, H.z, L.z);
+        tc::split_f16x2(r3, i3, H.w, L.w);
+        *reinterpret_cast<uint4*>(bhi + boff + g4 * kGLbo) = H;
+        *reinterpret_cast<uint4*>(bhi + kGOpBytes + boff + g4 * kGLbo) = L;
+    }
+}
+
+struct TileIdx {
+    int mt, kt, k0, l0, pkv, plv;  // x tile, y tile, first y and z cell, valid y and z cells of the patch
+};
+__device__ __forceinline__ TileIdx tile_idx(const GridDesc& d, int64_t tile) {
+    TileIdx t;
+    t.mt = static_cast<int>(tile % d.n_mt);
+    const int64_t rest = tile / d.n_mt;
+    t.kt = static_cast<int>(rest % d.n_kt);
+    t.k0 = t.kt << d.pk_log2;
+    t.l0 = static_cast<int>(rest / d.n_kt) * (kGN >> d.pk_log2);
+    t.pkv = min(1 << d.pk_log2, d.ny - t.k0);
+    t.plv = min(kGN >> d.pk_log2, d.nz - t.l0);
+    return t;
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int32_t* status) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + d.off_bar);
+    uint64_t* afull = bars;                // [sa] stage's copies landed (transaction bytes)
+    uint64_t* afree = bars + kGMaxSA;      // [sa] stage's MMAs completed
+    uint64_t* bfull = bars + 2 * kGMaxSA;  // [2] B formed (one arrival per epilogue warp)
+    uint64_t* bfree = bfull + kGSB;        // [2] B's MMAs completed
+    uint64_t* accfull = bfree + kGSB;      // [2] interval's MMAs completed
+    uint64_t* accfree = accfull + 2;       // [2] accumulator read by every epilogue warp
+    uint64_t* corrfree = accfree + 2;      // correction accumulator read (tile end)
+    uint64_t* done = corrfree + 1;         // all MMAs of this CTA completed
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int32_t* abort = reinterpret_cast<volatile int32_t*>(done + 2);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const bool form = d.form != 0;
+    const bool mm = (d.map.bits & kMapMismatch) != 0;
+    const int SA = d.sa;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGMaxSA; ++s) {
+            mbar_init(afull + s, 1);
+            mbar_init(afree + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bfull + b, kGEpiWarps);
+            mbar_init(bfree + b, 1);
+            mbar_init(accfull + b, 1);
+            mbar_init(accfree + b, kGEpiWarps);
+        }
+        mbar_init(corrfree, kGEpiWarps);
+        mbar_init(done, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == kGEpiWarps + 1) tc::alloc(tslot, kGTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    const int NI = d.nc / d.fc;  // fold intervals per tile
+    const int pkm = (1 << d.pk_log2) - 1;
+
+    if (warp < kGEpiWarps) {
+        // ---- B formation (3-D), folds, maps ---------------------------------------
+        const int q = warp & 3;           // TMEM lane quarter (rows 32 q .. 32 q + 31)
+        const int h = warp >> 2;          // column half (64 h .. 64 h + 63)
+        const int t = threadIdx.x;        // 0 .. 255
+        const int n_col = t & 127;        // column this thread forms
+        const int hm = t >> 7;            // half of the chunk's modes it forms
+        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        const uint32_t boff = tile_off(n_col, 4 * hm);
+        const float S = grid_scale(d.thdr);
+        uint32_t g = 0, gi = 0, tile_count = 0;
+        for (int64_t tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x, ++tile_count) {
+            const TileIdx ti = tile_idx(d, tile);
+            // staged table rows this thread reads: y row and (amplitude, psi, z) row
+            const int ry = min(n_col & pkm, ti.pkv - 1);
+            const int rz = min(n_col >> d.pk_log2, ti.plv - 1);
+            const int toff_y = kGPair + ry * kGRowBytes + 16 * hm * 8;
+            const int toff_w = kGPair + ((1 << d.pk_log2) + rz) * kGRowBytes + 16 * hm * 8;
+
+            // fold of interval gidx: the hi.hi accumulator into the running sum
+            // (plain FP32: a few tens of folds per cell); the last fold of a
+            // tile adds the correction accumulator and writes the cells
+            double lsum = 0.0;  // kMapMismatch: this lane's sum of (K - T)^2 over the tile
+            auto fold = [&](uint32_t gidx, bool first, bool last) -> bool {
+                const uint32_t b = gidx & 1u;
+                // warp-uniform outcome: the TMEM moves below are warp-wide
+                if (!__all_sync(0xffffffffu, gwait(accfull + b, (gidx >> 1) & 1u, abort, status))) return false;
+                tc::fence_after();
+                if (!last) {
+#pragma unroll 1
+                    for (int blk = 0; blk < 2; ++blk) {  // 32 columns per TMEM round trip
+                        const uint32_t col = static_cast<uint32_t>(64 * h + 32 * blk);
+                        uint32_t p[32], sm[32];
+                        tc::ld32(tbase + lane_off + b * kGN + col, p);
+                        if (!first) tc::ld32(tbase + lane_off + kGSumCol + col, sm);
+                        tc::wait_ld();
+                        if (blk == 1) {
+                            tc::fence_before();
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(accfree + b);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 32; ++cc)
+                            sm[cc] = first ? p[cc] : __float_as_uint(__uint_as_float(sm[cc]) + __uint_as_float(p[cc]));
+                        tc::st32(tbase + lane_off + kGSumCol + col, sm);
+                    }
+                    tc::wait_st();
+                } else {
+                    const int i = ti.mt * kGM + 32 * q + lane;
+#pragma unroll 1
+                    for (int blk = 0; blk < 4; ++blk) {  // 16 columns at a time, then the maps
+                        const uint32_t col = static_cast<uint32_t>(64 * h + 16 * blk);
+                        uint32_t p[16], sm[16], cr[16];
+                        tc::ld16(tbase + lane_off + b * kGN + col, p);
+                        tc::ld16(tbase + lane_off + kGCorrCol + col, cr);
+                        if (!first) tc::ld16(tbase + lane_off + kGSumCol + col, sm);
+                        tc::wait_ld();
+                        if (blk == 3) {
+                            tc::fence_before();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tc::mbar_arrive(accfree + b);
+                                tc::mbar_arrive(corrfree);
+                            }
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc) {
+                            float v = __uint_as_float(p[cc]);
+                            if (!first) v = __uint_as_float(sm[cc]) + v;
+                            v += __uint_as_float(cr[cc]);
+                            const int c = static_cast<int>(col) + cc;
+                            const int k = ti.k0 + (c & pkm);
+                            const int l = ti.l0 + (c >> d.pk_log2);
+                            if (i < d.nx && k < d.ny && l < d.nz) {
+                                const int64_t o = i + static_cast<int64_t>(d.nx) *
+                                                          (k + static_cast<int64_t>(d.ny) * l);
+                                const float y = v * S + d.map.mu;
+                                map_store(d.map, o, y);
+                                if (mm) lsum += mismatch_store(d.map, o, y);
+                            }
+                        }
+                    }
+                }
+                return true;
+            };
+
+            bool ok = true;
+            if (form) {
+                for (int c = 0; c < d.nc; ++c, ++g) {
+                    const int sb = static_cast<int>(g % kGSB);
+                    const int sa = static_cast<int>(g % SA);
+                    if (g >= kGSB &&
+                        !__all_sync(0xffffffffu, gwait(bfree + sb, ((g / kGSB) - 1u) & 1u, abort, status))) {
+                        ok = false;
+                        break;
+                    }
+                    if (!__all_sync(0xffffffffu, gwait(afull + sa, (g / SA) & 1u, abort, status))) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned char* st = gsm + sa * d.a_stage;
+                    form_b(gsm + d.off_b + sb * kGPair, reinterpret_cast<const float4*>(st + toff_y),
+                           reinterpret_cast<const float4*>(st + toff_w), boff);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bfull + sb);
+                    if ((c + 1) % d.fc == 0) {
+                        const int iv = (c + 1) / d.fc - 1;  // interval whose chunks are all formed
+                        if (iv >= 1) {
+                            if (!fold(gi, iv == 1, false)) {
+                                ok = false;
+                                break;
+                            }
+                            ++gi;
+                        }
+                    }
+                }
+                if (!ok || !fold(gi, NI == 1, true)) break;
+                ++gi;
+            } else {
+                for (int iv = 0; iv < NI; ++iv, ++gi) {
+                    if (!fold(gi, iv == 0, iv == NI - 1)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) break;
+            }
+            if (mm) {
+                // fixed butterfly order, one partial per (tile, warp): the loss
+                // does not depend on which CTA took the tile
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+                if (lane == 0) d.map.lpart[tile * kGEpiWarps + warp] = lsum;
+            }
+        }
+    } else if (warp == kGEpiWarps) {
+        // ---- MMA issue ------------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16_f32(kGM, kGN);
+            uint32_t g = 0, gi = 0, tile_count = 0;
+            bool ok = true;
+            const uint32_t dc = tbase + kGCorrCol;
+            for (int64_t tile = blockIdx.x; tile < d.n_tiles && ok; tile += gridDim.x, ++tile_count) {
+                // the previous tile's correction accumulator has been read
+                if (tile_count >= 1 && !gwait(corrfree, (tile_count - 1u) & 1u, abort, status)) {
+                    ok = false;
+                    break;
+                }
+                for (int iv = 0; iv < NI && ok; ++iv, ++gi) {
+                    const uint32_t b = gi & 1u;
+                    if (gi >= 2 && !gwait(accfree + b, ((gi >> 1) - 1u) & 1u, abort, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t dt = tbase + b * kGN;
+                    for (int cc = 0; cc < d.fc; ++cc, ++g) {
+                        const int sa = static_cast<int>(g % SA);
+                        const int sb = static_cast<int>(g % kGSB);
+                        if (!gwait(afull + sa, (g / SA) & 1u, abort, status) ||
+                            (form && !gwait(bfull + sb, (g / kGSB) & 1u, abort, status))) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+                        const uint32_t aa = smem_u32(gsm + sa * d.a_stage);
+                        const uint32_t ba = form ? smem_u32(gsm + d.off_b + sb * kGPair) : aa + kGPair;
+#pragma unroll
+                        for (int ks = 0; ks < kGK / 16; ++ks) {
+                            const uint32_t ko = static_cast<uint32_t>(ks) * 2u * kGLbo;  // 16 K elements
+                            const uint64_t ah = tc::smem_desc(aa + ko, kGLbo, kGSbo);
+                            const uint64_t al = tc::smem_desc(aa + kGOpBytes + ko, kGLbo, kGSbo);
+                            const uint64_t bh = tc::smem_desc(ba + ko, kGLbo, kGSbo);
+                            const uint64_t bl = tc::smem_desc(ba + kGOpBytes + ko, kGLbo, kGSbo);
+                            tc::mma_f16(dt, ah, bh, idesc, (cc | ks) != 0 ? 1u : 0u);
+                            tc::mma_f16(dc, ah, bl, idesc, (iv | cc | ks) != 0 ? 1u : 0u);
+                            tc::mma_f16(dc, al, bh, idesc, 1u);
+                        }
+                        tc::commit(afree + sa);
+                        if (form) tc::commit(bfree + sb);
+                    }
+                    if (ok) tc::commit(accfull + b);
+                }
+                if (ok) atomicAdd(&g_grid_tiles, 1ull);
+            }
+            // every MMA this CTA issued has completed before TMEM is released
+            tc::commit(done);
+            mbar_wait_bounded(done, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---- bulk copies: A chunks and, per chunk, the tables or B ---------------------
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < d.n_tiles && ok; tile += gridDim.x) {
+                const TileIdx ti = tile_idx(d, tile);
+                const unsigned char* asrc = d.atab + static_cast<int64_t>(ti.mt) * d.nc * kGPair;
+                for (int c = 0; c < d.nc; ++c, ++g) {
+                    const int sa = static_cast<int>(g % SA);
+                    if (g >= static_cast<uint32_t>(SA) &&
+                        !gwait(afree + sa, ((g / SA) - 1u) & 1u, abort, status)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* dst = gsm + sa * d.a_stage;
+                    const unsigned char* ac = asrc + static_cast<int64_t>(c) * kGPair;
+                    if (form) {
+                        const uint32_t by = static_cast<uint32_t>(ti.pkv) * kGRowBytes;
+                        const uint32_t bw = static_cast<uint32_t>(ti.plv) * kGRowBytes;
+                        mbar_arrive_expect_tx(afull + sa, kGPair + by + bw);
+                        bulk_g2s(dst, ac, kGOpBytes, afull + sa);
+                        bulk_g2s(dst + kGOpBytes, ac + kGOpBytes, kGOpBytes, afull + sa);
+                        bulk_g2s(dst + kGPair, d.ytab + (static_cast<int64_t>(c) * d.ny + ti.k0) * (kGRowBytes / 8), by,
+                                 afull + sa);
+                        bulk_g2s(dst + kGPair + (1 << d.pk_log2) * kGRowBytes,
+                                 d.wztab + (static_cast<int64_t>(c) * d.nz + ti.l0) * (kGRowBytes / 8), bw,
+                                 afull + sa);
+                    } else {
+                        const unsigned char* bc = d.btab + (static_cast<int64_t>(ti.kt) * d.nc + c) * kGPair;
+                        mbar_arrive_expect_tx(afull + sa, 2 * kGPair);
+                        bulk_g2s(dst, ac, kGOpBytes, afull + sa);
+                        bulk_g2s(dst + kGOpBytes, ac + kGOpBytes, kGOpBytes, afull + sa);
+                        bulk_g2s(dst + kGPair, bc, kGOpBytes, afull + sa);
+                        bulk_g2s(dst + kGPair + kGOpBytes, bc + kGOpBytes, kGOpBytes, afull + sa);
+                    }
+                }
+            }
+            // copies still in flight land before the CTA's shared memory goes away
+            for (uint32_t q = g > static_cast<uint32_t>(SA) ? g - SA : 0u; q < g; ++q)
+                mbar_wait_bounded(afull + q % SA, (q / SA) & 1u);
+        }
+        __syncwarp();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == kGEpiWarps + 1) {
+        tc::fence_after();
+        tc::dealloc(tbase, kGTmemCols);
+    }
+}
+
+// x, y, (z + psi) phase of mode j in turns, each exactly reduced: a = ah + al
+// (FP32 pairs) at the axis coordinate.
+__device__ __forceinline__ float psi_z_turns(const float4 c1, float z, bool has_z) {
+    float t = has_z ? turns_axis(c1.x, c1.y, z) : 0.0f;
+    t = frac_turn(t + c1.z);
+    return frac_turn(t + c1.w);
+}
+
+// Tables of one call (workspace).  Work items, flattened:
+//   A : (mt, chunk, row, quad of 4 modes) -> one 16-byte row segment of the
+//       hi and of the lo tile ((re, -im) pairs of e^{2 pi i a_x X_i}; rows
+//       beyond nx are zero);
+//   3-D (form):  Y : (chunk, k, m) -> e^{2 pi i a_jy Y_k},
+//                W : (chunk, l, m) -> (A_j / S) e^{2 pi i (psi_j + a_jz Z_l)}, j = 32 chunk + m;
+//   2-D (load):  B : (kt, chunk, column, quad) -> (A_j / S) e^{2 pi i (psi_j + a_jy Y_k + a_jz Z_0)}
+//                as (re, im) hi and lo tiles (columns beyond ny are zero).
+__global__ void grid_prep_kernel(GridPrep p) {
+    const int64_t nA = static_cast<int64_t>(p.n_mt) * p.nc * kGM * 8;
+    const int64_t nY = p.form ? static_cast<int64_t>(p.ny) * p.n_pad : static_cast<int64_t>(p.n_kt) * p.nc * kGN * 8;
+    const int64_t nW = p.form ? static_cast<int64_t>(p.nz) * p.n_pad : 0;
+    const float s_inv = 1.0f / grid_scale(p.thdr);  // exact: a power of two
+    const bool has_z = p.dim > 2;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < nA + nY + nW;
+         idx += stride) {
+        if (idx < nA || (!p.form && idx < nA + nY)) {
+            // an operand tile row segment: A (x phasors) or, in 2-D, B
+            const bool is_a = idx < nA;
+            const int64_t u = is_a ? idx : idx - nA;
+            const int quad = static_cast<int>(u & 7);
+            const int r = static_cast<int>((u >> 3) & 127);
+            const int64_t rest = u >> 10;
+            const int c = static_cast<int>(rest % p.nc);
+            const int64_t tt = rest / p.nc;  // mt or kt
+            const int64_t i = tt * kGM + r;  // x or y cell
+            float v[8];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = c * kGModes + quad * 4 + m;
+                float cs = 0.0f, sn = 0.0f;
+                if (is_a) {
+                    if (i < p.nx) {
+                        const float4 c0 = __ldg(p.cold + 2 * j);
+                        sincospif(2.0f * turns_axis(c0.x, c0.y, __ldg(p.X + i)), &sn, &cs);
+                    }
+                    v[2 * m] = cs;
+                    v[2 * m + 1] = -sn;
+                } else {
+                    if (i < p.ny) {
+                        const float4 c0 = __ldg(p.cold + 2 * j);
+                        const float4 c1 = __ldg(p.cold + 2 * j + 1);
+                        const float tz = psi_z_turns(c1, has_z ? __ldg(p.Z) : 0.0f, has_z);
+                        const float t = frac_turn(turns_axis(c0.z, c0.w, __ldg(p.Y + i)) + tz);
+                        sincospif(2.0f * t, &sn, &cs);
+                        const float amp = __ldg(&p.hot[j].w) * s_inv;
+                        cs *= amp;
+                        sn *= amp;
+                    }
+                    v[2 * m] = cs;
+                    v[2 * m + 1] = sn;
+                }
+            }
+            uint4 H, L;
+            tc::split_f16x2(v[0], v[1], H.x, L.x);
+            tc::split_f16x2(v[2], v[3], H.y, L.y);
+            tc::split_f16x2(v[4], v[5], H.z, L.z);
+            tc::split_f16x2(v[6], v[7], H.w, L.w);
+            unsigned char* o = (is_a ? p.atab : p.btab) + (tt * p.nc + c) * static_cast<int64_t>(kGPair) +
+                               tile_off(r, quad);
+            *reinterpret_cast<uint4*>(o) = H;
+            *reinterpret_cast<uint4*>(o + kGOpBytes) = L;
+        } else if (idx < nA + nY) {
+            const int64_t u = idx - nA;  // (chunk, k, m)
+            const int m = static_cast<int>(u % kGModes);
+            const int64_t k = (u / kGModes) % p.ny;
+            const int c = static_cast<int>(u / (static_cast<int64_t>(kGModes) * p.ny));
+            const int j = c * kGModes + m;
+            const float4 c0 = __ldg(p.cold + 2 * j);
+            float cs, sn;
+            sincospif(2.0f * turns_axis(c0.z, c0.w, __ldg(p.Y + k)), &sn, &cs);
+            p.ytab[(u / kGModes) * (kGRowBytes / 8) + m] = make_float2(cs, sn);
+        } else {
+            const int64_t u = idx - nA - nY;  // (chunk, l, m)
+            const int m = static_cast<int>(u % kGModes);
+            const int64_t l = (u / kGModes) % p.nz;
+            const int c = static_cast<int>(u / (static_cast<int64_t>(kGModes) * p.nz));
+            const int j = c * kGModes + m;
+            const float4 c1 = __ldg(p.cold + 2 * j + 1);
+            const float amp = __ldg(&p.hot[j].w) * s_inv;
+            float cs, sn;
+            sincospif(2.0f * psi_z_turns(c1, has_z ? __ldg(p.Z + l) : 0.0f, has_z), &sn, &cs);
+            p.wztab[(u / kGModes) * (kGRowBytes / 8) + m] = make_float2(amp * cs, amp * sn);
+        }
+    }
+}
+
+// D[128][128] = sum_K A[128][K] B[128][K] (FP16 inputs, K-contiguous rows,
+// K = 64 k_chunks, FP32 result row-major) through the same layout,
+// descriptors and TMEM path as the grid kernel.  One CTA of 128 threads.
+__global__ void __launch_bounds__(128, 1) mma_probe_kernel(const uint16_t* A, const uint16_t* B, int32_t k_chunks,
+                                                             float* D, int32_t* status) {
+    __shared__ __align__(1024) unsigned char sm[2 * kGOpBytes];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tc::alloc(&slot, 128);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = slot;
+    const int K = kGK * k_chunks;
+    bool ok = true;
+    for (int ch = 0; ch < k_chunks; ++ch) {
+        // canonical layout of the 128 x 64 chunk of A and of B
+        for (int e = threadIdx.x; e < kGM * kGK; e += blockDim.x) {
+            const int r = e / kGK, kk = e % kGK;
+            const uint32_t off = static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(kk >> 3) * kGLbo +
+                                 static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(kk & 7) * 2u;
+            *reinterpret_cast<uint16_t*>(sm + off) = A[static_cast<int64_t>(r) * K + ch * kGK + kk];
+            *reinterpret_cast<uint16_t*>(sm + kGOpBytes + off) = B[static_cast<int64_t>(r) * K + ch * kGK + kk];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after();
+            const uint32_t sa = smem_u32(sm);
+            for (int ks = 0; ks < kGK / 16; ++ks) {
+                const uint32_t ko = static_cast<uint32_t>(ks) * 2u * kGLbo;
+                tc::mma_f16(tbase, tc::smem_desc(sa + ko, kGLbo, kGSbo), tc::smem_desc(sa + kGOpBytes + ko, kGLbo, kGSbo),
+                            tc::idesc_f16_f32(kGM, kGN), (ch | ks) != 0 ? 1u : 0u);
+            }
+            tc::commit(&bar);
+        }
+        if (!mbar_wait_bounded(&bar, static_cast<uint32_t>(ch) & 1u)) {
+            if (threadIdx.x == 0) atomicOr(status, 2);
+            ok = false;
+        }
+        tc::fence_after();
+        __syncthreads();  // the chunk's shared data is no longer read
+        if (!ok) break;
+    }
+    if (ok) {
+        for (int cb = 0; cb < kGN; cb += 32) {
+            uint32_t r[32];
+            tc::ld32(tbase + (static_cast<uint32_t>(32 * warp) << 16) + cb, r);
+            tc::wait_ld();
+            const int row = 32 * warp + lane;
+            for (int c = 0; c < 32; ++c) D[row * kGN + cb + c] = __uint_as_float(r[c]);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tbase, 128);
+    }
+}
+
+int g_num_sms = 0;
+
+// Layout of one grid synthesis: mode, patch, tiles, shared-memory rings and
+// workspace tables.
+struct GridPlan {
+    bool form;
+    int pk_log2, n_mt, n_kt, n_lt, nc, sa, a_stage, off_b, off_bar, smem;
+    int64_t n_tiles, a_bytes, y_bytes, w_bytes, b_bytes;
+};
+
+GridPlan grid_plan(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
+    GridPlan g{};
+    g.form = nz > 1;
+    g.nc = static_cast<int>(n_pad / kGModes);
+    g.n_mt = (nx + kGM - 1) / kGM;
+    if (g.form) {
+        // patch 2^p y-cells by 128 / 2^p z-cells (p = 2 .. 6): fewest wasted
+        // columns, then the fewest staged table rows
+        double best = 1e300;
+        for (int pk = 2; pk <= 6; ++pk) {
+            const int64_t PK = int64_t(1) << pk, PL = kGN / PK;
+            const double cols = double((ny + PK - 1) / PK * PK) * double((nz + PL - 1) / PL * PL);
+            const double w = cols / (double(ny) * double(nz)) + 1e-4 * double(PK + PL);
+            if (w < best) {
+                best = w;
+                g.pk_log2 = pk;
+            }
+        }
+        const int tb = ((1 << g.pk_log2) + (kGN >> g.pk_log2)) * kGRowBytes;
+        g.a_stage = kGPair + tb;
+        g.sa = std::min(kGMaxSA, (kGSmemMax - kGBarBytes - kGSB * kGPair) / g.a_stage);
+        g.off_b = g.sa * g.a_stage;
+        g.off_bar = g.off_b + kGSB * kGPair;
+    } else {
+        g.pk_log2 = 7;
+        g.a_stage = 2 * kGPair;
+        g.sa = std::min(kGMaxSA, (kGSmemMax - kGBarBytes) / g.a_stage);
+        g.off_b = g.sa * g.a_stage;
+        g.off_bar = g.off_b;
+    }
+    g.smem = g.off_bar + kGBarBytes;
+    g.n_kt = (ny + (1 << g.pk_log2) - 1) >> g.pk_log2;
+    const int PL = kGN >> g.pk_log2;
+    g.n_lt = (nz + PL - 1) / PL;
+    g.n_tiles = int64_t(g.n_mt) * g.n_kt * g.n_lt;
+    g.a_bytes = align256(int64_t(g.n_mt) * g.nc * kGPair);
+    if (g.form) {
+        g.y_bytes = align256(int64_t(g.nc) * ny * kGRowBytes);
+        g.w_bytes = align256(int64_t(g.nc) * nz * kGRowBytes);
+    } else {
+        g.b_bytes = align256(int64_t(g.n_kt) * g.nc * kGPair);
+    }
+    return g;
+}
+
+}  // namespace
+
+size_t grid_ws_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
+    const GridPlan g = grid_plan(nx, ny, nz, n_pad);
+    return static_cast<size_t>(g.a_bytes + g.y_bytes + g.w_bytes + g.b_bytes);
+}
+
+int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const GridGeom& gg, const MapDev& map,
+                      void* ws, int32_t fc, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned char* tb = static_cast<const unsigned char*>(table);
+    const TableLayout TL = table_layout(n_modes);
+    if (g_num_sms == 0) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(grid_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemMax);
+        if (e != cudaSuccess) return e;
+        g_num_sms = sms;
+    }
+    const GridPlan gp = grid_plan(gg.nx, gg.ny, gg.nz, TL.n_pad);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    GridPrep p{};
+    p.thdr = reinterpret_cast<const TableHeader*>(tb);
+    p.hot = reinterpret_cast<const float4*>(tb + TL.off_hot);
+    p.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
+    p.X = gg.X;
+    p.Y = gg.Y;
+    p.Z = gg.Z;
+    p.nx = gg.nx;
+    p.ny = gg.ny;
+    p.nz = gg.nz;
+    p.n_pad = static_cast<int32_t>(TL.n_pad);
+    p.nc = gp.nc;
+    p.n_mt = gp.n_mt;
+    p.n_kt = gp.n_kt;
+    p.dim = dim;
+    p.form = gp.form ? 1 : 0;
+    p.atab = w;
+    if (gp.form) {
+        p.ytab = reinterpret_cast<float2*>(w + gp.a_bytes);
+        p.wztab = reinterpret_cast<float2*>(w + gp.a_bytes + gp.y_bytes);
+    } else {
+        p.btab = w + gp.a_bytes;
+    }
+    const int64_t items = int64_t(gp.n_mt) * gp.nc * kGM * 8 +
+                          (gp.form ? (int64_t(gg.ny) + gg.nz) * TL.n_pad : int64_t(gp.n_kt) * gp.nc * kGN * 8);
+    const int pb = 256;
+    const int64_t pg = std::min<int64_t>((items + pb - 1) / pb, int64_t(g_num_sms) * 16);
+    grid_prep_kernel<<<static_cast<unsigned>(pg), pb, 0, st>>>(p);
+    count_launches(1);
+
+    GridDesc d{};
+    d.atab = p.atab;
+    d.btab = p.btab;
+    d.ytab = p.ytab;
+    d.wztab = p.wztab;
+    d.thdr = p.thdr;
+    d.nx = gg.nx;
+    d.ny = gg.ny;
+    d.nz = gg.nz;
+    d.n_pad = p.n_pad;
+    d.nc = gp.nc;
+    d.fc = fc;
+    while (d.fc > 1 && gp.nc % d.fc != 0) d.fc >>= 1;  // whole fold intervals per tile
+    d.n_mt = gp.n_mt;
+    d.n_kt = gp.n_kt;
+    d.n_lt = gp.n_lt;
+    d.pk_log2 = gp.pk_log2;
+    d.n_tiles = gp.n_tiles;
+    d.form = p.form;
+    d.sa = gp.sa;
+    d.a_stage = gp.a_stage;
+    d.off_b = gp.off_b;
+    d.off_bar = gp.off_bar;
+    d.map = map;
+    const int64_t grid = std::min<int64_t>(d.n_tiles, g_num_sms);
+    grid_mma_kernel<<<static_cast<unsigned>(grid), kGThreads, gp.smem, st>>>(d, status);
+    count_launches(1);
+    if (map.bits & kMapMismatch) {
+        const int e = launch_loss_sum(map.lpart, d.n_tiles * kGEpiWarps, map.inv_n_mean, map.loss, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+int64_t grid_loss_partials(int32_t nx, int32_t ny, int32_t nz) {
+    return grid_plan(nx, ny, nz, kGModes * 4).n_tiles * kGEpiWarps;
+}
+
+int take_grid_tiles(unsigned long long* tiles) {
+    unsigned long long v = 0ull;
+    const unsigned long long zero = 0ull;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_grid_tiles, sizeof(v));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_grid_tiles, &zero, sizeof(zero));
+    if (e != cudaSuccess) return e;
+    *tiles = v;
+    return cudaSuccess;
+}
+
+int launch_mma_probe(const uint16_t* A, const uint16_t* B, int32_t k_chunks, float* D, int32_t* status,
+                     void* stream) {
+    mma_probe_kernel<<<1, 128, 0, static_cast<cudaStream_t>(stream)>>>(A, B, k_chunks, D, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace grf

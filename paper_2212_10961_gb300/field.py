@@ -367,6 +367,13 @@ class CellPlan:
         check(lib().grf_read_status(_ptr(self.buf), ctypes.byref(v), _stream_handle(stream)))
         return v.value
 
+    def grid_shape(self):
+        """(nx, ny, nz) when the cells are a Cartesian grid handed over
+        x-fastest (grf_plan_grid_shape), else (0, 0, 0)."""
+        v = [ctypes.c_int32(0) for _ in range(3)]
+        check(lib().grf_plan_grid_shape(_ptr(self.buf), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     @property
     def ptr(self):
         return _ptr(self.buf)
@@ -435,6 +442,22 @@ def _outputs_struct(out):
     return o
 
 
+def synth_workspace_bytes(plan: CellPlan, segment, n_modes):
+    """Workspace that lets grf_synth_field use the mode split and, on a
+    Cartesian-grid plan, the tensor-core grid path (the larger of
+    grf_synth_workspace_bytes and grf_synth_grid_workspace_bytes)."""
+    return max(int(lib().grf_synth_workspace_bytes(plan.segment_size(segment))),
+               int(lib().grf_synth_grid_workspace_bytes(plan.ptr, int(segment), int(n_modes))))
+
+
+def synth_mismatch_workspace_bytes(plan: CellPlan, segment, n_modes):
+    """Workspace of grf_synth_mismatch: the loss partials, then room for the
+    mode split or, on a Cartesian-grid plan, the grid path's tables."""
+    n = plan.segment_size(segment)
+    lbytes = int(lib().grf_synth_mismatch_workspace_bytes(n)) - int(lib().grf_synth_workspace_bytes(n))
+    return lbytes + synth_workspace_bytes(plan, segment, n_modes)
+
+
 def synth(table: ModeTable, params: FieldParams, plan: CellPlan, segment=0, maps=None, out=None,
           stream=None, workspace=None):
     """Field and fused maps at every cell of `segment` (original cell order).
@@ -448,7 +471,7 @@ def synth(table: ModeTable, params: FieldParams, plan: CellPlan, segment=0, maps
     if workspace is False:
         ws, nbytes = None, 0
     else:
-        nbytes = int(lib().grf_synth_workspace_bytes(n))
+        nbytes = synth_workspace_bytes(plan, segment, params.n_modes)
         ws = (workspace or _ws_fwd).get(nbytes, plan.buf.device)
     check(lib().grf_synth_field(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
                                 ctypes.byref(maps.to_c()), ctypes.byref(_outputs_struct(out)),
@@ -469,7 +492,7 @@ class PreparedSynth:
         self._p = params.to_c()
         self._m = maps.to_c()
         self._o = _outputs_struct(self.out)
-        self._nbytes = int(lib().grf_synth_workspace_bytes(n))
+        self._nbytes = synth_workspace_bytes(plan, segment, params.n_modes)
         self._ws = torch.empty(max(self._nbytes, 256), dtype=torch.uint8, device=plan.buf.device)
         self._stream = None if stream is None else _stream_handle(stream)
         self._args = (ctypes.byref(self._p), plan.ptr, int(segment), ctypes.byref(self._m), ctypes.byref(self._o),
@@ -631,7 +654,7 @@ def synth_mismatch(table: ModeTable, params: FieldParams, plan: CellPlan, K_targ
         out["Y"] = torch.empty(n, dtype=torch.float32, device=dev)
     if want_K:
         out["K"] = torch.empty(n, dtype=torch.float32, device=dev)
-    nbytes = int(lib().grf_synth_mismatch_workspace_bytes(n))
+    nbytes = synth_mismatch_workspace_bytes(plan, segment, params.n_modes)
     ws = (workspace or _ws_mm).get(nbytes, dev)
     check(lib().grf_synth_mismatch(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment), _ptr(T),
                                    int(n_mean), _ptr(gY), _ptr(loss), _ptr(out.get("Y")), _ptr(out.get("K")),
@@ -866,6 +889,33 @@ def take_adjoint_path_counts():
     g, l_ = ctypes.c_int64(0), ctypes.c_int64(0)
     check(lib().grf_take_adjoint_path_counts(ctypes.byref(g), ctypes.byref(l_)))
     return g.value, l_.value
+
+
+def take_grid_tiles():
+    """128 x 128-cell tiles computed by the tensor-core grid path since the
+    last call (grf_take_grid_tiles); synchronises the device."""
+    t = ctypes.c_int64(0)
+    check(lib().grf_take_grid_tiles(ctypes.byref(t)))
+    return t.value
+
+
+def grid_path(enable=True, fold_chunks=4):
+    """Process-wide switch of the grid path and its fold interval in chunks
+    of 32 modes (grf_debug_grid_path)."""
+    check(lib().grf_debug_grid_path(1 if enable else 0, int(fold_chunks)))
+
+
+def mma_selftest(A, B, stream=None):
+    """D = A B^T through the tensor-core path's layout (grf_debug_mma_f16):
+    A, B CUDA float16 tensors of shape (128, 64 k) -> D (128, 128) float32."""
+    A = _require_cuda(A, torch.float16, "A")
+    B = _require_cuda(B, torch.float16, "B")
+    if A.shape != B.shape or A.dim() != 2 or A.shape[0] != 128 or A.shape[1] % 64 != 0:
+        raise ValueError("A and B must both be (128, 64 k)")
+    D = torch.empty((128, 128), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    check(lib().grf_debug_mma_f16(_ptr(A), _ptr(B), A.shape[1] // 64, _ptr(D), _ptr(status), _stream_handle(stream)))
+    return D, status
 
 
 def mufu_probe(blocks, iters, stream=None):

@@ -207,6 +207,9 @@ def test_pack_table_layout(abi, n, dim):
     assert t["has_kappa"] == 1 and t["off_kappa"] % 256 == 0 and t["off_kappa"] + t["n_pad"] * 24 <= nbytes
     np.testing.assert_array_equal(t["kappa"][:n, :dim], md["kappa"][order[:n]])
     assert np.all(t["kappa"][:n, dim:] == 0) and np.all(t["kappa"][n:] == 0)
+    # the grid path's operand scale: the largest stored |A| (header bytes 80..84)
+    amp_max = np.frombuffer(bytes(buf)[80:84], dtype=np.float32)[0]
+    assert amp_max == np.max(np.abs(t["hot"][:n, 3]))
     # packed without kappa: the flag is 0 and the section stays zero
     m0 = F._modes_struct(n, dim, {k: md[k] for k in ("amp", "psi", "a")})
     assert abi.lib().grf_pack_table(ctypes.byref(m0), buf, nbytes) == 0
@@ -333,6 +336,18 @@ def test_null_and_unknown_handles_rejected(abi):
     assert L.grf_map_property(ctypes.byref(mp), 0.0, 1.0, 10, ctypes.c_void_p(4096), ctypes.byref(out),
                               None) == abi.GRF_EINVAL
     assert L.grf_batch_launch(ctypes.c_void_p(1 << 12), None) == abi.GRF_EINVAL
+    # grid path entry points: unknown plans are not grids, bad settings rejected
+    assert L.grf_synth_grid_workspace_bytes(fake_plan, 0, 100) == 0
+    assert L.grf_synth_grid_workspace_bytes(None, 0, 100) == 0
+    v = ctypes.c_int32(7)
+    assert L.grf_plan_grid_shape(fake_plan, ctypes.byref(v), ctypes.byref(v), ctypes.byref(v)) == abi.GRF_EINVAL
+    assert L.grf_plan_grid_shape(None, None, None, None) == abi.GRF_EINVAL
+    assert L.grf_debug_grid_path(1, 3) == abi.GRF_EINVAL
+    assert L.grf_debug_grid_path(1, 4) == abi.GRF_OK
+    assert L.grf_take_grid_tiles(None) == abi.GRF_EINVAL
+    assert L.grf_debug_mma_f16(None, None, 1, None, None, None) == abi.GRF_EINVAL
+    assert L.grf_debug_mma_f16(ctypes.c_void_p(4096), ctypes.c_void_p(4096), 0, ctypes.c_void_p(4096),
+                               ctypes.c_void_p(4096), None) == abi.GRF_EINVAL
     offs = (ctypes.c_int64 * 2)(5, 10)
     assert L.grf_plan_cells(3, 1, offs, None, None, None, ctypes.c_void_p(1 << 12), 1 << 20,
                             None) == abi.GRF_EINVAL

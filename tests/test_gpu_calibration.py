@@ -94,9 +94,15 @@ def test_fused_mismatch_mean_count_and_empty_segment(env):
     with pytest.raises(F._abi.GRFError):
         F.synth_mismatch(gf.table, p, plan, T, segment=1, n_mean=n - 1)
     # the segment's gradient equals the one of a plan of those cells alone
+    # (taking the same CUDA-core path: a single-grid plan would otherwise use
+    # the tensor-core grid path)
     plan1 = F.CellPlan(*to_dev(torch, cells))
-    l3, g3, _ = F.synth_mismatch(gf.table, p, plan1, T)
-    torch.cuda.synchronize()
+    F.grid_path(False)
+    try:
+        l3, g3, _ = F.synth_mismatch(gf.table, p, plan1, T)
+        torch.cuda.synchronize()
+    finally:
+        F.grid_path(True)
     assert l3.item() == pytest.approx(l1.item(), rel=1e-6)
     assert torch.max(torch.abs(g3 - g1)).item() <= 1e-6 * torch.max(torch.abs(g1)).item()
 

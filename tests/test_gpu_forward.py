@@ -371,10 +371,14 @@ def test_mode_split_matches_unsplit_and_oracle(env):
     p = F.FieldParams(family="exponential", sigma2=4.0, ell=(0.2, 0.2, 0.05), dim=3, n_modes=3000, seed=12)
     gf = F.GaussianField(p)
     maps = F.MapSpec(y=True, lognormal=True, thresholds=(-0.5, 0.5), facies=True)
-    split = F.synth(gf.table, p, plan, 0, maps)
-    split2 = F.synth(gf.table, p, plan, 0, maps)
-    whole = F.synth(gf.table, p, plan, 0, maps, workspace=False)
-    torch.cuda.synchronize()
+    F.grid_path(False)  # the CUDA-core kernel's mode split (the grid path has its own tests)
+    try:
+        split = F.synth(gf.table, p, plan, 0, maps)
+        split2 = F.synth(gf.table, p, plan, 0, maps)
+        whole = F.synth(gf.table, p, plan, 0, maps, workspace=False)
+        torch.cuda.synchronize()
+    finally:
+        F.grid_path(True)
     ys, yw = split["Y"].cpu().numpy(), whole["Y"].cpu().numpy()
     assert np.array_equal(ys, split2["Y"].cpu().numpy())
     assert np.max(np.abs(ys - yw)) <= 2e-6 * 2.0
@@ -454,10 +458,14 @@ def test_lattice_lanes_against_oracle(env, shape, family):
     plan = F.CellPlan(*to_dev(torch, cells))
     gf = F.GaussianField(p)
     y_or = oracle_field(oracle_modes(family, 1.6, ell, d, 700, 29), -0.2, cells)
+    F.grid_path(False)  # the CUDA-core lattice and general paths (the grid path has its own tests)
     for ws in (False, None):  # without and with the mode split
-        out = F.synth(gf.table, p, plan, 0, F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True),
-                      workspace=ws)
-        torch.cuda.synchronize()
+        try:
+            out = F.synth(gf.table, p, plan, 0, F.MapSpec(y=True, lognormal=True, thresholds=(0.0,), facies=True),
+                          workspace=ws)
+            torch.cuda.synchronize()
+        finally:
+            F.grid_path(True)
         assert plan.status() == 0
         check_forward(out["Y"].cpu().numpy(), y_or, math.sqrt(1.6), "%s %s" % (shape, family))
         check_lognormal(out["K"].cpu().numpy(), y_or, math.sqrt(1.6))
