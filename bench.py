@@ -51,6 +51,35 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+def tensor_peak():
+    """Measured dense BF16 tensor throughput of this machine's GPUs (TFLOP/s,
+    cuBLAS burst; FP16 runs at the BF16 rate on the tensor cores), else the
+    fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+def take_paths(F):
+    """Work items of the synthesis paths since the last call (all counters
+    reset): warp tiles of the general and lattice paths, 128 x 128 tiles of
+    the tensor-core grid path."""
+    g, l_ = F.take_path_counts()
+    t = F.take_grid_tiles()
+    return {"general_warps": g, "lattice_warps": l_, "grid_tiles": t}
+
+
+def path_fields(paths):
+    """Path mix of a bench line: the counts, the lattice share of the
+    CUDA-core warp tiles and whether the grid path did the work."""
+    g, l_ = paths["general_warps"], paths["lattice_warps"]
+    return {"path_warps": {"general": g, "lattice": l_, "grid_tiles": paths["grid_tiles"]},
+            "lattice_share": l_ / float(g + l_) if g + l_ else 0.0,
+            "grid_path": paths["grid_tiles"] > 0 and g + l_ == 0}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,13 +307,13 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
         used[k].record(st)
         kev.append((a, b))
 
-    F.take_path_counts()  # reset
+    take_paths(F)  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     torch.cuda.synchronize()
     pf.close()
-    gen_w, lat_w = F.take_path_counts()
+    paths = take_paths(F)
     kern_all = [a.elapsed_time(b) for a, b in kev[warmup:]]
     kern_ms = float(np.mean(kern_all))
     assert plan.status() == 0
@@ -302,9 +331,7 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
            "kernel_ms_median": max_over_ranks(torch, world, float(np.median(kern_all))),
            "kernel_ms_best": max_over_ranks(torch, world, float(np.min(kern_all))), "plan_ms": plan_ms,
            "cell_modes_per_step": float(M) * N, "launches_in_timed_region": int(round(per_step * steps)),
-           "launches_per_step": per_step, "y_seed": y_seed,
-           "path_warps": {"general": gen_w, "lattice": lat_w},
-           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
+           "launches_per_step": per_step, "y_seed": y_seed, **path_fields(paths)}
     if check and rank == 0:
         res["fp64_check"] = fp64_check(cells, y_seed, oracle_modes_for(w, dim, w["seed"]), w["mean"], sig,
                                        thresholds=thr, facies=fac_seed)
@@ -451,12 +478,12 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
         c.record(st)
         kev.append((a, b, c))
 
-    F.take_path_counts()  # reset
+    take_paths(F)  # reset
     F.take_adjoint_path_counts()
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
-    gen_w, lat_w = F.take_path_counts()
+    paths = take_paths(F)
     bgen, blat = F.take_adjoint_path_counts()
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, c in kev[warmup:]]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for a, b, c in kev[warmup:]]))
@@ -464,8 +491,7 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
            "ms_per_step": ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "cell_modes_per_step": float(M) * N,
            "launches_per_step": launches / float(steps + warmup),
            "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)",
-           "path_warps": {"general": gen_w, "lattice": lat_w},
-           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0,
+           **path_fields(paths),
            "adjoint_path_tiles": {"general": bgen, "lattice": blat},
            "adjoint_lattice_share": blat / float(bgen + blat) if bgen + blat else 0.0}
     if rank == 0:
@@ -559,16 +585,14 @@ def bench_bitruncated(torch, F, W, rank, world, steps, warmup, scale):
     t = W.quantile_thresholds(0.0, math.sqrt(w["sigma2"]), (1.0 / 3.0, 2.0 / 3.0))
     rule = [[0, 1], [2, 3], [4, 5]]
     values = [0.01, 0.1, 1.0, 10.0, 100.0, 1000.0]
-    F.take_path_counts()  # reset
+    take_paths(F)  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: pg.synth(plan, t, (0.0,), rule, values))
     launches = F.launch_count() - l0
-    gen_w, lat_w = F.take_path_counts()
+    paths = take_paths(F)
     res = {"workload": "grid3d_256 bitruncated: exponential l=(0.2,0.2,0.05) x Gaussian l=0.1, 3 x 2 rule",
            "cells": M, "modes_per_field": N, "ms_per_step": ms, "cell_modes_per_step": 2.0 * M * N,
-           "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms,
-           "path_warps": {"general": gen_w, "lattice": lat_w},
-           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0}
+           "launches_per_step": launches / float(steps + warmup), "kernel_ms": ms, **path_fields(paths)}
     if rank == 0:
         # both fields against the oracle's own draws (streams 0 and 1), and the
         # merged facies against the rule applied to the oracle fields
@@ -622,13 +646,11 @@ def bench_batched(torch, F, W, rank, world, steps, warmup, scale, tile="auto"):
     batch = F.Batch(plan, items, tile_cells=tile)
     batch.launch()
     batch.capture()
-    F.take_path_counts()  # reset
+    take_paths(F)  # reset
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, lambda i: batch.replay())
-    gen_w, lat_w = F.take_path_counts()
-    res = {"workload": "ensemble256", "realisations": len(recipe), "cells": int(sum(segs)),
-           "path_warps": {"general": gen_w, "lattice": lat_w},
-           "lattice_share": lat_w / float(gen_w + lat_w) if gen_w + lat_w else 0.0,
+    paths = take_paths(F)
+    res = {"workload": "ensemble256", "realisations": len(recipe), "cells": int(sum(segs)), **path_fields(paths),
            "ms_per_step": ms, "cell_modes_per_step": cm, "launches_per_step": 1,
            "tile_cells": batch.tile_cells, "autotune_ms": batch.tuned_ms,
            # one cell per lane takes its cosine from the FMA-pipe polynomial
@@ -701,13 +723,9 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
-# headline synthesis kernel (synth_fwd_kernel<3,16,4,0> on the lattice path,
-# 256^3 cells, 4096 modes), from one ncu capture of
-# `bench.py --only fwd --steps 3 --warmup 3 --no-cpu-baseline`: 269.62 MB read
-# + 115.69 MB written.  Algorithmic: 16 B read (sorted coordinates,
-# permutation) + 9 B written (Y, K, facies) per cell = 419 MB; part of the
-# writes was still in L2 when the launch ended.
-HEAD_TRAFFIC_BYTES = 269.623552e6 + 115.687168e6
+# headline's kernels (256^3 cells, 4096 modes), from an ncu capture; None
+# until the current kernels have been captured.
+HEAD_TRAFFIC_BYTES = None  # the headline now runs on the grid path: no capture of its kernels yet
 
 
 # FP32 instructions per cell-mode of the lattice path (lanes of 4-cell grid
@@ -725,13 +743,34 @@ FP32_PER_CLK_PER_SM = 128
 ADJOINT_LATTICE_FP32_PER_CELL_MODE = 6.6
 
 
-def roofline(kern_ms, cell_modes, clocks, sms, traffic=None, lattice_share=0.0):
+# Tensor-core work of the grid path per cell-mode: the real part of a complex
+# product is a 2-term dot product (2 multiply-adds = 4 flops), evaluated as
+# three FP16 products (hi.hi, hi.lo, lo.hi) for FP32-level accuracy.
+GRID_TENSOR_FLOPS_PER_CELL_MODE = 12.0
+
+
+def roofline(kern_ms, cell_modes, clocks, sms, traffic=None, lattice_share=0.0, grid=False):
     """Roofline of a synthesis kernel.  General path: the MUFU pipe, 1
     hardware cosine per cell-mode.  Lattice path (lattice_share >= 1/2 of the
     warp tiles): the FP32 pipe at LATTICE_FP32_PER_CELL_MODE instructions per
-    cell-mode (1/8 MUFU per cell-mode); the MUFU fraction is kept beside it."""
+    cell-mode (1/8 MUFU per cell-mode); the MUFU fraction is kept beside it.
+    Grid path: the tensor cores at GRID_TENSOR_FLOPS_PER_CELL_MODE FP16 flops
+    per cell-mode against the measured dense BF16 peak (kern_ms covers the
+    call's two kernels: table preparation and the tensor-core kernel)."""
     mufu_peak = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 1e9  # Gcell.mode/s at the maximum SM clock
     achieved = cell_modes / (kern_ms * 1e-3) / 1e9
+    if grid:
+        tpk, kind = tensor_peak()
+        tf = cell_modes * GRID_TENSOR_FLOPS_PER_CELL_MODE / (kern_ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": tf, "peak": tpk, "unit": "TFLOP/s", "frac": tf / tpk,
+                "traffic": traffic, "peak_kind": kind,
+                "peak_basis": ("tensor-core grid path: %.0f FP16 tensor flops per cell-mode (a 2-term real dot "
+                               "product as three FP16 products hi.hi + hi.lo + lo.hi) against the %s dense BF16 "
+                               "cuBLAS burst peak (FP16 runs at the BF16 rate)" %
+                               (GRID_TENSOR_FLOPS_PER_CELL_MODE, kind)),
+                "gcell_modes_per_s": achieved, "frac_of_mufu_roofline": achieved / mufu_peak,
+                "frac_of_lattice_fp32_roofline": achieved / (FP32_PER_CLK_PER_SM * sms * 2070e6 /
+                                                             LATTICE_FP32_PER_CELL_MODE / 1e9)}
     if lattice_share >= 0.5:
         peak_max = FP32_PER_CLK_PER_SM * sms * 2070e6 / LATTICE_FP32_PER_CELL_MODE / 1e9
         basis = ("lattice path (%.3f of the warp tiles): %d FP32 lanes/clk/SM x %d SMs x 2070 MHz / %.1f FP32 "
@@ -875,7 +914,7 @@ def main():
         v["gcell_modes_per_s"] = v["cell_modes_per_step"] * world / (v["ms_per_step"] * 1e-3) / 1e9
         if "kernel_ms" in v:
             v["roofline"] = roofline(v["kernel_ms"], v["cell_modes_per_step"], ck, sms,
-                                     lattice_share=v.get("lattice_share", 0.0))
+                                     lattice_share=v.get("lattice_share", 0.0), grid=v.get("grid_path", False))
     if k_b := extra.get("batched"):
         # one cosine per lane of the general path comes from the FMA pipe: the
         # MUFU pipe's share of that path's work; the lattice lanes (the 64^3
@@ -898,7 +937,8 @@ def main():
                                                   "cosine); the forward's own bound is in fwd_roofline")
         # each half against its own bound
         k_fb["fwd_roofline"] = roofline(k_fb["fwd_ms"], k_fb["cell_modes_per_step"], ck, sms,
-                                        lattice_share=k_fb.get("lattice_share", 0.0))
+                                        lattice_share=k_fb.get("lattice_share", 0.0),
+                                        grid=k_fb.get("grid_path", False))
         bw = k_fb["cell_modes_per_step"] / (k_fb["bwd_ms"] * 1e-3) / 1e9
         bmufu = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 2 / 1e9
         if k_fb.get("adjoint_lattice_share", 0.0) >= 0.5:
@@ -926,7 +966,8 @@ def main():
         "plan_ms_once_per_mesh": head["plan_ms"],
         "roofline": roofline(head["kernel_ms"], head["cell_modes_per_step"], ck, sms,
                              HEAD_TRAFFIC_BYTES if args.scale == 1 and HEAD_TRAFFIC_BYTES else None,
-                             head.get("lattice_share", 0.0)),
+                             head.get("lattice_share", 0.0), grid=head.get("grid_path", False)),
+        "grid_path": head.get("grid_path", False),
         "path_warps": head.get("path_warps"),
         "kernel_ms": head["kernel_ms"], "kernel_ms_median": head["kernel_ms_median"],
         "kernel_ms_best": head["kernel_ms_best"],

@@ -264,12 +264,21 @@ constexpr int kGridSlots = 1024;
 GridCheck* g_slots = nullptr;
 int g_next_slot = 0;
 std::atomic<uint64_t> g_next_tag{1};
-std::atomic<int32_t> g_grid_enabled{1};  // grf_debug_grid_path
+std::atomic<int32_t> g_grid_enabled{1};  // grf_debug_grid_path: 0 off, 1 auto, 2 always
 std::atomic<int32_t> g_grid_fold{4};     // chunks of 32 modes per fold interval
 
 void drop_plan_event(PlanMeta& m) {
     if (m.ev) cudaEventDestroy(m.ev);
     m.ev = nullptr;
+}
+
+// Grid path for a grid of this shape: always (setting 2), or (setting 1)
+// when it has at least 8 tiles of 128 x 128 cells -- below that the few SMs
+// it occupies take longer than the CUDA-core kernels spread over the GPU.
+bool use_grid_path(const GridGeom& gg) {
+    const int32_t e = g_grid_enabled.load();
+    if (e == 2) return true;
+    return e == 1 && grid_loss_partials(gg.nx, gg.ny, gg.nz) / 8 >= 8;
 }
 
 // The grid shape of `plan` (single segment), resolving a pending check by
@@ -825,7 +834,7 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     // workspace holds its tables
     GridGeom gg{};
     if (n > 0 && workspace && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim &&
-        plan_grid(plan, &gg) &&
+        plan_grid(plan, &gg) && use_grid_path(gg) &&
         ws_bytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
         const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, workspace, g_grid_fold.load(), status,
                                           stream);
@@ -914,7 +923,7 @@ int grf_synth_mismatch(const void* table, const grf_params* p, const void* plan,
     // holds its tables and the loss partials fit
     GridGeom gg{};
     if (n > 0 && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim && plan_grid(plan, &gg) &&
-        ws_bytes - lbytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad) &&
+        use_grid_path(gg) && ws_bytes - lbytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad) &&
         grid_loss_partials(gg.nx, gg.ny, gg.nz) <= mismatch_partials(n)) {
         const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, split_ws, g_grid_fold.load(),
                                           status, stream);
@@ -1519,7 +1528,8 @@ int grf_take_grid_tiles(int64_t* tiles) try {
 int grf_debug_grid_path(int32_t enable, int32_t fold_chunks) {
     if (fold_chunks != 1 && fold_chunks != 2 && fold_chunks != 4 && fold_chunks != 8)
         return fail(GRF_EINVAL, "fold_chunks must be 1, 2, 4 or 8");
-    g_grid_enabled.store(enable ? 1 : 0);
+    if (enable < 0 || enable > 2) return fail(GRF_EINVAL, "enable must be 0, 1 or 2");
+    g_grid_enabled.store(enable);
     g_grid_fold.store(fold_chunks);
     return GRF_OK;
 }

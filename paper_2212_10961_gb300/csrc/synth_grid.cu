@@ -66,12 +66,13 @@ constexpr int kGMaxSA = 4;
 constexpr int kGSB = 2;                     // formed B stages (3-D)
 constexpr int kGEpiWarps = 8;
 constexpr int kGThreads = 32 * (kGEpiWarps + 2);
-constexpr uint32_t kGLbo = 128;             // core matrices adjacent along K: contiguous
-constexpr uint32_t kGSbo = 1024;            // 8-row groups: 8 core matrices of K apart
+constexpr uint32_t kGSbo = 1024;            // 8-row groups of a tile: one 128-byte-swizzle atom apart
+constexpr uint32_t kGKStep = 32;            // bytes of 16 K elements inside an atom row
 constexpr uint32_t kGTmemCols = 512;
 constexpr uint32_t kGCorrCol = 256;         // hi.lo + lo.hi accumulator of the tile
 constexpr uint32_t kGSumCol = 384;          // running FP32 sum of the folded hi.hi intervals
 constexpr int kGBarBytes = 256;
+constexpr int kGAlignPad = 1024;            // room to start the stages on a 1024-byte boundary
 constexpr int kGSmemMax = 232448;           // dynamic shared memory per CTA (227 KB)
 static_assert(kGM == 128 && kGN == 128, "tile shape is fixed by the TMEM layout");
 
@@ -101,20 +102,23 @@ __device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile i
 }
 
 // Byte offset of the 16-byte row segment (row r, K elements 8 kk8 .. 8 kk8 + 7)
-// in a 128 x 64 K-major FP16 tile: element (r, kk) lives at
-// (r / 8) * 1024 + (kk / 8) * 128 + (r % 8) * 16 + (kk % 8) * 2.
+// in a 128 x 64 K-major FP16 tile in the 128-byte swizzled layout: row r at
+// (r / 8) * 1024 + (r % 8) * 128, its 16-byte chunk kk8 at position
+// kk8 ^ (r % 8) of the row (so 8 consecutive rows' chunks kk8 fall in 8
+// different bank groups).
 __host__ __device__ __forceinline__ uint32_t tile_off(int r, int kk8) {
-    return static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(kk8) * kGLbo +
-           static_cast<uint32_t>(r & 7) * 16u;
+    return static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(r & 7) * 128u +
+           (static_cast<uint32_t>(kk8 ^ (r & 7)) << 4);
 }
 
 // B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the 16 modes
 // 16 hm .. 16 hm + 15 of the chunk, from the staged table rows ty (y) and tw
-// (amplitude, psi, z), written as (re, im) FP16 pairs into the hi and lo
-// tiles at boff.
-__device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw, uint32_t boff) {
+// (amplitude, psi, z), written as (re, im) FP16 pairs into row n of the hi
+// and lo tiles, K segments kk8_0 .. kk8_0 + 3.
+__device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw, int n, int kk8_0) {
 #pragma unroll
     for (int g4 = 0; g4 < 4; ++g4) {
+        const uint32_t boff = tile_off(n, kk8_0 + g4);
         const float4 ya = ty[2 * g4], yb = ty[2 * g4 + 1];
         const float4 wa = tw[2 * g4], wb = tw[2 * g4 + 1];
         const float r0 = fmaf(wa.x, ya.x, -wa.y * ya.y), i0 = fmaf(wa.x, ya.y, wa.y * ya.x);
@@ -126,8 +130,8 @@ __device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, con
         tc::split_f16x2(r1, i1, H.y, L.y);
         tc::split_f16x2(r2, i2, H.z, L.z);
         tc::split_f16x2(r3, i3, H.w, L.w);
-        *reinterpret_cast<uint4*>(bhi + boff + g4 * kGLbo) = H;
-        *reinterpret_cast<uint4*>(bhi + kGOpBytes + boff + g4 * kGLbo) = L;
+        *reinterpret_cast<uint4*>(bhi + boff) = H;
+        *reinterpret_cast<uint4*>(bhi + kGOpBytes + boff) = L;
     }
 }
 
@@ -147,7 +151,9 @@ __device__ __forceinline__ TileIdx tile_idx(const GridDesc& d, int64_t tile) {
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int32_t* status) {
-    extern __shared__ __align__(1024) unsigned char gsm[];
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    // stages on a 1024-byte boundary of the shared window (swizzle atoms)
+    unsigned char* gsm = gsm_raw + ((1024u - (smem_u32(gsm_raw) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + d.off_bar);
     uint64_t* afull = bars;                // [sa] stage's copies landed (transaction bytes)
     uint64_t* afree = bars + kGMaxSA;      // [sa] stage's MMAs completed
@@ -197,7 +203,6 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         const int n_col = t & 127;        // column this thread forms
         const int hm = t >> 7;            // half of the chunk's modes it forms
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-        const uint32_t boff = tile_off(n_col, 4 * hm);
         const float S = grid_scale(d.thdr);
         uint32_t g = 0, gi = 0, tile_count = 0;
         for (int64_t tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x, ++tile_count) {
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                     }
                     const unsigned char* st = gsm + sa * d.a_stage;
                     form_b(gsm + d.off_b + sb * kGPair, reinterpret_cast<const float4*>(st + toff_y),
-                           reinterpret_cast<const float4*>(st + toff_w), boff);
+                           reinterpret_cast<const float4*>(st + toff_w), n_col, 4 * hm);
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bfull + sb);
@@ -359,11 +364,11 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                         const uint32_t ba = form ? smem_u32(gsm + d.off_b + sb * kGPair) : aa + kGPair;
 #pragma unroll
                         for (int ks = 0; ks < kGK / 16; ++ks) {
-                            const uint32_t ko = static_cast<uint32_t>(ks) * 2u * kGLbo;  // 16 K elements
-                            const uint64_t ah = tc::smem_desc(aa + ko, kGLbo, kGSbo);
-                            const uint64_t al = tc::smem_desc(aa + kGOpBytes + ko, kGLbo, kGSbo);
-                            const uint64_t bh = tc::smem_desc(ba + ko, kGLbo, kGSbo);
-                            const uint64_t bl = tc::smem_desc(ba + kGOpBytes + ko, kGLbo, kGSbo);
+                            const uint32_t ko = static_cast<uint32_t>(ks) * kGKStep;  // 16 K elements
+                            const uint64_t ah = tc::smem_desc_sw128(aa + ko, kGSbo);
+                            const uint64_t al = tc::smem_desc_sw128(aa + kGOpBytes + ko, kGSbo);
+                            const uint64_t bh = tc::smem_desc_sw128(ba + ko, kGSbo);
+                            const uint64_t bl = tc::smem_desc_sw128(ba + kGOpBytes + ko, kGSbo);
                             tc::mma_f16(dt, ah, bh, idesc, (cc | ks) != 0 ? 1u : 0u);
                             tc::mma_f16(dc, ah, bl, idesc, (iv | cc | ks) != 0 ? 1u : 0u);
                             tc::mma_f16(dc, al, bh, idesc, 1u);
@@ -533,7 +538,9 @@ __global__ void grid_prep_kernel(GridPrep p) {
 // descriptors and TMEM path as the grid kernel.  One CTA of 128 threads.
 __global__ void __launch_bounds__(128, 1) mma_probe_kernel(const uint16_t* A, const uint16_t* B, int32_t k_chunks,
                                                              float* D, int32_t* status) {
-    __shared__ __align__(1024) unsigned char sm[2 * kGOpBytes];
+    __shared__ __align__(1024) unsigned char sm_raw[2 * kGOpBytes + 1024];
+    // operand tiles on a 1024-byte boundary of the shared window (swizzle atoms)
+    unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     __shared__ uint64_t bar;
     __shared__ uint32_t slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -552,8 +559,7 @@ __global__ void __launch_bounds__(128, 1) mma_probe_kernel(const uint16_t* A, co
         // canonical layout of the 128 x 64 chunk of A and of B
         for (int e = threadIdx.x; e < kGM * kGK; e += blockDim.x) {
             const int r = e / kGK, kk = e % kGK;
-            const uint32_t off = static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(kk >> 3) * kGLbo +
-                                 static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(kk & 7) * 2u;
+            const uint32_t off = tile_off(r, kk >> 3) + static_cast<uint32_t>(kk & 7) * 2u;
             *reinterpret_cast<uint16_t*>(sm + off) = A[static_cast<int64_t>(r) * K + ch * kGK + kk];
             *reinterpret_cast<uint16_t*>(sm + kGOpBytes + off) = B[static_cast<int64_t>(r) * K + ch * kGK + kk];
         }
@@ -563,8 +569,8 @@ __global__ void __launch_bounds__(128, 1) mma_probe_kernel(const uint16_t* A, co
             tc::fence_after();
             const uint32_t sa = smem_u32(sm);
             for (int ks = 0; ks < kGK / 16; ++ks) {
-                const uint32_t ko = static_cast<uint32_t>(ks) * 2u * kGLbo;
-                tc::mma_f16(tbase, tc::smem_desc(sa + ko, kGLbo, kGSbo), tc::smem_desc(sa + kGOpBytes + ko, kGLbo, kGSbo),
+                const uint32_t ko = static_cast<uint32_t>(ks) * kGKStep;
+                tc::mma_f16(tbase, tc::smem_desc_sw128(sa + ko, kGSbo), tc::smem_desc_sw128(sa + kGOpBytes + ko, kGSbo),
                             tc::idesc_f16_f32(kGM, kGN), (ch | ks) != 0 ? 1u : 0u);
             }
             tc::commit(&bar);
@@ -623,18 +629,18 @@ GridPlan grid_plan(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
             }
         }
         const int tb = ((1 << g.pk_log2) + (kGN >> g.pk_log2)) * kGRowBytes;
-        g.a_stage = kGPair + tb;
-        g.sa = std::min(kGMaxSA, (kGSmemMax - kGBarBytes - kGSB * kGPair) / g.a_stage);
+        g.a_stage = (kGPair + tb + 1023) / 1024 * 1024;  // swizzle atoms start on 1024-byte boundaries
+        g.sa = std::min(kGMaxSA, (kGSmemMax - kGAlignPad - kGBarBytes - kGSB * kGPair) / g.a_stage);
         g.off_b = g.sa * g.a_stage;
         g.off_bar = g.off_b + kGSB * kGPair;
     } else {
         g.pk_log2 = 7;
         g.a_stage = 2 * kGPair;
-        g.sa = std::min(kGMaxSA, (kGSmemMax - kGBarBytes) / g.a_stage);
+        g.sa = std::min(kGMaxSA, (kGSmemMax - kGAlignPad - kGBarBytes) / g.a_stage);
         g.off_b = g.sa * g.a_stage;
         g.off_bar = g.off_b;
     }
-    g.smem = g.off_bar + kGBarBytes;
+    g.smem = g.off_bar + kGBarBytes + kGAlignPad;
     g.n_kt = (ny + (1 << g.pk_log2) - 1) >> g.pk_log2;
     const int PL = kGN >> g.pk_log2;
     g.n_lt = (nz + PL - 1) / PL;

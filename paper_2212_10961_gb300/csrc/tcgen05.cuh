@@ -11,16 +11,18 @@
 namespace grf {
 namespace tc {
 
-// Shared-memory matrix descriptor of an operand in the canonical K-major
-// layout without swizzle: core matrices of 8 rows x 16 bytes (the rows of a
-// core matrix 16 bytes apart, 128 contiguous bytes), `lbo` bytes between
-// core matrices adjacent along K and `sbo` bytes between adjacent groups of
-// 8 rows (M or N).  Address and offsets are multiples of 16 bytes.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: atoms of 8 rows x 128 bytes (64 FP16 elements of K per
+// row), the 16-byte chunk c of row r stored at chunk c ^ (r mod 8) of its
+// row, atoms of consecutive 8-row groups `sbo` bytes apart.  The atoms start
+// on 1024-byte boundaries; a K step of 16 elements advances the start
+// address by 32 bytes inside the atom.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo) {
     uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= 1ull << 16;  // leading-dimension offset (unused by swizzled K-major layouts), 16 bytes
     d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
-    d |= 1ull << 46;  // descriptor version of the tcgen05 family; base offset 0, no swizzle
+    d |= 1ull << 46;  // descriptor version of the tcgen05 family; base offset 0
+    d |= 2ull << 61;  // 128-byte swizzle
     return d;
 }
 

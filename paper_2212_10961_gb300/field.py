@@ -900,9 +900,11 @@ def take_grid_tiles():
 
 
 def grid_path(enable=True, fold_chunks=4):
-    """Process-wide switch of the grid path and its fold interval in chunks
-    of 32 modes (grf_debug_grid_path)."""
-    check(lib().grf_debug_grid_path(1 if enable else 0, int(fold_chunks)))
+    """Process-wide setting of the grid path (False: off, True: automatic,
+    "always": every grid plan) and its fold interval in chunks of 32 modes
+    (grf_debug_grid_path)."""
+    mode = 2 if enable == "always" else (1 if enable else 0)
+    check(lib().grf_debug_grid_path(mode, int(fold_chunks)))
 
 
 def mma_selftest(A, B, stream=None):

@@ -103,7 +103,7 @@ def _grid_run(env, cells, family, sigma2, ell, n_modes, seed, mean, fold=4, thre
     p = F.FieldParams(family=family, sigma2=sigma2, mean=mean, ell=ell, dim=d, n_modes=n_modes, seed=seed, nu=1.5)
     gf = F.GaussianField(p)
     plan = F.CellPlan(*to_dev(torch, cells))
-    F.grid_path(True, fold)
+    F.grid_path("always", fold)
     F.take_grid_tiles()
     F.take_path_counts()
     out = gf.synth(plan, F.MapSpec(y=True, lognormal=True, thresholds=thresholds, facies=True))
@@ -168,7 +168,7 @@ def test_grid_path_matches_general_path(env):
     y_or = oracle_field(oracle_modes("exponential", 4.0, ell, 3, 1000, 5), 0.0, cells)
     res = {}
     for on in (False, True):
-        F.grid_path(on)
+        F.grid_path("always" if on else False)
         F.take_grid_tiles()
         out = gf.synth(plan, maps)
         torch.cuda.synchronize()
@@ -178,6 +178,24 @@ def test_grid_path_matches_general_path(env):
         check_facies(res[on]["facies"], y_or, (-0.861454, 0.861454), 2.0)
     F.grid_path(True)
     assert np.max(np.abs(res[True]["Y"].astype(np.float64) - res[False]["Y"])) <= 2e-5 * 2.0
+
+
+def test_auto_setting_small_and_large_grids(env):
+    # the default setting leaves grids of fewer than 8 tiles of 128 x 128
+    # cells to the CUDA-core kernels and takes the grid path from 8 tiles on
+    torch, F, W = env
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=256, seed=3)
+    gf = F.GaussianField(p)
+    for shape, grid in (((64, 64), False), ((896, 128), False), ((1024, 128), True)):
+        plan = F.CellPlan(*to_dev(torch, W.grid_centres(shape)))
+        F.take_grid_tiles()
+        F.take_path_counts()
+        out = gf.synth(plan, F.MapSpec(y=True))
+        torch.cuda.synchronize()
+        assert (F.take_grid_tiles() > 0) == grid, shape
+        assert (sum(F.take_path_counts()) == 0) == grid, shape
+        y_or = oracle_field(oracle_modes("gaussian", 1.0, (0.1, 0.1), 2, 256, 3), 0.0, W.grid_centres(shape))
+        check_forward(out["Y"].cpu().numpy(), y_or, 1.0, "auto %s" % (shape,))
 
 
 def test_grid3d_256_full_size_grid_path_sampled(env):
