@@ -278,7 +278,7 @@ void drop_plan_event(PlanMeta& m) {
 bool use_grid_path(const GridGeom& gg) {
     const int32_t e = g_grid_enabled.load();
     if (e == 2) return true;
-    return e == 1 && grid_loss_partials(gg.nx, gg.ny, gg.nz) / 8 >= 8;
+    return e == 1 && grid_tiles(gg.nx, gg.ny, gg.nz) >= 8;
 }
 
 // The grid shape of `plan` (single segment), resolving a pending check by

@@ -331,6 +331,8 @@ int launch_mufu_probe(int32_t blocks, int32_t iters, float* sink, void* stream);
 size_t grid_ws_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad);
 // Loss partials (kMapMismatch) the grid path writes: one per epilogue warp per tile.
 int64_t grid_loss_partials(int32_t nx, int32_t ny, int32_t nz);
+// Tiles of 128 x 128 cells of a grid.
+int64_t grid_tiles(int32_t nx, int32_t ny, int32_t nz);
 int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const GridGeom& gg, const MapDev& map,
                       void* ws, int32_t fc, int32_t* status, void* stream);
 int take_grid_tiles(unsigned long long* tiles);

@@ -31,11 +31,12 @@
 // that spans the whole tile.
 //
 // Kernel structure (one CTA per SM, persistent over tiles):
-//   warps 0-7 : form B for each chunk (3-D), fold the accumulator, write the maps;
-//   warp 8    : one thread issues the MMAs (tcgen05.mma kind::f16, M = N = 128);
-//   warp 9    : one thread issues the bulk copies; the warp owns TMEM.
+//   warps 0-15: form B for each chunk (3-D), fold the accumulator, write the maps
+//               (warp w reads TMEM lanes 32 (w mod 4) .., columns 32 (w / 4) ..);
+//   warp 16   : one thread issues the MMAs (tcgen05.mma kind::f16, M = N = 128);
+//   warp 17   : one thread issues the bulk copies; the warp owns TMEM.
 // A ring of `sa` stages (A hi/lo and the chunk's tables, or A and B) and,
-// in 3-D, a ring of 2 formed B stages.  TMEM (512 columns): the hi.hi
+// in 3-D, a ring of 3 formed B stages.  TMEM (512 columns): the hi.hi
 // accumulator double-buffered (2 x 128), the correction accumulator (128) and
 // the running sums (128).  Every mbarrier wait is bounded and reports through
 // the status word.
@@ -63,9 +64,13 @@ constexpr int kGPair = 2 * kGOpBytes;       // hi and lo tiles of one operand
 constexpr int kGRowBytes = kGModes * 8 + 16;  // one table row of a chunk: 32 float2 + 16 bytes of padding
                                               // (consecutive rows start in different shared-memory banks)
 constexpr int kGMaxSA = 4;
-constexpr int kGSB = 2;                     // formed B stages (3-D)
-constexpr int kGEpiWarps = 8;
+constexpr int kGSB = 3;                     // formed B stages (3-D)
+constexpr int kGEpiWarps = 16;
 constexpr int kGThreads = 32 * (kGEpiWarps + 2);
+constexpr int kGColsPerWarp = kGN / (kGEpiWarps / 4);    // TMEM columns a warp folds (4 lane quarters)
+constexpr int kGFormGroups = 32 * kGEpiWarps / kGN;       // threads that form one column of B
+constexpr int kGFormQuads = kGModes / 4 / kGFormGroups;   // 4-mode groups each of them forms
+static_assert(kGColsPerWarp % 32 == 0 && kGFormQuads >= 1, "epilogue warp layout");
 constexpr uint32_t kGSbo = 1024;            // 8-row groups of a tile: one 128-byte-swizzle atom apart
 constexpr uint32_t kGKStep = 32;            // bytes of 16 K elements inside an atom row
 constexpr uint32_t kGTmemCols = 512;
@@ -111,13 +116,13 @@ __host__ __device__ __forceinline__ uint32_t tile_off(int r, int kk8) {
            (static_cast<uint32_t>(kk8 ^ (r & 7)) << 4);
 }
 
-// B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the 16 modes
-// 16 hm .. 16 hm + 15 of the chunk, from the staged table rows ty (y) and tw
+// B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the
+// 4 kGFormQuads modes from 4 kk8_0 on, from the staged table rows ty (y) and tw
 // (amplitude, psi, z), written as (re, im) FP16 pairs into row n of the hi
 // and lo tiles, K segments kk8_0 .. kk8_0 + 3.
 __device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw, int n, int kk8_0) {
 #pragma unroll
-    for (int g4 = 0; g4 < 4; ++g4) {
+    for (int g4 = 0; g4 < kGFormQuads; ++g4) {
         const uint32_t boff = tile_off(n, kk8_0 + g4);
         const float4 ya = ty[2 * g4], yb = ty[2 * g4 + 1];
         const float4 wa = tw[2 * g4], wb = tw[2 * g4 + 1];
@@ -157,8 +162,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
     uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + d.off_bar);
     uint64_t* afull = bars;                // [sa] stage's copies landed (transaction bytes)
     uint64_t* afree = bars + kGMaxSA;      // [sa] stage's MMAs completed
-    uint64_t* bfull = bars + 2 * kGMaxSA;  // [2] B formed (one arrival per epilogue warp)
-    uint64_t* bfree = bfull + kGSB;        // [2] B's MMAs completed
+    uint64_t* bfull = bars + 2 * kGMaxSA;  // [kGSB] B formed (one arrival per epilogue warp)
+    uint64_t* bfree = bfull + kGSB;        // [kGSB] B's MMAs completed
     uint64_t* accfull = bfree + kGSB;      // [2] interval's MMAs completed
     uint64_t* accfree = accfull + 2;       // [2] accumulator read by every epilogue warp
     uint64_t* corrfree = accfree + 2;      // correction accumulator read (tile end)
@@ -176,9 +181,11 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
             mbar_init(afull + s, 1);
             mbar_init(afree + s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kGSB; ++b) {
             mbar_init(bfull + b, kGEpiWarps);
             mbar_init(bfree + b, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(accfull + b, 1);
             mbar_init(accfree + b, kGEpiWarps);
         }
@@ -198,10 +205,10 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
     if (warp < kGEpiWarps) {
         // ---- B formation (3-D), folds, maps ---------------------------------------
         const int q = warp & 3;           // TMEM lane quarter (rows 32 q .. 32 q + 31)
-        const int h = warp >> 2;          // column half (64 h .. 64 h + 63)
+        const int h = warp >> 2;          // column block (kGColsPerWarp h ..)
         const int t = threadIdx.x;        // 0 .. 255
         const int n_col = t & 127;        // column this thread forms
-        const int hm = t >> 7;            // half of the chunk's modes it forms
+        const int hm = t >> 7;            // group of the chunk's modes it forms (kGFormQuads x 4 modes)
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
         const float S = grid_scale(d.thdr);
         uint32_t g = 0, gi = 0, tile_count = 0;
@@ -210,8 +217,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
             // staged table rows this thread reads: y row and (amplitude, psi, z) row
             const int ry = min(n_col & pkm, ti.pkv - 1);
             const int rz = min(n_col >> d.pk_log2, ti.plv - 1);
-            const int toff_y = kGPair + ry * kGRowBytes + 16 * hm * 8;
-            const int toff_w = kGPair + ((1 << d.pk_log2) + rz) * kGRowBytes + 16 * hm * 8;
+            const int toff_y = kGPair + ry * kGRowBytes + 4 * kGFormQuads * hm * 8;
+            const int toff_w = kGPair + ((1 << d.pk_log2) + rz) * kGRowBytes + 4 * kGFormQuads * hm * 8;
 
             // fold of interval gidx: the hi.hi accumulator into the running sum
             // (plain FP32: a few tens of folds per cell); the last fold of a
@@ -224,34 +231,34 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                 tc::fence_after();
                 if (!last) {
 #pragma unroll 1
-                    for (int blk = 0; blk < 2; ++blk) {  // 32 columns per TMEM round trip
-                        const uint32_t col = static_cast<uint32_t>(64 * h + 32 * blk);
-                        uint32_t p[32], sm[32];
-                        tc::ld32(tbase + lane_off + b * kGN + col, p);
-                        if (!first) tc::ld32(tbase + lane_off + kGSumCol + col, sm);
+                    for (int blk = 0; blk < kGColsPerWarp / 16; ++blk) {  // 16 columns per TMEM round trip
+                        const uint32_t col = static_cast<uint32_t>(kGColsPerWarp * h + 16 * blk);
+                        uint32_t p[16], sm[16];
+                        tc::ld16(tbase + lane_off + b * kGN + col, p);
+                        if (!first) tc::ld16(tbase + lane_off + kGSumCol + col, sm);
                         tc::wait_ld();
-                        if (blk == 1) {
+                        if (blk == kGColsPerWarp / 16 - 1) {
                             tc::fence_before();
                             __syncwarp();
                             if (lane == 0) tc::mbar_arrive(accfree + b);
                         }
 #pragma unroll
-                        for (int cc = 0; cc < 32; ++cc)
+                        for (int cc = 0; cc < 16; ++cc)
                             sm[cc] = first ? p[cc] : __float_as_uint(__uint_as_float(sm[cc]) + __uint_as_float(p[cc]));
-                        tc::st32(tbase + lane_off + kGSumCol + col, sm);
+                        tc::st16(tbase + lane_off + kGSumCol + col, sm);
                     }
                     tc::wait_st();
                 } else {
                     const int i = ti.mt * kGM + 32 * q + lane;
 #pragma unroll 1
-                    for (int blk = 0; blk < 4; ++blk) {  // 16 columns at a time, then the maps
-                        const uint32_t col = static_cast<uint32_t>(64 * h + 16 * blk);
-                        uint32_t p[16], sm[16], cr[16];
-                        tc::ld16(tbase + lane_off + b * kGN + col, p);
-                        tc::ld16(tbase + lane_off + kGCorrCol + col, cr);
-                        if (!first) tc::ld16(tbase + lane_off + kGSumCol + col, sm);
+                    for (int blk = 0; blk < kGColsPerWarp / 8; ++blk) {  // 8 columns at a time, then the maps
+                        const uint32_t col = static_cast<uint32_t>(kGColsPerWarp * h + 8 * blk);
+                        uint32_t p[8], sm[8], cr[8];
+                        tc::ld8(tbase + lane_off + b * kGN + col, p);
+                        tc::ld8(tbase + lane_off + kGCorrCol + col, cr);
+                        if (!first) tc::ld8(tbase + lane_off + kGSumCol + col, sm);
                         tc::wait_ld();
-                        if (blk == 3) {
+                        if (blk == kGColsPerWarp / 8 - 1) {
                             tc::fence_before();
                             __syncwarp();
                             if (lane == 0) {
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                             }
                         }
 #pragma unroll
-                        for (int cc = 0; cc < 16; ++cc) {
+                        for (int cc = 0; cc < 8; ++cc) {
                             float v = __uint_as_float(p[cc]);
                             if (!first) v = __uint_as_float(sm[cc]) + v;
                             v += __uint_as_float(cr[cc]);
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                     }
                     const unsigned char* st = gsm + sa * d.a_stage;
                     form_b(gsm + d.off_b + sb * kGPair, reinterpret_cast<const float4*>(st + toff_y),
-                           reinterpret_cast<const float4*>(st + toff_w), n_col, 4 * hm);
+                           reinterpret_cast<const float4*>(st + toff_w), n_col, kGFormQuads * hm);
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bfull + sb);
@@ -745,6 +752,8 @@ int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const Gri
 int64_t grid_loss_partials(int32_t nx, int32_t ny, int32_t nz) {
     return grid_plan(nx, ny, nz, kGModes * 4).n_tiles * kGEpiWarps;
 }
+
+int64_t grid_tiles(int32_t nx, int32_t ny, int32_t nz) { return grid_plan(nx, ny, nz, kGModes * 4).n_tiles; }
 
 int take_grid_tiles(unsigned long long* tiles) {
     unsigned long long v = 0ull;

@@ -108,6 +108,15 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
+// Warp-wide store of 16 columns (layout as ld16).
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        GRF_W8(0), GRF_W8(8)
+        : "memory");
+}
+
 // Warp-wide store of 32 columns (layout as ld32).
 __device__ __forceinline__ void st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
