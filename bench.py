@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-tile", default="auto", choices=["auto", "128", "256", "512"],
                     help="cells per warp work item of the ensemble (default: autotuned)")
+    ap.add_argument("--grid-path", default="auto", choices=["auto", "off", "always"],
+                    help="tensor-core grid path for cells on a Cartesian grid (default: from 8 tiles of "
+                         "128 x 128 cells up; off: the CUDA-core kernels)")
     ap.add_argument("--jsonl", default=None,
                     help="also append the result line to this JSON-lines run log (with a UTC timestamp)")
     return ap.parse_args()
@@ -722,10 +725,13 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
     return res
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
-# headline's kernels (256^3 cells, 4096 modes), from an ncu capture; None
-# until the current kernels have been captured.
-HEAD_TRAFFIC_BYTES = None  # the headline now runs on the grid path: no capture of its kernels yet
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size call of the
+# headline's grid-path kernels (grid_prep_kernel + grid_mma_kernel, 256^3
+# cells, 4096 modes), one ncu capture (`--metrics dram__bytes_read.sum,
+# dram__bytes_write.sum -k regex:grid`): 0.25 + 0.03 MB and 27.21 + 90.98 MB.
+# Algorithmic: 9 B written per cell (Y, K, facies) = 151 MB plus 26 MB of
+# tables; part of the writes was still in L2 when the launch ended.
+HEAD_TRAFFIC_BYTES = 0.25318e6 + 0.0279e6 + 27.21e6 + 90.98e6
 
 
 # FP32 instructions per cell-mode of the lattice path (lanes of 4-cell grid
@@ -870,6 +876,7 @@ def main():
         native.build()  # the FP64 accuracy checks run outside every timed region
 
     sms, _ = F.device_info()
+    F.grid_path({"auto": True, "off": False, "always": "always"}[args.grid_path])
     clocks = ClockSampler(local)
     extra = {}
     head = None
