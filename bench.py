@@ -483,11 +483,13 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
 
     take_paths(F)  # reset
     F.take_adjoint_path_counts()
+    F.take_grid_adjoint_units()
     l0 = F.launch_count()
     ms = timed_steps(torch, world, steps, warmup, step)
     launches = F.launch_count() - l0
     paths = take_paths(F)
     bgen, blat = F.take_adjoint_path_counts()
+    bgrid = F.take_grid_adjoint_units()
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, c in kev[warmup:]]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for a, b, c in kev[warmup:]]))
     res = {"workload": "diff128" if scale == 1 else "diff128/%d" % scale, "cells": M, "modes": N,
@@ -495,17 +497,20 @@ def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
            "launches_per_step": launches / float(steps + warmup),
            "forward": "fused synthesis + lognormal mismatch loss and gradient (grf_synth_mismatch)",
            **path_fields(paths),
-           "adjoint_path_tiles": {"general": bgen, "lattice": blat},
-           "adjoint_lattice_share": blat / float(bgen + blat) if bgen + blat else 0.0}
+           "adjoint_path_tiles": {"general": bgen, "lattice": blat, "grid_units": bgrid},
+           "adjoint_lattice_share": blat / float(bgen + blat) if bgen + blat else 0.0,
+           "adjoint_grid_path": bgrid > 0 and bgen + blat == 0}
     if rank == 0:
-        res["fp64_check"] = grad_check_40(torch, F, W)
+        res["fp64_check"] = grad_check_40(torch, F, W, grid=res["adjoint_grid_path"])
     return res
 
 
-def grad_check_40(torch, F, W):
+def grad_check_40(torch, F, W, grid=False):
     """Loss and per-family gradient errors of the fused forward + adjoint on a
     40^3 grid with the 128^3 workload's parameters, against the FP64 oracle's
-    own loss gradient (relative to each family's largest oracle value)."""
+    own loss gradient (relative to each family's largest oracle value).  grid:
+    the timed step ran on the grid path, so this check does too (40^3 is
+    below the automatic threshold)."""
     from oracle import field as of
     from oracle import native
     w = W.WORKLOADS["diff128"]
@@ -516,9 +521,14 @@ def grad_check_40(torch, F, W):
     pt = params_for(F, w, 3, w["target_seed"])
     gf = F.GaussianField(p)
     T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
-    loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True)
-    g = F.backward(gf.table, p, plan, gY)
-    torch.cuda.synchronize()
+    if grid:
+        F.grid_path("always")
+    try:
+        loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True)
+        g = F.backward(gf.table, p, plan, gY)
+        torch.cuda.synchronize()
+    finally:
+        F.grid_path(GRID_SETTING)
     om = oracle_modes_for(w, 3, w["seed"])
     y_or = native.synth(om["a"], om["amp"], om["psi"], w["mean"], c)
     l_or, g_or = of.mismatch_loss(np.exp(y_or), T.cpu().numpy().astype(np.float64))
@@ -528,7 +538,8 @@ def grad_check_40(torch, F, W):
     for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dsigma2", "dell", "drot", "drho", "dkappa"):
         r = np.asarray(ref[k], dtype=np.float64)
         errs[k] = float(np.max(np.abs(g[k].cpu().numpy().reshape(r.shape) - r)) / np.max(np.abs(r)))
-    return {"grid": "40^3 with the 128^3 parameters", "grad_err_rel": errs, "tol_rel": 1e-4,
+    return {"grid": "40^3 with the 128^3 parameters", "path": "grid (tensor cores)" if grid else "CUDA cores",
+            "grad_err_rel": errs, "tol_rel": 1e-4,
             "within_tol": bool(max(errs.values()) <= 1e-4),
             "loss_err_rel": abs(loss.item() - l_or) / abs(l_or),
             "max_abs_err_sigma": float(np.max(np.abs(out["Y"].cpu().numpy() - y_or))) / math.sqrt(w["sigma2"])}
@@ -753,6 +764,13 @@ ADJOINT_LATTICE_FP32_PER_CELL_MODE = 6.6
 # product is a 2-term dot product (2 multiply-adds = 4 flops), evaluated as
 # three FP16 products (hi.hi, hi.lo, lo.hi) for FP32-level accuracy.
 GRID_TENSOR_FLOPS_PER_CELL_MODE = 12.0
+# The grid adjoint: per cell-mode the cosine and the sine product of g and of
+# the x-weighted g (4 multiply-adds = 8 flops), each as three FP16 products.
+GRID_ADJ_TENSOR_FLOPS_PER_CELL_MODE = 24.0
+
+# Grid-path setting of this run (--grid-path), restored after checks that
+# force the grid path on grids below the automatic threshold.
+GRID_SETTING = True
 
 
 def roofline(kern_ms, cell_modes, clocks, sms, traffic=None, lattice_share=0.0, grid=False):
@@ -876,7 +894,9 @@ def main():
         native.build()  # the FP64 accuracy checks run outside every timed region
 
     sms, _ = F.device_info()
-    F.grid_path({"auto": True, "off": False, "always": "always"}[args.grid_path])
+    global GRID_SETTING
+    GRID_SETTING = {"auto": True, "off": False, "always": "always"}[args.grid_path]
+    F.grid_path(GRID_SETTING)
     clocks = ClockSampler(local)
     extra = {}
     head = None
@@ -948,16 +968,27 @@ def main():
                                         grid=k_fb.get("grid_path", False))
         bw = k_fb["cell_modes_per_step"] / (k_fb["bwd_ms"] * 1e-3) / 1e9
         bmufu = MUFU_PER_CLK_PER_SM * sms * 2070e6 / 2 / 1e9
-        if k_fb.get("adjoint_lattice_share", 0.0) >= 0.5:
+        if k_fb.get("adjoint_grid_path", False):
+            tpk, kind = tensor_peak()
+            tf = k_fb["cell_modes_per_step"] * GRID_ADJ_TENSOR_FLOPS_PER_CELL_MODE / (k_fb["bwd_ms"] * 1e-3) / 1e12
+            k_fb["bwd_roofline"] = {
+                "bound": "tensor", "achieved": tf, "peak": tpk, "unit": "TFLOP/s", "frac": tf / tpk,
+                "peak_kind": kind, "gcell_modes_per_s": bw, "frac_of_mufu_roofline": bw / bmufu,
+                "peak_basis": ("tensor-core grid adjoint: %.0f FP16 tensor flops per cell-mode (cos and sin "
+                               "products of g and of x-weighted g, three FP16 products each) against the %s dense "
+                               "BF16 burst peak" % (GRID_ADJ_TENSOR_FLOPS_PER_CELL_MODE, kind)),
+                "note": "scan, table preparation, tensor-core kernel and the two reductions"}
+        elif k_fb.get("adjoint_lattice_share", 0.0) >= 0.5:
             bpk = FP32_PER_CLK_PER_SM * sms * 2070e6 / ADJOINT_LATTICE_FP32_PER_CELL_MODE / 1e9
             basis = ("lattice tiles (%.3f of the tiles): %d FP32 lanes/clk/SM x %d SMs x 2070 MHz / %.1f FP32 "
                      "instructions per cell-mode" % (k_fb["adjoint_lattice_share"], FP32_PER_CLK_PER_SM, sms,
                                                      ADJOINT_LATTICE_FP32_PER_CELL_MODE))
         else:
             bpk, basis = bmufu, "2 MUFU per cell-mode (sine and cosine)"
-        k_fb["bwd_roofline"] = {"bound": "alu", "achieved": bw, "peak": bpk, "unit": "Gcell.mode/s",
-                                "frac": bw / bpk, "peak_basis": basis, "frac_of_mufu_roofline": bw / bmufu,
-                                "note": "adjoint kernel and its two reductions"}
+        if not k_fb.get("adjoint_grid_path", False):
+            k_fb["bwd_roofline"] = {"bound": "alu", "achieved": bw, "peak": bpk, "unit": "Gcell.mode/s",
+                                    "frac": bw / bpk, "peak_basis": basis, "frac_of_mufu_roofline": bw / bmufu,
+                                    "note": "adjoint kernel and its two reductions"}
     if head is None:
         head = next(iter(extra.values()))
         emit(args, {"partial": args.only, "results": extra, "clocks": ck})

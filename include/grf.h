@@ -420,6 +420,16 @@ typedef struct grf_grads {
 size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);
 
 /*
+ * grf_backward_grid_workspace_bytes -- workspace bytes grf_synth_backward
+ * needs to take the tensor-core grid adjoint on `plan` (segment 0, a
+ * Cartesian grid in x-fastest order, dim >= 2) with n_modes modes: the
+ * per-mode partials, the tables of x, y and z phasors and the FP16 tiles of
+ * gY.  0 when the plan is not such a grid, its check is unresolved only
+ * through a failed event, or the arguments are invalid.
+ */
+size_t grf_backward_grid_workspace_bytes(const void *plan, int32_t segment, int64_t n_modes);
+
+/*
  * grf_synth_backward -- gradients of a loss L with respect to the mode
  * amplitudes, phases and frequencies, the mean, sigma and the correlation
  * lengths, given gY = dL/dY (device float32, original cell order, cells of
@@ -432,6 +442,14 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
  * The sines and cosines are recomputed, never stored.  Per-block FP64
  * partials go to `workspace` and are reduced in a fixed order, so results
  * are deterministic.  All non-optional outputs in `g` are written (device).
+ * Grid path: when the plan is a Cartesian grid in x-fastest order (dim >= 2,
+ * one segment), the grid path is enabled for it (grf_debug_grid_path) and
+ * ws_bytes >= grf_backward_grid_workspace_bytes(), the per-mode sums are
+ * matrix products on the tensor cores: D_j(k, l) = sum_i e^{2 pi i a_jx X_i}
+ * g(i, k, l) over the x cells (FP16 hi + lo operands, three products per
+ * term, FP32 accumulators over 64 x cells), contracted with the y and z
+ * phasors per mode on the CUDA cores.  Otherwise ws_bytes must be at least
+ * grf_backward_workspace_bytes() (GRF_EWORKSPACE).
  */
 int grf_synth_backward(const void *table, const grf_params *p, const void *plan, int32_t segment,
                        const float *gY, const grf_grads *g, void *workspace, size_t ws_bytes,
@@ -629,6 +647,14 @@ int grf_take_adjoint_path_counts(int64_t *general_tiles, int64_t *lattice_tiles)
  * device.  GRF_EINVAL for NULL, GRF_ECUDA if the counter cannot be read.
  */
 int grf_take_grid_tiles(int64_t *tiles);
+
+/*
+ * grf_take_grid_adjoint_units -- units (128 modes x 64 x cells x 64 (y, z)
+ * cells) computed by the tensor-core grid adjoint since the last call, then
+ * resets the count.  Synchronises the device.  GRF_EINVAL for NULL,
+ * GRF_ECUDA if the counter cannot be read.
+ */
+int grf_take_grid_adjoint_units(int64_t *units);
 
 /*
  * grf_debug_grid_path -- process-wide setting of the grid path (enable = 0:

@@ -117,6 +117,7 @@ _SIGS = {
     "grf_map_bitruncated": (ctypes.c_int, [ctypes.POINTER(grf_bimap), ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]),
+    "grf_backward_grid_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "grf_synth_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grf_params), ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(grf_grads),
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -148,6 +149,7 @@ _SIGS = {
     "grf_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_mufu_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "grf_take_grid_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "grf_take_grid_adjoint_units": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "grf_debug_grid_path": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "grf_debug_mma_f16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]),

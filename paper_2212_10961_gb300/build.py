@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libgrf.so")
 FLAVOURS = {"release": (LIB, os.path.join(BUILD, "release"), []),
             "checked": (os.path.join(PKG, "libgrf_checked.so"), os.path.join(BUILD, "checked"),
                         ["-DGRF_CHECKED=1"])}
-SOURCES = ["synth_fwd.cu", "synth_bwd.cu", "synth_grid.cu", "plan.cu", "maps.cu", "grf_host.cpp"]
+SOURCES = ["synth_fwd.cu", "synth_bwd.cu", "synth_grid.cu", "synth_grid_bwd.cu", "plan.cu", "maps.cu", "grf_host.cpp"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

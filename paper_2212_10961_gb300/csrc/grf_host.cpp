@@ -981,6 +981,17 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
     return bwd_workspace_bytes(n_cells, n_modes, dim);
 }
 
+size_t grf_backward_grid_workspace_bytes(const void* plan, int32_t segment, int64_t n_modes) {
+    try {
+        if (!plan || segment != 0 || n_modes < 1 || n_modes > GRF_MAX_MODES) return 0;
+        GridGeom gg{};
+        if (!plan_grid(plan, &gg)) return 0;
+        return bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+    } catch (...) {
+        return 0;
+    }
+}
+
 int grf_synth_backward(const void* table, const grf_params* p, const void* plan, int32_t segment,
                        const float* gY, const grf_grads* g, void* workspace, size_t ws_bytes,
                        void* stream) try {
@@ -1000,8 +1011,6 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
     if (!workspace) return fail(GRF_EINVAL, "workspace is NULL");
     if (!aligned256(workspace)) return fail(GRF_EINVAL, "workspace must be 256-byte aligned");
     if (!aligned256(table)) return fail(GRF_EINVAL, "device table must be 256-byte aligned");
-    const size_t need = bwd_workspace_bytes(n, p->n_modes, p->dim);
-    if (ws_bytes < need) return fail(GRF_EWORKSPACE, "backward workspace %zu < %zu bytes", ws_bytes, need);
     const unsigned char* pb = static_cast<const unsigned char*>(plan);
     int32_t* status = &static_cast<PlanHeader*>(const_cast<void*>(plan))->status;
     double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -1010,6 +1019,18 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
     int32_t periodic = 0;
     for (int c = 0; c < p->dim; ++c)
         if (p->period[c] > 0.0) periodic |= 1 << c;
+    // Cartesian grid handed over x-fastest: the tensor-core adjoint when the
+    // workspace holds its tables
+    GridGeom gg{};
+    if (n > 0 && g_grid_enabled.load() != 0 && meta.offsets.size() == 2 && p->dim >= 2 && plan_grid(plan, &gg) &&
+        use_grid_path(gg) && ws_bytes >= bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
+        const int err = launch_synth_bwd_grid(table, p->n_modes, p->dim, gg, gY, std::sqrt(p->sigma2), p->ell, rot,
+                                              periodic, *g, workspace, status, stream);
+        if (err != cudaSuccess) return cuda_fail(err, "grid backward kernels");
+        return GRF_OK;
+    }
+    const size_t need = bwd_workspace_bytes(n, p->n_modes, p->dim);
+    if (ws_bytes < need) return fail(GRF_EWORKSPACE, "backward workspace %zu < %zu bytes", ws_bytes, need);
     const int err = launch_synth_bwd(
         table, p->n_modes, p->dim, std::sqrt(p->sigma2), p->ell, rot, periodic,
         reinterpret_cast<const float*>(pb + meta.layout.off_xs) + begin,
@@ -1520,6 +1541,20 @@ int grf_take_grid_tiles(int64_t* tiles) try {
     e = static_cast<cudaError_t>(take_grid_tiles(&v));
     if (e != cudaSuccess) return cuda_fail(e, "grid tile counter");
     *tiles = static_cast<int64_t>(v);
+    return GRF_OK;
+} catch (...) {
+    return host_exception();
+}
+
+int grf_take_grid_adjoint_units(int64_t* units) try {
+    if (!units) return fail(GRF_EINVAL, "NULL argument");
+    *units = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the grid adjoint unit counter");
+    unsigned long long v = 0ull;
+    e = static_cast<cudaError_t>(take_grid_adj_units(&v));
+    if (e != cudaSuccess) return cuda_fail(e, "grid adjoint unit counter");
+    *units = static_cast<int64_t>(v);
     return GRF_OK;
 } catch (...) {
     return host_exception();

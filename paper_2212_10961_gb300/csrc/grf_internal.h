@@ -321,6 +321,24 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
                      const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
                      const grf_grads& g, void* workspace, int32_t* status, void* stream);
 size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim);
+// Per-mode terms of the scalar gradients the adjoint's reduction writes
+// (contrib rows: (A / sigma) dA, three l terms, nine R terms).
+constexpr int kBwdContrib = 13;
+// The adjoint's reduction and chain rule from per-mode partial sums:
+// part[s][slot][5] = (sum g cos, sum g sin, sum g x sin, sum g y sin,
+// sum g z sin) for s < splits (summed in increasing s), gpart[0 .. n_gpart)
+// partial sums of g, contrib: kBwdContrib x n_pad doubles of scratch.
+int launch_bwd_reduce(const void* table, int64_t n_modes, int32_t dim, double sigma, const double* ell,
+                      const double* rot, int32_t periodic_mask, const grf_grads& g, double* part, int32_t splits,
+                      double* gpart, int32_t n_gpart, double* contrib, void* stream);
+// Tensor-core adjoint on a Cartesian grid in x-fastest order (synth_grid_bwd.cu):
+// workspace bytes, the launch (scan, prep, tensor-core kernel, reduction) and
+// the units computed since the last call (synchronous).
+size_t bwd_grid_ws_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad);
+int launch_synth_bwd_grid(const void* table, int64_t n_modes, int32_t dim, const GridGeom& gg, const float* gY,
+                          double sigma, const double* ell, const double* rot, int32_t periodic_mask,
+                          const grf_grads& g, void* ws, int32_t* status, void* stream);
+int take_grid_adj_units(unsigned long long* units);
 int launch_mismatch(int64_t n, const float* K, const float* T, float* gY, double* loss, void* ws,
                     void* stream);
 size_t mismatch_workspace_bytes(int64_t n);

@@ -39,7 +39,7 @@ constexpr int kBwdThreads = 128;
 constexpr int kBwdTile = 256;
 constexpr int kBwdMaxSplits = 256;
 constexpr int kMPT = 4;  // modes per thread
-constexpr int kContrib = 13;  // per-mode terms of the scalar gradients
+constexpr int kContrib = kBwdContrib;  // per-mode terms of the scalar gradients
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 struct BwdArgs {
@@ -66,7 +66,8 @@ struct BwdArgs {
     int64_t n_cells;
     const float* gY;
     double* part;     // [splits][n_pad][5]
-    double* gpart;    // [splits]
+    double* gpart;    // [n_gpart]: partial sums of g
+    int32_t n_gpart;
     double* contrib;  // [kContrib][n_pad]: (A/sigma) dA, dl terms (3), dR terms (9)
     grf_grads g;
 };
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kScalarThreads) bwd_scalar_kernel(BwdArgs args
     for (int64_t m = threadIdx.x; m < np; m += kScalarThreads)
 #pragma unroll
         for (int q = 0; q < kContrib; ++q) acc[q] += args.contrib[q * np + m];
-    for (int k = threadIdx.x; k < args.splits; k += kScalarThreads) acc[kContrib] += args.gpart[k];
+    for (int k = threadIdx.x; k < args.n_gpart; k += kScalarThreads) acc[kContrib] += args.gpart[k];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
 #pragma unroll
@@ -647,16 +648,13 @@ size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
     return static_cast<size_t>(align256(part) + align256(gpart) + align256(contrib));
 }
 
-int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
-                     const double* ell, const double* rot, int32_t periodic_mask, const float* xs,
-                     const float* ys, const float* zs,
-                     const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
-                     const grf_grads& g, void* workspace, int32_t* status, void* stream) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (const int e = bwd_allow_smem(dim)) return e;
+namespace {
+
+// The table, parameter and transform fields of the adjoint's arguments.
+void bwd_common_args(BwdArgs& a, const void* table, int64_t n_modes, int32_t dim, double sigma, const double* ell,
+                     const double* rot, int32_t periodic_mask, const grf_grads& g) {
     const TableLayout TL = table_layout(n_modes);
     const unsigned char* tb = static_cast<const unsigned char*>(table);
-    BwdArgs a{};
     a.hot = reinterpret_cast<const float4*>(tb + TL.off_hot);
     a.cold = reinterpret_cast<const float4*>(tb + TL.off_cold);
     a.order = reinterpret_cast<const int32_t*>(tb + TL.off_order);
@@ -691,6 +689,38 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
         for (int i = 0; i < 3; ++i)
             for (int k = 0; k < 3; ++k) a.rot_it[i * 3 + k] = cof[i][k] / det;
     }
+    a.g = g;
+}
+
+}  // namespace
+
+int launch_bwd_reduce(const void* table, int64_t n_modes, int32_t dim, double sigma, const double* ell,
+                      const double* rot, int32_t periodic_mask, const grf_grads& g, double* part, int32_t splits,
+                      double* gpart, int32_t n_gpart, double* contrib, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BwdArgs a{};
+    bwd_common_args(a, table, n_modes, dim, sigma, ell, rot, periodic_mask, g);
+    a.part = part;
+    a.splits = splits;
+    a.gpart = gpart;
+    a.n_gpart = n_gpart;
+    a.contrib = contrib;
+    bwd_reduce_kernel<<<static_cast<unsigned>(a.n_pad / 32), 32 * kRedWarps, 0, st>>>(a);
+    bwd_scalar_kernel<<<1, kScalarThreads, 0, st>>>(a);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sigma,
+                     const double* ell, const double* rot, int32_t periodic_mask, const float* xs,
+                     const float* ys, const float* zs,
+                     const int32_t* perm, int64_t perm_base, int64_t n_cells, const float* gY,
+                     const grf_grads& g, void* workspace, int32_t* status, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (const int e = bwd_allow_smem(dim)) return e;
+    const TableLayout TL = table_layout(n_modes);
+    BwdArgs a{};
+    bwd_common_args(a, table, n_modes, dim, sigma, ell, rot, periodic_mask, g);
     a.xs = xs;
     a.ys = ys;
     a.zs = zs;
@@ -698,7 +728,6 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.perm_base = perm_base;
     a.n_cells = n_cells;
     a.gY = gY;
-    a.g = g;
     const int mode_blocks = static_cast<int>((TL.n_pad + kBwdThreads * kMPT - 1) / (kBwdThreads * kMPT));
     a.splits = 1;
     if (n_cells > 0) {
@@ -730,6 +759,7 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
         }
         count_launches(1);
     }
+    a.n_gpart = a.splits;
     bwd_reduce_kernel<<<static_cast<unsigned>(n_pad / 32), 32 * kRedWarps, 0, st>>>(a);
     bwd_scalar_kernel<<<1, kScalarThreads, 0, st>>>(a);
     count_launches(2);

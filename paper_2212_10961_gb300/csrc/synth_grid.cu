@@ -46,6 +46,7 @@
 #include <cmath>
 
 #include "device_common.cuh"
+#include "grid_common.cuh"
 #include "tcgen05.cuh"
 
 namespace grf {
@@ -54,6 +55,10 @@ namespace grf {
 static __device__ unsigned long long g_grid_tiles;
 
 namespace {
+
+using gridc::gwait;
+using gridc::psi_z_turns;
+using gridc::tile_off;
 
 constexpr int kGM = 128;                    // x cells per tile (TMEM lanes)
 constexpr int kGN = 128;                    // (y, z) cells per tile (accumulator columns)
@@ -78,7 +83,7 @@ constexpr uint32_t kGCorrCol = 256;         // hi.lo + lo.hi accumulator of the 
 constexpr uint32_t kGSumCol = 384;          // running FP32 sum of the folded hi.hi intervals
 constexpr int kGBarBytes = 256;
 constexpr int kGAlignPad = 1024;            // room to start the stages on a 1024-byte boundary
-constexpr int kGSmemMax = 232448;           // dynamic shared memory per CTA (227 KB)
+constexpr int kGSmemMax = gridc::kSmemMax;
 static_assert(kGM == 128 && kGN == 128, "tile shape is fixed by the TMEM layout");
 
 // Amplitude scale: the smallest power of two S >= max |A_j| (1 when all
@@ -89,31 +94,6 @@ __device__ __forceinline__ float grid_scale(const TableHeader* h) {
     int e;
     frexpf(m, &e);
     return ldexpf(1.0f, e);
-}
-
-// Bounded wait that also gives up once another role has set the abort flag.
-__device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int32_t* abort, int32_t* status) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t round = 0; round < kWaitMaxRounds; ++round) {
-        for (int i = 0; i < 64; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (*abort) return false;
-        if (global_ns() - t0 > kWaitLimitNs) break;
-    }
-    *abort = 1;
-    atomicOr(status, 2);
-    return false;
-}
-
-// Byte offset of the 16-byte row segment (row r, K elements 8 kk8 .. 8 kk8 + 7)
-// in a 128 x 64 K-major FP16 tile in the 128-byte swizzled layout: row r at
-// (r / 8) * 1024 + (r % 8) * 128, its 16-byte chunk kk8 at position
-// kk8 ^ (r % 8) of the row (so 8 consecutive rows' chunks kk8 fall in 8
-// different bank groups).
-__host__ __device__ __forceinline__ uint32_t tile_off(int r, int kk8) {
-    return static_cast<uint32_t>(r >> 3) * kGSbo + static_cast<uint32_t>(r & 7) * 128u +
-           (static_cast<uint32_t>(kk8 ^ (r & 7)) << 4);
 }
 
 // B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the
@@ -442,14 +422,6 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         tc::fence_after();
         tc::dealloc(tbase, kGTmemCols);
     }
-}
-
-// x, y, (z + psi) phase of mode j in turns, each exactly reduced: a = ah + al
-// (FP32 pairs) at the axis coordinate.
-__device__ __forceinline__ float psi_z_turns(const float4 c1, float z, bool has_z) {
-    float t = has_z ? turns_axis(c1.x, c1.y, z) : 0.0f;
-    t = frac_turn(t + c1.z);
-    return frac_turn(t + c1.w);
 }
 
 // Tables of one call (workspace).  Work items, flattened:

@@ -586,6 +586,14 @@ _ws_loss = Workspace()
 _ws_fwd = Workspace()
 
 
+def backward_workspace_bytes(plan: CellPlan, segment, n_modes, dim):
+    """Workspace bytes of grf_synth_backward on this plan: enough for the
+    CUDA-core adjoint and, on a grid plan, for the tensor-core one
+    (grf_backward_workspace_bytes and grf_backward_grid_workspace_bytes)."""
+    return max(int(lib().grf_backward_workspace_bytes(plan.segment_size(segment), int(n_modes), int(dim))),
+               int(lib().grf_backward_grid_workspace_bytes(plan.ptr, int(segment), int(n_modes))))
+
+
 def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=0, stream=None,
              workspace=None, gscale=None):
     """Gradients (device FP64) of a loss with dL/dY = gY (CUDA float32,
@@ -611,7 +619,7 @@ def backward(table: ModeTable, params: FieldParams, plan: CellPlan, gY, segment=
         setattr(gs, k, g[k].data_ptr())
     if gscale is not None:
         gs.gscale = _require_cuda(gscale, torch.float64, "gscale").data_ptr()
-    nbytes = int(lib().grf_backward_workspace_bytes(plan.segment_size(segment), n, d))
+    nbytes = backward_workspace_bytes(plan, segment, n, d)
     ws = (workspace or _ws_bwd).get(nbytes, dev)
     check(lib().grf_synth_backward(table.ptr, ctypes.byref(params.to_c()), plan.ptr, int(segment),
                                    _ptr(gY), ctypes.byref(gs), _ptr(ws), ws.numel(),
@@ -896,6 +904,15 @@ def take_grid_tiles():
     last call (grf_take_grid_tiles); synchronises the device."""
     t = ctypes.c_int64(0)
     check(lib().grf_take_grid_tiles(ctypes.byref(t)))
+    return t.value
+
+
+def take_grid_adjoint_units():
+    """Units (128 modes x 64 x cells x 64 (y, z) cells) computed by the
+    tensor-core grid adjoint since the last call (grf_take_grid_adjoint_units);
+    synchronises the device."""
+    t = ctypes.c_int64(0)
+    check(lib().grf_take_grid_adjoint_units(ctypes.byref(t)))
     return t.value
 
 
