@@ -68,7 +68,11 @@ struct BwdArgs {
     double* part;     // [splits][n_pad][5]
     double* gpart;    // [n_gpart]: partial sums of g
     int32_t n_gpart;
-    double* contrib;  // [kContrib][n_pad]: (A/sigma) dA, dl terms (3), dR terms (9)
+    double* contrib;  // [kContrib][n_pad / 32]: per reduction block, the sums over its 32 modes
+                      // of (A/sigma) dA, the dl terms (3) and the dR terms (9)
+    double inv_sigma;
+    double inv_ell[3];
+    double inv_2pi_ell[3];
     grf_grads g;
 };
 
@@ -473,11 +477,15 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_partial_kernel(BwdArgs arg
 // original mode index.  A block owns 32 modes (one per lane); warp w sums
 // the splits w, w + 8, w + 16, ... in increasing order (coalesced rows of the
 // partials, many loads in flight), and warp 0 adds the 8 warp sums in warp
-// order: a fixed order, so the result does not depend on timing.
+// order, applies the chain rule (reciprocals of sigma and l precomputed: few
+// FP64 operations, which are slow on this part) and writes the block's sums
+// of the 13 scalar-gradient terms over its 32 modes, in mode order: a fixed
+// order throughout, so the result does not depend on timing.
 constexpr int kRedWarps = 8;
 
 __global__ void __launch_bounds__(32 * kRedWarps) bwd_reduce_kernel(BwdArgs args) {
     __shared__ double red[kRedWarps][32][5];
+    __shared__ double cts[kContrib][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = blockIdx.x * 32 + lane;  // n_pad is a multiple of 128
     {
@@ -492,93 +500,89 @@ __global__ void __launch_bounds__(32 * kRedWarps) bwd_reduce_kernel(BwdArgs args
         for (int q = 0; q < 5; ++q) red[warp][lane][q] = v[q];
     }
     __syncthreads();
-    if (warp != 0) return;
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < kRedWarps; ++w)
+    if (warp == 0) {
+        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kRedWarps; ++w)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) v[q] += red[w][lane][q];
-    const int j = args.order[m];
-    const int64_t np = args.n_pad;
-    double* ct = args.contrib + m;  // contrib[q * n_pad + m]
-    if (j < 0) {
-        for (int q = 0; q < kContrib; ++q) ct[q * np] = 0.0;
-        return;
-    }
-    const float4 h = args.hot[m];
-    const float4 q0 = args.cold[2 * m];
-    const float4 q1 = args.cold[2 * m + 1];
-    const double A = static_cast<double>(h.w);
-    const double a[3] = {static_cast<double>(q0.x) + static_cast<double>(q0.y),
-                         static_cast<double>(q0.z) + static_cast<double>(q0.w),
-                         static_cast<double>(q1.x) + static_cast<double>(q1.y)};
-    const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
-    // the table holds the mode as (-A, psi + 1/2) at odd positions, where the
-    // cosine sum v[0] has the opposite sign; A * v[1] and A * v[2..] do not
-    const double dA = mode_flipped(m) ? -v[0] : v[0];
-    args.g.dA[j] = gs * dA;
-    args.g.dpsi[j] = gs * (-kTwoPi * A * v[1]);
-    if (args.g.drho != nullptr) args.g.drho[j] = gs * (args.sigma * dA);
-    ct[0] = (A / args.sigma) * v[0];
-    const int d = args.dim;
-    double da[3] = {0.0, 0.0, 0.0};
-    double e[3] = {0.0, 0.0, 0.0};  // da with the periodic components zeroed
+            for (int q = 0; q < 5; ++q) v[q] += red[w][lane][q];
+        double ct[kContrib];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (c >= d) break;
-        da[c] = -kTwoPi * A * v[2 + c];
-        e[c] = (args.periodic >> c) & 1 ? 0.0 : da[c];
-        args.g.da[static_cast<int64_t>(j) * d + c] = gs * da[c];
-    }
-    // u = kappa / (2 pi l) from the table when it holds kappa, else R^-T a
-    // (the frequencies before the transform, a = R^T u); dL/du = R e
-    const bool from_kappa = *args.has_kap != 0;
+        for (int q = 0; q < kContrib; ++q) ct[q] = 0.0;
+        const int j = args.order[m];
+        if (j >= 0) {
+            const float4 h = args.hot[m];
+            const float4 q0 = args.cold[2 * m];
+            const float4 q1 = args.cold[2 * m + 1];
+            const double A = static_cast<double>(h.w);
+            const double a[3] = {static_cast<double>(q0.x) + static_cast<double>(q0.y),
+                                 static_cast<double>(q0.z) + static_cast<double>(q0.w),
+                                 static_cast<double>(q1.x) + static_cast<double>(q1.y)};
+            const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
+            // the table holds the mode as (-A, psi + 1/2) at odd positions, where the
+            // cosine sum v[0] has the opposite sign; A * v[1] and A * v[2..] do not
+            const double dA = mode_flipped(m) ? -v[0] : v[0];
+            args.g.dA[j] = gs * dA;
+            args.g.dpsi[j] = gs * (-kTwoPi * A * v[1]);
+            if (args.g.drho != nullptr) args.g.drho[j] = gs * (args.sigma * dA);
+            ct[0] = (A * args.inv_sigma) * v[0];
+            const int d = args.dim;
+            double e[3] = {0.0, 0.0, 0.0};  // da with the periodic components zeroed
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double u = 0.0, du = 0.0;
-        if (from_kappa) u = c < d ? args.kap[static_cast<int64_t>(m) * 3 + c] / (kTwoPi * args.ell[c]) : 0.0;
+            for (int c = 0; c < 3; ++c) {
+                if (c >= d) break;
+                const double da = -kTwoPi * A * v[2 + c];
+                e[c] = (args.periodic >> c) & 1 ? 0.0 : da;
+                args.g.da[static_cast<int64_t>(j) * d + c] = gs * da;
+            }
+            // u = kappa / (2 pi l) from the table when it holds kappa, else R^-T a
+            // (the frequencies before the transform, a = R^T u); dL/du = R e
+            const bool from_kappa = *args.has_kap != 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (k >= d) break;
-            if (!from_kappa) u += args.rot_it[c * 3 + k] * a[k];
-            du += args.rot[c * 3 + k] * e[k];
+            for (int c = 0; c < 3; ++c) {
+                if (c >= d) break;
+                double u = 0.0, du = 0.0;
+                if (from_kappa) u = args.kap[static_cast<int64_t>(m) * 3 + c] * args.inv_2pi_ell[c];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if (k >= d) break;
+                    if (!from_kappa) u += args.rot_it[c * 3 + k] * a[k];
+                    du += args.rot[c * 3 + k] * e[k];
+                }
+                if (args.g.dkappa != nullptr) args.g.dkappa[static_cast<int64_t>(j) * d + c] = gs * (du * args.inv_2pi_ell[c]);
+                ct[1 + c] = -(u * args.inv_ell[c]) * du;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) ct[4 + c * 3 + q] = q < d ? u * e[q] : 0.0;
+            }
         }
-        if (c < d && args.g.dkappa != nullptr)
-            args.g.dkappa[static_cast<int64_t>(j) * d + c] = gs * (du / (kTwoPi * args.ell[c]));
-        ct[(1 + c) * np] = c < d ? -(u / args.ell[c]) * du : 0.0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) ct[(4 + c * 3 + q) * np] = (c < d && q < d) ? u * e[q] : 0.0;
+        for (int q = 0; q < kContrib; ++q) cts[q][lane] = ct[q];
+        __syncwarp();
+        // the block's sum of each term over its 32 modes, in mode order
+        if (lane < kContrib) {
+            double t = 0.0;
+            for (int l = 0; l < 32; ++l) t += cts[lane][l];
+            args.contrib[static_cast<int64_t>(lane) * gridDim.x + blockIdx.x] = t;
+        }
     }
 }
 
-// Kernel 3: scalar gradients, one block.  Every thread first sums its
-// strided share of all kContrib rows (and of the per-split sums of g) with
-// all loads in flight, then each row is reduced by warp butterflies and the
-// warp sums added in warp order: a fixed order throughout.
-constexpr int kScalarThreads = 512;
+// Kernel 3: scalar gradients, one block of one warp per row: warp q sums row
+// q (the reduction blocks' partials of term q, or the partial sums of g for
+// dmu) with a lane stride, then adds the lanes by butterflies: a fixed order.
+constexpr int kScalarRows = kContrib + 1;  // + the sum of g (dmu)
 
-__global__ void __launch_bounds__(kScalarThreads) bwd_scalar_kernel(BwdArgs args) {
-    constexpr int kRows = kContrib + 1;  // + the sum of g (dmu)
-    __shared__ double red[kScalarThreads / 32][kRows];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double acc[kRows];
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) acc[q] = 0.0;
-    const int64_t np = args.n_pad;
-    for (int64_t m = threadIdx.x; m < np; m += kScalarThreads)
-#pragma unroll
-        for (int q = 0; q < kContrib; ++q) acc[q] += args.contrib[q * np + m];
-    for (int k = threadIdx.x; k < args.n_gpart; k += kScalarThreads) acc[kContrib] += args.gpart[k];
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-        if (lane == 0) red[warp][q] = acc[q];
-    }
-    __syncthreads();
-    if (threadIdx.x >= kRows) return;
-    const int q = threadIdx.x;
+__global__ void __launch_bounds__(32 * kScalarRows) bwd_scalar_kernel(BwdArgs args, int32_t n_blocks) {
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
     double t = 0.0;
-    for (int w = 0; w < kScalarThreads / 32; ++w) t += red[w][q];
+    if (q < kContrib) {
+        const double* row = args.contrib + static_cast<int64_t>(q) * n_blocks;
+        for (int k = lane; k < n_blocks; k += 32) t += row[k];
+    } else {
+        for (int k = lane; k < args.n_gpart; k += 32) t += args.gpart[k];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane != 0) return;
     const double gs = args.g.gscale != nullptr ? *args.g.gscale : 1.0;
     if (q == 0) {
         args.g.dsigma[0] = gs * t;
@@ -667,6 +671,11 @@ void bwd_common_args(BwdArgs& a, const void* table, int64_t n_modes, int32_t dim
     a.dim = dim;
     a.sigma = sigma;
     for (int c = 0; c < 3; ++c) a.ell[c] = c < dim ? ell[c] : 1.0;
+    a.inv_sigma = 1.0 / sigma;
+    for (int c = 0; c < 3; ++c) {
+        a.inv_ell[c] = 1.0 / a.ell[c];
+        a.inv_2pi_ell[c] = 1.0 / (kTwoPi * a.ell[c]);
+    }
     for (int k = 0; k < 9; ++k) a.rot[k] = rot[k];
     // inverse transpose of the leading dim x dim block (adjugate / determinant;
     // the host checks that the block is invertible)
@@ -706,7 +715,7 @@ int launch_bwd_reduce(const void* table, int64_t n_modes, int32_t dim, double si
     a.n_gpart = n_gpart;
     a.contrib = contrib;
     bwd_reduce_kernel<<<static_cast<unsigned>(a.n_pad / 32), 32 * kRedWarps, 0, st>>>(a);
-    bwd_scalar_kernel<<<1, kScalarThreads, 0, st>>>(a);
+    bwd_scalar_kernel<<<1, 32 * kScalarRows, 0, st>>>(a, a.n_pad / 32);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -761,7 +770,7 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     }
     a.n_gpart = a.splits;
     bwd_reduce_kernel<<<static_cast<unsigned>(n_pad / 32), 32 * kRedWarps, 0, st>>>(a);
-    bwd_scalar_kernel<<<1, kScalarThreads, 0, st>>>(a);
+    bwd_scalar_kernel<<<1, 32 * kScalarRows, 0, st>>>(a, static_cast<int32_t>(n_pad / 32));
     count_launches(2);
     return cudaGetLastError();
 }

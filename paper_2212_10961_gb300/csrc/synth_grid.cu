@@ -321,7 +321,12 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         // ---- MMA issue ------------------------------------------------------------
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16_f32(kGM, kGN);
+            constexpr uint32_t dhi = tc::smem_desc_sw128_hi(kGSbo);
+            constexpr uint32_t tstep = kGOpBytes >> 4;  // one operand tile in descriptor units
+            const uint32_t alo0 = tc::smem_desc_sw128_lo(smem_u32(gsm));
+            const uint32_t blo0 = tc::smem_desc_sw128_lo(smem_u32(gsm + d.off_b));
             uint32_t g = 0, gi = 0, tile_count = 0;
+            uint32_t sa = 0, pa = 0, sb = 0, pb = 0;  // ring stages and their phase parities
             bool ok = true;
             const uint32_t dc = tbase + kGCorrCol;
             for (int64_t tile = blockIdx.x; tile < d.n_tiles && ok; tile += gridDim.x, ++tile_count) {
@@ -339,29 +344,34 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                     tc::fence_after();
                     const uint32_t dt = tbase + b * kGN;
                     for (int cc = 0; cc < d.fc; ++cc, ++g) {
-                        const int sa = static_cast<int>(g % SA);
-                        const int sb = static_cast<int>(g % kGSB);
-                        if (!gwait(afull + sa, (g / SA) & 1u, abort, status) ||
-                            (form && !gwait(bfull + sb, (g / kGSB) & 1u, abort, status))) {
+                        if (!gwait(afull + sa, pa, abort, status) || (form && !gwait(bfull + sb, pb, abort, status))) {
                             ok = false;
                             break;
                         }
                         tc::fence_after();
-                        const uint32_t aa = smem_u32(gsm + sa * d.a_stage);
-                        const uint32_t ba = form ? smem_u32(gsm + d.off_b + sb * kGPair) : aa + kGPair;
+                        const uint32_t alo = alo0 + sa * (static_cast<uint32_t>(d.a_stage) >> 4);
+                        const uint32_t blo = form ? blo0 + sb * (kGPair >> 4) : alo + (kGPair >> 4);
 #pragma unroll
                         for (int ks = 0; ks < kGK / 16; ++ks) {
-                            const uint32_t ko = static_cast<uint32_t>(ks) * kGKStep;  // 16 K elements
-                            const uint64_t ah = tc::smem_desc_sw128(aa + ko, kGSbo);
-                            const uint64_t al = tc::smem_desc_sw128(aa + kGOpBytes + ko, kGSbo);
-                            const uint64_t bh = tc::smem_desc_sw128(ba + ko, kGSbo);
-                            const uint64_t bl = tc::smem_desc_sw128(ba + kGOpBytes + ko, kGSbo);
+                            const uint32_t ko = static_cast<uint32_t>(ks) * (kGKStep >> 4);  // 16 K elements
+                            const uint64_t ah = tc::desc_of(alo + ko, dhi);
+                            const uint64_t al = tc::desc_of(alo + tstep + ko, dhi);
+                            const uint64_t bh = tc::desc_of(blo + ko, dhi);
+                            const uint64_t bl = tc::desc_of(blo + tstep + ko, dhi);
                             tc::mma_f16(dt, ah, bh, idesc, (cc | ks) != 0 ? 1u : 0u);
                             tc::mma_f16(dc, ah, bl, idesc, (iv | cc | ks) != 0 ? 1u : 0u);
                             tc::mma_f16(dc, al, bh, idesc, 1u);
                         }
                         tc::commit(afree + sa);
                         if (form) tc::commit(bfree + sb);
+                        if (++sa == static_cast<uint32_t>(SA)) {
+                            sa = 0;
+                            pa ^= 1u;
+                        }
+                        if (++sb == kGSB) {
+                            sb = 0;
+                            pb ^= 1u;
+                        }
                     }
                     if (ok) tc::commit(accfull + b);
                 }

@@ -66,7 +66,8 @@ constexpr int kAStageB = 2 * gridc::kTileBytes;   // hi, lo (rows: 64 cells, 64 
 constexpr int kAYRow = kAM * 8;                   // one staged y row: 128 modes x (cos, sin)
 constexpr int kAOffB = kAStageA;
 constexpr int kAOffY = kAOffB + kABStages * kAStageB;
-constexpr int kAOffBar = kAOffY + kAYZ * kAYRow;
+constexpr int kAOffYw = kAOffY + kAYZ * kAYRow;   // y weights of the run's rows (patches of 64 x 1 cells)
+constexpr int kAOffBar = kAOffYw + kAYZ * 4;
 constexpr int kABarBytes = 256;
 constexpr int kASmem = kAOffBar + kABarBytes + 1024;  // + room to align the stages to 1024 bytes
 constexpr uint32_t kATmemCols = 512;
@@ -89,7 +90,28 @@ struct AdjDesc {
     const float* Z;             // nullptr without a z axis
     double* part;               // [groups][n_pad][5]
     int32_t ny, nz, n_pad, n_kc, n_yb, n_lt, py_log2, n_mt, groups;
-    int64_t units;              // per mode tile: n_kc n_yb n_lt
+    int32_t units;              // per mode tile: n_kc n_yb n_lt
+};
+
+// Walks a CTA's units u0 .. u1 - 1 in order: z block lt fastest, then y
+// block yb, then x chunk kc (no divisions in the loops).
+struct UnitIter {
+    int32_t lt, yb, kc;
+    __device__ __forceinline__ UnitIter(int32_t u, const AdjDesc& d) {
+        lt = u % d.n_lt;
+        const int32_t combo = u / d.n_lt;
+        yb = combo % d.n_yb;
+        kc = combo / d.n_yb;
+    }
+    __device__ __forceinline__ void next(const AdjDesc& d) {
+        if (++lt == d.n_lt) {
+            lt = 0;
+            if (++yb == d.n_yb) {
+                yb = 0;
+                ++kc;
+            }
+        }
+    }
 };
 
 struct AdjPrep {
@@ -311,8 +333,8 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
     const int lane = threadIdx.x & 31;
     const int mt = static_cast<int>(blockIdx.x % d.n_mt);
     const int grp = static_cast<int>(blockIdx.x / d.n_mt);
-    const int64_t u0 = d.units * grp / d.groups;
-    const int64_t u1 = d.units * (grp + 1) / d.groups;
+    const int32_t u0 = static_cast<int32_t>(static_cast<int64_t>(d.units) * grp / d.groups);
+    const int32_t u1 = static_cast<int32_t>(static_cast<int64_t>(d.units) * (grp + 1) / d.groups);
     const int py = 1 << d.py_log2;
 
     if (threadIdx.x == 0) {
@@ -345,13 +367,16 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
         const int m = mt * kAM + ml;
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
         const float2* ys = reinterpret_cast<const float2*>(gsm + kAOffY) + ml;
+        const float* yws = reinterpret_cast<const float*>(gsm + kAOffYw);
+        const bool run64 = d.py_log2 == 6;
         float ah[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, al[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         bool ok = true;
         uint32_t run = 0;
-        for (int64_t u = u0; u < u1; ++u) {
+        UnitIter it(u0, d);
+        for (int32_t u = u0; u < u1; ++u, it.next(d)) {
             const uint32_t ui = static_cast<uint32_t>(u - u0);
-            const int lt = static_cast<int>(u % d.n_lt);
-            const int yb = static_cast<int>((u / d.n_lt) % d.n_yb);
+            const int lt = it.lt;
+            const int yb = it.yb;
             if (u == u0 || lt == 0) {
                 // a new run: the previous run's y rows are no longer read
                 if (u != u0) {
@@ -371,6 +396,69 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
             }
             tc::fence_after();
             float uc = 0.0f, us = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+            if (run64) {
+                // patches of 64 y-cells x 1 z-cell: the warp's 16 columns are
+                // consecutive y cells of z cell lt
+                const int c0 = kACols * h;
+                const int nv = min(kACols, d.ny - yb * kAYZ - c0);  // valid columns (warp-uniform)
+                const float2 zv = __ldg(d.ztab + static_cast<int64_t>(lt) * d.n_pad + m);
+                const float zwl = __ldg(d.zw + lt);
+                // four groups of 4 columns; the next group's TMEM loads are in
+                // flight while the current group is contracted
+                float qr = 0.0f, qi = 0.0f, qxr = 0.0f, qxi = 0.0f, qyr = 0.0f, qyi = 0.0f;
+                const uint32_t col = tbase + lane_off + b * 256u + static_cast<uint32_t>(c0);
+                uint32_t dv[2][4][4];  // [buffer][cos, cos weighted, sin, sin weighted][column]
+                tc::ld4(col, dv[0][0]);
+                tc::ld4(col + 64, dv[0][1]);
+                tc::ld4(col + 128, dv[0][2]);
+                tc::ld4(col + 192, dv[0][3]);
+                tc::wait_ld();
+                const float2* yr = ys + c0 * kAM;
+                const float* ywr = yws + c0;
+#pragma unroll
+                for (int gq = 0; gq < 4; ++gq) {
+                    const int cur = gq & 1;
+                    if (gq < 3) {
+                        const uint32_t cn = col + 4u * static_cast<uint32_t>(gq + 1);
+                        tc::ld4(cn, dv[cur ^ 1][0]);
+                        tc::ld4(cn + 64, dv[cur ^ 1][1]);
+                        tc::ld4(cn + 128, dv[cur ^ 1][2]);
+                        tc::ld4(cn + 192, dv[cur ^ 1][3]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int cc = 4 * gq + c;
+                        if (nv == kACols || cc < nv) {
+                            const float2 y = yr[cc * kAM];
+                            const float w = ywr[cc];
+                            const float cv = __uint_as_float(dv[cur][0][c]), sv = __uint_as_float(dv[cur][2][c]);
+                            const float xcv = __uint_as_float(dv[cur][1][c]), xsv = __uint_as_float(dv[cur][3][c]);
+                            const float pr = fmaf(cv, y.x, -sv * y.y), pi = fmaf(cv, y.y, sv * y.x);
+                            qr += pr;
+                            qi += pi;
+                            qyr = fmaf(w, pr, qyr);
+                            qyi = fmaf(w, pi, qyi);
+                            qxr = fmaf(xcv, y.x, qxr);
+                            qxr = fmaf(-xsv, y.y, qxr);
+                            qxi = fmaf(xcv, y.y, qxi);
+                            qxi = fmaf(xsv, y.x, qxi);
+                        }
+                    }
+                    if (gq < 3) tc::wait_ld();
+                    if (gq == 2) {
+                        // every column of the unit is in registers: release the accumulators
+                        tc::fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(accfree + b);
+                    }
+                }
+                const float ei = fmaf(qr, zv.y, qi * zv.x);
+                uc = fmaf(qr, zv.x, -qi * zv.y);
+                us = ei;
+                ux = fmaf(qxr, zv.y, qxi * zv.x);
+                uy = fmaf(qyr, zv.y, qyi * zv.x);
+                uz = zwl * ei;
+            } else {
             float qr = 0.0f, qi = 0.0f, qxr = 0.0f, qxi = 0.0f, qyr = 0.0f, qyi = 0.0f;
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
@@ -420,6 +508,7 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                     }
                 }
             }
+            }
             two_sum_acc(ah[0], al[0], uc);
             two_sum_acc(ah[1], al[1], us);
             two_sum_acc(ah[2], al[2], ux);
@@ -452,29 +541,33 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
         // ---- MMA issue ------------------------------------------------------------
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16_f32(kAM, 2 * kAYZ);
-            const uint32_t aa = smem_u32(gsm);
+            constexpr uint32_t dhi = tc::smem_desc_sw128_hi(gridc::kSbo);
+            constexpr uint32_t tstep = gridc::kTileBytes >> 4;  // one operand tile in descriptor units
+            const uint32_t alo = tc::smem_desc_sw128_lo(smem_u32(gsm));
+            const uint32_t blo0 = tc::smem_desc_sw128_lo(smem_u32(gsm + kAOffB));
             bool ok = true;
             uint32_t run = 0;
-            for (int64_t u = u0; u < u1 && ok; ++u) {
+            UnitIter it(u0, d);
+            for (int32_t u = u0; u < u1 && ok; ++u, it.next(d)) {
                 const uint32_t ui = static_cast<uint32_t>(u - u0);
-                const int lt = static_cast<int>(u % d.n_lt);
+                const int lt = it.lt;
                 if ((u == u0 || lt == 0) && !gwait(afull, (run++) & 1u, abort, status)) break;
                 const uint32_t b = ui & 1u;
                 const uint32_t s = ui % kABStages;
                 if (ui >= 2 && !gwait(accfree + b, ((ui >> 1) - 1u) & 1u, abort, status)) break;
                 if (!gwait(bfull + s, (ui / kABStages) & 1u, abort, status)) break;
                 tc::fence_after();
-                const uint32_t ba = smem_u32(gsm + kAOffB + s * kAStageB);
+                const uint32_t blo = blo0 + s * (kAStageB >> 4);
                 const uint32_t dcos = tbase + b * 256u, dsin = dcos + 128u;
 #pragma unroll
                 for (int ks = 0; ks < kAX / 16; ++ks) {
-                    const uint32_t ko = static_cast<uint32_t>(ks) * gridc::kKStep;  // 16 K elements
-                    const uint64_t ch = tc::smem_desc_sw128(aa + ko, gridc::kSbo);
-                    const uint64_t cl = tc::smem_desc_sw128(aa + gridc::kTileBytes + ko, gridc::kSbo);
-                    const uint64_t sh = tc::smem_desc_sw128(aa + 2 * gridc::kTileBytes + ko, gridc::kSbo);
-                    const uint64_t sl = tc::smem_desc_sw128(aa + 3 * gridc::kTileBytes + ko, gridc::kSbo);
-                    const uint64_t bh = tc::smem_desc_sw128(ba + ko, gridc::kSbo);
-                    const uint64_t bl = tc::smem_desc_sw128(ba + gridc::kTileBytes + ko, gridc::kSbo);
+                    const uint32_t ko = static_cast<uint32_t>(ks) * (gridc::kKStep >> 4);  // 16 K elements
+                    const uint64_t ch = tc::desc_of(alo + ko, dhi);
+                    const uint64_t cl = tc::desc_of(alo + tstep + ko, dhi);
+                    const uint64_t sh = tc::desc_of(alo + 2 * tstep + ko, dhi);
+                    const uint64_t sl = tc::desc_of(alo + 3 * tstep + ko, dhi);
+                    const uint64_t bh = tc::desc_of(blo + ko, dhi);
+                    const uint64_t bl = tc::desc_of(blo + tstep + ko, dhi);
                     tc::mma_f16(dcos, ch, bh, idesc, ks != 0 ? 1u : 0u);
                     tc::mma_f16(dcos, ch, bl, idesc, 1u);
                     tc::mma_f16(dcos, cl, bh, idesc, 1u);
@@ -484,7 +577,7 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                 }
                 tc::commit(bfree + s);
                 tc::commit(accfull + b);
-                if (u + 1 == u1 || (u + 1) % d.n_lt == 0) tc::commit(afree);  // last unit of the run
+                if (u + 1 == u1 || lt + 1 == d.n_lt) tc::commit(afree);  // last unit of the run
                 atomicAdd(&g_grid_adj_units, 1ull);
             }
             // every MMA this CTA issued has completed before TMEM is released
@@ -496,18 +589,21 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
         // ---- bulk copies: per run the A tiles and y rows, per unit the B tiles ---------
         if (lane == 0) {
             uint32_t run = 0, issued_b = 0;
-            for (int64_t u = u0; u < u1; ++u) {
+            UnitIter it(u0, d);
+            for (int32_t u = u0; u < u1; ++u, it.next(d)) {
                 const uint32_t ui = static_cast<uint32_t>(u - u0);
-                const int lt = static_cast<int>(u % d.n_lt);
-                if (u == u0 || lt == 0) {
+                if (u == u0 || it.lt == 0) {
                     if (run > 0 && (!gwait(afree, (run - 1u) & 1u, abort, status) ||
                                     !gwait(yfree, (run - 1u) & 1u, abort, status)))
                         break;
-                    const int64_t combo = u / d.n_lt;
-                    const int yb = static_cast<int>(combo % d.n_yb);
-                    const int kc = static_cast<int>(combo / d.n_yb);
+                    const int yb = it.yb;
+                    const int kc = it.kc;
                     const int pkv = min(py, d.ny - yb * py);
-                    mbar_arrive_expect_tx(afull, kAStageA + pkv * kAYRow);
+                    // y weights of the rows (64 x 1 patches): whole 16-byte
+                    // groups; the section is padded to 256 bytes
+                    const uint32_t ywb = py == kAYZ ? static_cast<uint32_t>((pkv + 3) / 4 * 16) : 0u;
+                    mbar_arrive_expect_tx(afull, kAStageA + pkv * kAYRow + ywb);
+                    if (ywb) bulk_g2s(gsm + kAOffYw, d.yw + yb * py, ywb, afull);
                     const unsigned char* asrc = d.atab + (static_cast<int64_t>(mt) * d.n_kc + kc) * kAStageA;
                     for (int t = 0; t < 4; ++t)
                         bulk_g2s(gsm + t * gridc::kTileBytes, asrc + t * gridc::kTileBytes, gridc::kTileBytes, afull);
@@ -519,7 +615,8 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                 const uint32_t s = ui % kABStages;
                 if (ui >= kABStages && !gwait(bfree + s, ((ui / kABStages) - 1u) & 1u, abort, status)) break;
                 mbar_arrive_expect_tx(bfull + s, kAStageB);
-                bulk_g2s(gsm + kAOffB + s * kAStageB, d.btab + u * kAStageB, kAStageB, bfull + s);
+                bulk_g2s(gsm + kAOffB + s * kAStageB, d.btab + static_cast<int64_t>(u) * kAStageB, kAStageB,
+                         bfull + s);
                 ++issued_b;
             }
             // copies still in flight land before the CTA's shared memory goes away
@@ -617,6 +714,7 @@ int launch_synth_bwd_grid(const void* table, int64_t n_modes, int32_t dim, const
     const TableLayout TL = table_layout(n_modes);
     const unsigned char* tb = static_cast<const unsigned char*>(table);
     const AdjPlan ap = adj_plan(gg.nx, gg.ny, gg.nz, TL.n_pad, g_adj_sms);
+    if (ap.units > INT32_MAX) return cudaErrorInvalidValue;
     unsigned char* w = static_cast<unsigned char*>(ws);
     const int64_t n = int64_t(gg.nx) * gg.ny * gg.nz;
     const float* Z = dim > 2 ? gg.Z : nullptr;
@@ -678,7 +776,7 @@ int launch_synth_bwd_grid(const void* table, int64_t n_modes, int32_t dim, const
     d.py_log2 = ap.py_log2;
     d.n_mt = ap.n_mt;
     d.groups = ap.groups;
-    d.units = ap.units;
+    d.units = static_cast<int32_t>(ap.units);
     grid_adj_kernel<<<static_cast<unsigned>(ap.groups * ap.n_mt), kAThreads, kASmem, st>>>(d, status);
     count_launches(1);
     return launch_bwd_reduce(table, n_modes, dim, sigma, ell, rot, periodic_mask, g, d.part, ap.groups,

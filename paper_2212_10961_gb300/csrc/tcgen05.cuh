@@ -26,6 +26,21 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo
     return d;
 }
 
+// The same descriptor as two 32-bit words: lo (start address field and the
+// unused leading-dimension offset) and hi (stride offset, version, swizzle).
+// A start address advanced by k bytes (k a multiple of 16, the result below
+// 256 KB) is lo + k / 16: the field cannot carry into the next one, so the
+// issuing thread adds K steps and tile offsets with one 32-bit add.
+__device__ __forceinline__ uint32_t smem_desc_sw128_lo(uint32_t saddr) {
+    return ((saddr & 0x3FFFFu) >> 4) | (1u << 16);
+}
+__host__ __device__ constexpr uint32_t smem_desc_sw128_hi(uint32_t sbo) {
+    return ((sbo >> 4) & 0x3FFFu) | (1u << 14) | (2u << 29);
+}
+__device__ __forceinline__ uint64_t desc_of(uint32_t lo, uint32_t hi) {
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
 // Instruction descriptor of kind::f16: FP16 A and B, FP32 accumulator, both
 // operands K-major, no negation, dense; shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
@@ -88,6 +103,14 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : GRF_R8(0), GRF_R8(8), GRF_R8(16), GRF_R8(24)
         : "r"(taddr)
         : "memory");
+}
+
+// As ld32 with 4 columns.
+__device__ __forceinline__ void ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 // As ld32 with 8 columns.
