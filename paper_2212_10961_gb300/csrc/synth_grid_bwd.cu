@@ -414,10 +414,12 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                 tc::ld4(col + 192, dv[0][3]);
                 tc::wait_ld();
                 const float2* yr = ys + c0 * kAM;
-                const float* ywr = yws + c0;
+                const float4* ywr = reinterpret_cast<const float4*>(yws + c0);  // 4 columns per broadcast load
 #pragma unroll
                 for (int gq = 0; gq < 4; ++gq) {
                     const int cur = gq & 1;
+                    const float4 w4 = ywr[gq];
+                    const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
                     if (gq < 3) {
                         const uint32_t cn = col + 4u * static_cast<uint32_t>(gq + 1);
                         tc::ld4(cn, dv[cur ^ 1][0]);
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                         const int cc = 4 * gq + c;
                         if (nv == kACols || cc < nv) {
                             const float2 y = yr[cc * kAM];
-                            const float w = ywr[cc];
+                            const float w = wq[c];
                             const float cv = __uint_as_float(dv[cur][0][c]), sv = __uint_as_float(dv[cur][2][c]);
                             const float xcv = __uint_as_float(dv[cur][1][c]), xsv = __uint_as_float(dv[cur][3][c]);
                             const float pr = fmaf(cv, y.x, -sv * y.y), pi = fmaf(cv, y.y, sv * y.x);
@@ -551,11 +553,17 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
             for (int32_t u = u0; u < u1 && ok; ++u, it.next(d)) {
                 const uint32_t ui = static_cast<uint32_t>(u - u0);
                 const int lt = it.lt;
-                if ((u == u0 || lt == 0) && !gwait(afull, (run++) & 1u, abort, status)) break;
+                if ((u == u0 || lt == 0) && !gwait(afull, (run++) & 1u, abort, status)) {
+                    ok = false;
+                    break;
+                }
                 const uint32_t b = ui & 1u;
                 const uint32_t s = ui % kABStages;
-                if (ui >= 2 && !gwait(accfree + b, ((ui >> 1) - 1u) & 1u, abort, status)) break;
-                if (!gwait(bfull + s, (ui / kABStages) & 1u, abort, status)) break;
+                if ((ui >= 2 && !gwait(accfree + b, ((ui >> 1) - 1u) & 1u, abort, status)) ||
+                    !gwait(bfull + s, (ui / kABStages) & 1u, abort, status)) {
+                    ok = false;
+                    break;
+                }
                 tc::fence_after();
                 const uint32_t blo = blo0 + s * (kAStageB >> 4);
                 const uint32_t dcos = tbase + b * 256u, dsin = dcos + 128u;
@@ -578,8 +586,8 @@ __global__ void __launch_bounds__(kAThreads, 1) grid_adj_kernel(AdjDesc d, int32
                 tc::commit(bfree + s);
                 tc::commit(accfull + b);
                 if (u + 1 == u1 || lt + 1 == d.n_lt) tc::commit(afree);  // last unit of the run
-                atomicAdd(&g_grid_adj_units, 1ull);
             }
+            if (ok) atomicAdd(&g_grid_adj_units, static_cast<unsigned long long>(u1 - u0));
             // every MMA this CTA issued has completed before TMEM is released
             tc::commit(done);
             mbar_wait_bounded(done, 0);
