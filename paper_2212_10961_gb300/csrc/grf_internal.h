@@ -258,7 +258,9 @@ struct GridDesc {
     int32_t a_stage;  // bytes per copy stage
     int32_t off_b;    // formed B ring (form)
     int32_t off_bar;  // barriers
-    int32_t pad_;
+    int32_t n_split;  // mode splits per tile (whole fold intervals each); > 1: partial fields in part
+    int64_t n_items;  // tiles x splits
+    float* part;      // [n_split][nx ny nz] partial fields (n_split > 1), summed by the finalize kernel
     MapDev map;
 };
 

@@ -135,6 +135,7 @@ __device__ __forceinline__ TileIdx tile_idx(const GridDesc& d, int64_t tile) {
     return t;
 }
 
+template <bool kSplit>
 __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int32_t* status) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     // stages on a 1024-byte boundary of the shared window (swizzle atoms)
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
     tc::fence_after();
     const uint32_t tbase = *tslot;
     const int NI = d.nc / d.fc;  // fold intervals per tile
+    const int n_split = kSplit ? d.n_split : 1;
     const int pkm = (1 << d.pk_log2) - 1;
 
     if (warp < kGEpiWarps) {
@@ -191,8 +193,13 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         const int hm = t >> 7;            // group of the chunk's modes it forms (kGFormQuads x 4 modes)
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
         const float S = grid_scale(d.thdr);
-        uint32_t g = 0, gi = 0, tile_count = 0;
-        for (int64_t tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x, ++tile_count) {
+        uint32_t g = 0, gi = 0;
+        for (int64_t item = blockIdx.x; item < (kSplit ? d.n_items : d.n_tiles); item += gridDim.x) {
+            const int64_t tile = kSplit ? item / n_split : item;
+            const int split = kSplit ? static_cast<int>(item - tile * n_split) : 0;
+            // the item's fold intervals iv0 .. iv1 - 1 (all of the tile's without a split)
+            const int iv0 = kSplit ? NI * split / n_split : 0;
+            const int NIl = kSplit ? NI * (split + 1) / n_split - iv0 : NI;
             const TileIdx ti = tile_idx(d, tile);
             // staged table rows this thread reads: y row and (amplitude, psi, z) row
             const int ry = min(n_col & pkm, ti.pkv - 1);
@@ -257,9 +264,13 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                             if (i < d.nx && k < d.ny && l < d.nz) {
                                 const int64_t o = i + static_cast<int64_t>(d.nx) *
                                                           (k + static_cast<int64_t>(d.ny) * l);
-                                const float y = v * S + d.map.mu;
-                                map_store(d.map, o, y);
-                                if (mm) lsum += mismatch_store(d.map, o, y);
+                                if (kSplit) {
+                                    d.part[static_cast<int64_t>(split) * d.nx * d.ny * d.nz + o] = v * S;
+                                } else {
+                                    const float y = v * S + d.map.mu;
+                                    map_store(d.map, o, y);
+                                    if (mm) lsum += mismatch_store(d.map, o, y);
+                                }
                             }
                         }
                     }
@@ -269,7 +280,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
 
             bool ok = true;
             if (form) {
-                for (int c = 0; c < d.nc; ++c, ++g) {
+                const int c_end = kSplit ? (iv0 + NIl) * d.fc : d.nc;
+                for (int c = kSplit ? iv0 * d.fc : 0; c < c_end; ++c, ++g) {
                     const int sb = static_cast<int>(g % kGSB);
                     const int sa = static_cast<int>(g % SA);
                     if (g >= kGSB &&
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bfull + sb);
                     if ((c + 1) % d.fc == 0) {
-                        const int iv = (c + 1) / d.fc - 1;  // interval whose chunks are all formed
+                        const int iv = (c + 1) / d.fc - 1 - (kSplit ? iv0 : 0);  // the item's interval whose chunks are all formed
                         if (iv >= 1) {
                             if (!fold(gi, iv == 1, false)) {
                                 ok = false;
@@ -298,18 +310,18 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                         }
                     }
                 }
-                if (!ok || !fold(gi, NI == 1, true)) break;
+                if (!ok || !fold(gi, NIl == 1, true)) break;
                 ++gi;
             } else {
-                for (int iv = 0; iv < NI; ++iv, ++gi) {
-                    if (!fold(gi, iv == 0, iv == NI - 1)) {
+                for (int iv = 0; iv < NIl; ++iv, ++gi) {
+                    if (!fold(gi, iv == 0, iv == NIl - 1)) {
                         ok = false;
                         break;
                     }
                 }
                 if (!ok) break;
             }
-            if (mm) {
+            if (mm && !kSplit) {
                 // fixed butterfly order, one partial per (tile, warp): the loss
                 // does not depend on which CTA took the tile
 #pragma unroll
@@ -329,13 +341,15 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
             uint32_t sa = 0, pa = 0, sb = 0, pb = 0;  // ring stages and their phase parities
             bool ok = true;
             const uint32_t dc = tbase + kGCorrCol;
-            for (int64_t tile = blockIdx.x; tile < d.n_tiles && ok; tile += gridDim.x, ++tile_count) {
-                // the previous tile's correction accumulator has been read
+            for (int64_t item = blockIdx.x; item < (kSplit ? d.n_items : d.n_tiles) && ok; item += gridDim.x, ++tile_count) {
+                const int split = kSplit ? static_cast<int>(item % n_split) : 0;
+                const int NIl = kSplit ? NI * (split + 1) / n_split - NI * split / n_split : NI;
+                // the previous item's correction accumulator has been read
                 if (tile_count >= 1 && !gwait(corrfree, (tile_count - 1u) & 1u, abort, status)) {
                     ok = false;
                     break;
                 }
-                for (int iv = 0; iv < NI && ok; ++iv, ++gi) {
+                for (int iv = 0; iv < NIl && ok; ++iv, ++gi) {
                     const uint32_t b = gi & 1u;
                     if (gi >= 2 && !gwait(accfree + b, ((gi >> 1) - 1u) & 1u, abort, status)) {
                         ok = false;
@@ -387,10 +401,13 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         if (lane == 0) {
             uint32_t g = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < d.n_tiles && ok; tile += gridDim.x) {
+            for (int64_t item = blockIdx.x; item < (kSplit ? d.n_items : d.n_tiles) && ok; item += gridDim.x) {
+                const int64_t tile = kSplit ? item / n_split : item;
+                const int split = kSplit ? static_cast<int>(item - tile * n_split) : 0;
                 const TileIdx ti = tile_idx(d, tile);
                 const unsigned char* asrc = d.atab + static_cast<int64_t>(ti.mt) * d.nc * kGPair;
-                for (int c = 0; c < d.nc; ++c, ++g) {
+                const int c_end = kSplit ? NI * (split + 1) / n_split * d.fc : d.nc;
+                for (int c = kSplit ? NI * split / n_split * d.fc : 0; c < c_end; ++c, ++g) {
                     const int sa = static_cast<int>(g % SA);
                     if (g >= static_cast<uint32_t>(SA) &&
                         !gwait(afree + sa, ((g / SA) - 1u) & 1u, abort, status)) {
@@ -522,6 +539,35 @@ __global__ void grid_prep_kernel(GridPrep p) {
     }
 }
 
+// Mode-split grids: per cell the partial fields of the splits, added in split
+// order (a fixed order), plus mu, then the maps; with the mismatch bit every
+// block also writes its sum of (K - T)^2 to lpart.
+__global__ void __launch_bounds__(256) grid_split_finalize(const float* __restrict__ part, int n_split, int64_t n,
+                                                           MapDev map) {
+    const int64_t o = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool mm = (map.bits & kMapMismatch) != 0;
+    double l = 0.0;
+    if (o < n) {
+        float s = 0.0f, e = 0.0f;
+        for (int k = 0; k < n_split; ++k) two_sum_acc(s, e, part[static_cast<int64_t>(k) * n + o]);
+        const float y = (s + e) + map.mu;
+        map_store(map, o, y);
+        if (mm) l = mismatch_store(map, o, y);
+    }
+    if (mm) {
+        __shared__ double red[8];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[w];
+            map.lpart[blockIdx.x] = t;
+        }
+    }
+}
+
 // D[128][128] = sum_K A[128][K] B[128][K] (FP16 inputs, K-contiguous rows,
 // K = 64 k_chunks, FP32 result row-major) through the same layout,
 // descriptors and TMEM path as the grid kernel.  One CTA of 128 threads.
@@ -596,8 +642,14 @@ int g_num_sms = 0;
 struct GridPlan {
     bool form;
     int pk_log2, n_mt, n_kt, n_lt, nc, sa, a_stage, off_b, off_bar, smem;
-    int64_t n_tiles, a_bytes, y_bytes, w_bytes, b_bytes;
+    int max_split;  // mode splits for grids of few tiles (the launch takes at most one per fold interval)
+    int64_t n_tiles, a_bytes, y_bytes, w_bytes, b_bytes, part_bytes;
 };
+
+// Grids of at most 64 tiles split each tile's modes over up to 8 CTAs, so
+// that about 128 work items fill the GPU.
+constexpr int kGMaxSplit = 8;
+constexpr int64_t kGSplitItems = 128;
 
 GridPlan grid_plan(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
     GridPlan g{};
@@ -634,6 +686,8 @@ GridPlan grid_plan(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
     const int PL = kGN >> g.pk_log2;
     g.n_lt = (nz + PL - 1) / PL;
     g.n_tiles = int64_t(g.n_mt) * g.n_kt * g.n_lt;
+    g.max_split = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kGMaxSplit, kGSplitItems / g.n_tiles)));
+    g.part_bytes = g.max_split > 1 ? align256(int64_t(g.max_split) * nx * ny * nz * 4) : 0;
     g.a_bytes = align256(int64_t(g.n_mt) * g.nc * kGPair);
     if (g.form) {
         g.y_bytes = align256(int64_t(g.nc) * ny * kGRowBytes);
@@ -648,7 +702,7 @@ GridPlan grid_plan(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
 
 size_t grid_ws_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_pad) {
     const GridPlan g = grid_plan(nx, ny, nz, n_pad);
-    return static_cast<size_t>(g.a_bytes + g.y_bytes + g.w_bytes + g.b_bytes);
+    return static_cast<size_t>(g.a_bytes + g.y_bytes + g.w_bytes + g.b_bytes + g.part_bytes);
 }
 
 int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const GridGeom& gg, const MapDev& map,
@@ -661,7 +715,9 @@ int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const Gri
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(grid_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemMax);
+            e = cudaFuncSetAttribute(grid_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(grid_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemMax);
         if (e != cudaSuccess) return e;
         g_num_sms = sms;
     }
@@ -715,24 +771,40 @@ int launch_synth_grid(const void* table, int64_t n_modes, int32_t dim, const Gri
     d.n_lt = gp.n_lt;
     d.pk_log2 = gp.pk_log2;
     d.n_tiles = gp.n_tiles;
+    d.n_split = std::min(gp.max_split, gp.nc / d.fc);  // whole fold intervals per split
+    d.n_items = d.n_tiles * d.n_split;
+    d.part = d.n_split > 1 ? reinterpret_cast<float*>(w + gp.a_bytes + gp.y_bytes + gp.w_bytes + gp.b_bytes)
+                           : nullptr;
     d.form = p.form;
     d.sa = gp.sa;
     d.a_stage = gp.a_stage;
     d.off_b = gp.off_b;
     d.off_bar = gp.off_bar;
     d.map = map;
-    const int64_t grid = std::min<int64_t>(d.n_tiles, g_num_sms);
-    grid_mma_kernel<<<static_cast<unsigned>(grid), kGThreads, gp.smem, st>>>(d, status);
+    const int64_t grid = std::min<int64_t>(d.n_items, g_num_sms);
+    if (d.n_split > 1)
+        grid_mma_kernel<true><<<static_cast<unsigned>(grid), kGThreads, gp.smem, st>>>(d, status);
+    else
+        grid_mma_kernel<false><<<static_cast<unsigned>(grid), kGThreads, gp.smem, st>>>(d, status);
     count_launches(1);
+    const int64_t n = int64_t(gg.nx) * gg.ny * gg.nz;
+    const int64_t fin_blocks = (n + 255) / 256;
+    if (d.n_split > 1) {
+        grid_split_finalize<<<static_cast<unsigned>(fin_blocks), 256, 0, st>>>(d.part, d.n_split, n, map);
+        count_launches(1);
+    }
     if (map.bits & kMapMismatch) {
-        const int e = launch_loss_sum(map.lpart, d.n_tiles * kGEpiWarps, map.inv_n_mean, map.loss, st);
+        const int e = launch_loss_sum(map.lpart, d.n_split > 1 ? fin_blocks : d.n_tiles * kGEpiWarps, map.inv_n_mean,
+                                      map.loss, st);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
 int64_t grid_loss_partials(int32_t nx, int32_t ny, int32_t nz) {
-    return grid_plan(nx, ny, nz, kGModes * 4).n_tiles * kGEpiWarps;
+    // at most: one per (tile, warp) without a split, one per finalize block with one
+    const GridPlan g = grid_plan(nx, ny, nz, kGModes * 4);
+    return std::max<int64_t>(g.n_tiles * kGEpiWarps, (int64_t(nx) * ny * nz + 255) / 256);
 }
 
 int64_t grid_tiles(int32_t nx, int32_t ny, int32_t nz) { return grid_plan(nx, ny, nz, kGModes * 4).n_tiles; }

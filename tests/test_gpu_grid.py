@@ -221,3 +221,43 @@ def test_grid3d_256_full_size_grid_path_sampled(env):
     check_forward(out["Y"].cpu().numpy()[idx], y_or, s, "grid3d_256 grid path")
     check_lognormal(out["K"].cpu().numpy()[idx], y_or, s)
     check_facies(out["facies"].cpu().numpy()[idx], y_or, thr, s)
+
+
+@pytest.mark.parametrize("shape", [(150, 90), (100, 40, 24)])
+def test_mode_split_fields_and_fused_mismatch(env, shape):
+    # grids of few tiles split each tile's modes over several CTAs (partial
+    # fields summed in split order by a finalize kernel, which also applies the
+    # maps and the loss): the same field as the unsplit CUDA-core path within
+    # the tolerance, the fused loss and gradient equal to synthesis followed by
+    # the standalone loss, and both against the oracle
+    torch, F, W = env
+    from oracle import field as of
+    dim = len(shape)
+    cells = W.grid_centres(shape)
+    ell = (0.15, 0.1, 0.2)[:dim]
+    p = F.FieldParams(family="exponential", sigma2=1.2, mean=0.05, ell=ell, dim=dim, n_modes=900, seed=31)
+    pt = F.FieldParams(family="exponential", sigma2=1.2, mean=0.05, ell=ell, dim=dim, n_modes=900, seed=32)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    gf = F.GaussianField(p)
+    F.grid_path(False)
+    T = F.GaussianField(pt).synth(plan, F.MapSpec(y=False, lognormal=True))["K"]
+    core = gf.synth(plan, F.MapSpec(y=True))["Y"]
+    F.grid_path("always")
+    try:
+        F.take_grid_tiles()
+        ref = gf.synth(plan, F.MapSpec(y=True, lognormal=True))
+        loss_u, gY_u = F.mismatch_grad(ref["K"], T)
+        loss, gY, out = F.synth_mismatch(gf.table, p, plan, T, want_Y=True, want_K=True)
+        torch.cuda.synchronize()
+        assert F.take_grid_tiles() > 0
+    finally:
+        F.grid_path(True)
+    assert torch.equal(out["Y"], ref["Y"]) and torch.equal(out["K"], ref["K"])
+    assert torch.equal(gY, gY_u)
+    assert loss.item() == pytest.approx(loss_u.item(), rel=1e-12)
+    assert np.max(np.abs(out["Y"].cpu().numpy().astype(np.float64) - core.cpu().numpy())) <= 2e-5 * math.sqrt(1.2)
+    y_or = oracle_field(oracle_modes("exponential", 1.2, ell, dim, 900, 31), 0.05, cells)
+    check_forward(out["Y"].cpu().numpy(), y_or, math.sqrt(1.2), "split %s" % (shape,))
+    l_or, g_or = of.mismatch_loss(np.exp(y_or), T.cpu().numpy().astype(np.float64))
+    assert loss.item() == pytest.approx(l_or, rel=1e-4)
+    assert np.max(np.abs(gY.cpu().numpy() - g_or)) <= 1e-4 * np.max(np.abs(g_or))
