@@ -92,8 +92,8 @@ def parse():
     ap.add_argument("--batched-tile", default="auto", choices=["auto", "128", "256", "512"],
                     help="cells per warp work item of the ensemble (default: autotuned)")
     ap.add_argument("--grid-path", default="auto", choices=["auto", "off", "always"],
-                    help="tensor-core grid path for cells on a Cartesian grid (default: from 8 tiles of "
-                         "128 x 128 cells up; off: the CUDA-core kernels)")
+                    help="tensor-core grid path for cells on a Cartesian grid (default: every grid plan; "
+                         "off: the CUDA-core kernels)")
     ap.add_argument("--jsonl", default=None,
                     help="also append the result line to this JSON-lines run log (with a UTC timestamp)")
     return ap.parse_args()
@@ -286,7 +286,11 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     # a new realisation every step: drawn and packed ahead by the native
     # prefetcher's worker threads; its upload runs on a copy stream into one
     # of two device tables while the previous synthesis runs
-    pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=4)
+    # (all host cores but two draw, one realisation per worker, and the ring
+    # holds a slot for every worker beside those whose uploads are in flight:
+    # a small field's step is otherwise bound by the host's drawing rate)
+    workers = max(1, (os.cpu_count() or 4) - 2)
+    pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=min(64, workers + 4), threads=workers)
     ps = F.PreparedSynth(params_for(F, w, dim, base_seed), plan, 0, maps)
     out = ps.out
     tabs = [F.ModeTable.device_only(N, dim) for _ in range(2)]

@@ -334,8 +334,8 @@ size_t grf_synth_workspace_bytes(int64_t n_cells);
  * holds the cells of a Cartesian grid handed over x-fastest -- cell
  * n = i + nx (k + ny l) at (X_i, Y_k, Z_l) for axes X, Y, Z of any spacing,
  * with ny >= 2 -- grf_plan_cells records the grid (a check that runs with the
- * planning kernels).  grf_synth_field on such a plan (at least 8 tiles of
- * 128 x 128 cells, see grf_debug_grid_path), with a field of the plan's
+ * planning kernels).  grf_synth_field on such a plan (with the grid path
+ * on, see grf_debug_grid_path), with a field of the plan's
  * dimension and a workspace of at least
  * grf_synth_grid_workspace_bytes() bytes, then evaluates Eq. (DiscreteFT) as
  * a matrix product on the tensor cores: every term factorises into an x
@@ -658,9 +658,10 @@ int grf_take_grid_adjoint_units(int64_t *units);
 
 /*
  * grf_debug_grid_path -- process-wide setting of the grid path (enable = 0:
- * grid plans take the CUDA-core paths, for comparisons; 1, the default: the
- * grid path for grids of at least 8 tiles of 128 x 128 cells, where it is the
- * faster one; 2: every grid) and the number of
+ * grid plans take the CUDA-core paths, for comparisons; 1, the default, and
+ * 2: every grid plan takes the grid path, forward and adjoint; grids of at
+ * most 64 tiles of 128 x 128 cells split each tile's modes over several
+ * CTAs) and the number of
  * 32-mode chunks the tensor-core accumulator sums before each fold into the
  * running sum (fold_chunks = 1, 2, 4 or 8, lowered to a divisor of the
  * table's chunk count; default 4).  GRF_EINVAL otherwise.

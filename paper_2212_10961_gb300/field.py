@@ -286,7 +286,9 @@ class ModePrefetcher:
     pinned staging buffers (grf_prefetch_*); next() only enqueues the upload
     of the next one into a device table.  For Monte-Carlo loops over many
     realisations of small fields, where drawing on the launching thread would
-    leave the GPU idle."""
+    leave the GPU idle.  Each realisation is drawn by one worker thread, so
+    `depth` should exceed the worker count plus the slots whose uploads are in
+    flight (two for a two-table ring) for the workers to run in parallel."""
 
     def __init__(self, params: FieldParams, depth=4, threads=None):
         self.params = params

@@ -274,7 +274,8 @@ def test_rotated_anisotropy_forward_and_adjoint(env, kind):
                                                   ((64, 32, 16), "exponential", False),
                                                   ((32, 32, 32), "matern", True),
                                                   ((64, 48, 16), "gaussian", False),
-                                                  ((40, 32, 24), "exponential", True)])
+                                                  ((40, 32, 24), "exponential", True),
+                                                  ((128, 128, 128), "gaussian", False)])
 def test_lattice_adjoint_against_oracle(env, shape, family, rotated):
     # tiles of 256 cells that are four 4 x 4 x 4 bricks of one grid spacing
     # (Cartesian grids handed over x-fastest) take the adjoint's lattice path
@@ -293,8 +294,17 @@ def test_lattice_adjoint_against_oracle(env, shape, family, rotated):
     gf = F.GaussianField(p)
     plan = F.CellPlan(*to_dev(torch, cells))
     g = np.random.default_rng(7).standard_normal(len(cells[0])).astype(np.float32)
-    gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
-    torch.cuda.synchronize()
+    F.grid_path(False)  # the CUDA-core adjoint's lattice tiles (the grid adjoint has its own tests)
+    try:
+        F.take_adjoint_path_counts()
+        gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
+        torch.cuda.synchronize()
+        gen, lat = F.take_adjoint_path_counts()
+        assert gen + lat > 0  # the CUDA-core adjoint ran
+        if shape == (128, 128, 128):
+            assert lat > 0
+    finally:
+        F.grid_path(True)
     assert plan.status() == 0
     from oracle import field as of
     from oracle import modes as omod
@@ -305,4 +315,5 @@ def test_lattice_adjoint_against_oracle(env, shape, family, rotated):
                            math.sqrt(1.3), ell, g.astype(np.float64), rot=R)
     errs = {k: _check(gr[k].cpu().numpy(), ref[k], k)
             for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dsigma2", "dell", "drot", "drho", "dkappa")}
-    print(shape, family, "rotated" if rotated else "", "lattice adjoint errors:", errs)
+    print(shape, family, "rotated" if rotated else "", "lattice tiles %d of %d," % (lat, gen + lat),
+          "adjoint errors:", errs)

@@ -181,12 +181,19 @@ def test_grid_path_matches_general_path(env):
 
 
 def test_auto_setting_small_and_large_grids(env):
-    # the default setting leaves grids of fewer than 8 tiles of 128 x 128
-    # cells to the CUDA-core kernels and takes the grid path from 8 tiles on
+    # the default setting takes the grid path for every grid plan (grids of
+    # few tiles split their modes over several CTAs), and the CUDA-core
+    # kernels for cells that are not a grid
     torch, F, W = env
     p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.1, 0.1), dim=2, n_modes=256, seed=3)
     gf = F.GaussianField(p)
-    for shape, grid in (((64, 64), False), ((896, 128), False), ((1024, 128), True)):
+    jit = W.jittered_lattice((64, 64), 1.0 / 64, 0.3, seed=2)
+    plan = F.CellPlan(*to_dev(torch, jit))
+    F.take_grid_tiles()
+    gf.synth(plan, F.MapSpec(y=True))
+    torch.cuda.synchronize()
+    assert F.take_grid_tiles() == 0
+    for shape, grid in (((64, 64), True), ((896, 128), True), ((1024, 128), True)):
         plan = F.CellPlan(*to_dev(torch, W.grid_centres(shape)))
         F.take_grid_tiles()
         F.take_path_counts()
