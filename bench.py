@@ -743,10 +743,10 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size call of the
 # headline's grid-path kernels (grid_prep_kernel + grid_mma_kernel, 256^3
 # cells, 4096 modes), one ncu capture (`--metrics dram__bytes_read.sum,
-# dram__bytes_write.sum -k regex:grid`): 0.25 + 0.03 MB and 27.21 + 90.98 MB.
+# dram__bytes_write.sum -k regex:grid`): 0.251 + 0.028 MB and 26.75 + 90.78 MB.
 # Algorithmic: 9 B written per cell (Y, K, facies) = 151 MB plus 26 MB of
 # tables; part of the writes was still in L2 when the launch ended.
-HEAD_TRAFFIC_BYTES = 0.25318e6 + 0.0279e6 + 27.21e6 + 90.98e6
+HEAD_TRAFFIC_BYTES = 0.25114e6 + 0.02842e6 + 26.75e6 + 90.78e6
 
 
 # FP32 instructions per cell-mode of the lattice path (lanes of 4-cell grid
