@@ -73,9 +73,11 @@ constexpr int kGSB = 3;                     // formed B stages (3-D)
 constexpr int kGEpiWarps = 16;
 constexpr int kGThreads = 32 * (kGEpiWarps + 2);
 constexpr int kGColsPerWarp = kGN / (kGEpiWarps / 4);    // TMEM columns a warp folds (4 lane quarters)
-constexpr int kGFormGroups = 32 * kGEpiWarps / kGN;       // threads that form one column of B
-constexpr int kGFormQuads = kGModes / 4 / kGFormGroups;   // 4-mode groups each of them forms
-static_assert(kGColsPerWarp % 32 == 0 && kGFormQuads >= 1, "epilogue warp layout");
+// B formation: thread t forms one 4-mode group (t / 64) of two columns that
+// share a y cell (z cells 2 q and 2 q + 1 of the patch, pair t mod 64), so the
+// y row is read once for both
+constexpr int kGFormPairs = kGN / 2;
+static_assert(kGColsPerWarp % 32 == 0 && 32 * kGEpiWarps == kGFormPairs * (kGModes / 4), "epilogue warp layout");
 constexpr uint32_t kGSbo = 1024;            // 8-row groups of a tile: one 128-byte-swizzle atom apart
 constexpr uint32_t kGKStep = 32;            // bytes of 16 K elements inside an atom row
 constexpr uint32_t kGTmemCols = 512;
@@ -96,16 +98,19 @@ __device__ __forceinline__ float grid_scale(const TableHeader* h) {
     return ldexpf(1.0f, e);
 }
 
-// B of one chunk for column n: W_jc = WZ[l, j] * Yp[k, j] for the
-// 4 kGFormQuads modes from 4 kk8_0 on, from the staged table rows ty (y) and tw
-// (amplitude, psi, z), written as (re, im) FP16 pairs into row n of the hi
-// and lo tiles, K segments kk8_0 .. kk8_0 + 3.
-__device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw, int n, int kk8_0) {
+// B of one chunk for the columns n0 and n1 (one y cell, two z cells):
+// W_jc = WZ[l, j] * Yp[k, j] for the 4 modes of group kk8, from the staged
+// table rows ty (y) and tw0, tw1 ((amplitude, psi, z) of the two z cells),
+// written as (re, im) FP16 pairs into rows n0 and n1 of the hi and lo tiles,
+// K segment kk8.
+__device__ __forceinline__ void form_b(unsigned char* bhi, const float4* ty, const float4* tw0, const float4* tw1,
+                                       int n0, int n1, int kk8) {
+    const float4 ya = ty[0], yb = ty[1];
 #pragma unroll
-    for (int g4 = 0; g4 < kGFormQuads; ++g4) {
-        const uint32_t boff = tile_off(n, kk8_0 + g4);
-        const float4 ya = ty[2 * g4], yb = ty[2 * g4 + 1];
-        const float4 wa = tw[2 * g4], wb = tw[2 * g4 + 1];
+    for (int h = 0; h < 2; ++h) {
+        const float4* tw = h == 0 ? tw0 : tw1;
+        const uint32_t boff = tile_off(h == 0 ? n0 : n1, kk8);
+        const float4 wa = tw[0], wb = tw[1];
         const float r0 = fmaf(wa.x, ya.x, -wa.y * ya.y), i0 = fmaf(wa.x, ya.y, wa.y * ya.x);
         const float r1 = fmaf(wa.z, ya.z, -wa.w * ya.w), i1 = fmaf(wa.z, ya.w, wa.w * ya.z);
         const float r2 = fmaf(wb.x, yb.x, -wb.y * yb.y), i2 = fmaf(wb.x, yb.y, wb.y * yb.x);
@@ -189,8 +194,11 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
         const int q = warp & 3;           // TMEM lane quarter (rows 32 q .. 32 q + 31)
         const int h = warp >> 2;          // column block (kGColsPerWarp h ..)
         const int t = threadIdx.x;        // 0 .. 255
-        const int n_col = t & 127;        // column this thread forms
-        const int hm = t >> 7;            // group of the chunk's modes it forms (kGFormQuads x 4 modes)
+        const int fp = t & (kGFormPairs - 1);  // column pair this thread forms
+        const int fg = t / kGFormPairs;        // 4-mode group of the chunk it forms
+        const int fk = fp & pkm;               // y cell of the pair in the patch
+        const int fz = (fp >> d.pk_log2) * 2;  // first z cell of the pair in the patch
+        const int n0 = fk + (fz << d.pk_log2), n1 = n0 + (1 << d.pk_log2);
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
         const float S = grid_scale(d.thdr);
         uint32_t g = 0, gi = 0;
@@ -202,10 +210,11 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
             const int NIl = kSplit ? NI * (split + 1) / n_split - iv0 : NI;
             const TileIdx ti = tile_idx(d, tile);
             // staged table rows this thread reads: y row and (amplitude, psi, z) row
-            const int ry = min(n_col & pkm, ti.pkv - 1);
-            const int rz = min(n_col >> d.pk_log2, ti.plv - 1);
-            const int toff_y = kGPair + ry * kGRowBytes + 4 * kGFormQuads * hm * 8;
-            const int toff_w = kGPair + ((1 << d.pk_log2) + rz) * kGRowBytes + 4 * kGFormQuads * hm * 8;
+            const int ry = min(fk, ti.pkv - 1);
+            const int rz0 = min(fz, ti.plv - 1), rz1 = min(fz + 1, ti.plv - 1);
+            const int toff_y = kGPair + ry * kGRowBytes + 32 * fg;
+            const int toff_w0 = kGPair + ((1 << d.pk_log2) + rz0) * kGRowBytes + 32 * fg;
+            const int toff_w1 = kGPair + ((1 << d.pk_log2) + rz1) * kGRowBytes + 32 * fg;
 
             // fold of interval gidx: the hi.hi accumulator into the running sum
             // (plain FP32: a few tens of folds per cell); the last fold of a
@@ -295,7 +304,8 @@ __global__ void __launch_bounds__(kGThreads, 1) grid_mma_kernel(GridDesc d, int3
                     }
                     const unsigned char* st = gsm + sa * d.a_stage;
                     form_b(gsm + d.off_b + sb * kGPair, reinterpret_cast<const float4*>(st + toff_y),
-                           reinterpret_cast<const float4*>(st + toff_w), n_col, kGFormQuads * hm);
+                           reinterpret_cast<const float4*>(st + toff_w0), reinterpret_cast<const float4*>(st + toff_w1),
+                           n0, n1, fg);
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bfull + sb);
