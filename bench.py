@@ -743,10 +743,10 @@ def cpu_baseline(W, name, scale, target_s=10.0, y_gpu=None):
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size call of the
 # headline's grid-path kernels (grid_prep_kernel + grid_mma_kernel, 256^3
 # cells, 4096 modes), one ncu capture (`--metrics dram__bytes_read.sum,
-# dram__bytes_write.sum -k regex:grid`): 0.251 + 0.028 MB and 26.75 + 90.78 MB.
+# dram__bytes_write.sum -k regex:grid`): 0.252 + 0.027 MB and 26.95 + 91.10 MB.
 # Algorithmic: 9 B written per cell (Y, K, facies) = 151 MB plus 26 MB of
 # tables; part of the writes was still in L2 when the launch ended.
-HEAD_TRAFFIC_BYTES = 0.25114e6 + 0.02842e6 + 26.75e6 + 90.78e6
+HEAD_TRAFFIC_BYTES = 0.25242e6 + 0.02688e6 + 26.95e6 + 91.10e6
 
 
 # FP32 instructions per cell-mode of the lattice path (lanes of 4-cell grid
