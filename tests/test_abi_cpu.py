@@ -345,6 +345,9 @@ def test_null_and_unknown_handles_rejected(abi):
     assert L.grf_debug_grid_path(1, 3) == abi.GRF_EINVAL
     assert L.grf_debug_grid_path(1, 4) == abi.GRF_OK
     assert L.grf_take_grid_tiles(None) == abi.GRF_EINVAL
+    assert L.grf_backward_grid_workspace_bytes(fake_plan, 0, 100) == 0
+    assert L.grf_backward_grid_workspace_bytes(None, 0, 100) == 0
+    assert L.grf_take_grid_adjoint_units(None) == abi.GRF_EINVAL
     assert L.grf_debug_mma_f16(None, None, 1, None, None, None) == abi.GRF_EINVAL
     assert L.grf_debug_mma_f16(ctypes.c_void_p(4096), ctypes.c_void_p(4096), 0, ctypes.c_void_p(4096),
                                ctypes.c_void_p(4096), None) == abi.GRF_EINVAL
