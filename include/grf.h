@@ -353,7 +353,9 @@ size_t grf_synth_workspace_bytes(int64_t n_cells);
  *
  * grf_synth_grid_workspace_bytes -- workspace bytes the grid path needs for
  * `plan` (segment 0) and a table of n_modes modes, or 0 when the plan is not
- * such a grid (or is unknown).  The first query (or synthesis) of a new plan
+ * such a grid (or is unknown), or when those tables would exceed
+ * max(1 GB, 64 bytes per cell) (N far above the cell count: such calls take
+ * the CUDA-core kernels).  The first query (or synthesis) of a new plan
  * waits on the host for that plan's own kernels to finish.
  * grf_plan_grid_shape -- the plan's grid (nx, ny, nz), or zeros.  Same wait.
  * GRF_EINVAL for NULL pointers or an unknown plan.
@@ -425,7 +427,8 @@ size_t grf_backward_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t di
  * Cartesian grid in x-fastest order, dim >= 2) with n_modes modes: the
  * per-mode partials, the tables of x, y and z phasors and the FP16 tiles of
  * gY.  0 when the plan is not such a grid, its check is unresolved only
- * through a failed event, or the arguments are invalid.
+ * through a failed event, the arguments are invalid, or the tables would
+ * exceed max(1 GB, 64 bytes per cell) (the CUDA-core adjoint serves it).
  */
 size_t grf_backward_grid_workspace_bytes(const void *plan, int32_t segment, int64_t n_modes);
 

@@ -286,6 +286,14 @@ bool use_grid_path(const GridGeom& gg) {
     return g_grid_enabled.load() != 0;
 }
 
+// The grid path's workspace (tables and partials) grows with the grid's axes
+// times N; beyond max(1 GB, 64 B per cell) -- N far above the cell count,
+// where the CUDA-core kernels need no tables -- it is not offered.
+bool grid_ws_ok(size_t bytes, const GridGeom& gg) {
+    const double cells = static_cast<double>(gg.nx) * gg.ny * gg.nz;
+    return static_cast<double>(bytes) <= std::max(double(1u << 30), 64.0 * cells);
+}
+
 // The grid shape of `plan` (single segment), resolving a pending check by
 // waiting for the plan's own event (the planning kernels only).  Returns
 // false when the cells are not a Cartesian grid in x-fastest order.
@@ -840,6 +848,7 @@ int grf_synth_field(const void* table, const grf_params* p, const void* plan, in
     GridGeom gg{};
     if (n > 0 && workspace && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim &&
         plan_grid(plan, &gg) && use_grid_path(gg) &&
+        grid_ws_ok(grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad), gg) &&
         ws_bytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
         const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, workspace, g_grid_fold.load(), status,
                                           stream);
@@ -858,7 +867,8 @@ size_t grf_synth_grid_workspace_bytes(const void* plan, int32_t segment, int64_t
         if (!plan || segment != 0 || n_modes < 1 || n_modes > GRF_MAX_MODES) return 0;
         GridGeom gg{};
         if (!plan_grid(plan, &gg)) return 0;
-        return grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+        const size_t b = grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+        return grid_ws_ok(b, gg) ? b : 0;
     } catch (...) {
         return 0;
     }
@@ -928,7 +938,8 @@ int grf_synth_mismatch(const void* table, const grf_params* p, const void* plan,
     // holds its tables and the loss partials fit
     GridGeom gg{};
     if (n > 0 && g_grid_enabled.load() != 0 && n_seg == 1 && p->dim == meta.dim && plan_grid(plan, &gg) &&
-        use_grid_path(gg) && ws_bytes - lbytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad) &&
+        use_grid_path(gg) && grid_ws_ok(grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad), gg) &&
+        ws_bytes - lbytes >= grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad) &&
         grid_loss_partials(gg.nx, gg.ny, gg.nz) <= mismatch_partials(n)) {
         const int err = launch_synth_grid(table, p->n_modes, p->dim, gg, d.map, split_ws, g_grid_fold.load(),
                                           status, stream);
@@ -991,7 +1002,8 @@ size_t grf_backward_grid_workspace_bytes(const void* plan, int32_t segment, int6
         if (!plan || segment != 0 || n_modes < 1 || n_modes > GRF_MAX_MODES) return 0;
         GridGeom gg{};
         if (!plan_grid(plan, &gg)) return 0;
-        return bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+        const size_t b = bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(n_modes).n_pad);
+        return grid_ws_ok(b, gg) ? b : 0;
     } catch (...) {
         return 0;
     }
@@ -1028,7 +1040,8 @@ int grf_synth_backward(const void* table, const grf_params* p, const void* plan,
     // workspace holds its tables
     GridGeom gg{};
     if (n > 0 && g_grid_enabled.load() != 0 && meta.offsets.size() == 2 && p->dim >= 2 && plan_grid(plan, &gg) &&
-        use_grid_path(gg) && ws_bytes >= bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
+        use_grid_path(gg) && grid_ws_ok(bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad), gg) &&
+        ws_bytes >= bwd_grid_ws_bytes(gg.nx, gg.ny, gg.nz, table_layout(p->n_modes).n_pad)) {
         const int err = launch_synth_bwd_grid(table, p->n_modes, p->dim, gg, gY, std::sqrt(p->sigma2), p->ell, rot,
                                               periodic, *g, workspace, status, stream);
         if (err != cudaSuccess) return cuda_fail(err, "grid backward kernels");

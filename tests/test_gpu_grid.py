@@ -268,3 +268,25 @@ def test_mode_split_fields_and_fused_mismatch(env, shape):
     l_or, g_or = of.mismatch_loss(np.exp(y_or), T.cpu().numpy().astype(np.float64))
     assert loss.item() == pytest.approx(l_or, rel=1e-4)
     assert np.max(np.abs(gY.cpu().numpy() - g_or)) <= 1e-4 * np.max(np.abs(g_or))
+
+
+def test_grid_path_not_offered_when_tables_outgrow_the_cells(env):
+    # N = 2^20 modes on a 64^2 grid: the grid tables would be far larger than
+    # max(1 GB, 64 B per cell), so the workspace queries return 0 (forward and
+    # adjoint) and the CUDA-core kernels compute the field
+    torch, F, W = env
+    cells = W.grid_centres((64, 64))
+    n_modes = 1 << 20
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.2, 0.1), dim=2, n_modes=n_modes, seed=12)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    assert F.lib().grf_synth_grid_workspace_bytes(plan.ptr, 0, n_modes) == 0
+    assert F.lib().grf_backward_grid_workspace_bytes(plan.ptr, 0, n_modes) == 0
+    assert F.lib().grf_synth_grid_workspace_bytes(plan.ptr, 0, 4096) > 0
+    gf = F.GaussianField(p)
+    F.take_grid_tiles()
+    out = gf.synth(plan, F.MapSpec(y=True))
+    torch.cuda.synchronize()
+    assert F.take_grid_tiles() == 0
+    idx = np.arange(0, len(cells[0]), 97)
+    y_or = oracle_field(oracle_modes("gaussian", 1.0, (0.2, 0.1), 2, n_modes, 12), 0.0, cells, idx)
+    check_forward(out["Y"].cpu().numpy()[idx], y_or, 1.0, "2^20 modes on a 64^2 grid")
