@@ -38,6 +38,14 @@ namespace {
 constexpr int kBwdThreads = 128;
 constexpr int kBwdTile = 256;
 constexpr int kBwdMaxSplits = 256;
+
+// Most cell splits the workspace holds for a table of n_pad slots: 256, but
+// no more than keep splits x mode blocks at 65536 (with that many mode blocks
+// the GPU is full without splits), so the FP64 partials stay O(65536 x 512 x
+// 40 bytes) whatever N.
+__host__ __device__ constexpr int64_t bwd_max_splits(int64_t n_pad) {
+    return n_pad / 512 >= 256 ? (65536 / (n_pad / 512) > 1 ? 65536 / (n_pad / 512) : 1) : kBwdMaxSplits;
+}
 constexpr int kMPT = 4;  // modes per thread
 constexpr int kContrib = kBwdContrib;  // per-mode terms of the scalar gradients
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -613,7 +621,7 @@ int bwd_allow_smem(int dim) {
 }
 
 template <int DIM>
-int choose_splits(int64_t n_cells, int mode_blocks) {
+int choose_splits(int64_t n_cells, int mode_blocks, int64_t max_splits) {
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -624,7 +632,7 @@ int choose_splits(int64_t n_cells, int mode_blocks) {
     const int64_t tiles = (n_cells + kBwdTile - 1) / kBwdTile;
     int64_t best = 1;
     double best_eff = -1.0;
-    for (int64_t s = 1; s <= kBwdMaxSplits && s <= tiles; ++s) {
+    for (int64_t s = 1; s <= max_splits && s <= tiles; ++s) {
         const int64_t blocks = s * mode_blocks;
         const int64_t waves = (blocks + resident - 1) / resident;
         const double fill = static_cast<double>(blocks) / static_cast<double>(waves * resident);
@@ -646,8 +654,8 @@ size_t bwd_workspace_bytes(int64_t n_cells, int64_t n_modes, int32_t dim) {
     (void)n_cells;
     (void)dim;
     const int64_t n_pad = pad_modes(n_modes);
-    const int64_t part = int64_t(kBwdMaxSplits) * n_pad * 5 * 8;
-    const int64_t gpart = int64_t(kBwdMaxSplits) * 8;
+    const int64_t part = bwd_max_splits(n_pad) * n_pad * 5 * 8;
+    const int64_t gpart = bwd_max_splits(n_pad) * 8;
     const int64_t contrib = n_pad * kContrib * 8;
     return static_cast<size_t>(align256(part) + align256(gpart) + align256(contrib));
 }
@@ -741,17 +749,17 @@ int launch_synth_bwd(const void* table, int64_t n_modes, int32_t dim, double sig
     a.splits = 1;
     if (n_cells > 0) {
         switch (dim) {
-            case 1: a.splits = choose_splits<1>(n_cells, mode_blocks); break;
-            case 2: a.splits = choose_splits<2>(n_cells, mode_blocks); break;
-            default: a.splits = choose_splits<3>(n_cells, mode_blocks); break;
+            case 1: a.splits = choose_splits<1>(n_cells, mode_blocks, bwd_max_splits(TL.n_pad)); break;
+            case 2: a.splits = choose_splits<2>(n_cells, mode_blocks, bwd_max_splits(TL.n_pad)); break;
+            default: a.splits = choose_splits<3>(n_cells, mode_blocks, bwd_max_splits(TL.n_pad)); break;
         }
     }
     const int64_t n_pad = TL.n_pad;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     a.part = reinterpret_cast<double*>(ws);
-    a.gpart = reinterpret_cast<double*>(ws + align256(int64_t(kBwdMaxSplits) * n_pad * 5 * 8));
-    a.contrib = reinterpret_cast<double*>(ws + align256(int64_t(kBwdMaxSplits) * n_pad * 5 * 8) +
-                                          align256(int64_t(kBwdMaxSplits) * 8));
+    a.gpart = reinterpret_cast<double*>(ws + align256(bwd_max_splits(n_pad) * n_pad * 5 * 8));
+    a.contrib = reinterpret_cast<double*>(ws + align256(bwd_max_splits(n_pad) * n_pad * 5 * 8) +
+                                          align256(bwd_max_splits(n_pad) * 8));
     if (n_cells == 0) {
         // no cells: all gradients are zero
         cudaError_t e = cudaMemsetAsync(a.part, 0, sizeof(double) * n_pad * 5, st);

@@ -317,3 +317,35 @@ def test_lattice_adjoint_against_oracle(env, shape, family, rotated):
             for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dsigma2", "dell", "drot", "drho", "dkappa")}
     print(shape, family, "rotated" if rotated else "", "lattice tiles %d of %d," % (lat, gen + lat),
           "adjoint errors:", errs)
+
+
+def test_backward_maximum_mode_count(env):
+    # N = GRF_MAX_MODES = 2^24 modes on a few hundred cells: the adjoint's
+    # partials stay bounded (few cell splits when the mode blocks fill the GPU),
+    # the per-mode gradients against the oracle on a sample of modes
+    torch, F, W = env
+    from paper_2212_10961_gb300 import _abi
+    from oracle import native
+    n_modes = _abi.GRF_MAX_MODES
+    assert F.lib().grf_backward_workspace_bytes(300, n_modes, 3) < (3 << 30)
+    rng = np.random.default_rng(8)
+    cells = [rng.random(300).astype(np.float32) for _ in range(3)]
+    p = F.FieldParams(family="gaussian", sigma2=1.0, ell=(0.3, 0.2, 0.1), dim=3, n_modes=n_modes, seed=6)
+    gf = F.GaussianField(p)
+    plan = F.CellPlan(*to_dev(torch, cells))
+    g = np.random.default_rng(3).standard_normal(300).astype(np.float32)
+    gr = F.backward(gf.table, p, plan, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    om = oracle_modes("gaussian", 1.0, (0.3, 0.2, 0.1), 3, n_modes, 6)
+    sel = np.arange(0, n_modes, n_modes // 1000)
+    s_cos, s_sin, s_sinx = native.mode_sums(om["a"][sel], om["psi"][sel], np.stack(cells, axis=-1),
+                                            g.astype(np.float64))
+    dA = gr["dA"].cpu().numpy()[sel]
+    dpsi = gr["dpsi"].cpu().numpy()[sel]
+    da = gr["da"].cpu().numpy()[sel]
+    assert np.max(np.abs(dA - s_cos)) <= GRAD_TOL * np.max(np.abs(s_cos))
+    ref_psi = -2 * np.pi * om["amp"][sel] * s_sin
+    assert np.max(np.abs(dpsi - ref_psi)) <= GRAD_TOL * np.max(np.abs(ref_psi))
+    ref_a = -2 * np.pi * om["amp"][sel][:, None] * s_sinx
+    assert np.max(np.abs(da - ref_a)) <= GRAD_TOL * np.max(np.abs(ref_a))
