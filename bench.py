@@ -400,44 +400,54 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
     """Same step through the public API with host buffers: pinned host cell
     centres copied in, plan, modes, synthesis, outputs copied back.
 
-    Two slots of device buffers alternate between steps: the copy-in and the
-    plan of step i + 1 run on a side stream and the copy-back of step i - 1 on
-    another while step i synthesises on the main stream; a slot is reused only
-    after its previous step's outputs have reached the host (events)."""
+    Two slots of device buffers alternate between steps: right after step i's
+    synthesis is enqueued, the copy-in and the plan of step i + 1 go to a side
+    stream (so step i + 1 finds its plan complete and the host does not wait
+    for it), and the copy-back of step i to another; a slot is reused only
+    after its previous step's outputs have reached the host (events).  The
+    modes of every step are a new realisation, drawn ahead by the native
+    prefetcher (grf_prefetch_*) and uploaded on the main stream."""
     M = len(cells[0])
     host_cells = [torch.from_numpy(c).pin_memory() for c in cells]
     keys = [k for k in ("Y", "K", "facies")
             if (k == "Y" and maps.y) or (k == "K" and maps.lognormal) or (k == "facies" and maps.facies)]
     dtypes = {"Y": torch.float32, "K": torch.float32, "facies": torch.uint8}
+    N = w["n_modes"]
     slots = []
     for _ in range(2):
         slots.append({
             "cells": [torch.empty(M, dtype=torch.float32, device="cuda") for _ in cells],
             "host_out": {k: torch.empty(M, dtype=dtypes[k], pin_memory=True) for k in keys},
             "dev_out": maps.allocate(M, torch.device("cuda")),
-            "tab": F.ModeTable.from_modes(F.gen_modes(params_for(F, w, dim, base_seed))),
+            "tab": F.ModeTable.device_only(N, dim),
             "plan": None, "planned": torch.cuda.Event(), "done": torch.cuda.Event()})
+    workers = max(1, (os.cpu_count() or 4) - 2)
+    pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=min(64, workers + 4), threads=workers)
+    p = params_for(F, w, dim, base_seed)
     main = torch.cuda.current_stream()
     side = torch.cuda.Stream()  # copy-in and planning of the next step
-    back = torch.cuda.Stream()  # copy-back of the previous step
+    back = torch.cuda.Stream()  # copy-back of the current step
     for sl in slots:
         sl["done"].record(main)
         sl["synthesised"] = torch.cuda.Event()
 
-    def step(i):
-        sl = slots[i % 2]
+    def copy_in_and_plan(sl):
         side.wait_event(sl["done"])  # the slot's previous step has finished on the device
         with torch.cuda.stream(side):
             for h, d in zip(host_cells, sl["cells"]):
                 d.copy_(h, non_blocking=True)
             sl["plan"] = F.CellPlan(*sl["cells"], stream=side)
             sl["planned"].record(side)
-        p = params_for(F, w, dim, base_seed + i)
-        m = F.gen_modes(p)
-        sl["tab"].update(m["amp"], m["psi"], m["a"], stream=main)
+
+    copy_in_and_plan(slots[0])
+
+    def step(i):
+        sl = slots[i % 2]
+        pf.next(sl["tab"], stream=main)
         main.wait_event(sl["planned"])
         F.synth(sl["tab"], p, sl["plan"], 0, maps, sl["dev_out"], stream=main)
         sl["synthesised"].record(main)
+        copy_in_and_plan(slots[(i + 1) % 2])  # the next step's inputs
         back.wait_event(sl["synthesised"])
         with torch.cuda.stream(back):
             for k, h in sl["host_out"].items():
@@ -445,13 +455,15 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
         sl["done"].record(back)
 
     ms = timed_steps(torch, world, steps, 3, step)
+    torch.cuda.synchronize()
+    pf.close()
     for sl in slots:
         assert sl["plan"].status() == 0
     h2d = 4 * M * len(cells)
     d2h = sum(M * (1 if k == "facies" else 4) for k in keys)
     return {"ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "pipelined": "copy-in and plan of step i+1 and copy-back of step i-1 on side streams during "
-                         "step i's synthesis"}
+            "pipelined": "copy-in and plan of step i+1 and copy-back of step i on side streams during "
+                         "step i's synthesis; modes of every step drawn ahead by the native prefetcher"}
 
 
 def bench_fwd_bwd(torch, F, W, rank, world, steps, warmup, scale):
