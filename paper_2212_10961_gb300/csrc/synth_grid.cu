@@ -30,9 +30,12 @@
 // the two correction products, 2^-11 smaller, go to a second accumulator
 // that spans the whole tile.
 //
-// Kernel structure (one CTA per SM, persistent over tiles):
-//   warps 0-15: form B for each chunk (3-D), fold the accumulator, write the maps
-//               (warp w reads TMEM lanes 32 (w mod 4) .., columns 32 (w / 4) ..);
+// Kernel structure (one CTA per SM, persistent over work items: tiles, or
+// for grids of at most 64 tiles (tile, mode split) pairs of whole fold
+// intervals whose partial fields a finalize kernel adds in split order):
+//   warps 0-15: form B for each chunk (3-D; a thread forms 4 modes of two
+//               columns that share a y cell), fold the accumulator, write the
+//               maps (warp w reads TMEM lanes 32 (w mod 4) .., columns 32 (w / 4) ..);
 //   warp 16   : one thread issues the MMAs (tcgen05.mma kind::f16, M = N = 128);
 //   warp 17   : one thread issues the bulk copies; the warp owns TMEM.
 // A ring of `sa` stages (A hi/lo and the chunk's tables, or A and B) and,
