@@ -191,3 +191,20 @@ def test_auto_setting_uses_grid_adjoint(env):
         ref = _oracle_reparam("gaussian", 1.0, (0.1, 0.1), 2, 256, 3, cells, g)
         for k in ("dA", "dpsi", "da", "dmu", "dsigma", "dell"):
             _check(gr[k], ref[k], k)
+
+
+@pytest.mark.slow
+def test_grid_adjoint_256_cube_matches_cuda_core(env):
+    # the full 256^3 cube (4 x chunks, 4 y blocks, 256 z cells per mode tile,
+    # a 134 MB B table): every gradient family of the grid adjoint against the
+    # CUDA-core adjoint on the same g
+    torch, F, W = env
+    cells = W.workload_cells("grid3d_256")
+    p = F.FieldParams(family="exponential", sigma2=4.0, ell=(0.2, 0.2, 0.05), dim=3, n_modes=1024, seed=3)
+    g = np.random.default_rng(6).standard_normal(len(cells[0])).astype(np.float32)
+    on, units, plan = _grid_backward(env, p, cells, g)
+    assert plan.grid_shape() == (256, 256, 256) and units == 8 * 4 * 4 * 256
+    off, units_off, _ = _grid_backward(env, p, cells, g, mode=False)
+    assert units_off == 0
+    errs = {k: _check(on[k], off[k], k) for k in FAMILIES_OUT}
+    print("256^3 grid vs CUDA-core adjoint:", errs)
