@@ -5,20 +5,22 @@ Headline step (default): one realisation of the 3-D workload
   exponential covariance, l = (0.2, 0.2, 0.05), sigma^2 = 4, FP32 field,
   lognormal K and a 3-facies map at the Gaussian 1/3, 2/3 quantiles:
 a new realisation per step (modes drawn and packed by the library's native
-prefetcher threads, table upload on a copy stream) and the fused synthesis
-kernel writing Y, K and facies.  Metric: Gcell.mode/s = cells x modes per
-second.  The same JSON line also reports the forward+backward step (128^3,
+prefetcher threads, table upload on a copy stream) and the synthesis call
+writing Y, K and facies -- on this Cartesian grid the tensor-core grid path
+(table preparation and the tcgen05 kernel; --grid-path off selects the
+CUDA-core kernels).  Metric: Gcell.mode/s = cells x modes per second.  The same JSON line also reports the forward+backward step (128^3,
 N = 2048, mismatch loss and adjoint), the batched ensemble (256 realisations
 in one graph-replayed persistent launch), the unstructured 2M-cell workload
 (in lattice order and in a seeded random order), the 1024 x 512 HRL-shaped
 workload, the bitruncated two-field facies and the periodic, rotated field on
 the 256^3 cube, and the 64^2 workload.  roofline.traffic
-is the DRAM bytes (read + written) of one headline kernel launch measured by
+is the DRAM bytes (read + written) of one headline call's kernels measured by
 ncu.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--only all|fwd|bwd|batched|jitter|hrl|next] [--scale S]
-                  [--batched-tile auto|128|256|512] [--no-cpu-baseline] [--jsonl PATH]
+                  [--batched-tile auto|128|256|512] [--grid-path auto|off|always]
+                  [--no-cpu-baseline] [--jsonl PATH]
 
 Under torchrun each rank runs its own realisations (different seeds) of the
 same workloads: per-GPU work is fixed (weak scaling) and the forward path has
