@@ -288,10 +288,11 @@ def bench_forward(torch, F, W, name, rank, world, steps, warmup, scale, with_e2e
     # a new realisation every step: drawn and packed ahead by the native
     # prefetcher's worker threads; its upload runs on a copy stream into one
     # of two device tables while the previous synthesis runs
-    # (all host cores but two draw, one realisation per worker, and the ring
-    # holds a slot for every worker beside those whose uploads are in flight:
-    # a small field's step is otherwise bound by the host's drawing rate)
-    workers = max(1, (os.cpu_count() or 4) - 2)
+    # (the host's cores but two, shared among the ranks, draw one realisation
+    # per worker, and the ring holds a slot for every worker beside those whose
+    # uploads are in flight: a small field's step is otherwise bound by the
+    # host's drawing rate)
+    workers = max(1, ((os.cpu_count() or 4) - 2) // max(1, world))
     pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=min(64, workers + 4), threads=workers)
     ps = F.PreparedSynth(params_for(F, w, dim, base_seed), plan, 0, maps)
     out = ps.out
@@ -423,7 +424,7 @@ def bench_forward_e2e(torch, F, W, w, cells, maps, dim, base_seed, world, steps)
             "dev_out": maps.allocate(M, torch.device("cuda")),
             "tab": F.ModeTable.device_only(N, dim),
             "plan": None, "planned": torch.cuda.Event(), "done": torch.cuda.Event()})
-    workers = max(1, (os.cpu_count() or 4) - 2)
+    workers = max(1, ((os.cpu_count() or 4) - 2) // max(1, world))  # the host's cores, shared among the ranks
     pf = F.ModePrefetcher(params_for(F, w, dim, base_seed), depth=min(64, workers + 4), threads=workers)
     p = params_for(F, w, dim, base_seed)
     main = torch.cuda.current_stream()
